@@ -1,0 +1,664 @@
+/*
+ * fmc_oracle.c -- plain, slow, FP64 CPU oracle for the fast Monte Carlo method
+ * of Qiu, Lin, Chen, Liu and Song, "Fast Monte Carlo Simulation of Dynamic Power
+ * Systems Under Continuous Random Disturbances" (arXiv 2007.03847).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA library is checked against.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library; both sides are written from
+ * the paper and from the published definitions they cite.
+ *
+ * Every function follows one step of Algorithm 1 (Section IV-C):
+ *   step 1  Latin hypercube sampling of the KL coefficients      (Section IV-B)
+ *   step 2  reconstruction of the disturbance paths              (Eqs. kl, kle, eqkl)
+ *   step 3  the dynamic simulation of every sample               (Eqs. state, algebra)
+ *   step 4  expectation and variance of the response             (Algorithm 1 step 4)
+ * The order of arithmetic is the order of the definitions; nothing is blocked,
+ * fused or reordered for speed.
+ *
+ * Readings of points the paper leaves open (listed with reasons in the design
+ * notes of the repository):
+ *   - KL basis: the eigenfunctions of the Brownian covariance min(s,t),
+ *     W(t) = sum_k zeta_k sqrt(2T)/((k-1/2)pi) sin((k-1/2)pi t/T).
+ *   - The reconstructed path is consumed as increments dW_n = W(t_{n+1})-W(t_n).
+ *   - Disturbance: Ornstein-Uhlenbeck dx = -theta x dt + sigma dW (Table I,
+ *     Gaussian row with a general rate), advanced by Euler-Maruyama (Eq. distito
+ *     with the missing xi_t restored).
+ *   - System: Kron-reduced classical model, d(delta)/dt = omega_s * domega,
+ *     2H d(domega)/dt = Pm + sum_w inj[i,w] x_w - Pe - D domega, with
+ *     Pe_i = sum_j E_i E_j (G_ij cos(delta_i-delta_j) + B_ij sin(delta_i-delta_j))
+ *            [+ E_i V (Ginf_i cos delta_i + Binf_i sin delta_i) with an infinite bus].
+ *   - Integrator: classical RK4 (or Heun); the disturbance enters the stages at
+ *     x_n, (x_n+x_{n+1})/2, (x_n+x_{n+1})/2, x_{n+1} (Heun: x_n, x_{n+1}).
+ *   - Initial state: equilibrium at t = 0 (Section V-A), found by Newton; without
+ *     an infinite bus machine 0 is the angle reference and balances power.
+ *   - Variance: unbiased (N-1 denominator); NaN for N = 1.
+ *   - LHS permutation: a keyed Feistel bijection with cycle walking, round
+ *     function Philox4x32-10; uniform within the stratum from Philox4x32-10.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11.  Ten rounds of the 4x32 S-box with the published
+ * multipliers and Weyl key increments.                                        */
+/* ------------------------------------------------------------------------- */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {            /* key schedule: Weyl sequence */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t philox_word0(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3)
+{
+    uint32_t ctr[4] = {w0, w1, w2, w3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* ------------------------------------------------------------------------- */
+/* LHS permutation (Section IV-B, step 2: "random permutation").  For each
+ * dimension i the permutation pi_i of {0..N-1} is a balanced Feistel network
+ * on w = 2h bits (h = max(1, ceil(b/2)), 2^b the smallest power of two >= N),
+ * six rounds, round function F_r(R) = Philox(key = seed,
+ * counter = (R, i, 1 + r, 0)) word 0 masked to h bits, restricted to [0, N)
+ * by cycle walking.                                                           */
+/* ------------------------------------------------------------------------- */
+#define ORACLE_FEISTEL_ROUNDS 6
+
+static int bits_for(int64_t N)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < N) ++b;
+    return b;
+}
+
+static uint32_t feistel_encrypt(uint64_t seed, uint32_t dim, int h, uint32_t x)
+{
+    uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
+    uint32_t L = (x >> h) & mask;
+    uint32_t R = x & mask;
+    for (int r = 0; r < ORACLE_FEISTEL_ROUNDS; ++r) {
+        uint32_t F = philox_word0(seed, R, dim, 1u + (uint32_t)r, 0u) & mask;
+        uint32_t newL = R;
+        uint32_t newR = L ^ F;
+        L = newL;
+        R = newR;
+    }
+    return (L << h) | R;
+}
+
+uint32_t oracle_lhs_stratum(uint64_t seed, int64_t N, int32_t dim, int64_t k)
+{
+    int b = bits_for(N);
+    int h = (b + 1) / 2;
+    if (h < 1) h = 1;
+    uint32_t y = (uint32_t)k;
+    do {
+        y = feistel_encrypt(seed, (uint32_t)dim, h, y);
+    } while ((int64_t)y >= N);
+    return y;
+}
+
+/* Uniform in (0,1) attached to (sample k, dimension i): u = (r + 1/2) 2^-32
+ * with r = Philox(key = seed, counter = (k, i, 0, 0)) word 0.                  */
+double oracle_lhs_uniform(uint64_t seed, int32_t dim, int64_t k)
+{
+    uint32_t r = philox_word0(seed, (uint32_t)k, (uint32_t)dim, 0u, 0u);
+    return ((double)r + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Inverse standard normal CDF: Wichura, "Algorithm AS 241: The percentage
+ * points of the normal distribution", Applied Statistics 37 (1988), PPND16
+ * (about 1e-16 relative accuracy).                                             */
+/* ------------------------------------------------------------------------- */
+double oracle_ppnd16(double p)
+{
+    if (p <= 0.0) return -INFINITY;
+    if (p >= 1.0) return INFINITY;
+    double q = p - 0.5;
+    if (fabs(q) <= 0.425) {
+        double r = 0.180625 - q * q;
+        double num = (((((((2.5090809287301226727e+3 * r + 3.3430575583588128105e+4) * r
+                        + 6.7265770927008700853e+4) * r + 4.5921953931549871457e+4) * r
+                        + 1.3731693765509461125e+4) * r + 1.9715909503065514427e+3) * r
+                        + 1.3314166789178437745e+2) * r + 3.3871328727963666080e+0);
+        double den = (((((((5.2264952788528545610e+3 * r + 2.8729085735721942674e+4) * r
+                        + 3.9307895800092710610e+4) * r + 2.1213794301586595867e+4) * r
+                        + 5.3941960214247511077e+3) * r + 6.8718700749205790830e+2) * r
+                        + 4.2313330701600911252e+1) * r + 1.0);
+        return q * num / den;
+    }
+    double r = (q < 0.0) ? p : 1.0 - p;
+    r = sqrt(-log(r));
+    double val;
+    if (r <= 5.0) {
+        r -= 1.6;
+        double num = (((((((7.74545014278341407640e-4 * r + 2.27238449892691845833e-2) * r
+                        + 2.41780725177450611770e-1) * r + 1.27045825245236838258e+0) * r
+                        + 3.64784832476320460504e+0) * r + 5.76949722146069140550e+0) * r
+                        + 4.63033784615654529590e+0) * r + 1.42343711074968357734e+0);
+        double den = (((((((1.05075007164441684324e-9 * r + 5.47593808499534494600e-4) * r
+                        + 1.51986665636164571966e-2) * r + 1.48103976427480074590e-1) * r
+                        + 6.89767334985100004550e-1) * r + 1.67638483018380384940e+0) * r
+                        + 2.05319162663775882187e+0) * r + 1.0);
+        val = num / den;
+    } else {
+        r -= 5.0;
+        double num = (((((((2.01033439929228813265e-7 * r + 2.71155556874348757815e-5) * r
+                        + 1.24266094738807843860e-3) * r + 2.65321895265761230930e-2) * r
+                        + 2.96560571828504891230e-1) * r + 1.78482653991729133580e+0) * r
+                        + 5.46378491116411436990e+0) * r + 6.65790464350110377720e+0);
+        double den = (((((((2.04426310338993978564e-15 * r + 1.42151175831644588870e-7) * r
+                        + 1.84631831751005468180e-5) * r + 7.86869131145613259100e-4) * r
+                        + 1.48753612908506148525e-2) * r + 1.36929880922735805310e-1) * r
+                        + 5.99832206555887937690e-1) * r + 1.0);
+        val = num / den;
+    }
+    return (q < 0.0) ? -val : val;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1 step 1 / Section IV-B step 1: for dimension i and sample k the
+ * stratum is s = pi_i(k), the probability p = (s + u)/N, and zeta = Phi^-1(p).
+ * mode 0: LHS; mode 1: simple random sampling (p = u); mode 2: LHS at the
+ * stratum midpoint (u = 1/2).  Rows k0 .. k0+count-1 of the N-sample design
+ * are produced: zeta[(k-k0)*M + i], strata[i*count + (k-k0)] (may be NULL).    */
+/* ------------------------------------------------------------------------- */
+int oracle_lhs_sample(uint64_t seed, int64_t N, int64_t k0, int64_t count, int32_t M, int32_t mode,
+                      double* zeta, uint32_t* strata)
+{
+    if (N < 1 || M < 1 || k0 < 0 || count < 0 || k0 + count > N || N > 2147483648LL) return -1;
+    if (mode < 0 || mode > 2) return -1;
+    for (int32_t i = 0; i < M; ++i) {
+        for (int64_t j = 0; j < count; ++j) {
+            int64_t k = k0 + j;
+            double u = (mode == 2) ? 0.5 : oracle_lhs_uniform(seed, i, k);
+            double p;
+            uint32_t s = 0;
+            if (mode == 1) {
+                p = u;
+                s = (uint32_t)k;
+            } else {
+                s = oracle_lhs_stratum(seed, N, i, k);
+                p = ((double)s + u) / (double)N;
+            }
+            zeta[j * M + i] = oracle_ppnd16(p);
+            if (strata) strata[(int64_t)i * count + j] = s;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1 step 2, Eqs. (kl)/(kle): truncated KL expansion of a standard
+ * Wiener process on [0,T] with the Brownian eigenbasis,
+ *   W(t) = sum_{k=1..K} zeta_k c_k sin(a_k t),  a_k = (k-1/2) pi / T,
+ *   c_k = sqrt(2T) / ((k-1/2) pi),
+ * consumed as increments on the grid t_n = n dt, dt = T/Nt:
+ *   phi[k-1][n] = c_k (sin(a_k t_{n+1}) - sin(a_k t_n)).                        */
+/* ------------------------------------------------------------------------- */
+void oracle_kl_increment_basis(int32_t K, double T, int32_t Nt, double* phi)
+{
+    double dt = T / (double)Nt;
+    for (int32_t k = 1; k <= K; ++k) {
+        double a = ((double)k - 0.5) * ORACLE_PI / T;
+        double c = sqrt(2.0 * T) / (((double)k - 0.5) * ORACLE_PI);
+        for (int32_t n = 0; n < Nt; ++n) {
+            double t0 = (double)n * dt;
+            double t1 = (double)(n + 1) * dt;
+            phi[(int64_t)(k - 1) * Nt + n] = c * (sin(a * t1) - sin(a * t0));
+        }
+    }
+}
+
+/* W(t_n) itself (not used on the path; a pin for the covariance of the basis). */
+void oracle_kl_path_basis(int32_t K, double T, int32_t Nt, double* psi)
+{
+    double dt = T / (double)Nt;
+    for (int32_t k = 1; k <= K; ++k) {
+        double a = ((double)k - 0.5) * ORACLE_PI / T;
+        double c = sqrt(2.0 * T) / (((double)k - 0.5) * ORACLE_PI);
+        for (int32_t n = 0; n <= Nt; ++n)
+            psi[(int64_t)(k - 1) * (Nt + 1) + n] = c * sin(a * (double)n * dt);
+    }
+}
+
+/* Eq. (eqkl) as increments: dW[s][w][n] = sum_k zeta[s][w*K + k] phi[k][n]. */
+void oracle_kle_reconstruct(const double* zeta, int64_t count, int32_t d, int32_t K, const double* phi,
+                            int32_t Nt, double* dW)
+{
+    for (int64_t s = 0; s < count; ++s)
+        for (int32_t w = 0; w < d; ++w)
+            for (int32_t n = 0; n < Nt; ++n) {
+                double acc = 0.0;
+                for (int32_t k = 0; k < K; ++k)
+                    acc += zeta[s * (int64_t)d * K + (int64_t)w * K + k] * phi[(int64_t)k * Nt + n];
+                dW[(s * d + w) * (int64_t)Nt + n] = acc;
+            }
+}
+
+/* Euler-Maruyama for the OU disturbance driven by given increments (Eq. distito
+ * with the drift of Table I's Gaussian row at rate theta):
+ *   x_{n+1} = x_n - theta x_n dt + sigma dW_n,  x_0 = 0.
+ * dW [count x Nt], x [count x (Nt+1)].                                          */
+void oracle_ou_em(const double* dW, int64_t count, int32_t Nt, double dt, double theta, double sigma, double* x)
+{
+    for (int64_t s = 0; s < count; ++s) {
+        double v = 0.0;
+        x[s * (Nt + 1)] = 0.0;
+        for (int32_t n = 0; n < Nt; ++n) {
+            v = v + (-theta * v) * dt + sigma * dW[s * Nt + n];
+            x[s * (Nt + 1) + n + 1] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The system (Eqs. state/algebra reduced to the classical model).            */
+/* ------------------------------------------------------------------------- */
+typedef struct oracle_system {
+    int32_t n;           /* machines */
+    int32_t d;           /* OU disturbances = Wiener processes */
+    int32_t K;           /* KL terms per Wiener process */
+    int32_t Nt;          /* time steps, T = Nt dt */
+    double T;
+    double dt;
+    double omega_s;      /* synchronous speed, rad/s */
+    int32_t has_inf_bus;
+    int32_t integrator;  /* 0 = RK4, 1 = Heun */
+    double Vinf;
+    const double* G;     /* [n*n] Kron-reduced conductance */
+    const double* B;     /* [n*n] Kron-reduced susceptance */
+    const double* Ginf;  /* [n] machine-to-infinite-bus conductance (has_inf_bus) */
+    const double* Binf;  /* [n] machine-to-infinite-bus susceptance */
+    const double* H;     /* [n] inertia constants, s */
+    const double* D;     /* [n] damping, p.u. power per p.u. speed */
+    const double* E;     /* [n] internal EMFs */
+    const double* Pm;    /* [n] mechanical power; Pm[0] is replaced by the balance
+                            of machine 0 when there is no infinite bus */
+    const double* theta; /* [d] OU mean-reversion rates, 1/s */
+    const double* sigma; /* [d] OU diffusion, p.u./sqrt(s) */
+    const double* inject;/* [n*d] how disturbance w enters machine i's power */
+    const double* init_delta; /* [n] initial angles instead of the equilibrium, or NULL */
+} oracle_system;
+
+/* Electrical power, textbook pairwise form:
+ *   Pe_i = sum_j E_i E_j (G_ij cos(delta_i - delta_j) + B_ij sin(delta_i - delta_j))
+ * (form 0), or the same sum written with a_j = E_j cos delta_j, b_j = E_j sin delta_j
+ * as Pe_i = a_i (G a - B b)_i + b_i (G b + B a)_i (form 1).                   */
+void oracle_electrical_power(const oracle_system* s, const double* delta, double* pe, int32_t form)
+{
+    int n = s->n;
+    if (form == 0) {
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) {
+                double dij = delta[i] - delta[j];
+                acc += s->E[i] * s->E[j] * (s->G[i * n + j] * cos(dij) + s->B[i * n + j] * sin(dij));
+            }
+            if (s->has_inf_bus)
+                acc += s->E[i] * s->Vinf * (s->Ginf[i] * cos(delta[i]) + s->Binf[i] * sin(delta[i]));
+            pe[i] = acc;
+        }
+    } else {
+        double* a = (double*)malloc(sizeof(double) * 2 * n);
+        double* b = a + n;
+        for (int j = 0; j < n; ++j) {
+            a[j] = s->E[j] * cos(delta[j]);
+            b[j] = s->E[j] * sin(delta[j]);
+        }
+        for (int i = 0; i < n; ++i) {
+            double u = 0.0, v = 0.0;
+            for (int j = 0; j < n; ++j) {
+                u += s->G[i * n + j] * a[j] - s->B[i * n + j] * b[j];
+                v += s->G[i * n + j] * b[j] + s->B[i * n + j] * a[j];
+            }
+            double acc = a[i] * u + b[i] * v;
+            if (s->has_inf_bus)
+                acc += s->Vinf * (s->Ginf[i] * a[i] + s->Binf[i] * b[i]);
+            pe[i] = acc;
+        }
+        free(a);
+    }
+}
+
+/* Dense linear solve A x = r by Gaussian elimination with partial pivoting.
+ * A is m x m row-major and is overwritten.  Returns 0, or -1 if singular.       */
+static int solve_dense(double* A, double* r, int m)
+{
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int row = col + 1; row < m; ++row)
+            if (fabs(A[row * m + col]) > fabs(A[piv * m + col])) piv = row;
+        if (fabs(A[piv * m + col]) == 0.0) return -1;
+        if (piv != col) {
+            for (int j = 0; j < m; ++j) {
+                double t = A[col * m + j]; A[col * m + j] = A[piv * m + j]; A[piv * m + j] = t;
+            }
+            double t = r[col]; r[col] = r[piv]; r[piv] = t;
+        }
+        for (int row = col + 1; row < m; ++row) {
+            double f = A[row * m + col] / A[col * m + col];
+            for (int j = col; j < m; ++j) A[row * m + j] -= f * A[col * m + j];
+            r[row] -= f * r[col];
+        }
+    }
+    for (int row = m - 1; row >= 0; --row) {
+        double acc = r[row];
+        for (int j = row + 1; j < m; ++j) acc -= A[row * m + j] * r[j];
+        r[row] = acc / A[row * m + row];
+    }
+    return 0;
+}
+
+/* Equilibrium at t = 0 (Section V-A: "the system is assumed at equilibrium"):
+ * Newton's method on Pm_i - Pe_i(delta) = 0 from a flat start delta = 0, with
+ * the analytic Jacobian of the pairwise form.  With an infinite bus all n
+ * angles are unknown.  Without one, delta_0 = 0 is the reference and machine 0
+ * balances the power: equations i = 1..n-1 fix delta_1..delta_{n-1}, then
+ * pm_eq[0] = Pe_0(delta).  Returns the iteration count, or -1 on failure.      */
+int oracle_equilibrium(const oracle_system* s, double* delta0, double* pm_eq)
+{
+    int n = s->n;
+    int first = s->has_inf_bus ? 0 : 1;
+    int m = n - first;
+    double* pe = (double*)malloc(sizeof(double) * n);
+    double* J = (double*)malloc(sizeof(double) * (m > 0 ? m * m : 1));
+    double* F = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+    for (int i = 0; i < n; ++i) { delta0[i] = 0.0; pm_eq[i] = s->Pm[i]; }
+    int it = 0, ok = (m == 0);
+    for (it = 0; it < 100 && m > 0; ++it) {
+        oracle_electrical_power(s, delta0, pe, 0);
+        double fmax = 0.0;
+        for (int a = 0; a < m; ++a) {
+            int i = a + first;
+            F[a] = s->Pm[i] - pe[i];
+            if (fabs(F[a]) > fmax) fmax = fabs(F[a]);
+        }
+        if (fmax < 1e-13) { ok = 1; break; }
+        /* J[a][b] = d Pe_i / d delta_j, i = a+first, j = b+first */
+        for (int a = 0; a < m; ++a) {
+            int i = a + first;
+            double diag = 0.0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double dij = delta0[i] - delta0[j];
+                double dPe_ddj = s->E[i] * s->E[j] * (s->G[i * n + j] * sin(dij) - s->B[i * n + j] * cos(dij));
+                diag -= dPe_ddj;
+                if (j >= first) J[a * m + (j - first)] = dPe_ddj;
+            }
+            if (s->has_inf_bus)
+                diag += s->E[i] * s->Vinf * (-s->Ginf[i] * sin(delta0[i]) + s->Binf[i] * cos(delta0[i]));
+            J[a * m + a] = diag;
+        }
+        /* Newton: J ddelta = F (since F = Pm - Pe and dF/ddelta = -J) */
+        if (solve_dense(J, F, m) != 0) break;
+        for (int a = 0; a < m; ++a) delta0[a + first] += F[a];
+    }
+    if (ok && !s->has_inf_bus) {
+        oracle_electrical_power(s, delta0, pe, 0);
+        pm_eq[0] = pe[0];
+    }
+    free(pe); free(J); free(F);
+    return ok ? it : -1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1 step 3: the dynamic simulation of one sample.                   */
+/* ------------------------------------------------------------------------- */
+typedef struct sim_ws {
+    double *delta, *omega, *pe, *force, *x, *xn, *xs;
+    double *k1d, *k1w, *k2d, *k2w, *k3d, *k3w, *k4d, *k4w, *tmpd, *tmpw;
+    double *dW;
+} sim_ws;
+
+static void ws_alloc(sim_ws* w, int n, int d, int Nt)
+{
+    double* buf = (double*)calloc((size_t)(16 * n + 3 * d) + (size_t)d * Nt, sizeof(double));
+    w->delta = buf; w->omega = buf + n; w->pe = buf + 2 * n; w->force = buf + 3 * n;
+    w->k1d = buf + 4 * n; w->k1w = buf + 5 * n; w->k2d = buf + 6 * n; w->k2w = buf + 7 * n;
+    w->k3d = buf + 8 * n; w->k3w = buf + 9 * n; w->k4d = buf + 10 * n; w->k4w = buf + 11 * n;
+    w->tmpd = buf + 12 * n; w->tmpw = buf + 13 * n;
+    w->x = buf + 16 * n; w->xn = w->x + d; w->xs = w->xn + d;
+    w->dW = w->xs + d;
+}
+
+/* Right-hand side of the swing equations at disturbance state xs. */
+static void swing_rhs(const oracle_system* s, const double* pm_eq, const double* delta, const double* omega,
+                      const double* xs, sim_ws* w, int32_t pe_form, double* ddelta, double* domega)
+{
+    int n = s->n, d = s->d;
+    oracle_electrical_power(s, delta, w->pe, pe_form);
+    for (int i = 0; i < n; ++i) {
+        double force = pm_eq[i];
+        for (int q = 0; q < d; ++q) force += s->inject[i * d + q] * xs[q];
+        ddelta[i] = s->omega_s * omega[i];
+        domega[i] = (force - w->pe[i] - s->D[i] * omega[i]) / (2.0 * s->H[i]);
+    }
+}
+
+/* Integrates one sample whose increments are dW[w][n]; writes the trajectory
+ * traj[n][j] (j < n: delta_j, j >= n: domega_j) for n = 0..Nt.                 */
+static void simulate_one(const oracle_system* s, const double* delta0, const double* pm_eq, sim_ws* w,
+                         int32_t pe_form, double* traj)
+{
+    int n = s->n, d = s->d, Nt = s->Nt;
+    double dt = s->dt;
+    for (int i = 0; i < n; ++i) { w->delta[i] = delta0[i]; w->omega[i] = 0.0; }
+    for (int q = 0; q < d; ++q) w->x[q] = 0.0;
+    for (int i = 0; i < n; ++i) { traj[i] = w->delta[i]; traj[n + i] = w->omega[i]; }
+    for (int step = 0; step < Nt; ++step) {
+        /* Euler-Maruyama for the OU disturbance (Eq. distito, Table I) */
+        for (int q = 0; q < d; ++q)
+            w->xn[q] = w->x[q] + (-s->theta[q] * w->x[q]) * dt + s->sigma[q] * w->dW[(int64_t)q * Nt + step];
+        if (s->integrator == 0) {
+            /* classical RK4 */
+            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, w->k1d, w->k1w);
+            for (int q = 0; q < d; ++q) w->xs[q] = 0.5 * (w->x[q] + w->xn[q]);
+            for (int i = 0; i < n; ++i) {
+                w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k1d[i];
+                w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k1w[i];
+            }
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, w->k2d, w->k2w);
+            for (int i = 0; i < n; ++i) {
+                w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k2d[i];
+                w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k2w[i];
+            }
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, w->k3d, w->k3w);
+            for (int i = 0; i < n; ++i) {
+                w->tmpd[i] = w->delta[i] + dt * w->k3d[i];
+                w->tmpw[i] = w->omega[i] + dt * w->k3w[i];
+            }
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, w->k4d, w->k4w);
+            for (int i = 0; i < n; ++i) {
+                w->delta[i] += dt / 6.0 * (w->k1d[i] + 2.0 * w->k2d[i] + 2.0 * w->k3d[i] + w->k4d[i]);
+                w->omega[i] += dt / 6.0 * (w->k1w[i] + 2.0 * w->k2w[i] + 2.0 * w->k3w[i] + w->k4w[i]);
+            }
+        } else {
+            /* Heun (explicit trapezoid) */
+            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, w->k1d, w->k1w);
+            for (int i = 0; i < n; ++i) {
+                w->tmpd[i] = w->delta[i] + dt * w->k1d[i];
+                w->tmpw[i] = w->omega[i] + dt * w->k1w[i];
+            }
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, w->k2d, w->k2w);
+            for (int i = 0; i < n; ++i) {
+                w->delta[i] += 0.5 * dt * (w->k1d[i] + w->k2d[i]);
+                w->omega[i] += 0.5 * dt * (w->k1w[i] + w->k2w[i]);
+            }
+        }
+        for (int q = 0; q < d; ++q) w->x[q] = w->xn[q];
+        double* row = traj + (int64_t)(step + 1) * 2 * n;
+        for (int i = 0; i < n; ++i) { row[i] = w->delta[i]; row[n + i] = w->omega[i]; }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1 steps 2-4 over `count` samples whose coefficients are the rows
+ * of zeta [count x d*K].  Optional outputs: the increments dW [count x d x Nt],
+ * the trajectories traj [count x (Nt+1) x 2n], and the moments mean, var
+ * [(Nt+1) x 2n].  Moments use the shifted-sum identity
+ *   mean = c + S1/N,  var = (S2 - S1^2/N)/(N-1),  S1 = sum(x-c), S2 = sum (x-c)^2,
+ * with c the trajectory of the first sample (any c gives the same values in
+ * exact arithmetic; a c near the data keeps the FP64 sums well conditioned).
+ * Work is split over nthreads POSIX threads by contiguous sample blocks and the
+ * per-thread sums are added in thread order.                                   */
+/* ------------------------------------------------------------------------- */
+typedef struct sim_job {
+    const oracle_system* s;
+    const double* zeta;
+    const double* phi;
+    const double* delta0;
+    const double* pm_eq;
+    const double* shift;
+    int64_t s0, s1;
+    int32_t pe_form;
+    double* dW_out;
+    double* traj_out;
+    double* S1;
+    double* S2;
+} sim_job;
+
+static void* sim_worker(void* arg)
+{
+    sim_job* job = (sim_job*)arg;
+    const oracle_system* s = job->s;
+    int n = s->n, d = s->d, K = s->K, Nt = s->Nt;
+    int64_t cols = (int64_t)(Nt + 1) * 2 * n;
+    sim_ws w;
+    ws_alloc(&w, n, d, Nt);
+    double* traj_local = (double*)malloc(sizeof(double) * cols);
+    for (int64_t smp = job->s0; smp < job->s1; ++smp) {
+        const double* z = job->zeta + smp * (int64_t)d * K;
+        for (int q = 0; q < d; ++q)
+            for (int step = 0; step < Nt; ++step) {
+                double acc = 0.0;
+                for (int k = 0; k < K; ++k) acc += z[q * K + k] * job->phi[(int64_t)k * Nt + step];
+                w.dW[(int64_t)q * Nt + step] = acc;
+            }
+        if (job->dW_out) memcpy(job->dW_out + smp * (int64_t)d * Nt, w.dW, sizeof(double) * (size_t)d * Nt);
+        double* traj = job->traj_out ? job->traj_out + smp * cols : traj_local;
+        simulate_one(s, job->delta0, job->pm_eq, &w, job->pe_form, traj);
+        if (job->S1) {
+            for (int64_t c = 0; c < cols; ++c) {
+                double v = traj[c] - job->shift[c];
+                job->S1[c] += v;
+                job->S2[c] += v * v;
+            }
+        }
+    }
+    free(traj_local);
+    free(w.delta);
+    return NULL;
+}
+
+int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, int32_t pe_form, int32_t nthreads,
+                    double* delta0_out, double* pm_eq_out, double* dW_out, double* traj_out, double* mean,
+                    double* var)
+{
+    int n = s->n, Nt = s->Nt;
+    if (n < 1 || s->d < 1 || s->K < 1 || Nt < 1 || count < 1 || s->dt <= 0.0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > count) nthreads = (int32_t)count;
+    int64_t cols = (int64_t)(Nt + 1) * 2 * n;
+    double* phi = (double*)malloc(sizeof(double) * (size_t)s->K * Nt);
+    oracle_kl_increment_basis(s->K, s->T, Nt, phi);
+    double* delta0 = (double*)malloc(sizeof(double) * n);
+    double* pm_eq = (double*)malloc(sizeof(double) * n);
+    if (oracle_equilibrium(s, delta0, pm_eq) < 0) {
+        free(phi); free(delta0); free(pm_eq);
+        return -2;
+    }
+    /* a prescribed initial state (used to test the integrator off equilibrium) */
+    if (s->init_delta)
+        for (int i = 0; i < n; ++i) delta0[i] = s->init_delta[i];
+    if (delta0_out) memcpy(delta0_out, delta0, sizeof(double) * n);
+    if (pm_eq_out) memcpy(pm_eq_out, pm_eq, sizeof(double) * n);
+
+    double* shift = NULL;
+    double* S1 = NULL;
+    double* S2 = NULL;
+    int want_moments = (mean != NULL || var != NULL);
+    if (want_moments) {
+        /* shift = trajectory of the first sample, integrated once on its own */
+        shift = (double*)malloc(sizeof(double) * cols);
+        sim_job j0 = {s, zeta, phi, delta0, pm_eq, NULL, 0, 1, pe_form, NULL, shift, NULL, NULL};
+        /* traj_out for sample 0 only points at `shift`; S1 == NULL disables sums */
+        sim_worker(&j0);
+        S1 = (double*)calloc((size_t)cols * nthreads, sizeof(double));
+        S2 = (double*)calloc((size_t)cols * nthreads, sizeof(double));
+    }
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+    sim_job* jobs = (sim_job*)malloc(sizeof(sim_job) * nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].s = s; jobs[t].zeta = zeta; jobs[t].phi = phi; jobs[t].delta0 = delta0;
+        jobs[t].pm_eq = pm_eq; jobs[t].shift = shift;
+        jobs[t].s0 = count * t / nthreads;
+        jobs[t].s1 = count * (t + 1) / nthreads;
+        jobs[t].pe_form = pe_form;
+        jobs[t].dW_out = dW_out;
+        jobs[t].traj_out = traj_out;
+        jobs[t].S1 = want_moments ? S1 + (int64_t)t * cols : NULL;
+        jobs[t].S2 = want_moments ? S2 + (int64_t)t * cols : NULL;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
+    sim_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    if (want_moments) {
+        for (int64_t c = 0; c < cols; ++c) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int t = 0; t < nthreads; ++t) { s1 += S1[(int64_t)t * cols + c]; s2 += S2[(int64_t)t * cols + c]; }
+            double Nn = (double)count;
+            if (mean) mean[c] = shift[c] + s1 / Nn;
+            if (var) var[c] = (count > 1) ? (s2 - s1 * s1 / Nn) / (Nn - 1.0) : NAN;
+        }
+        free(shift); free(S1); free(S2);
+    }
+    free(th); free(jobs); free(phi); free(delta0); free(pm_eq);
+    return 0;
+}
+
+/* Algorithm 1 step 4 on stored values: two-pass mean and unbiased variance of
+ * x[N][C] over the N rows, column by column.                                  */
+void oracle_moments_twopass(const double* x, int64_t N, int64_t C, double* mean, double* var)
+{
+    for (int64_t c = 0; c < C; ++c) {
+        double s = 0.0;
+        for (int64_t r = 0; r < N; ++r) s += x[r * C + c];
+        double m = s / (double)N;
+        double ss = 0.0;
+        for (int64_t r = 0; r < N; ++r) {
+            double e = x[r * C + c] - m;
+            ss += e * e;
+        }
+        mean[c] = m;
+        var[c] = (N > 1) ? ss / (double)(N - 1) : NAN;
+    }
+}
