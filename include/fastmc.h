@@ -1,0 +1,266 @@
+/*
+ * fastmc.h -- C ABI of the GB300 (sm_103a) implementation of the fast Monte
+ * Carlo method of Qiu, Lin, Chen, Liu and Song, "Fast Monte Carlo Simulation of
+ * Dynamic Power Systems Under Continuous Random Disturbances" (arXiv 2007.03847).
+ *
+ * The method (Algorithm 1, Section IV-C): the disturbance is an Ito process
+ * (Eq. ito) driven by Wiener processes; each Wiener process is replaced by its
+ * truncated Karhunen-Loeve expansion in K independent standard normals
+ * (Eqs. kl, kle, eqkl); the M = d*K normals are drawn by Latin hypercube
+ * sampling (Section IV-B); every sample's disturbance path drives a dynamic
+ * simulation of the power system (Eqs. state, algebra); the expectation and
+ * variance of the response are taken over the samples.
+ *
+ * This library computes that path on one GPU:
+ *   fmc_lhs_sample, fmc_lhs_sample_split  -- Algorithm 1 step 1
+ *   fmc_kl_basis, fmc_kle_reconstruct     -- Algorithm 1 step 2
+ *   fmc_equilibrium                       -- the initial equilibrium (Section V-A)
+ *   fmc_simulate                          -- Algorithm 1 steps 1-4 fused
+ *   fmc_moments                           -- Algorithm 1 step 4 on given values
+ *
+ * Conventions for every entry point:
+ *   - Return value: FMC_OK (0) or a positive FMC_E* code; fmc_last_error(ctx)
+ *     then describes the failure.  No C++ exception crosses this boundary.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never frees them.  Host pointers are read during the call only.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it and the call returns without waiting, unless stated.
+ *   - All arrays are dense row-major with the shapes given.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef FASTMC_H
+#define FASTMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FMC_OK 0
+#define FMC_EINVAL 1        /* invalid argument (message in fmc_last_error) */
+#define FMC_ENOMEM 2        /* device allocation failed or over budget */
+#define FMC_ECUDA 3         /* a CUDA runtime/driver call failed */
+#define FMC_ETIMEOUT 4      /* a bounded device-side wait gave up */
+#define FMC_NOT_READY 5     /* asynchronous result not available yet */
+#define FMC_EBUSY 6         /* resource in use */
+#define FMC_ECANCELLED 7    /* request cancelled */
+#define FMC_EUNSUPPORTED 8  /* valid request outside what this build handles */
+#define FMC_ENOCONVERGE 9   /* equilibrium Newton iteration did not converge */
+
+/* ---- sampling modes (Section IV-B) ---------------------------------------- */
+#define FMC_LHS 0           /* Latin hypercube: stratum pi_i(k), uniform inside */
+#define FMC_SRS 1           /* simple random sampling: p = u */
+#define FMC_LHS_MIDPOINT 2  /* Latin hypercube at the stratum midpoint */
+
+/* ---- contraction precision of the KL reconstruction ------------------------- */
+#define FMC_PREC_F32 0      /* FP32 SIMT (the plain form) */
+#define FMC_PREC_BF16 1     /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+#define FMC_PREC_BF16X3 2   /* split BF16 hi+lo, three tcgen05 products: FP32-level accuracy */
+
+/* ---- integrators for the swing equations --------------------------------- */
+#define FMC_RK4 0
+#define FMC_HEUN 1
+
+/* ---- simulation paths --------------------------------------------------- */
+#define FMC_PATH_FUSED 0    /* one kernel: contraction in TMEM -> integrator -> moment partials */
+#define FMC_PATH_PLAIN 1    /* unfused FP32: increments and trajectories through HBM */
+
+/* ---- limits of this build -------------------------------------------------- */
+#define FMC_MAX_MACHINES 16
+#define FMC_MAX_DISTURBANCES 8
+
+typedef struct fmc_ctx fmc_ctx;
+
+/*
+ * One uncertainty-evaluation problem.
+ *
+ * System: the Kron-reduced classical model of n machines (Eqs. state/algebra
+ * reduced to the swing equations),
+ *   d delta_i / dt  = omega_s * domega_i
+ *   2 H_i d domega_i / dt = Pm_i + sum_w inject[i][w] x_w - Pe_i(delta) - D_i domega_i
+ *   Pe_i = sum_j E_i E_j (G_ij cos(delta_i - delta_j) + B_ij sin(delta_i - delta_j))
+ *          + E_i Vinf (Ginf_i cos delta_i + Binf_i sin delta_i)   [if has_inf_bus]
+ * Disturbances: d Ornstein-Uhlenbeck processes dx_w = -theta_w x_w dt +
+ * sigma_w dW_w (Eq. ito with Table I's Gaussian drift at rate theta_w),
+ * advanced by Euler-Maruyama (Eq. distito) on the grid t_n = n dt, n < Nt,
+ * T = Nt dt.  Each W_w is its K-term KL expansion with the Brownian eigenbasis
+ *   W(t) = sum_k zeta_k sqrt(2T)/((k-1/2) pi) sin((k-1/2) pi t / T).
+ * Sampling: N samples of the M = d*K coefficients, seeded by `seed`.
+ * Initial state: the equilibrium (Section V-A) found by Newton's method; without
+ * an infinite bus machine 0 is the angle reference and balances the power
+ * (its Pm is replaced by the balance).
+ * All arrays are host memory, read during the call.
+ */
+typedef struct fmc_scenario {
+    int32_t n;              /* machines, 1..FMC_MAX_MACHINES */
+    int32_t d;              /* disturbances = Wiener processes, 1..FMC_MAX_DISTURBANCES */
+    int32_t K;              /* KL terms per Wiener process, >= 1 */
+    int32_t sampling;       /* FMC_LHS, FMC_SRS or FMC_LHS_MIDPOINT */
+    double T;               /* horizon, s; T/dt must be an integer to 1e-9 relative */
+    double dt;              /* step, s */
+    int64_t N;              /* samples, 1..2^31 */
+    uint64_t seed;          /* Philox key of the design */
+    int32_t precision;      /* FMC_PREC_* of the KL contraction */
+    int32_t integrator;     /* FMC_RK4 or FMC_HEUN */
+    int32_t has_inf_bus;    /* 0 or 1 */
+    int32_t reserved0;
+    double omega_s;         /* synchronous speed, rad/s */
+    double Vinf;            /* infinite-bus voltage */
+    const double* G;        /* [n][n] conductance */
+    const double* B;        /* [n][n] susceptance */
+    const double* Ginf;     /* [n] or NULL without infinite bus */
+    const double* Binf;     /* [n] or NULL without infinite bus */
+    const double* H;        /* [n] inertia constants, s, > 0 */
+    const double* D;        /* [n] damping */
+    const double* E;        /* [n] internal EMF magnitudes */
+    const double* Pm;       /* [n] mechanical powers */
+    const double* theta;    /* [d] OU rates, 1/s */
+    const double* sigma;    /* [d] OU diffusion coefficients */
+    const double* inject;   /* [n][d] weight of disturbance w in machine i's power balance */
+} fmc_scenario;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` (made current for the calling
+ * thread).  `mem_budget_bytes` caps the library's own device workspace
+ * (0 = no cap).  Returns FMC_OK and *out, or an error code. */
+int fmc_create(fmc_ctx** out, int device, size_t mem_budget_bytes);
+
+/* Synchronises the context's work, frees its workspace and the context. */
+int fmc_destroy(fmc_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context.  Accepts NULL (returns the message of the last
+ * failed fmc_create on this thread). */
+const char* fmc_last_error(const fmc_ctx* ctx);
+
+/* Number of SMs and the device name of the context's GPU. */
+int fmc_device_info(const fmc_ctx* ctx, int* sm_count, char* name, size_t name_len);
+
+/* ---- Algorithm 1 step 1: Latin hypercube sampling (Section IV-B) ------------ */
+
+/*
+ * Rows k0 .. k0+count-1 of the N-sample design over M standard normal
+ * coefficients.  For dimension i and sample k: stratum s = pi_i(k), where pi_i
+ * is a keyed Feistel bijection of {0..N-1} (six rounds on 2h bits,
+ * h = max(1, ceil(log2(N)/2)), round function Philox4x32-10 word 0 with
+ * counter (R, i, 1 + round, 0), key = seed, restricted to [0, N) by cycle
+ * walking); u = (r + 1/2) 2^-32 with r = Philox4x32-10(counter (k, i, 0, 0),
+ * key = seed) word 0; p = (s + u)/N (LHS), (s + 1/2)/N (LHS_MIDPOINT) or u
+ * (SRS); zeta = Phi^-1(p) in FP32.
+ *   zeta_dev   [count][M] float, or NULL
+ *   strata_dev [M][count] uint32 (s; k for SRS), or NULL
+ * Errors: FMC_EINVAL if N < 1, N > 2^31, M < 1, k0 < 0, count < 0,
+ * k0 + count > N, or both outputs NULL.
+ */
+int fmc_lhs_sample(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int64_t count, int32_t M,
+                   int32_t mode, float* zeta_dev, uint32_t* strata_dev, void* stream);
+
+/*
+ * The same design written as split BF16 for the tensor-core contraction: the
+ * M = d*K coefficients of a row are laid out as d groups of K_s =
+ * round_up(K, 8) entries (entries K..K_s-1 are zero):
+ *   hi_dev [count][d][K_s] bf16 (as uint16 bit patterns) = bf16(zeta)
+ *   lo_dev [count][d][K_s] bf16 = bf16(zeta - hi), or NULL
+ * Errors as fmc_lhs_sample; d or K < 1.
+ */
+int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int64_t count, int32_t d,
+                         int32_t K, int32_t mode, uint16_t* hi_dev, uint16_t* lo_dev, void* stream);
+
+/* ---- Algorithm 1 step 2: KL reconstruction (Eqs. kl, kle, eqkl) --------------- */
+
+/*
+ * Increment basis of the truncated Brownian KL expansion on the grid
+ * t_n = n T/Nt:  phi[k][n] = c_k (sin(a_k t_{n+1}) - sin(a_k t_n)),
+ * a_k = (k+1/2) pi / T, c_k = sqrt(2T)/((k+1/2) pi), k = 0..K-1 (0-based).
+ * Computed in FP64 on the GPU and rounded:  phi_dev [K][Nt] float.
+ * Errors: FMC_EINVAL if K < 1, Nt < 1 or T <= 0.
+ */
+int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, float* phi_dev, void* stream);
+
+/*
+ * Increments of the reconstructed Wiener paths of `count` samples:
+ *   dW[s][w][n] = sum_k zeta[s][w*K + k] phi[k][n],   T = Nt dt.
+ *   zeta_dev [count][d*K] float (as written by fmc_lhs_sample)
+ *   dW_dev   [count][d][Nt] float
+ * precision: FMC_PREC_F32 (FP32 SIMT), FMC_PREC_BF16 or FMC_PREC_BF16X3
+ * (tcgen05 tensor cores; zeta and phi split to BF16 inside the call, using
+ * library workspace).
+ * Errors: FMC_EINVAL on sizes < 1 or T/dt not an integer; FMC_ENOMEM.
+ */
+int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
+                        double dt, int32_t precision, float* dW_dev, void* stream);
+
+/* ---- equilibrium (Section V-A: "at equilibrium at t = 0") --------------------- */
+
+/*
+ * Newton's method in FP64 on the GPU for Pm_i = Pe_i(delta) from a flat start.
+ * Writes delta0[n] and the balanced mechanical powers pm_eq[n] (host memory).
+ * Synchronous.  Errors: FMC_EINVAL (scenario), FMC_ENOCONVERGE.
+ */
+int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, double* pm_eq);
+
+/* ---- Algorithm 1 steps 1-4 ---------------------------------------------------- */
+
+/*
+ * Runs the whole path for one scenario: LHS -> KL reconstruction -> EM for the
+ * OU disturbances -> integration of the swing equations for every sample ->
+ * mean and unbiased variance (N-1; NaN for N = 1) over the N samples at every
+ * grid time t_n, n = 0..Nt, for every state (delta_0..delta_{n-1},
+ * domega_0..domega_{n-1}).
+ *   mean_dev, var_dev [Nt+1][2n] double (device)
+ *   traj_dev  [N][Nt+1][2n] float, or NULL: every sample's trajectory (for
+ *             testing; N*(Nt+1)*2n*4 bytes)
+ *   path      FMC_PATH_FUSED or FMC_PATH_PLAIN (FMC_PATH_PLAIN needs
+ *             precision FMC_PREC_F32; FMC_PATH_FUSED needs BF16 or BF16X3)
+ * Errors: FMC_EINVAL, FMC_EUNSUPPORTED (n or d above this build's limits),
+ * FMC_ENOMEM, FMC_ENOCONVERGE, FMC_ETIMEOUT (a bounded device wait gave up),
+ * FMC_ECUDA.
+ */
+int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
+                 float* traj_dev, void* stream);
+
+/* ---- Algorithm 1 step 4 --------------------------------------------------- */
+
+/*
+ * Column-wise mean and unbiased variance of x[N][C] over its N rows, combined
+ * in FP64 from FP32 shifted partial sums (shift = row 0).
+ *   x_dev [N][C] float; mean_dev, var_dev [C] double.  NaN variance for N = 1.
+ * Errors: FMC_EINVAL if N < 1 or C < 1.
+ */
+int fmc_moments(fmc_ctx* ctx, const float* x_dev, int64_t N, int64_t C, double* mean_dev, double* var_dev,
+                void* stream);
+
+/* ---- diagnostics and measurement ------------------------------------------ */
+
+/*
+ * Waits for all work on the context's device, then reports the device-side
+ * status words of the last simulation or tensor-core reconstruction:
+ * *eq_iterations = Newton iterations of the last equilibrium (-1: did not
+ * converge), *kernel_error = 0 or the code of a bounded wait that gave up.
+ * Returns FMC_OK, FMC_ENOCONVERGE or FMC_ETIMEOUT accordingly.
+ */
+int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error);
+
+/*
+ * Kernel timing with CUDA events recorded on the launching stream around every
+ * kernel phase of later calls (at most max_records phases; enable = 0 stops and
+ * clears).  Phases: 0 LHS, 1 KL basis, 2 equilibrium, 3 fused simulation,
+ * 4 fused moment reduce, 5 FP32 contraction, 6 plain integrator, 7 moments.
+ */
+int fmc_profile(fmc_ctx* ctx, int32_t enable, int64_t max_records);
+
+/* Synchronises, then sums the recorded durations of one phase. */
+int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* launches);
+
+/* CTAs per SM the last fused launch could keep resident (occupancy API). */
+int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTMC_H */

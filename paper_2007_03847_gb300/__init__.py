@@ -1,0 +1,318 @@
+"""GB300 (sm_103a) implementation of the fast Monte Carlo method of Qiu et al.,
+"Fast Monte Carlo Simulation of Dynamic Power Systems Under Continuous Random
+Disturbances" (arXiv 2007.03847).
+
+The compute path lives in ``lib/libfastmc.so`` (CUDA C++ with a C ABI declared
+in ``include/fastmc.h``).  This module only marshals arguments: PyTorch tensors
+supply device memory and the current CUDA stream; every step of Algorithm 1 runs
+in the library's kernels.  There is no CPU fallback: if the library is missing
+or no GPU is present, the calls raise.
+
+Entry points (same names as the C ABI without the ``fmc_`` prefix):
+``lhs_sample``, ``lhs_sample_split``, ``kl_basis``, ``kle_reconstruct``,
+``equilibrium``, ``simulate``, ``moments``, plus ``Context``, ``device_status``
+and the kernel-timing helpers ``profile``/``profile_read``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfastmc.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_READY, EBUSY, ECANCELLED, EUNSUPPORTED, ENOCONVERGE = range(10)
+LHS, SRS, LHS_MIDPOINT = 0, 1, 2
+PREC_F32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+RK4, HEUN = 0, 1
+PATH_FUSED, PATH_PLAIN = 0, 1
+PH_LHS, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS = range(8)
+MAX_MACHINES, MAX_DISTURBANCES = 16, 8
+
+_PRECISION = {"f32": PREC_F32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3}
+_PATH = {"fused": PATH_FUSED, "plain": PATH_PLAIN}
+
+
+class FastMCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fastmc error {code}: {msg}")
+        self.code = code
+
+
+class _Scenario(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("d", ctypes.c_int32), ("K", ctypes.c_int32), ("sampling", ctypes.c_int32),
+        ("T", ctypes.c_double), ("dt", ctypes.c_double), ("N", ctypes.c_int64), ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32), ("has_inf_bus", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("omega_s", ctypes.c_double), ("Vinf", ctypes.c_double),
+        ("G", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Ginf", ctypes.c_void_p), ("Binf", ctypes.c_void_p),
+        ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
+        ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compiles libfastmc.so in-tree with nvcc (sm_103a)."""
+    from . import _buildlib
+    return _buildlib.build(force=force)
+
+
+def load_library():
+    """Loads libfastmc.so; raises if it has not been built."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise FastMCError(ECUDA, f"{LIB_PATH} is missing: build it with paper_2007_03847_gb300.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "fmc_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+            "fmc_destroy": ([vp], ctypes.c_int),
+            "fmc_last_error": ([vp], ctypes.c_char_p),
+            "fmc_device_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+            "fmc_lhs_sample": ([vp, u64, i64, i64, i64, i32, i32, vp, vp, vp], ctypes.c_int),
+            "fmc_lhs_sample_split": ([vp, u64, i64, i64, i64, i32, i32, i32, vp, vp, vp], ctypes.c_int),
+            "fmc_kl_basis": ([vp, i32, dbl, i32, vp, vp], ctypes.c_int),
+            "fmc_kle_reconstruct": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
+            "fmc_equilibrium": ([vp, ctypes.POINTER(_Scenario), vp, vp], ctypes.c_int),
+            "fmc_simulate": ([vp, ctypes.POINTER(_Scenario), i32, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_moments": ([vp, vp, i64, i64, vp, vp, vp], ctypes.c_int),
+            "fmc_device_status": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "fmc_profile": ([vp, i32, i64], ctypes.c_int),
+            "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
+            "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+class Context:
+    """A library context on one CUDA device (workspace, kernel timing)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise FastMCError(ECUDA, "no CUDA device is available")
+        torch.cuda.init()
+        self.lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.fmc_create(ctypes.byref(h), device, mem_budget_bytes)
+        if rc != OK:
+            raise FastMCError(rc, self.lib.fmc_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int):
+        if rc != OK:
+            raise FastMCError(rc, self.lib.fmc_last_error(self.h).decode())
+
+    def info(self):
+        sms = ctypes.c_int()
+        name = ctypes.create_string_buffer(256)
+        self.check(self.lib.fmc_device_info(self.h, ctypes.byref(sms), name, 256))
+        return sms.value, name.value.decode()
+
+
+_default_ctx = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(0)
+    return _default_ctx
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise FastMCError(EINVAL, "device tensor expected")
+    if not t.is_contiguous():
+        raise FastMCError(EINVAL, "contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class ScenarioStruct:
+    """fmc_scenario built from an object with the fields of fmc_synth.Scenario."""
+
+    def __init__(self, sc, precision=None, sampling=None, integrator=None):
+        f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        self.keep = {k: f(getattr(sc, k)) for k in ("G", "B", "H", "D", "E", "Pm", "theta", "sigma", "inject")}
+        s = _Scenario()
+        s.n, s.d, s.K = int(sc.n), int(sc.d), int(sc.K)
+        s.sampling = int(getattr(sc, "sampling", LHS) if sampling is None else sampling)
+        s.T, s.dt, s.N, s.seed = float(sc.T), float(sc.dt), int(sc.N), int(sc.seed)
+        prec = getattr(sc, "precision", PREC_BF16X3) if precision is None else precision
+        s.precision = _PRECISION.get(prec, prec) if isinstance(prec, str) else int(prec)
+        s.integrator = int(getattr(sc, "integrator", RK4) if integrator is None else integrator)
+        s.has_inf_bus = 1 if sc.has_inf_bus else 0
+        s.omega_s, s.Vinf = float(sc.omega_s), float(sc.Vinf)
+        if sc.has_inf_bus:
+            self.keep["Ginf"] = f(sc.Ginf)
+            self.keep["Binf"] = f(sc.Binf)
+        for k, a in self.keep.items():
+            setattr(s, k, a.ctypes.data)
+        self.s = s
+        self.Nt = int(round(sc.T / sc.dt))
+
+
+# ---------------------------------------------------------------------------- entry points
+
+
+def lhs_sample(seed: int, N: int, M: int, mode: int = LHS, k0: int = 0, count: int | None = None, zeta=None,
+               strata=None, ctx: Context | None = None, stream=None):
+    """Algorithm 1 step 1: rows k0..k0+count-1 of the N-sample design -> zeta [count, M] float32."""
+    import torch
+    ctx = ctx or default_context()
+    count = N - k0 if count is None else count
+    if zeta is None and strata is None:
+        zeta = torch.empty((count, M), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.fmc_lhs_sample(ctx.h, seed, N, k0, count, M, mode, _ptr(zeta), _ptr(strata), _stream(stream)))
+    return zeta, strata
+
+
+def lhs_sample_split(seed: int, N: int, d: int, K: int, mode: int = LHS, k0: int = 0, count: int | None = None,
+                     ctx: Context | None = None, stream=None):
+    """Split-BF16 design [count, d, round_up(K, 8)] as (hi, lo) bfloat16 tensors."""
+    import torch
+    ctx = ctx or default_context()
+    count = N - k0 if count is None else count
+    Ks = (K + 7) // 8 * 8
+    hi = torch.empty((count, d, Ks), dtype=torch.bfloat16, device="cuda")
+    lo = torch.empty_like(hi)
+    ctx.check(ctx.lib.fmc_lhs_sample_split(ctx.h, seed, N, k0, count, d, K, mode, _ptr(hi), _ptr(lo),
+                                           _stream(stream)))
+    return hi, lo
+
+
+def kl_basis(K: int, T: float, Nt: int, phi=None, ctx: Context | None = None, stream=None):
+    """Increment basis phi [K, Nt] float32 (FP64 on the GPU, rounded)."""
+    import torch
+    ctx = ctx or default_context()
+    if phi is None:
+        phi = torch.empty((K, Nt), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.fmc_kl_basis(ctx.h, K, T, Nt, _ptr(phi), _stream(stream)))
+    return phi
+
+
+def kle_reconstruct(zeta, d: int, K: int, T: float, dt: float, precision="f32", dW=None, ctx: Context | None = None,
+                    stream=None):
+    """Algorithm 1 step 2: increments dW [count, d, Nt] float32 from zeta [count, d*K]."""
+    import torch
+    ctx = ctx or default_context()
+    count = zeta.shape[0]
+    Nt = int(round(T / dt))
+    prec = _PRECISION.get(precision, precision) if isinstance(precision, str) else precision
+    if dW is None:
+        dW = torch.empty((count, d, Nt), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.fmc_kle_reconstruct(ctx.h, _ptr(zeta), count, d, K, T, dt, prec, _ptr(dW), _stream(stream)))
+    return dW
+
+
+def equilibrium(scenario, ctx: Context | None = None):
+    """FP64 Newton equilibrium on the GPU -> (delta0, pm_eq) numpy arrays."""
+    ctx = ctx or default_context()
+    ss = ScenarioStruct(scenario)
+    delta0 = np.zeros(scenario.n)
+    pm = np.zeros(scenario.n)
+    ctx.check(ctx.lib.fmc_equilibrium(ctx.h, ctypes.byref(ss.s), delta0.ctypes.data_as(ctypes.c_void_p),
+                                      pm.ctypes.data_as(ctypes.c_void_p)))
+    return delta0, pm
+
+
+def simulate(scenario, path="fused", precision=None, sampling=None, integrator=None, mean=None, var=None,
+             traj=None, want_traj: bool = False, ctx: Context | None = None, stream=None):
+    """Algorithm 1 steps 1-4 for one scenario.
+
+    Returns (mean, var[, traj]) as device tensors: mean/var [Nt+1, 2n] float64,
+    traj [N, Nt+1, 2n] float32 when requested.
+    """
+    import torch
+    ctx = ctx or default_context()
+    p = _PATH.get(path, path) if isinstance(path, str) else path
+    if precision is None:
+        precision = "f32" if p == PATH_PLAIN else "bf16x3"
+    ss = ScenarioStruct(scenario, precision=precision, sampling=sampling, integrator=integrator)
+    Nt1, S = ss.Nt + 1, 2 * scenario.n
+    if mean is None:
+        mean = torch.empty((Nt1, S), dtype=torch.float64, device="cuda")
+    if var is None:
+        var = torch.empty((Nt1, S), dtype=torch.float64, device="cuda")
+    if want_traj and traj is None:
+        traj = torch.empty((scenario.N, Nt1, S), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.fmc_simulate(ctx.h, ctypes.byref(ss.s), p, _ptr(mean), _ptr(var), _ptr(traj),
+                                   _stream(stream)))
+    return (mean, var, traj) if (want_traj or traj is not None) else (mean, var)
+
+
+def moments(x, mean=None, var=None, ctx: Context | None = None, stream=None):
+    """Algorithm 1 step 4: column mean and unbiased variance of x [N, C] float32 -> float64 [C]."""
+    import torch
+    ctx = ctx or default_context()
+    N = x.shape[0]
+    C = int(np.prod(x.shape[1:])) if x.dim() > 1 else 1
+    if mean is None:
+        mean = torch.empty(x.shape[1:], dtype=torch.float64, device="cuda")
+    if var is None:
+        var = torch.empty(x.shape[1:], dtype=torch.float64, device="cuda")
+    ctx.check(ctx.lib.fmc_moments(ctx.h, _ptr(x), N, C, _ptr(mean), _ptr(var), _stream(stream)))
+    return mean, var
+
+
+def device_status(ctx: Context | None = None):
+    """(equilibrium iterations, kernel error code) after synchronising; raises on errors."""
+    ctx = ctx or default_context()
+    it, err = ctypes.c_int(), ctypes.c_int()
+    ctx.check(ctx.lib.fmc_device_status(ctx.h, ctypes.byref(it), ctypes.byref(err)))
+    return it.value, err.value
+
+
+def profile(enable: bool, max_records: int = 100000, ctx: Context | None = None):
+    ctx = ctx or default_context()
+    ctx.check(ctx.lib.fmc_profile(ctx.h, 1 if enable else 0, max_records))
+
+
+def profile_read(phase: int, ctx: Context | None = None):
+    """(total milliseconds, launches) of one kernel phase since profiling was enabled."""
+    ctx = ctx or default_context()
+    ms, cnt = ctypes.c_double(), ctypes.c_int64()
+    ctx.check(ctx.lib.fmc_profile_read(ctx.h, phase, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def fused_occupancy(ctx: Context | None = None) -> int:
+    ctx = ctx or default_context()
+    v = ctypes.c_int()
+    ctx.check(ctx.lib.fmc_last_fused_occupancy(ctx.h, ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,686 @@
+// C ABI of the fastmc library: argument validation, workspace, tensor maps and
+// the sequencing of the kernels of Algorithm 1 on the caller's stream.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fmc_common.cuh"
+#include "kernels.cuh"
+#include "swing.cuh"
+#include "tc_common.cuh"
+
+using namespace fmc;
+
+namespace {
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum Phase { PH_LHS = 0, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS, PH_COUNT };
+
+struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct fmc_ctx {
+    int device = 0;
+    int sms = 0;
+    char name[256] = {0};
+    size_t budget = 0;
+    size_t used = 0;
+    std::string err;
+    DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
+    // profiling of kernel phases (CUDA events on the launching stream)
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    size_t prof_cap = 0;
+    int last_fused_ctas_per_sm = 0;
+};
+
+static thread_local std::string g_create_err;
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode()
+{
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+    }
+    return fn;
+}
+
+static int fail(fmc_ctx* ctx, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+static int cuda_fail(fmc_ctx* ctx, cudaError_t e, const char* what)
+{
+    return fail(ctx, FMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FMC_CUDA(ctx, expr, what)                         \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, what); \
+    } while (0)
+
+static int ensure(fmc_ctx* ctx, DevBuf& b, size_t bytes)
+{
+    if (b.bytes >= bytes) return FMC_OK;
+    size_t want = bytes + bytes / 8;
+    if (ctx->budget && ctx->used - b.bytes + want > ctx->budget) {
+        want = bytes;
+        if (ctx->used - b.bytes + want > ctx->budget)
+            return fail(ctx, FMC_ENOMEM, "workspace of %zu bytes exceeds the budget of %zu", bytes, ctx->budget);
+    }
+    if (b.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(b.ptr);
+        ctx->used -= b.bytes;
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FMC_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    ctx->used += want;
+    return FMC_OK;
+}
+
+// ---- profiling --------------------------------------------------------------
+
+static void prof_begin(fmc_ctx* ctx, int phase, cudaStream_t st, ProfRec** out)
+{
+    *out = nullptr;
+    if (!ctx->prof || ctx->recs.size() >= ctx->prof_cap) return;
+    ProfRec r;
+    r.phase = phase;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaEventDestroy(r.a);
+        return;
+    }
+    cudaEventRecord(r.a, st);
+    ctx->recs.push_back(r);
+    *out = &ctx->recs.back();
+}
+
+static void prof_end(ProfRec* r, cudaStream_t st)
+{
+    if (r) cudaEventRecord(r->b, st);
+}
+
+static void prof_clear(fmc_ctx* ctx)
+{
+    for (auto& r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    ctx->recs.clear();
+}
+
+// ---- scenario checks --------------------------------------------------------
+
+static int nm_bucket_for(int n)
+{
+    static const int buckets[] = {1, 2, 4, 8, 10, 12, 16};
+    for (int b : buckets)
+        if (n <= b) return b;
+    return -1;
+}
+
+static int steps_of(fmc_ctx* ctx, double T, double dt, int* Nt)
+{
+    if (!(T > 0.0) || !(dt > 0.0) || !std::isfinite(T) || !std::isfinite(dt))
+        return fail(ctx, FMC_EINVAL, "T and dt must be positive and finite (T=%g, dt=%g)", T, dt);
+    double r = T / dt;
+    double k = std::round(r);
+    if (k < 1 || k > 2147483647.0 || std::fabs(k * dt - T) > 1e-9 * T)
+        return fail(ctx, FMC_EINVAL, "T/dt = %.12g is not an integer number of steps", r);
+    *Nt = (int)k;
+    return FMC_OK;
+}
+
+static int check_scenario(fmc_ctx* ctx, const fmc_scenario* s, int* Nt)
+{
+    if (!s) return fail(ctx, FMC_EINVAL, "scenario is NULL");
+    if (s->n < 1) return fail(ctx, FMC_EINVAL, "n = %d < 1", s->n);
+    if (s->n > FMC_MAX_MACHINES) return fail(ctx, FMC_EUNSUPPORTED, "n = %d above %d", s->n, FMC_MAX_MACHINES);
+    if (s->d < 1) return fail(ctx, FMC_EINVAL, "d = %d < 1", s->d);
+    if (s->d > FMC_MAX_DISTURBANCES)
+        return fail(ctx, FMC_EUNSUPPORTED, "d = %d above %d", s->d, FMC_MAX_DISTURBANCES);
+    if (s->K < 1) return fail(ctx, FMC_EINVAL, "K = %d < 1", s->K);
+    if ((int64_t)s->d * s->K > (1 << 24)) return fail(ctx, FMC_EINVAL, "d*K too large");
+    if (s->N < 1 || s->N > (int64_t(1) << 30)) return fail(ctx, FMC_EINVAL, "N = %lld outside [1, 2^30]", (long long)s->N);
+    if (s->sampling < 0 || s->sampling > 2) return fail(ctx, FMC_EINVAL, "sampling mode %d", s->sampling);
+    if (s->precision < 0 || s->precision > 2) return fail(ctx, FMC_EINVAL, "precision %d", s->precision);
+    if (s->integrator != FMC_RK4 && s->integrator != FMC_HEUN)
+        return fail(ctx, FMC_EINVAL, "integrator %d", s->integrator);
+    if (!s->G || !s->B || !s->H || !s->D || !s->E || !s->Pm || !s->theta || !s->sigma || !s->inject)
+        return fail(ctx, FMC_EINVAL, "a scenario array is NULL");
+    if (s->has_inf_bus && (!s->Ginf || !s->Binf)) return fail(ctx, FMC_EINVAL, "infinite bus arrays are NULL");
+    for (int i = 0; i < s->n; ++i)
+        if (!(s->H[i] > 0.0)) return fail(ctx, FMC_EINVAL, "H[%d] must be > 0", i);
+    if (!(s->omega_s > 0.0)) return fail(ctx, FMC_EINVAL, "omega_s must be > 0");
+    return steps_of(ctx, s->T, s->dt, Nt);
+}
+
+static int nd_bucket_for(int d)
+{
+    static const int buckets[] = {1, 2, 4, 8};
+    for (int b : buckets)
+        if (d <= b) return b;
+    return -1;
+}
+
+template <int NM, int ND>
+static void build_params(const fmc_scenario* s, std::vector<unsigned char>& out)
+{
+    out.assign(sizeof(SwingParams<NM, ND>), 0);
+    SwingParams<NM, ND>& p = *reinterpret_cast<SwingParams<NM, ND>*>(out.data());
+    const int n = s->n, d = s->d;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            p.GE[i][j] = (float)(s->E[i] * s->E[j] * s->G[i * n + j]);
+            p.BE[i][j] = (float)(s->E[i] * s->E[j] * s->B[i * n + j]);
+        }
+        p.GEinf[i] = s->has_inf_bus ? (float)(s->E[i] * s->Vinf * s->Ginf[i]) : 0.f;
+        p.BEinf[i] = s->has_inf_bus ? (float)(s->E[i] * s->Vinf * s->Binf[i]) : 0.f;
+        p.inv2H[i] = (float)(1.0 / (2.0 * s->H[i]));
+        p.D[i] = (float)s->D[i];
+        p.Pm[i] = (float)s->Pm[i];
+        for (int q = 0; q < d; ++q) p.inj[i][q] = (float)s->inject[i * d + q];
+    }
+    for (int q = 0; q < d; ++q) {
+        p.ou_a[q] = (float)(1.0 - s->theta[q] * s->dt);
+        p.ou_s[q] = (float)s->sigma[q];
+    }
+    p.omega_s = (float)s->omega_s;
+    p.dt = (float)s->dt;
+    p.d = d;
+    p.n = n;
+    p.integrator = s->integrator;
+    p.slack = s->has_inf_bus ? 0 : 1;
+}
+
+template <int NM>
+static void build_params_nd(int nd, const fmc_scenario* s, std::vector<unsigned char>& out)
+{
+    switch (nd) {
+        case 1: build_params<NM, 1>(s, out); break;
+        case 2: build_params<NM, 2>(s, out); break;
+        case 4: build_params<NM, 4>(s, out); break;
+        default: build_params<NM, 8>(s, out); break;
+    }
+}
+
+static void build_params_bucket(int nm, int nd, const fmc_scenario* s, std::vector<unsigned char>& out)
+{
+    switch (nm) {
+        case 1: build_params_nd<1>(nd, s, out); break;
+        case 2: build_params_nd<2>(nd, s, out); break;
+        case 4: build_params_nd<4>(nd, s, out); break;
+        case 8: build_params_nd<8>(nd, s, out); break;
+        case 10: build_params_nd<10>(nd, s, out); break;
+        case 12: build_params_nd<12>(nd, s, out); break;
+        default: build_params_nd<16>(nd, s, out); break;
+    }
+}
+
+// Copies the system arrays to the device and launches the FP64 Newton kernel.
+// eq: [delta0 n][pm n][shift 2n]; status: iteration count or -1.
+static int run_equilibrium(fmc_ctx* ctx, const fmc_scenario* s, cudaStream_t st)
+{
+    const int n = s->n;
+    size_t nd = (size_t)2 * n * n + 5 * (size_t)n;
+    int rc = ensure(ctx, ctx->scen, nd * sizeof(double));
+    if (rc) return rc;
+    rc = ensure(ctx, ctx->eq, 4 * (size_t)n * sizeof(double));
+    if (rc) return rc;
+    rc = ensure(ctx, ctx->status, 64);
+    if (rc) return rc;
+    std::vector<double> h(nd, 0.0);
+    double* G = h.data();
+    double* B = G + n * n;
+    double* Gi = B + n * n;
+    double* Bi = Gi + n;
+    double* E = Bi + n;
+    double* Pm = E + n;
+    memcpy(G, s->G, sizeof(double) * n * n);
+    memcpy(B, s->B, sizeof(double) * n * n);
+    if (s->has_inf_bus) {
+        memcpy(Gi, s->Ginf, sizeof(double) * n);
+        memcpy(Bi, s->Binf, sizeof(double) * n);
+    }
+    memcpy(E, s->E, sizeof(double) * n);
+    memcpy(Pm, s->Pm, sizeof(double) * n);
+    double* dG = (double*)ctx->scen.ptr;
+    FMC_CUDA(ctx, cudaMemcpyAsync(dG, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy scenario");
+    ProfRec* pr;
+    prof_begin(ctx, PH_EQ, st, &pr);
+    FMC_CUDA(ctx,
+             launch_equilibrium(n, s->has_inf_bus, s->Vinf, dG, dG + n * n, dG + 2 * n * n, dG + 2 * n * n + n,
+                                dG + 2 * n * n + 2 * n, dG + 2 * n * n + 3 * n, (double*)ctx->eq.ptr,
+                                (int*)ctx->status.ptr, st),
+             "equilibrium kernel");
+    prof_end(pr, st);
+    return FMC_OK;
+}
+
+static int make_map_bf16(fmc_ctx* ctx, CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+                         uint32_t box_inner, uint32_t box_outer)
+{
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return fail(ctx, FMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, FMC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FMC_OK;
+}
+
+// Tensor maps of the split operands: zeta [rows][d*Ks], phi [Nt][Kpad].
+static int make_contract_maps(fmc_ctx* ctx, CUtensorMap maps[4], int64_t rows, int d, int Ks, int Nt, int Kpad, int TN,
+                              int split)
+{
+    int rc = make_map_bf16(ctx, &maps[0], ctx->zeta_hi.ptr, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+    if (rc) return rc;
+    rc = make_map_bf16(ctx, &maps[2], ctx->phi_hi.ptr, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
+    if (rc) return rc;
+    if (split) {
+        rc = make_map_bf16(ctx, &maps[1], ctx->zeta_lo.ptr, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+        if (rc) return rc;
+        rc = make_map_bf16(ctx, &maps[3], ctx->phi_lo.ptr, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
+        if (rc) return rc;
+    } else {
+        maps[1] = maps[0];
+        maps[3] = maps[2];
+    }
+    return FMC_OK;
+}
+
+extern "C" {
+
+int fmc_create(fmc_ctx** out, int device, size_t mem_budget_bytes)
+{
+    if (!out) {
+        g_create_err = "out is NULL";
+        return FMC_EINVAL;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_err = std::string("no CUDA device ") + std::to_string(device) + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        return FMC_ECUDA;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        return FMC_ECUDA;
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        return FMC_ECUDA;
+    }
+    if (prop.major * 10 + prop.minor < 100) {
+        g_create_err = "this library needs a Blackwell GPU (sm_103a)";
+        return FMC_EUNSUPPORTED;
+    }
+    fmc_ctx* c = new fmc_ctx();
+    c->device = device;
+    c->sms = prop.multiProcessorCount;
+    snprintf(c->name, sizeof c->name, "%s", prop.name);
+    c->budget = mem_budget_bytes;
+    *out = c;
+    return FMC_OK;
+}
+
+int fmc_destroy(fmc_ctx* ctx)
+{
+    if (!ctx) return FMC_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    prof_clear(ctx);
+    DevBuf* bufs[] = {&ctx->zeta_hi, &ctx->zeta_lo, &ctx->phi_hi, &ctx->phi_lo, &ctx->phi32, &ctx->dW,
+                      &ctx->traj,    &ctx->part,    &ctx->eq,     &ctx->scen,   &ctx->status, &ctx->zeta32};
+    for (DevBuf* b : bufs)
+        if (b->ptr) cudaFree(b->ptr);
+    delete ctx;
+    return FMC_OK;
+}
+
+const char* fmc_last_error(const fmc_ctx* ctx)
+{
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+int fmc_device_info(const fmc_ctx* ctx, int* sm_count, char* name, size_t name_len)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (sm_count) *sm_count = ctx->sms;
+    if (name && name_len) snprintf(name, name_len, "%s", ctx->name);
+    return FMC_OK;
+}
+
+int fmc_lhs_sample(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int64_t count, int32_t M, int32_t mode,
+                   float* zeta_dev, uint32_t* strata_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (N < 1 || N > (int64_t(1) << 30)) return fail(ctx, FMC_EINVAL, "N = %lld outside [1, 2^30]", (long long)N);
+    if (M < 1) return fail(ctx, FMC_EINVAL, "M = %d < 1", M);
+    if (k0 < 0 || count < 0 || k0 + count > N) return fail(ctx, FMC_EINVAL, "rows [k0, k0+count) outside [0, N)");
+    if (mode < 0 || mode > 2) return fail(ctx, FMC_EINVAL, "mode %d", mode);
+    if (!zeta_dev && !strata_dev) return fail(ctx, FMC_EINVAL, "both outputs are NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfRec* pr;
+    prof_begin(ctx, PH_LHS, st, &pr);
+    FMC_CUDA(ctx, launch_lhs_f32(seed, N, k0, count, M, mode, zeta_dev, strata_dev, ctx->sms, st), "lhs kernel");
+    prof_end(pr, st);
+    return FMC_OK;
+}
+
+int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int64_t count, int32_t d, int32_t K,
+                         int32_t mode, uint16_t* hi_dev, uint16_t* lo_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (N < 1 || N > (int64_t(1) << 30)) return fail(ctx, FMC_EINVAL, "N = %lld outside [1, 2^30]", (long long)N);
+    if (d < 1 || K < 1) return fail(ctx, FMC_EINVAL, "d = %d, K = %d", d, K);
+    if (k0 < 0 || count < 0 || k0 + count > N) return fail(ctx, FMC_EINVAL, "rows [k0, k0+count) outside [0, N)");
+    if (mode < 0 || mode > 2) return fail(ctx, FMC_EINVAL, "mode %d", mode);
+    if (!hi_dev) return fail(ctx, FMC_EINVAL, "hi output is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    FMC_CUDA(ctx, launch_lhs_split(seed, N, k0, count, d, K, mode, hi_dev, lo_dev, ctx->sms, st), "lhs kernel");
+    return FMC_OK;
+}
+
+int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, float* phi_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (K < 1 || Nt < 1 || !(T > 0.0)) return fail(ctx, FMC_EINVAL, "K = %d, Nt = %d, T = %g", K, Nt, T);
+    if (!phi_dev) return fail(ctx, FMC_EINVAL, "phi is NULL");
+    FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, phi_dev, ctx->sms, (cudaStream_t)stream), "basis kernel");
+    return FMC_OK;
+}
+
+int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T, double dt,
+                        int32_t precision, float* dW_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (count < 1 || d < 1 || K < 1) return fail(ctx, FMC_EINVAL, "count, d, K must be >= 1");
+    if (!zeta_dev || !dW_dev) return fail(ctx, FMC_EINVAL, "NULL buffer");
+    int Nt = 0;
+    int rc = steps_of(ctx, T, dt, &Nt);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == FMC_PREC_F32) {
+        rc = ensure(ctx, ctx->phi32, (size_t)K * Nt * sizeof(float));
+        if (rc) return rc;
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, (float*)ctx->phi32.ptr, ctx->sms, st), "basis kernel");
+        FMC_CUDA(ctx, launch_sgemm_nn(count * d, Nt, K, zeta_dev, (const float*)ctx->phi32.ptr, dW_dev, st),
+                 "sgemm kernel");
+        return FMC_OK;
+    }
+    if (precision != FMC_PREC_BF16 && precision != FMC_PREC_BF16X3)
+        return fail(ctx, FMC_EINVAL, "precision %d", precision);
+    if (count > (int64_t(1) << 31) - 256) return fail(ctx, FMC_EINVAL, "count too large for the tensor-core path");
+    const int split = (precision == FMC_PREC_BF16X3);
+    const int Ks = round_up(K, 8);
+    const int Kpad = round_up(K, TC_BK);
+    const int nkb = (Ks + TC_BK - 1) / TC_BK;
+    const int TN = 64;
+    // split zeta [count][d*K] FP32 -> [count][d][Ks] BF16 hi/lo via a tiny conversion on the device
+    size_t zbytes = (size_t)count * d * Ks * 2;
+    if ((rc = ensure(ctx, ctx->zeta_hi, zbytes))) return rc;
+    if ((rc = ensure(ctx, ctx->zeta_lo, zbytes))) return rc;
+    if ((rc = ensure(ctx, ctx->phi_hi, (size_t)Nt * Kpad * 2))) return rc;
+    if ((rc = ensure(ctx, ctx->phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+    if ((rc = ensure(ctx, ctx->status, 64))) return rc;
+    FMC_CUDA(ctx, launch_split_rows(zeta_dev, count, d, K, Ks, ctx->zeta_hi.ptr, ctx->zeta_lo.ptr, st), "split");
+    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, Kpad, ctx->phi_hi.ptr, ctx->phi_lo.ptr, ctx->sms, st), "basis");
+    CUtensorMap maps[4];
+    if ((rc = make_contract_maps(ctx, maps, count, d, Ks, Nt, Kpad, TN, split))) return rc;
+    FMC_CUDA(ctx, cudaMemsetAsync(ctx->status.ptr, 0, 64, st), "memset");
+    FMC_CUDA(ctx, launch_contract_tc(maps, count, d, Ks, nkb, Nt, TN, split, dW_dev, (int*)ctx->status.ptr + 1, st),
+             "tensor-core contraction");
+    return FMC_OK;
+}
+
+int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, double* pm_eq)
+{
+    if (!ctx) return FMC_EINVAL;
+    int Nt;
+    int rc = check_scenario(ctx, scen, &Nt);
+    if (rc) return rc;
+    if (!delta0 || !pm_eq) return fail(ctx, FMC_EINVAL, "NULL output");
+    cudaStream_t st = 0;
+    if ((rc = run_equilibrium(ctx, scen, st))) return rc;
+    const int n = scen->n;
+    std::vector<double> h(2 * n);
+    int status = 0;
+    FMC_CUDA(ctx, cudaMemcpyAsync(h.data(), ctx->eq.ptr, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaMemcpyAsync(&status, ctx->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+    if (status < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    memcpy(delta0, h.data(), n * sizeof(double));
+    memcpy(pm_eq, h.data() + n, n * sizeof(double));
+    return FMC_OK;
+}
+
+int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
+                 float* traj_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    int Nt = 0;
+    int rc = check_scenario(ctx, s, &Nt);
+    if (rc) return rc;
+    if (!mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "mean/var outputs are NULL");
+    if (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) return fail(ctx, FMC_EINVAL, "path %d", path);
+    if (path == FMC_PATH_PLAIN && s->precision != FMC_PREC_F32)
+        return fail(ctx, FMC_EINVAL, "the plain path computes in FP32 (precision FMC_PREC_F32)");
+    if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
+        return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = s->n, d = s->d, K = s->K;
+    const int64_t N = s->N;
+    const int nm = nm_bucket_for(n);
+    const int nd = nd_bucket_for(d);
+    std::vector<unsigned char> params;
+    build_params_bucket(nm, nd, s, params);
+    if ((rc = run_equilibrium(ctx, s, st))) return rc;
+    const double* eq = (const double*)ctx->eq.ptr;
+    const int64_t Nt1 = (int64_t)Nt + 1;
+    const int S = 2 * n;
+
+    if (path == FMC_PATH_PLAIN) {
+        const int M = d * K;
+        if ((rc = ensure(ctx, ctx->zeta32, (size_t)N * M * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ctx->phi32, (size_t)K * Nt * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ctx->dW, (size_t)N * d * Nt * sizeof(float)))) return rc;
+        float* traj = traj_dev;
+        if (!traj) {
+            if ((rc = ensure(ctx, ctx->traj, (size_t)N * Nt1 * S * sizeof(float)))) return rc;
+            traj = (float*)ctx->traj.ptr;
+        }
+        ProfRec* pr;
+        prof_begin(ctx, PH_LHS, st, &pr);
+        FMC_CUDA(ctx, launch_lhs_f32(s->seed, N, 0, N, M, s->sampling, (float*)ctx->zeta32.ptr, nullptr, ctx->sms, st),
+                 "lhs kernel");
+        prof_end(pr, st);
+        prof_begin(ctx, PH_BASIS, st, &pr);
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, (float*)ctx->phi32.ptr, ctx->sms, st), "basis kernel");
+        prof_end(pr, st);
+        prof_begin(ctx, PH_CONTRACT, st, &pr);
+        FMC_CUDA(ctx,
+                 launch_sgemm_nn(N * d, Nt, K, (const float*)ctx->zeta32.ptr, (const float*)ctx->phi32.ptr,
+                                 (float*)ctx->dW.ptr, st),
+                 "sgemm kernel");
+        prof_end(pr, st);
+        prof_begin(ctx, PH_INTEGRATE, st, &pr);
+        FMC_CUDA(ctx, launch_simulate_plain(nm, nd, params.data(), eq, (const float*)ctx->dW.ptr, N, Nt, traj, st),
+                 "plain integrator");
+        prof_end(pr, st);
+        prof_begin(ctx, PH_MOMENTS, st, &pr);
+        FMC_CUDA(ctx, launch_moments(traj, N, Nt1 * S, mean_dev, var_dev, ctx->sms, st), "moments kernel");
+        prof_end(pr, st);
+        return FMC_OK;
+    }
+
+    // fused path
+    const int split = (s->precision == FMC_PREC_BF16X3);
+    const int Ks = round_up(K, 8);
+    const int Kpad = round_up(K, TC_BK);
+    const int nkb = (Ks + TC_BK - 1) / TC_BK;
+    const int TC = (d <= 4) ? 32 : 16;
+    uint32_t tmem_cols = 32;
+    while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
+    const int64_t ntiles = (N + TC_M - 1) / TC_M;
+    size_t zbytes = (size_t)N * d * Ks * 2;
+    if ((rc = ensure(ctx, ctx->zeta_hi, zbytes))) return rc;
+    if (split && (rc = ensure(ctx, ctx->zeta_lo, zbytes))) return rc;
+    if ((rc = ensure(ctx, ctx->phi_hi, (size_t)Nt * Kpad * 2))) return rc;
+    if (split && (rc = ensure(ctx, ctx->phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+    if ((rc = ensure(ctx, ctx->part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
+    if ((rc = ensure(ctx, ctx->status, 64))) return rc;
+    ProfRec* pr;
+    prof_begin(ctx, PH_LHS, st, &pr);
+    FMC_CUDA(ctx,
+             launch_lhs_split(s->seed, N, 0, N, d, K, s->sampling, ctx->zeta_hi.ptr, split ? ctx->zeta_lo.ptr : nullptr,
+                              ctx->sms, st),
+             "lhs kernel");
+    prof_end(pr, st);
+    prof_begin(ctx, PH_BASIS, st, &pr);
+    FMC_CUDA(ctx, launch_basis_split(K, Nt, s->T, Kpad, ctx->phi_hi.ptr, split ? ctx->phi_lo.ptr : nullptr, ctx->sms, st),
+             "basis kernel");
+    prof_end(pr, st);
+    CUtensorMap maps[4];
+    if ((rc = make_contract_maps(ctx, maps, N, d, Ks, Nt, Kpad, TC, split))) return rc;
+    FMC_CUDA(ctx, cudaMemsetAsync((char*)ctx->status.ptr + 4, 0, 4, st), "memset");
+    prof_begin(ctx, PH_FUSED, st, &pr);
+    int occ = 0;
+    cudaError_t e = launch_simulate_fused(nm, nd, params.data(), maps, N, Nt, TC, d, Ks, nkb, split, tmem_cols, eq,
+                                          (float*)ctx->part.ptr, traj_dev, (int*)ctx->status.ptr + 1, st, &occ);
+    ctx->last_fused_ctas_per_sm = occ;
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(ctx, FMC_EUNSUPPORTED, "fused kernel: %d CTAs per SM x %u TMEM columns exceeds 512", occ, tmem_cols);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fused simulation kernel");
+    prof_end(pr, st);
+    prof_begin(ctx, PH_REDUCE, st, &pr);
+    FMC_CUDA(ctx,
+             launch_fused_moments_reduce((const float*)ctx->part.ptr, (int)ntiles, Nt1, S, eq + 2 * n, N, mean_dev,
+                                         var_dev, st),
+             "moment reduce");
+    prof_end(pr, st);
+    return FMC_OK;
+}
+
+int fmc_moments(fmc_ctx* ctx, const float* x_dev, int64_t N, int64_t C, double* mean_dev, double* var_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (N < 1 || C < 1) return fail(ctx, FMC_EINVAL, "N = %lld, C = %lld", (long long)N, (long long)C);
+    if (!x_dev || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "NULL buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProfRec* pr;
+    prof_begin(ctx, PH_MOMENTS, st, &pr);
+    FMC_CUDA(ctx, launch_moments(x_dev, N, C, mean_dev, var_dev, ctx->sms, st), "moments kernel");
+    prof_end(pr, st);
+    return FMC_OK;
+}
+
+// ---- diagnostics -------------------------------------------------------------
+
+int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error)
+{
+    if (!ctx) return FMC_EINVAL;
+    int h[2] = {0, 0};
+    if (!ctx->status.ptr) {
+        if (eq_iterations) *eq_iterations = 0;
+        if (kernel_error) *kernel_error = 0;
+        return FMC_OK;
+    }
+    FMC_CUDA(ctx, cudaDeviceSynchronize(), "sync");
+    FMC_CUDA(ctx, cudaMemcpy(h, ctx->status.ptr, sizeof h, cudaMemcpyDeviceToHost), "copy");
+    if (eq_iterations) *eq_iterations = h[0];
+    if (kernel_error) *kernel_error = h[1];
+    if (h[0] < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    if (h[1] == DEV_TIMEOUT_MMA || h[1] == DEV_TIMEOUT_TMA)
+        return fail(ctx, FMC_ETIMEOUT, "a bounded device wait gave up (code %d)", h[1]);
+    if (h[1] != 0) return fail(ctx, FMC_ECUDA, "device error %d", h[1]);
+    return FMC_OK;
+}
+
+int fmc_profile(fmc_ctx* ctx, int32_t enable, int64_t max_records)
+{
+    if (!ctx) return FMC_EINVAL;
+    cudaDeviceSynchronize();
+    prof_clear(ctx);
+    ctx->prof = enable != 0;
+    ctx->prof_cap = max_records > 0 ? (size_t)max_records : 0;
+    ctx->recs.reserve(ctx->prof_cap);
+    return FMC_OK;
+}
+
+int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* launches)
+{
+    if (!ctx) return FMC_EINVAL;
+    FMC_CUDA(ctx, cudaDeviceSynchronize(), "sync");
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (auto& r : ctx->recs) {
+        if (r.phase != phase) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            tot += ms;
+            ++cnt;
+        }
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = cnt;
+    return FMC_OK;
+}
+
+int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm)
+{
+    if (!ctx || !ctas_per_sm) return FMC_EINVAL;
+    *ctas_per_sm = ctx->last_fused_ctas_per_sm;
+    return FMC_OK;
+}
+
+}  // extern "C"

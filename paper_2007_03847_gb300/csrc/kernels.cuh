@@ -1,0 +1,34 @@
+// Host-side launchers of the fastmc kernels (one translation unit each).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fmc {
+
+cudaError_t launch_lhs_f32(uint64_t seed, int64_t N, int64_t k0, int64_t count, int M, int mode, float* zeta,
+                           uint32_t* strata, int sms, cudaStream_t st);
+cudaError_t launch_lhs_split(uint64_t seed, int64_t N, int64_t k0, int64_t count, int d, int K, int mode, void* hi,
+                             void* lo, int sms, cudaStream_t st);
+cudaError_t launch_basis_f32(int K, int Nt, double T, float* phi, int sms, cudaStream_t st);
+cudaError_t launch_basis_split(int K, int Nt, double T, int Kpad, void* hi, void* lo, int sms, cudaStream_t st);
+cudaError_t launch_sgemm_nn(int64_t R, int Ncols, int K, const float* A, const float* B, float* C, cudaStream_t st);
+cudaError_t launch_contract_tc(const CUtensorMap* maps, int64_t count, int d, int Ks, int nkb, int Nt, int TN,
+                               int split, float* dW, int* err, cudaStream_t st);
+cudaError_t launch_split_rows(const float* z, int64_t count, int d, int K, int Ks, void* hi, void* lo, cudaStream_t st);
+cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G, const double* B, const double* Ginf,
+                               const double* Binf, const double* E, const double* Pm, double* out, int* status,
+                               cudaStream_t st);
+cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
+                                  int64_t count, int Nt, float* traj, cudaStream_t st);
+int fused_smem_bytes(int nm_bucket, int TC, int split);
+cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
+                                  int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
+                                  const double* eq, float* part, float* traj, int* err, cudaStream_t st,
+                                  int* max_ctas_per_sm);
+cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
+cudaError_t launch_fused_moments_reduce(const float* part, int nblk, int64_t Nt1, int S, const double* shift,
+                                        int64_t N, double* mean, double* var, cudaStream_t st);
+
+}  // namespace fmc

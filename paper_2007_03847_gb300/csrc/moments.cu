@@ -1,0 +1,117 @@
+// Algorithm 1 step 4: expectation and unbiased variance over the samples.
+//
+// Values are shifted by a reference c (row 0 of the data, or the undisturbed
+// equilibrium for the fused simulation), summed in FP32 over short runs of rows,
+// and the run sums are combined in FP64:
+//   mean = c + S1/N,  var = (S2 - S1^2/N) / (N - 1),
+//   S1 = sum (x - c),  S2 = sum (x - c)^2.
+// With c near the data the subtraction in var is well conditioned.
+#include "fmc_common.cuh"
+#include "kernels.cuh"
+
+namespace fmc {
+
+constexpr int MOM_THREADS = 256;
+constexpr int MOM_RUN = 32;  // rows summed in FP32 before moving into FP64
+
+// grid.x: column blocks; grid.y: row slabs of `rows_per_slab` rows.
+__global__ void __launch_bounds__(MOM_THREADS) moments_partial_kernel(const float* __restrict__ x, int64_t N, int64_t C,
+                                                                      int64_t rows_per_slab, double* __restrict__ S1,
+                                                                      double* __restrict__ S2)
+{
+    int64_t c = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x;
+    if (c >= C) return;
+    int64_t r0 = (int64_t)blockIdx.y * rows_per_slab;
+    int64_t r1 = r0 + rows_per_slab;
+    if (r1 > N) r1 = N;
+    const float shift = x[c];
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t r = r0; r < r1; r += MOM_RUN) {
+        int64_t re = r + MOM_RUN < r1 ? r + MOM_RUN : r1;
+        float a1 = 0.f, a2 = 0.f;
+        for (int64_t q = r; q < re; ++q) {
+            float v = x[q * C + c] - shift;
+            a1 += v;
+            a2 = fmaf(v, v, a2);
+        }
+        s1 += (double)a1;
+        s2 += (double)a2;
+    }
+    atomicAdd(&S1[c], s1);
+    atomicAdd(&S2[c], s2);
+}
+
+// In place: mean <- shift + S1/N, var <- (S2 - S1^2/N)/(N-1).
+__global__ void moments_finalize_kernel(const float* __restrict__ x, int64_t N, int64_t C, double* __restrict__ mean,
+                                        double* __restrict__ var)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    double s1 = mean[c], s2 = var[c];
+    double n = (double)N;
+    mean[c] = (double)x[c] + s1 / n;
+    var[c] = (N > 1) ? (s2 - s1 * s1 / n) / (n - 1.0) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(mean, 0, sizeof(double) * C, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(var, 0, sizeof(double) * C, st);
+    if (e != cudaSuccess) return e;
+    int64_t gx = (C + MOM_THREADS - 1) / MOM_THREADS;
+    // enough slabs to fill the GPU a few times over, each at least a few runs long
+    int64_t want_blocks = (int64_t)sms * 8;
+    int64_t slabs = (want_blocks + gx - 1) / gx;
+    int64_t max_slabs = (N + 4 * MOM_RUN - 1) / (4 * MOM_RUN);
+    if (slabs > max_slabs) slabs = max_slabs;
+    if (slabs < 1) slabs = 1;
+    if (slabs > 65535) slabs = 65535;
+    int64_t rows = (N + slabs - 1) / slabs;
+    rows = (rows + MOM_RUN - 1) / MOM_RUN * MOM_RUN;
+    slabs = (N + rows - 1) / rows;
+    if (gx > 2147483647LL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)gx, (unsigned)slabs);
+    moments_partial_kernel<<<grid, MOM_THREADS, 0, st>>>(x, N, C, rows, mean, var);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    moments_finalize_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(x, N, C, mean, var);
+    return cudaGetLastError();
+}
+
+// Fused-simulation partials: part [nblk][Nt1][2*S] floats holding, per block of
+// samples and per grid time, the FP32 sums (S1 for states 0..S-1, then S2 for
+// states 0..S-1) of values shifted by shift[s].  Combined over blocks in FP64
+// in a fixed order, so the result does not depend on scheduling.
+__global__ void fused_moments_reduce_kernel(const float* __restrict__ part, int nblk, int64_t Nt1, int S,
+                                            const double* __restrict__ shift, int64_t N, double* __restrict__ mean,
+                                            double* __restrict__ var)
+{
+    int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // col = n * S + s
+    if (col >= Nt1 * S) return;
+    int64_t n = col / S;
+    int s = (int)(col - n * S);
+    const int64_t row = 2 * (int64_t)S;
+    const int64_t stride = Nt1 * row;
+    const float* p = part + n * row + s;
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        s1 += (double)p[(int64_t)b * stride];
+        s2 += (double)p[(int64_t)b * stride + S];
+    }
+    double nn = (double)N;
+    // the kernel shifted by the FP32 rounding of the shift; add back the same value
+    mean[col] = (double)(float)shift[s] + s1 / nn;
+    var[col] = (N > 1) ? (s2 - s1 * s1 / nn) / (nn - 1.0) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+cudaError_t launch_fused_moments_reduce(const float* part, int nblk, int64_t Nt1, int S, const double* shift,
+                                        int64_t N, double* mean, double* var, cudaStream_t st)
+{
+    int64_t cols = Nt1 * S;
+    fused_moments_reduce_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, nblk, Nt1, S, shift, N, mean,
+                                                                                var);
+    return cudaGetLastError();
+}
+
+}  // namespace fmc

@@ -1,0 +1,71 @@
+// Dispatch of the simulation kernels over the (machine, disturbance) slot
+// buckets they are instantiated for, and the shared-memory plan of the fused
+// kernel.
+#include "simulate_fused.cuh"
+
+namespace fmc {
+
+cudaError_t launch_fused_nm1(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm1(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm2(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm2(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm4(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm4(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm8(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm8(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm10(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm10(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm12(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+cudaError_t launch_fused_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
+cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
+
+int fused_smem_bytes(int nm_bucket, int TC, int split)
+{
+    const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
+    const int ring = 2 * stage;
+    const int mom = (4 * 32 * (2 * nm_bucket + 1) + FU_MS * 4 * 4 * nm_bucket) * 4;
+    int need = (ring > mom ? ring : mom) + 1024;
+    // at most four CTAs per SM (233472 bytes of shared memory per SM, 1 KB
+    // reserved per CTA): each CTA then owns a quarter of the 512 TMEM columns
+    const int floor4 = 233472 / 5 - 1024 + 64;
+    return need > floor4 ? need : floor4;
+}
+
+cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
+                                  int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
+                                  const double* eq, float* part, float* traj, int* err, cudaStream_t st,
+                                  int* max_ctas_per_sm)
+{
+    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, tmem_cols, eq, part, traj, err};
+    const int smem = fused_smem_bytes(nm_bucket, TC, split);
+    const int64_t ntiles = (count + TC_M - 1) / TC_M;
+    if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
+    switch (nm_bucket) {
+        case 1: return launch_fused_nm1(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 2: return launch_fused_nm2(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 4: return launch_fused_nm4(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 8: return launch_fused_nm8(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 10: return launch_fused_nm10(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 12: return launch_fused_nm12(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        case 16: return launch_fused_nm16(nd_bucket, params, maps, a, smem, (int)ntiles, st, max_ctas_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
+                                  int64_t count, int Nt, float* traj, cudaStream_t st)
+{
+    switch (nm_bucket) {
+        case 1: return launch_plain_nm1(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 2: return launch_plain_nm2(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 4: return launch_plain_nm4(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 8: return launch_plain_nm8(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 10: return launch_plain_nm10(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 12: return launch_plain_nm12(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        case 16: return launch_plain_nm16(nd_bucket, params, eq, dW, count, Nt, traj, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fmc

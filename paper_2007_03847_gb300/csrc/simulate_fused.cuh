@@ -1,0 +1,234 @@
+// Algorithm 1 steps 2-4 fused on one SM-resident CTA per 128 samples:
+//
+//   for each time chunk of TC steps:
+//     tensor cores:  dW[128 x TC] per disturbance = Z_tile . Phi_chunk^T into TMEM
+//                    (BF16 or split BF16x3 operands streamed by TMA, FP32 accumulate)
+//     FP32 pipes:    thread r (= sample r of the tile, = TMEM lane r) reads its
+//                    increments with tcgen05.ld, advances the OU disturbances by
+//                    Euler-Maruyama and the swing equations by RK4/Heun, step by step
+//     moments:       per step, each warp transposes its 32 samples' shifted states
+//                    through shared memory and sums them (S1, S2) per state; the
+//                    four warps' sums are added in a fixed order and written as
+//                    FP32 partials [tile][t][S1 | S2]
+//
+// Trajectories never go to HBM (unless a debug buffer is given).  A separate
+// kernel combines the per-tile partials in FP64 in a fixed order.
+#pragma once
+
+#include "fmc_common.cuh"
+#include "kernels.cuh"
+#include "swing.cuh"
+#include "tc_common.cuh"
+
+namespace fmc {
+
+constexpr int FU_THREADS = 128;
+constexpr int FU_MS = 8;  // steps between flushes of the moment buffer
+
+struct FusedArgs {
+    int64_t count;
+    int Nt, TC, d, Ks, nkb, split;
+    uint32_t tmem_cols;
+    const double* eq;   // [delta0 n][pm n][shift 2n]
+    float* part;        // [ntiles][Nt+1][4n]
+    float* traj;        // [count][Nt+1][2n] or nullptr
+    int* err;
+};
+
+template <int NM, int ND>
+__global__ void __launch_bounds__(FU_THREADS, 4)
+    simulate_fused_kernel(const __grid_constant__ SwingParams<NM, ND> p, const __grid_constant__ CUtensorMap mAh,
+                          const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBh,
+                          const __grid_constant__ CUtensorMap mBl, FusedArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t bars[5];  // full[2], freed[2], done
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ float s_shift[NM];
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int n = p.n, d = p.d, S = 2 * n, S4 = 4 * n;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int64_t srow = row0 + tid;
+    const bool active = srow < a.count;
+    const int TC = a.TC;
+
+    // ring (used only while the tensor cores fill TMEM) aliases the moment buffers
+    TcRing r;
+    r.a_bytes = TC_M * 64;
+    r.b_bytes = TC * 64;
+    r.split = a.split;
+    const uint32_t stage_bytes = (r.a_bytes + r.b_bytes) * (a.split ? 2 : 1);
+    r.stage[0] = smem;
+    r.stage[1] = smem + stage_bytes;
+    r.full = &bars[0];
+    r.freed = &bars[2];
+    const int WROW = 2 * NM + 1;
+    float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;           // [32][WROW] per warp
+    float* msum = reinterpret_cast<float*>(smem) + 4 * 32 * WROW;              // [FU_MS][4][4*NM]
+
+    if (tid == 0) {
+        prefetch_tmap(&mAh);
+        prefetch_tmap(&mBh);
+        for (int b = 0; b < 5; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+
+    float del[NM], w[NM];
+    float x0[ND];
+    const float pm0 = p.slack ? (float)a.eq[n] : 0.f;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        del[i] = (i < n) ? (float)a.eq[i] : 0.f;
+        w[i] = 0.f;
+    }
+    if (tid < NM) s_shift[tid] = (tid < n) ? (float)a.eq[tid] : 0.f;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) x0[q] = 0.f;
+
+    const int64_t trow = 2 * (int64_t)n;
+    float* traj = (a.traj != nullptr && active) ? a.traj + srow * (int64_t)(a.Nt + 1) * trow : nullptr;
+    if (traj) {
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+            if (i < n) {
+                traj[i] = del[i];
+                traj[n + i] = w[i];
+            }
+    }
+    // time 0: every sample sits at the (rounded) shift, so both sums are zero
+    float* part_tile = a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4;
+    for (int v = tid; v < S4; v += FU_THREADS) part_tile[v] = 0.f;
+
+    const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
+    uint32_t g = 0;  // K blocks issued so far (thread 0)
+    const int J = d * a.nkb;
+
+    for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
+        // ---- tensor cores: dW of this chunk into TMEM ----
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            bool ok = ring_load(r, g, &mAh, &mAl, &mBh, &mBl, 0, (int)row0, 0, n0);
+            for (int j = 0; j < J && ok; ++j) {
+                if (j + 1 < J) {
+                    const int w1 = (j + 1) / a.nkb, kb1 = (j + 1) % a.nkb;
+                    ok = ring_load(r, g + j + 1, &mAh, &mAl, &mBh, &mBl, w1 * a.Ks + kb1 * TC_BK, (int)row0,
+                                   kb1 * TC_BK, n0);
+                }
+                const int wj = j / a.nkb, kbj = j % a.nkb;
+                if (ok) ok = ring_mma(r, g + j, tmem + (uint32_t)(wj * TC), idesc, kbj == 0);
+            }
+            g += (uint32_t)J;
+            if (ok) {
+                umma_commit(&bars[4]);
+            } else {
+                abort_flag = 1;
+                atomicExch(a.err, DEV_TIMEOUT_TMA);
+            }
+        }
+        __syncthreads();
+        bool ok = (abort_flag == 0);
+        if (ok && !mbar_wait(&bars[4], (uint32_t)c & 1u)) {
+            ok = false;
+            atomicExch(a.err, DEV_TIMEOUT_MMA);
+        }
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+
+        // ---- FP32 pipes: integrate this chunk ----
+        const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
+        for (int s = 0; s < steps; ++s) {
+            float dw[ND], x1[ND];
+#pragma unroll
+            for (int q = 0; q < ND; ++q) dw[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < ND; ++q)
+                if (q < d) dw[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
+            tmem_ld_wait();
+            ou_step<NM, ND>(p, x0, dw, x1);
+            swing_step<NM, ND>(p, pm0, del, w, x0, x1);
+#pragma unroll
+            for (int q = 0; q < ND; ++q) x0[q] = x1[q];
+
+            const int tn = n0 + s + 1;  // grid index of the new state
+            if (traj) {
+                float* o = traj + (int64_t)tn * trow;
+#pragma unroll
+                for (int i = 0; i < NM; ++i)
+                    if (i < n) {
+                        o[i] = del[i];
+                        o[n + i] = w[i];
+                    }
+            }
+            // ---- moments: transpose the warp's states and sum per state ----
+            float* myrow = wbuf + lane * WROW;
+#pragma unroll
+            for (int i = 0; i < NM; ++i)
+                if (i < n) {
+                    myrow[i] = active ? del[i] - s_shift[i] : 0.f;
+                    myrow[n + i] = active ? w[i] : 0.f;
+                }
+            __syncwarp();
+            const int ms = s % FU_MS;
+            if (lane < S) {
+                float s1 = 0.f, s2 = 0.f;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    float v = wbuf[rr * WROW + lane];
+                    s1 += v;
+                    s2 = fmaf(v, v, s2);
+                }
+                msum[(ms * 4 + warp) * (4 * NM) + lane] = s1;
+                msum[(ms * 4 + warp) * (4 * NM) + S + lane] = s2;
+            }
+            __syncwarp();
+            if (ms == FU_MS - 1 || s == steps - 1) {
+                asm volatile("bar.sync 1, %0;" ::"r"(FU_THREADS) : "memory");
+                const int nst = ms + 1;
+                const int tn0 = tn - ms;
+                for (int e = tid; e < nst * S4; e += FU_THREADS) {
+                    const int sl = e / S4, v = e - sl * S4;
+                    const float* m = msum + sl * 4 * (4 * NM) + v;
+                    float acc = ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM];
+                    part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(FU_THREADS) : "memory");
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+template <int NM, int ND>
+cudaError_t launch_fused_t(const void* params, const CUtensorMap* maps, const FusedArgs& a, int smem, int ntiles,
+                           cudaStream_t st, int* max_ctas_per_sm)
+{
+    const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
+    auto kern = simulate_fused_kernel<NM, ND>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, FU_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    *max_ctas_per_sm = occ;
+    // every resident CTA holds tmem_cols TMEM columns; 512 per SM
+    if (occ < 1 || (uint32_t)occ * a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
+    kern<<<ntiles, FU_THREADS, smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], a);
+    return cudaGetLastError();
+}
+
+}  // namespace fmc

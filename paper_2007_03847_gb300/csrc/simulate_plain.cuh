@@ -1,0 +1,68 @@
+// Algorithm 1 step 3, plain FP32 form: one thread per sample integrates the OU
+// disturbances (Euler-Maruyama, Eq. distito) and the swing equations (RK4 or
+// Heun) from increments dW [count][d][Nt] already in HBM, and writes the whole
+// trajectory traj [count][Nt+1][2n] back to HBM for a separate moment pass.
+#pragma once
+
+#include "fmc_common.cuh"
+#include "kernels.cuh"
+#include "swing.cuh"
+
+namespace fmc {
+
+template <int NM, int ND>
+__global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_constant__ SwingParams<NM, ND> p,
+                                                             const double* __restrict__ eq, const float* __restrict__ dW,
+                                                             int64_t count, int Nt, float* __restrict__ traj)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count) return;
+    const int n = p.n;
+    const int d = p.d;
+    float del[NM], w[NM];
+    float x0[ND], x1[ND], dw[ND];
+    const float pm0 = p.slack ? (float)eq[n] : 0.f;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        del[i] = (i < n) ? (float)eq[i] : 0.f;
+        w[i] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < ND; ++q) x0[q] = 0.f;
+    const int64_t row = 2 * (int64_t)n;
+    float* out = traj + s * (int64_t)(Nt + 1) * row;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+        if (i < n) {
+            out[i] = del[i];
+            out[n + i] = w[i];
+        }
+    const float* dws = dW + s * (int64_t)d * Nt;
+    for (int step = 0; step < Nt; ++step) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) dw[q] = (q < d) ? __ldg(dws + (int64_t)q * Nt + step) : 0.f;
+        ou_step<NM, ND>(p, x0, dw, x1);
+        swing_step<NM, ND>(p, pm0, del, w, x0, x1);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) x0[q] = x1[q];
+        float* o = out + (int64_t)(step + 1) * row;
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+            if (i < n) {
+                o[i] = del[i];
+                o[n + i] = w[i];
+            }
+    }
+}
+
+template <int NM, int ND>
+cudaError_t launch_plain_t(const void* params, const double* eq, const float* dW, int64_t count, int Nt, float* traj,
+                           cudaStream_t st)
+{
+    const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
+    int64_t g = (count + 127) / 128;
+    simulate_plain_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, eq, dW, count, Nt, traj);
+    return cudaGetLastError();
+}
+
+}  // namespace fmc
