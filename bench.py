@@ -48,13 +48,14 @@ def parse():
     ap.add_argument("--path", default="fused", choices=["fused", "plain"])
     ap.add_argument("--precision", default=None, choices=[None, "bf16x3", "bf16", "f32"])
     ap.add_argument("--samples", type=int, default=1 << 16)
+    ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(samples: int):
-    return fs.multimachine_case(n=10, d=3, K=200, T=20.0, dt=0.005, N=samples, seed=0)
+def workload(samples: int, horizon: float = 20.0):
+    return fs.multimachine_case(n=10, d=3, K=200, T=horizon, dt=0.005, N=samples, seed=0)
 
 
 def algorithmic_flops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
@@ -157,7 +158,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    sc = workload(args.samples)
+    sc = workload(args.samples, args.horizon)
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -213,7 +214,7 @@ def main():
     sms, gpu_name = ctx.info()
     path = args.path
     precision = args.precision or ("f32" if path == "plain" else "bf16x3")
-    sc = workload(args.samples)
+    sc = workload(args.samples, args.horizon)
     n, Nt = sc.n, sc.Nt
     units_per_step = sc.N * Nt * n
 

@@ -216,6 +216,9 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
  *             testing; N*(Nt+1)*2n*4 bytes)
  *   path      FMC_PATH_FUSED or FMC_PATH_PLAIN (FMC_PATH_PLAIN needs
  *             precision FMC_PREC_F32; FMC_PATH_FUSED needs BF16 or BF16X3)
+ * The FP64 equilibrium is solved on the GPU first; the call then waits for the
+ * stream once (to read the equilibrium angles, from which the integrator's
+ * constants are formed) and enqueues the rest without waiting.
  * Errors: FMC_EINVAL, FMC_EUNSUPPORTED (n or d above this build's limits),
  * FMC_ENOMEM, FMC_ENOCONVERGE, FMC_ETIMEOUT (a bounded device wait gave up),
  * FMC_ECUDA.
@@ -223,7 +226,29 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
 int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
                  float* traj_dev, void* stream);
 
+/*
+ * The same path for the block of samples k0 .. k0+count-1 of the N-sample
+ * design (so that blocks on different GPUs form one design), returning the
+ * per-time sums of shifted states instead of moments:
+ *   S1_dev, S2_dev [Nt+1][2n] double: sum (x - c), sum (x - c)^2 over the block,
+ *   shift_dev [2n] double: c (the equilibrium angles, then zeros; the sums use
+ *   its FP32 rounding).  Sums of blocks add; fmc_moments_from_sums finishes.
+ * Errors as fmc_simulate; FMC_EINVAL if the block is outside [0, N).
+ */
+int fmc_simulate_sums(fmc_ctx* ctx, const fmc_scenario* scen, int64_t k0, int64_t count, int32_t path,
+                      double* S1_dev, double* S2_dev, double* shift_dev, float* traj_dev, void* stream);
+
 /* ---- Algorithm 1 step 4 --------------------------------------------------- */
+
+/*
+ * Moments from shifted sums over N samples (see fmc_simulate_sums):
+ *   mean = c + S1/N, var = (S2 - S1^2/N)/(N - 1) (NaN for N = 1), c = FP32(shift).
+ *   S1_dev, S2_dev, mean_dev, var_dev [rows][S] double; shift_dev [S] double.
+ * mean_dev/var_dev may alias S1_dev/S2_dev.
+ */
+int fmc_moments_from_sums(fmc_ctx* ctx, const double* S1_dev, const double* S2_dev, const double* shift_dev,
+                          int64_t N, int64_t rows, int32_t S, double* mean_dev, double* var_dev, void* stream);
+
 
 /*
  * Column-wise mean and unbiased variance of x[N][C] over its N rows, combined
@@ -255,6 +280,14 @@ int fmc_profile(fmc_ctx* ctx, int32_t enable, int64_t max_records);
 
 /* Synchronises, then sums the recorded durations of one phase. */
 int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* launches);
+
+/*
+ * Test hook (no counterpart in the paper): evaluates the integrator's own
+ * sin/cos (Cody-Waite reduction + Taylor series, FP32) and CUDA's sincosf on
+ * x_dev[n], writing s_dev, c_dev and s_ref_dev, c_ref_dev (device, float[n]).
+ */
+int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, float* c_dev, float* s_ref_dev,
+                    float* c_ref_dev, void* stream);
 
 /* CTAs per SM the last fused launch could keep resident (occupancy API). */
 int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);

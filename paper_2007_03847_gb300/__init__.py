@@ -90,6 +90,9 @@ def load_library():
             "fmc_profile": ([vp, i32, i64], ctypes.c_int),
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_moments_from_sums": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -196,7 +199,7 @@ def lhs_sample(seed: int, N: int, M: int, mode: int = LHS, k0: int = 0, count: i
     import torch
     ctx = ctx or default_context()
     count = N - k0 if count is None else count
-    if zeta is None and strata is None:
+    if zeta is None:
         zeta = torch.empty((count, M), dtype=torch.float32, device="cuda")
     ctx.check(ctx.lib.fmc_lhs_sample(ctx.h, seed, N, k0, count, M, mode, _ptr(zeta), _ptr(strata), _stream(stream)))
     return zeta, strata
@@ -276,6 +279,37 @@ def simulate(scenario, path="fused", precision=None, sampling=None, integrator=N
     return (mean, var, traj) if (want_traj or traj is not None) else (mean, var)
 
 
+def simulate_sums(scenario, k0: int, count: int, path="fused", precision=None, sampling=None, integrator=None,
+                  traj=None, ctx: Context | None = None, stream=None):
+    """Samples k0..k0+count-1 of the design -> (S1, S2, shift) device float64 tensors:
+    S1, S2 [Nt+1, 2n] shifted sums, shift [2n]."""
+    import torch
+    ctx = ctx or default_context()
+    p = _PATH.get(path, path) if isinstance(path, str) else path
+    if precision is None:
+        precision = "f32" if p == PATH_PLAIN else "bf16x3"
+    ss = ScenarioStruct(scenario, precision=precision, sampling=sampling, integrator=integrator)
+    Nt1, S = ss.Nt + 1, 2 * scenario.n
+    S1 = torch.empty((Nt1, S), dtype=torch.float64, device="cuda")
+    S2 = torch.empty_like(S1)
+    shift = torch.empty(S, dtype=torch.float64, device="cuda")
+    ctx.check(ctx.lib.fmc_simulate_sums(ctx.h, ctypes.byref(ss.s), k0, count, p, _ptr(S1), _ptr(S2), _ptr(shift),
+                                        _ptr(traj), _stream(stream)))
+    return S1, S2, shift
+
+
+def moments_from_sums(S1, S2, shift, N: int, mean=None, var=None, ctx: Context | None = None, stream=None):
+    """mean, var [rows, S] float64 from shifted sums over N samples."""
+    import torch
+    ctx = ctx or default_context()
+    rows, S = S1.shape
+    mean = torch.empty_like(S1) if mean is None else mean
+    var = torch.empty_like(S1) if var is None else var
+    ctx.check(ctx.lib.fmc_moments_from_sums(ctx.h, _ptr(S1), _ptr(S2), _ptr(shift), N, rows, S, _ptr(mean),
+                                            _ptr(var), _stream(stream)))
+    return mean, var
+
+
 def moments(x, mean=None, var=None, ctx: Context | None = None, stream=None):
     """Algorithm 1 step 4: column mean and unbiased variance of x [N, C] float32 -> float64 [C]."""
     import torch
@@ -309,6 +343,15 @@ def profile_read(phase: int, ctx: Context | None = None):
     ms, cnt = ctypes.c_double(), ctypes.c_int64()
     ctx.check(ctx.lib.fmc_profile_read(ctx.h, phase, ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def test_sincos(x, ctx: Context | None = None, stream=None):
+    """The integrator's sin/cos and CUDA's sincosf on x (float32 device tensor)."""
+    import torch
+    ctx = ctx or default_context()
+    outs = [torch.empty_like(x) for _ in range(4)]
+    ctx.check(ctx.lib.fmc_test_sincos(ctx.h, _ptr(x), x.numel(), *[_ptr(o) for o in outs], _stream(stream)))
+    return outs
 
 
 def fused_occupancy(ctx: Context | None = None) -> int:

@@ -202,22 +202,45 @@ static int nd_bucket_for(int d)
     return -1;
 }
 
+// Integrator constants in deviation form (see swing_step): the network matrices
+// without their diagonal, and cos, sin of the equilibrium angles in the frame of
+// the integration (relative to machine 0 without an infinite bus) with the
+// off-diagonal sums u*, v* of the product form, all from the FP64 equilibrium.
 template <int NM, int ND>
-static void build_params(const fmc_scenario* s, std::vector<unsigned char>& out)
+static void build_params(const fmc_scenario* s, const double* delta0, std::vector<unsigned char>& out)
 {
     out.assign(sizeof(SwingParams<NM, ND>), 0);
     SwingParams<NM, ND>& p = *reinterpret_cast<SwingParams<NM, ND>*>(out.data());
     const int n = s->n, d = s->d;
+    const bool rel = !s->has_inf_bus;
+    std::vector<double> c(n), sn(n);
+    for (int j = 0; j < n; ++j) {
+        double a = rel ? delta0[j] - delta0[0] : delta0[j];
+        c[j] = std::cos(a);
+        sn[j] = std::sin(a);
+    }
     for (int i = 0; i < n; ++i) {
+        double u = 0.0, v = 0.0;
         for (int j = 0; j < n; ++j) {
-            p.GE[i][j] = (float)(s->E[i] * s->E[j] * s->G[i * n + j]);
-            p.BE[i][j] = (float)(s->E[i] * s->E[j] * s->B[i * n + j]);
+            if (j == i) continue;
+            double ge = s->E[i] * s->E[j] * s->G[i * n + j];
+            double be = s->E[i] * s->E[j] * s->B[i * n + j];
+            p.GE[i][j] = (float)ge;
+            p.BE[i][j] = (float)be;
+            u += ge * c[j] - be * sn[j];
+            v += ge * sn[j] + be * c[j];
         }
-        p.GEinf[i] = s->has_inf_bus ? (float)(s->E[i] * s->Vinf * s->Ginf[i]) : 0.f;
-        p.BEinf[i] = s->has_inf_bus ? (float)(s->E[i] * s->Vinf * s->Binf[i]) : 0.f;
+        if (s->has_inf_bus) {
+            u += s->E[i] * s->Vinf * s->Ginf[i];
+            v += s->E[i] * s->Vinf * s->Binf[i];
+        }
+        p.cst[i] = (float)c[i];
+        p.sst[i] = (float)sn[i];
+        p.ust[i] = (float)u;
+        p.vst[i] = (float)v;
+        p.dst[i] = (float)delta0[i];
         p.inv2H[i] = (float)(1.0 / (2.0 * s->H[i]));
         p.D[i] = (float)s->D[i];
-        p.Pm[i] = (float)s->Pm[i];
         for (int q = 0; q < d; ++q) p.inj[i][q] = (float)s->inject[i * d + q];
     }
     for (int q = 0; q < d; ++q) {
@@ -229,30 +252,31 @@ static void build_params(const fmc_scenario* s, std::vector<unsigned char>& out)
     p.d = d;
     p.n = n;
     p.integrator = s->integrator;
-    p.slack = s->has_inf_bus ? 0 : 1;
+    p.rel = rel ? 1 : 0;
 }
 
 template <int NM>
-static void build_params_nd(int nd, const fmc_scenario* s, std::vector<unsigned char>& out)
+static void build_params_nd(int nd, const fmc_scenario* s, const double* delta0, std::vector<unsigned char>& out)
 {
     switch (nd) {
-        case 1: build_params<NM, 1>(s, out); break;
-        case 2: build_params<NM, 2>(s, out); break;
-        case 4: build_params<NM, 4>(s, out); break;
-        default: build_params<NM, 8>(s, out); break;
+        case 1: build_params<NM, 1>(s, delta0, out); break;
+        case 2: build_params<NM, 2>(s, delta0, out); break;
+        case 4: build_params<NM, 4>(s, delta0, out); break;
+        default: build_params<NM, 8>(s, delta0, out); break;
     }
 }
 
-static void build_params_bucket(int nm, int nd, const fmc_scenario* s, std::vector<unsigned char>& out)
+static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const double* delta0,
+                                std::vector<unsigned char>& out)
 {
     switch (nm) {
-        case 1: build_params_nd<1>(nd, s, out); break;
-        case 2: build_params_nd<2>(nd, s, out); break;
-        case 4: build_params_nd<4>(nd, s, out); break;
-        case 8: build_params_nd<8>(nd, s, out); break;
-        case 10: build_params_nd<10>(nd, s, out); break;
-        case 12: build_params_nd<12>(nd, s, out); break;
-        default: build_params_nd<16>(nd, s, out); break;
+        case 1: build_params_nd<1>(nd, s, delta0, out); break;
+        case 2: build_params_nd<2>(nd, s, delta0, out); break;
+        case 4: build_params_nd<4>(nd, s, delta0, out); break;
+        case 8: build_params_nd<8>(nd, s, delta0, out); break;
+        case 10: build_params_nd<10>(nd, s, delta0, out); break;
+        case 12: build_params_nd<12>(nd, s, delta0, out); break;
+        default: build_params_nd<16>(nd, s, delta0, out); break;
     }
 }
 
@@ -504,44 +528,58 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
     return FMC_OK;
 }
 
-int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
-                 float* traj_dev, void* stream)
+// Samples k0 .. k0+count-1 of the N-sample design: equilibrium, LHS, KL
+// increments, integration and per-time shifted sums S1, S2 [Nt+1][2n] (FP64).
+// The shift (FP64 [2n]: delta*, then zeros) is left at ctx->eq + 2n.
+static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1,
+                         double* S2, float* traj_dev, cudaStream_t st)
 {
-    if (!ctx) return FMC_EINVAL;
     int Nt = 0;
     int rc = check_scenario(ctx, s, &Nt);
     if (rc) return rc;
-    if (!mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "mean/var outputs are NULL");
+    if (!S1 || !S2) return fail(ctx, FMC_EINVAL, "moment outputs are NULL");
+    if (k0 < 0 || count < 1 || k0 + count > s->N)
+        return fail(ctx, FMC_EINVAL, "sample block [%lld, %lld) outside [0, N)", (long long)k0,
+                    (long long)(k0 + count));
     if (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) return fail(ctx, FMC_EINVAL, "path %d", path);
     if (path == FMC_PATH_PLAIN && s->precision != FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the plain path computes in FP32 (precision FMC_PREC_F32)");
     if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
-    cudaStream_t st = (cudaStream_t)stream;
     const int n = s->n, d = s->d, K = s->K;
     const int64_t N = s->N;
     const int nm = nm_bucket_for(n);
     const int nd = nd_bucket_for(d);
-    std::vector<unsigned char> params;
-    build_params_bucket(nm, nd, s, params);
+    // FP64 Newton on the GPU; its angles come back to the host (one stream
+    // synchronisation) to form the integrator's constants in the parameter block
     if ((rc = run_equilibrium(ctx, s, st))) return rc;
     const double* eq = (const double*)ctx->eq.ptr;
+    std::vector<double> delta0(n);
+    int eq_status = 0;
+    FMC_CUDA(ctx, cudaMemcpyAsync(delta0.data(), eq, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaMemcpyAsync(&eq_status, ctx->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+    if (eq_status < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    std::vector<unsigned char> params;
+    build_params_bucket(nm, nd, s, delta0.data(), params);
     const int64_t Nt1 = (int64_t)Nt + 1;
     const int S = 2 * n;
+    const double* shift = eq + 2 * n;
+    ProfRec* pr;
 
     if (path == FMC_PATH_PLAIN) {
         const int M = d * K;
-        if ((rc = ensure(ctx, ctx->zeta32, (size_t)N * M * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ctx->zeta32, (size_t)count * M * sizeof(float)))) return rc;
         if ((rc = ensure(ctx, ctx->phi32, (size_t)K * Nt * sizeof(float)))) return rc;
-        if ((rc = ensure(ctx, ctx->dW, (size_t)N * d * Nt * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ctx->dW, (size_t)count * d * Nt * sizeof(float)))) return rc;
         float* traj = traj_dev;
         if (!traj) {
-            if ((rc = ensure(ctx, ctx->traj, (size_t)N * Nt1 * S * sizeof(float)))) return rc;
+            if ((rc = ensure(ctx, ctx->traj, (size_t)count * Nt1 * S * sizeof(float)))) return rc;
             traj = (float*)ctx->traj.ptr;
         }
-        ProfRec* pr;
         prof_begin(ctx, PH_LHS, st, &pr);
-        FMC_CUDA(ctx, launch_lhs_f32(s->seed, N, 0, N, M, s->sampling, (float*)ctx->zeta32.ptr, nullptr, ctx->sms, st),
+        FMC_CUDA(ctx,
+                 launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ctx->zeta32.ptr, nullptr, ctx->sms, st),
                  "lhs kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_BASIS, st, &pr);
@@ -549,16 +587,16 @@ int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean
         prof_end(pr, st);
         prof_begin(ctx, PH_CONTRACT, st, &pr);
         FMC_CUDA(ctx,
-                 launch_sgemm_nn(N * d, Nt, K, (const float*)ctx->zeta32.ptr, (const float*)ctx->phi32.ptr,
+                 launch_sgemm_nn(count * d, Nt, K, (const float*)ctx->zeta32.ptr, (const float*)ctx->phi32.ptr,
                                  (float*)ctx->dW.ptr, st),
                  "sgemm kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_INTEGRATE, st, &pr);
-        FMC_CUDA(ctx, launch_simulate_plain(nm, nd, params.data(), eq, (const float*)ctx->dW.ptr, N, Nt, traj, st),
+        FMC_CUDA(ctx, launch_simulate_plain(nm, nd, params.data(), eq, (const float*)ctx->dW.ptr, count, Nt, traj, st),
                  "plain integrator");
         prof_end(pr, st);
         prof_begin(ctx, PH_MOMENTS, st, &pr);
-        FMC_CUDA(ctx, launch_moments(traj, N, Nt1 * S, mean_dev, var_dev, ctx->sms, st), "moments kernel");
+        FMC_CUDA(ctx, launch_traj_sums(traj, count, Nt1 * S, shift, S, S1, S2, ctx->sms, st), "moments kernel");
         prof_end(pr, st);
         return FMC_OK;
     }
@@ -571,43 +609,87 @@ int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean
     const int TC = (d <= 4) ? 32 : 16;
     uint32_t tmem_cols = 32;
     while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
-    const int64_t ntiles = (N + TC_M - 1) / TC_M;
-    size_t zbytes = (size_t)N * d * Ks * 2;
+    const int64_t ntiles = (count + TC_M - 1) / TC_M;
+    size_t zbytes = (size_t)count * d * Ks * 2;
     if ((rc = ensure(ctx, ctx->zeta_hi, zbytes))) return rc;
     if (split && (rc = ensure(ctx, ctx->zeta_lo, zbytes))) return rc;
     if ((rc = ensure(ctx, ctx->phi_hi, (size_t)Nt * Kpad * 2))) return rc;
     if (split && (rc = ensure(ctx, ctx->phi_lo, (size_t)Nt * Kpad * 2))) return rc;
     if ((rc = ensure(ctx, ctx->part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
-    if ((rc = ensure(ctx, ctx->status, 64))) return rc;
-    ProfRec* pr;
     prof_begin(ctx, PH_LHS, st, &pr);
     FMC_CUDA(ctx,
-             launch_lhs_split(s->seed, N, 0, N, d, K, s->sampling, ctx->zeta_hi.ptr, split ? ctx->zeta_lo.ptr : nullptr,
-                              ctx->sms, st),
+             launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ctx->zeta_hi.ptr,
+                              split ? ctx->zeta_lo.ptr : nullptr, ctx->sms, st),
              "lhs kernel");
     prof_end(pr, st);
     prof_begin(ctx, PH_BASIS, st, &pr);
-    FMC_CUDA(ctx, launch_basis_split(K, Nt, s->T, Kpad, ctx->phi_hi.ptr, split ? ctx->phi_lo.ptr : nullptr, ctx->sms, st),
+    FMC_CUDA(ctx,
+             launch_basis_split(K, Nt, s->T, Kpad, ctx->phi_hi.ptr, split ? ctx->phi_lo.ptr : nullptr, ctx->sms, st),
              "basis kernel");
     prof_end(pr, st);
     CUtensorMap maps[4];
-    if ((rc = make_contract_maps(ctx, maps, N, d, Ks, Nt, Kpad, TC, split))) return rc;
+    if ((rc = make_contract_maps(ctx, maps, count, d, Ks, Nt, Kpad, TC, split))) return rc;
     FMC_CUDA(ctx, cudaMemsetAsync((char*)ctx->status.ptr + 4, 0, 4, st), "memset");
     prof_begin(ctx, PH_FUSED, st, &pr);
     int occ = 0;
-    cudaError_t e = launch_simulate_fused(nm, nd, params.data(), maps, N, Nt, TC, d, Ks, nkb, split, tmem_cols, eq,
-                                          (float*)ctx->part.ptr, traj_dev, (int*)ctx->status.ptr + 1, st, &occ);
+    cudaError_t e = launch_simulate_fused(nm, nd, params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
+                                          eq, (float*)ctx->part.ptr, traj_dev, (int*)ctx->status.ptr + 1, st, &occ);
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)
-        return fail(ctx, FMC_EUNSUPPORTED, "fused kernel: %d CTAs per SM x %u TMEM columns exceeds 512", occ, tmem_cols);
+        return fail(ctx, FMC_EUNSUPPORTED, "fused kernel: %d CTAs per SM x %u TMEM columns exceeds 512", occ,
+                    tmem_cols);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fused simulation kernel");
     prof_end(pr, st);
     prof_begin(ctx, PH_REDUCE, st, &pr);
-    FMC_CUDA(ctx,
-             launch_fused_moments_reduce((const float*)ctx->part.ptr, (int)ntiles, Nt1, S, eq + 2 * n, N, mean_dev,
-                                         var_dev, st),
-             "moment reduce");
+    FMC_CUDA(ctx, launch_fused_sums((const float*)ctx->part.ptr, (int)ntiles, Nt1, S, S1, S2, st), "moment sums");
     prof_end(pr, st);
+    return FMC_OK;
+}
+
+int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
+                 float* traj_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!s) return fail(ctx, FMC_EINVAL, "scenario is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = simulate_core(ctx, s, 0, s->N, path, mean_dev, var_dev, traj_dev, st);
+    if (rc) return rc;
+    int Nt = 0;
+    steps_of(ctx, s->T, s->dt, &Nt);
+    ProfRec* pr;
+    prof_begin(ctx, PH_REDUCE, st, &pr);
+    FMC_CUDA(ctx,
+             launch_finalize(mean_dev, var_dev, (const double*)ctx->eq.ptr + 2 * s->n, s->N, (int64_t)Nt + 1, 2 * s->n,
+                             mean_dev, var_dev, st),
+             "moment finalize");
+    prof_end(pr, st);
+    return FMC_OK;
+}
+
+int fmc_simulate_sums(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1_dev,
+                      double* S2_dev, double* shift_dev, float* traj_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!s) return fail(ctx, FMC_EINVAL, "scenario is NULL");
+    if (!shift_dev) return fail(ctx, FMC_EINVAL, "shift output is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = simulate_core(ctx, s, k0, count, path, S1_dev, S2_dev, traj_dev, st);
+    if (rc) return rc;
+    FMC_CUDA(ctx,
+             cudaMemcpyAsync(shift_dev, (const double*)ctx->eq.ptr + 2 * s->n, 2 * s->n * sizeof(double),
+                             cudaMemcpyDeviceToDevice, st),
+             "copy shift");
+    return FMC_OK;
+}
+
+int fmc_moments_from_sums(fmc_ctx* ctx, const double* S1_dev, const double* S2_dev, const double* shift_dev, int64_t N,
+                          int64_t T1, int32_t S, double* mean_dev, double* var_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (N < 1 || T1 < 1 || S < 1) return fail(ctx, FMC_EINVAL, "N, rows and states must be >= 1");
+    if (!S1_dev || !S2_dev || !shift_dev || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "NULL buffer");
+    FMC_CUDA(ctx, launch_finalize(S1_dev, S2_dev, shift_dev, N, T1, S, mean_dev, var_dev, (cudaStream_t)stream),
+             "moment finalize");
     return FMC_OK;
 }
 
@@ -673,6 +755,17 @@ int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* lau
     }
     if (total_ms) *total_ms = tot;
     if (launches) *launches = cnt;
+    return FMC_OK;
+}
+
+int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, float* c_dev, float* s_ref_dev,
+                    float* c_ref_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (n < 0 || (n > 0 && (!x_dev || !s_dev || !c_dev || !s_ref_dev || !c_ref_dev)))
+        return fail(ctx, FMC_EINVAL, "bad arguments");
+    FMC_CUDA(ctx, launch_sincos_probe(x_dev, n, s_dev, c_dev, s_ref_dev, c_ref_dev, (cudaStream_t)stream),
+             "sincos probe");
     return FMC_OK;
 }
 

@@ -28,7 +28,14 @@ cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* para
                                   const double* eq, float* part, float* traj, int* err, cudaStream_t st,
                                   int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
-cudaError_t launch_fused_moments_reduce(const float* part, int nblk, int64_t Nt1, int S, const double* shift,
-                                        int64_t N, double* mean, double* var, cudaStream_t st);
+cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
+                             int sms, cudaStream_t st);
+cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, double* S1, double* S2,
+                              cudaStream_t st);
+cudaError_t launch_finalize(const double* S1, const double* S2, const double* shift, int64_t N, int64_t Nt1, int S,
+                            double* mean, double* var, cudaStream_t st);
+
+cudaError_t launch_sincos_probe(const float* x, int64_t n, float* s_cw, float* c_cw, float* s_ref, float* c_ref,
+                                cudaStream_t st);
 
 }  // namespace fmc

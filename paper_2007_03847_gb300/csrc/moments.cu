@@ -14,9 +14,11 @@ namespace fmc {
 constexpr int MOM_THREADS = 256;
 constexpr int MOM_RUN = 32;  // rows summed in FP32 before moving into FP64
 
-// grid.x: column blocks; grid.y: row slabs of `rows_per_slab` rows.
+// grid.x: column blocks; grid.y: row slabs of `rows_per_slab` rows.  The shift
+// of column c is x[0][c] (shift == nullptr) or (float)shift[c % S].
 __global__ void __launch_bounds__(MOM_THREADS) moments_partial_kernel(const float* __restrict__ x, int64_t N, int64_t C,
-                                                                      int64_t rows_per_slab, double* __restrict__ S1,
+                                                                      int64_t rows_per_slab, const double* __restrict__ shift_s,
+                                                                      int S, double* __restrict__ S1,
                                                                       double* __restrict__ S2)
 {
     int64_t c = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x;
@@ -24,7 +26,7 @@ __global__ void __launch_bounds__(MOM_THREADS) moments_partial_kernel(const floa
     int64_t r0 = (int64_t)blockIdx.y * rows_per_slab;
     int64_t r1 = r0 + rows_per_slab;
     if (r1 > N) r1 = N;
-    const float shift = x[c];
+    const float shift = shift_s ? (float)shift_s[c % S] : x[c];
     double s1 = 0.0, s2 = 0.0;
     for (int64_t r = r0; r < r1; r += MOM_RUN) {
         int64_t re = r + MOM_RUN < r1 ? r + MOM_RUN : r1;
@@ -53,11 +55,12 @@ __global__ void moments_finalize_kernel(const float* __restrict__ x, int64_t N, 
     var[c] = (N > 1) ? (s2 - s1 * s1 / n) / (n - 1.0) : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st)
+static cudaError_t launch_partial(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1,
+                                  double* S2, int sms, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(mean, 0, sizeof(double) * C, st);
+    cudaError_t e = cudaMemsetAsync(S1, 0, sizeof(double) * C, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(var, 0, sizeof(double) * C, st);
+    e = cudaMemsetAsync(S2, 0, sizeof(double) * C, st);
     if (e != cudaSuccess) return e;
     int64_t gx = (C + MOM_THREADS - 1) / MOM_THREADS;
     // enough slabs to fill the GPU a few times over, each at least a few runs long
@@ -72,20 +75,31 @@ cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, d
     slabs = (N + rows - 1) / rows;
     if (gx > 2147483647LL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)gx, (unsigned)slabs);
-    moments_partial_kernel<<<grid, MOM_THREADS, 0, st>>>(x, N, C, rows, mean, var);
-    e = cudaGetLastError();
+    moments_partial_kernel<<<grid, MOM_THREADS, 0, st>>>(x, N, C, rows, shift, S, S1, S2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st)
+{
+    cudaError_t e = launch_partial(x, N, C, nullptr, 1, mean, var, sms, st);
     if (e != cudaSuccess) return e;
     moments_finalize_kernel<<<(unsigned)((C + 255) / 256), 256, 0, st>>>(x, N, C, mean, var);
     return cudaGetLastError();
 }
 
+// Shifted sums of trajectories x [N][Nt1*S] with the per-state shift[S].
+cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
+                             int sms, cudaStream_t st)
+{
+    return launch_partial(x, N, C, shift, S, S1, S2, sms, st);
+}
+
 // Fused-simulation partials: part [nblk][Nt1][2*S] floats holding, per block of
 // samples and per grid time, the FP32 sums (S1 for states 0..S-1, then S2 for
-// states 0..S-1) of values shifted by shift[s].  Combined over blocks in FP64
-// in a fixed order, so the result does not depend on scheduling.
-__global__ void fused_moments_reduce_kernel(const float* __restrict__ part, int nblk, int64_t Nt1, int S,
-                                            const double* __restrict__ shift, int64_t N, double* __restrict__ mean,
-                                            double* __restrict__ var)
+// states 0..S-1) of shifted values.  Combined over blocks in FP64 in a fixed
+// order, so the result does not depend on scheduling; out: S1, S2 [Nt1][S].
+__global__ void fused_sums_kernel(const float* __restrict__ part, int nblk, int64_t Nt1, int S,
+                                  double* __restrict__ S1o, double* __restrict__ S2o)
 {
     int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // col = n * S + s
     if (col >= Nt1 * S) return;
@@ -99,18 +113,38 @@ __global__ void fused_moments_reduce_kernel(const float* __restrict__ part, int 
         s1 += (double)p[(int64_t)b * stride];
         s2 += (double)p[(int64_t)b * stride + S];
     }
-    double nn = (double)N;
-    // the kernel shifted by the FP32 rounding of the shift; add back the same value
+    S1o[col] = s1;
+    S2o[col] = s2;
+}
+
+cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, double* S1, double* S2,
+                              cudaStream_t st)
+{
+    int64_t cols = Nt1 * S;
+    fused_sums_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, nblk, Nt1, S, S1, S2);
+    return cudaGetLastError();
+}
+
+// mean = shift + S1/N, var = (S2 - S1^2/N)/(N-1) with the FP32 rounding of the
+// per-state shift (the value the kernels subtracted); NaN variance for N = 1.
+// May run in place (mean == S1, var == S2).
+__global__ void finalize_kernel(const double* S1, const double* S2, const double* __restrict__ shift, int64_t N,
+                                int64_t Nt1, int S, double* mean, double* var)
+{
+    int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= Nt1 * S) return;
+    const int s = (int)(col % S);
+    const double s1 = S1[col], s2 = S2[col];
+    const double nn = (double)N;
     mean[col] = (double)(float)shift[s] + s1 / nn;
     var[col] = (N > 1) ? (s2 - s1 * s1 / nn) / (nn - 1.0) : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-cudaError_t launch_fused_moments_reduce(const float* part, int nblk, int64_t Nt1, int S, const double* shift,
-                                        int64_t N, double* mean, double* var, cudaStream_t st)
+cudaError_t launch_finalize(const double* S1, const double* S2, const double* shift, int64_t N, int64_t Nt1, int S,
+                            double* mean, double* var, cudaStream_t st)
 {
     int64_t cols = Nt1 * S;
-    fused_moments_reduce_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, nblk, Nt1, S, shift, N, mean,
-                                                                                var);
+    finalize_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(S1, S2, shift, N, Nt1, S, mean, var);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ struct FusedArgs {
     int64_t count;
     int Nt, TC, d, Ks, nkb, split;
     uint32_t tmem_cols;
-    const double* eq;   // [delta0 n][pm n][shift 2n]
+    const double* eq;   // [delta* n][pm n][moment shift 2n] (the shift is used by the reduce)
     float* part;        // [ntiles][Nt+1][4n]
     float* traj;        // [count][Nt+1][2n] or nullptr
     int* err;
@@ -46,7 +46,6 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     __shared__ uint64_t bars[5];  // full[2], freed[2], done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ float s_shift[NM];
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int n = p.n, d = p.d, S = 2 * n, S4 = 4 * n;
@@ -83,15 +82,13 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     const uint32_t tmem = tmem_base;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 
-    float del[NM], w[NM];
+    float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND];
-    const float pm0 = p.slack ? (float)a.eq[n] : 0.f;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-        del[i] = (i < n) ? (float)a.eq[i] : 0.f;
+        del[i] = 0.f;
         w[i] = 0.f;
     }
-    if (tid < NM) s_shift[tid] = (tid < n) ? (float)a.eq[tid] : 0.f;
 #pragma unroll
     for (int q = 0; q < ND; ++q) x0[q] = 0.f;
 
@@ -101,8 +98,8 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 #pragma unroll
         for (int i = 0; i < NM; ++i)
             if (i < n) {
-                traj[i] = del[i];
-                traj[n + i] = w[i];
+                traj[i] = p.dst[i];
+                traj[n + i] = 0.f;
             }
     }
     // time 0: every sample sits at the (rounded) shift, so both sums are zero
@@ -158,7 +155,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                 if (q < d) dw[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
             tmem_ld_wait();
             ou_step<NM, ND>(p, x0, dw, x1);
-            swing_step<NM, ND>(p, pm0, del, w, x0, x1);
+            swing_step<NM, ND>(p, del, w, theta, x0, x1);
 #pragma unroll
             for (int q = 0; q < ND; ++q) x0[q] = x1[q];
 
@@ -168,7 +165,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 #pragma unroll
                 for (int i = 0; i < NM; ++i)
                     if (i < n) {
-                        o[i] = del[i];
+                        o[i] = (theta + del[i]) + p.dst[i];
                         o[n + i] = w[i];
                     }
             }
@@ -177,7 +174,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 #pragma unroll
             for (int i = 0; i < NM; ++i)
                 if (i < n) {
-                    myrow[i] = active ? del[i] - s_shift[i] : 0.f;
+                    myrow[i] = active ? theta + del[i] : 0.f;
                     myrow[n + i] = active ? w[i] : 0.f;
                 }
             __syncwarp();

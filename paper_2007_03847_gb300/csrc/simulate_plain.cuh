@@ -19,12 +19,11 @@ __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_consta
     if (s >= count) return;
     const int n = p.n;
     const int d = p.d;
-    float del[NM], w[NM];
+    float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND], x1[ND], dw[ND];
-    const float pm0 = p.slack ? (float)eq[n] : 0.f;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-        del[i] = (i < n) ? (float)eq[i] : 0.f;
+        del[i] = 0.f;
         w[i] = 0.f;
     }
 #pragma unroll
@@ -34,22 +33,22 @@ __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_consta
 #pragma unroll
     for (int i = 0; i < NM; ++i)
         if (i < n) {
-            out[i] = del[i];
-            out[n + i] = w[i];
+            out[i] = p.dst[i];
+            out[n + i] = 0.f;
         }
     const float* dws = dW + s * (int64_t)d * Nt;
     for (int step = 0; step < Nt; ++step) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) dw[q] = (q < d) ? __ldg(dws + (int64_t)q * Nt + step) : 0.f;
         ou_step<NM, ND>(p, x0, dw, x1);
-        swing_step<NM, ND>(p, pm0, del, w, x0, x1);
+        swing_step<NM, ND>(p, del, w, theta, x0, x1);
 #pragma unroll
         for (int q = 0; q < ND; ++q) x0[q] = x1[q];
         float* o = out + (int64_t)(step + 1) * row;
 #pragma unroll
         for (int i = 0; i < NM; ++i)
             if (i < n) {
-                o[i] = del[i];
+                o[i] = (theta + del[i]) + p.dst[i];
                 o[n + i] = w[i];
             }
     }

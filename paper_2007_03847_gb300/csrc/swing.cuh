@@ -7,32 +7,69 @@
 //   2 H_i d domega_i/dt = Pm_i + sum_w inj[i][w] x_w - Pe_i - D_i domega_i,
 //   Pe_i = sum_j E_i E_j (G_ij cos(delta_i-delta_j) + B_ij sin(delta_i-delta_j))
 //          [+ E_i V (Ginf_i cos delta_i + Binf_i sin delta_i)].
-// Evaluated in product form: with c_j = cos delta_j, s_j = sin delta_j,
-//   Pe_i = c_i u_i + s_i v_i,  u_i = sum_j GE_ij c_j - BE_ij s_j,
-//   v_i = sum_j GE_ij s_j + BE_ij c_j,  GE_ij = E_i E_j G_ij, BE_ij = E_i E_j B_ij,
-// so a stage costs NM sincos and 4 NM^2 FMAs.  The matrices live in the kernel
-// parameter block: fully unrolled loops address them with immediate offsets,
-// so every FMA takes its matrix operand straight from the constant bank.
+// Evaluated in product form around the equilibrium (see swing_step), so a stage
+// costs NM small-angle sin/cos pairs and 4 NM (NM - 1) FMAs.  The matrices and
+// the equilibrium constants live in the kernel parameter block: fully unrolled
+// loops address them with immediate offsets, so every FMA takes its constant
+// operand straight from the constant bank.
 //
 // Register economy: a stage evaluates the right-hand side machine by machine and
 // immediately folds k_i into the RK accumulator and into the next stage's input,
-// so only state, accumulator, stage input and the stage's cos/sin stay live.
-// Padded disturbances (index >= d) have zero sigma and zero injection.
+// so only state, accumulator, stage input and the stage's deviations stay live.
+// Padded disturbances (index >= d) have zero sigma and zero injection; padded
+// machines have zero network rows and stay at rest.
 #pragma once
 
 #include "fmc_common.cuh"
 
 namespace fmc {
 
+// sin and cos of an FP32 angle to a few ulps, on the FP32 pipe (no MUFU):
+// Cody-Waite reduction x = k pi/2 + r with pi/2 split into its FP32 rounding
+// and the remainder (both products exact inside the FMAs), then the Taylor
+// series of sin r to degree 9 and of cos r to degree 10, whose truncation is
+// below 2e-9 on |r| <= pi/4, then the quadrant k mod 4.  The hardware
+// approximations (__sinf, __cosf) carry absolute errors near 4e-7, which the
+// stiff network terms (|B_ij| E_i E_j up to ~10 p.u.) turn into power errors
+// that dominate the speed deviation; this keeps the evaluation at FP32
+// rounding level.  Accurate for |x| < 2^20.
+__device__ __forceinline__ void sincos_cw(float x, float* s_out, float* c_out)
+{
+    const float TWO_OVER_PI = 0.636619772367581343f;
+    const float PIO2_HI = 1.57079637050628662109375f;   // pi/2 rounded to FP32
+    const float PIO2_LO = -4.37113900018624283e-8f;     // pi/2 - PIO2_HI
+    const float k = rintf(x * TWO_OVER_PI);
+    float r = fmaf(-k, PIO2_HI, x);
+    r = fmaf(-k, PIO2_LO, r);
+    const float r2 = r * r;
+    // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
+    float ps = fmaf(r2, 2.7557319223985891e-6f, -1.9841269841269841e-4f);
+    ps = fmaf(ps, r2, 8.3333333333333333e-3f);
+    ps = fmaf(ps, r2, -1.6666666666666667e-1f);
+    const float sr = fmaf(ps * r2, r, r);
+    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+    float pc = fmaf(r2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+    pc = fmaf(pc, r2, -1.3888888888888889e-3f);
+    pc = fmaf(pc, r2, 4.1666666666666667e-2f);
+    pc = fmaf(pc, r2, -0.5f);
+    const float cr = fmaf(pc, r2, 1.0f);
+    const int q = (int)k;
+    const bool odd = (q & 1) != 0;
+    const float a = odd ? cr : sr;
+    const float b = odd ? sr : cr;
+    *s_out = __int_as_float(__float_as_int(a) ^ ((q & 2) << 30));
+    *c_out = __int_as_float(__float_as_int(b) ^ (((q + 1) & 2) << 30));
+}
+
 template <int NM, int ND>
 struct SwingParams {
-    float GE[NM][NM];
-    float BE[NM][NM];
-    float GEinf[NM];             // E_i Vinf Ginf_i (0 without infinite bus)
-    float BEinf[NM];             // E_i Vinf Binf_i
+    float GE[NM][NM];            // E_i E_j G_ij, zero diagonal
+    float BE[NM][NM];            // E_i E_j B_ij, zero diagonal
+    float cst[NM], sst[NM];      // cos, sin of the equilibrium angle (reference frame)
+    float ust[NM], vst[NM];      // u*, v*: off-diagonal network sums at the equilibrium (+ infinite bus)
+    float dst[NM];               // equilibrium angles delta*_i (absolute)
     float inv2H[NM];
     float D[NM];
-    float Pm[NM];                // mechanical powers (machine 0's replaced when it is the slack)
     float inj[NM][ND];
     float ou_a[ND];              // 1 - theta_w dt
     float ou_s[ND];              // sigma_w
@@ -41,22 +78,63 @@ struct SwingParams {
     int d;                       // real disturbances (<= ND; the rest are zero)
     int n;                       // real machines (<= NM; the rest are inert padding)
     int integrator;              // FMC_RK4 / FMC_HEUN
-    int slack;                   // 1: machine 0 balances power; its Pm comes from the equilibrium
+    int rel;                     // 1: angles relative to machine 0 (no infinite bus)
 };
 
-// One step of the swing equations.  The stages run as a loop that is not
-// unrolled, so the right-hand side exists once in the code and its constant
-// operands are not held in registers across stages.  The disturbance enters
-// stage st at x0 + xw (x1 - x0): RK4 xw = 0, 1/2, 1/2, 1 (the midpoint value is
-// the average of the two grid values), Heun xw = 0, 1.
+// sin(a) and cos(a) - 1 of a small deviation angle, without cancellation: the
+// Taylor series to degree 9 and 10 (truncation < 3e-9 for |a| <= 0.8), else the
+// reduced-argument evaluation above.
+__device__ __forceinline__ void sin_cosm1(float a, float* sn, float* cm1)
+{
+    const float a2 = a * a;
+    if (fabsf(a) <= 0.8f) {
+        float ps = fmaf(a2, 2.7557319223985891e-6f, -1.9841269841269841e-4f);
+        ps = fmaf(ps, a2, 8.3333333333333333e-3f);
+        ps = fmaf(ps, a2, -1.6666666666666667e-1f);
+        *sn = fmaf(ps * a2, a, a);
+        float pc = fmaf(a2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+        pc = fmaf(pc, a2, -1.3888888888888889e-3f);
+        pc = fmaf(pc, a2, 4.1666666666666667e-2f);
+        pc = fmaf(pc, a2, -0.5f);
+        *cm1 = pc * a2;
+    } else {
+        float c;
+        sincos_cw(a, sn, &c);
+        *cm1 = c - 1.0f;
+    }
+}
+
+// One step of the swing equations, integrated in deviation variables
+//   Delta_i = delta_i - delta*_i - theta   (theta: angle of machine 0 when the
+//   system has no infinite bus, so that the common drift of all angles, which
+//   the network does not see, never enters the FP32 network terms; 0 otherwise)
+// With c_i = cos(delta_i) = c*_i + gamma_i, s_i = s*_i + eta_i,
+//   gamma_i = c*_i (cos Delta_i - 1) - s*_i sin Delta_i,
+//   eta_i   = s*_i (cos Delta_i - 1) + c*_i sin Delta_i,
+// the electrical power's deviation from equilibrium is
+//   dPe_i = c*_i du_i + s*_i dv_i + gamma_i (u*_i + du_i) + eta_i (v*_i + dv_i),
+//   du_i = sum_{j!=i} GE_ij gamma_j - BE_ij eta_j,  dv_i = sum_{j!=i} GE_ij eta_j + BE_ij gamma_j
+// (the diagonal contributes the constant E_i^2 G_ii), and since Pm = Pe(delta*)
+// at the equilibrium,
+//   2H_i d(domega_i)/dt = sum_w inj[i][w] x_w - dPe_i - D_i domega_i.
+// Every quantity in the network terms is small, so FP32 keeps its relative
+// precision; the state is the same RK4 trajectory as in absolute angles
+// (RK4 commutes with the linear change of variables).
+// The stages run as a loop that is not unrolled, so the right-hand side exists
+// once in the code and its constant operands are not held in registers across
+// stages.  The disturbance enters stage st at x0 + xw (x1 - x0): RK4 xw = 0,
+// 1/2, 1/2, 1 (the midpoint value is the average of the two grid values), Heun
+// xw = 0, 1.
 template <int NM, int ND>
-__device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float pm0, float (&del)[NM], float (&w)[NM],
-                                           const float (&x0)[ND], const float (&x1)[ND])
+__device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
+                                           float& theta, const float (&x0)[ND], const float (&x1)[ND])
 {
     const float dt = p.dt;
     const bool rk4 = (p.integrator == FMC_RK4);
     const int nst = rk4 ? 4 : 2;
+    const float ref = p.rel ? 1.f : 0.f;
     float ad[NM], aw[NM], yd[NM], yw[NM];
+    float ath = 0.f;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
         yd[i] = del[i];
@@ -79,25 +157,35 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float p
         float xs[ND];
 #pragma unroll
         for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
-        float c[NM], s[NM];
+        float ga[NM], et[NM];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) __sincosf(yd[j], &s[j], &c[j]);
+        for (int j = 0; j < NM; ++j) {
+            float sn, cm1;
+            sin_cosm1(yd[j], &sn, &cm1);
+            ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
+            et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
+        }
+        const float w0 = yw[0] * ref;
+        ath = fmaf(b, p.omega_s * w0, ath);
 #pragma unroll
         for (int i = 0; i < NM; ++i) {
-            float u = p.GEinf[i], v = p.BEinf[i];
+            float du = 0.f, dv = 0.f;
 #pragma unroll
             for (int j = 0; j < NM; ++j) {
-                u = fmaf(p.GE[i][j], c[j], u);
-                u = fmaf(-p.BE[i][j], s[j], u);
-                v = fmaf(p.GE[i][j], s[j], v);
-                v = fmaf(p.BE[i][j], c[j], v);
+                if (j == i) continue;
+                du = fmaf(p.GE[i][j], ga[j], du);
+                du = fmaf(-p.BE[i][j], et[j], du);
+                dv = fmaf(p.GE[i][j], et[j], dv);
+                dv = fmaf(p.BE[i][j], ga[j], dv);
             }
-            const float pe = fmaf(c[i], u, s[i] * v);
-            float f = (i == 0 && p.slack) ? pm0 : p.Pm[i];
+            float dpe = fmaf(p.cst[i], du, p.sst[i] * dv);
+            dpe = fmaf(ga[i], p.ust[i] + du, dpe);
+            dpe = fmaf(et[i], p.vst[i] + dv, dpe);
+            float f = 0.f;
 #pragma unroll
             for (int q = 0; q < ND; ++q) f = fmaf(p.inj[i][q], xs[q], f);
-            const float kd = p.omega_s * yw[i];
-            const float kw = (f - pe - p.D[i] * yw[i]) * p.inv2H[i];
+            const float kd = p.omega_s * (yw[i] - w0);
+            const float kw = (f - dpe - p.D[i] * yw[i]) * p.inv2H[i];
             ad[i] = fmaf(b, kd, ad[i]);
             aw[i] = fmaf(b, kw, aw[i]);
             yd[i] = fmaf(cn, kd, del[i]);
@@ -110,6 +198,7 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float p
         del[i] = fmaf(h, ad[i], del[i]);
         w[i] = fmaf(h, aw[i], w[i]);
     }
+    theta = fmaf(h, ath, theta);
 }
 
 // One Euler-Maruyama step of the OU disturbances: x1 = (1 - theta dt) x0 + sigma dW.
