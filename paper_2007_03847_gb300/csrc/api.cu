@@ -227,6 +227,8 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
             double be = s->E[i] * s->E[j] * s->B[i * n + j];
             p.GE[i][j] = (float)ge;
             p.BE[i][j] = (float)be;
+            p.P1[i][j] = make_float2((float)ge, (float)ge);
+            p.P2[i][j] = make_float2((float)-be, (float)be);
             u += ge * c[j] - be * sn[j];
             v += ge * sn[j] + be * c[j];
         }

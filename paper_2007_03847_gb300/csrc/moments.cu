@@ -98,30 +98,51 @@ cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double*
 // samples and per grid time, the FP32 sums (S1 for states 0..S-1, then S2 for
 // states 0..S-1) of shifted values.  Combined over blocks in FP64 in a fixed
 // order, so the result does not depend on scheduling; out: S1, S2 [Nt1][S].
-__global__ void fused_sums_kernel(const float* __restrict__ part, int nblk, int64_t Nt1, int S,
-                                  double* __restrict__ S1o, double* __restrict__ S2o)
+// A CTA owns 32 consecutive entries q of a part row; its 8 warps stride over
+// the blocks (warp g takes blocks g, g+8, ...), each with two accumulators,
+// and the 8 partial sums are added in warp order.
+constexpr int FS_COLS = 32, FS_GROUPS = 8;
+
+__global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const float* __restrict__ part, int nblk,
+                                                                         int64_t Nt1, int S, double* __restrict__ S1o,
+                                                                         double* __restrict__ S2o)
 {
-    int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // col = n * S + s
-    if (col >= Nt1 * S) return;
-    int64_t n = col / S;
-    int s = (int)(col - n * S);
+    __shared__ double red[FS_GROUPS][FS_COLS];
+    const int cx = threadIdx.x % FS_COLS, g = threadIdx.x / FS_COLS;
     const int64_t row = 2 * (int64_t)S;
-    const int64_t stride = Nt1 * row;
-    const float* p = part + n * row + s;
-    double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        s1 += (double)p[(int64_t)b * stride];
-        s2 += (double)p[(int64_t)b * stride + S];
+    const int64_t total = Nt1 * row;
+    const int64_t q = (int64_t)blockIdx.x * FS_COLS + cx;
+    double a0 = 0.0, a1 = 0.0;
+    if (q < total) {
+        const float* p = part + q;
+        int b = g;
+        for (; b + FS_GROUPS < nblk; b += 2 * FS_GROUPS) {
+            a0 += (double)p[(int64_t)b * total];
+            a1 += (double)p[(int64_t)(b + FS_GROUPS) * total];
+        }
+        if (b < nblk) a0 += (double)p[(int64_t)b * total];
     }
-    S1o[col] = s1;
-    S2o[col] = s2;
+    red[g][cx] = a0 + a1;
+    __syncthreads();
+    if (g == 0 && q < total) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < FS_GROUPS; ++k) t += red[k][cx];
+        const int64_t n = q / row;
+        const int v = (int)(q - n * row);
+        if (v < S)
+            S1o[n * S + v] = t;
+        else
+            S2o[n * S + (v - S)] = t;
+    }
 }
 
 cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, double* S1, double* S2,
                               cudaStream_t st)
 {
-    int64_t cols = Nt1 * S;
-    fused_sums_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(part, nblk, Nt1, S, S1, S2);
+    int64_t total = Nt1 * 2 * S;
+    fused_sums_kernel<<<(unsigned)((total + FS_COLS - 1) / FS_COLS), FS_COLS * FS_GROUPS, 0, st>>>(part, nblk, Nt1, S,
+                                                                                                 S1, S2);
     return cudaGetLastError();
 }
 

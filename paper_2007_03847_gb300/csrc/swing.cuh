@@ -22,6 +22,10 @@
 
 #include "fmc_common.cuh"
 
+#ifndef FMC_PACKED_FP32
+#define FMC_PACKED_FP32 1
+#endif
+
 namespace fmc {
 
 // sin and cos of an FP32 angle to a few ulps, on the FP32 pipe (no MUFU):
@@ -65,6 +69,8 @@ template <int NM, int ND>
 struct SwingParams {
     float GE[NM][NM];            // E_i E_j G_ij, zero diagonal
     float BE[NM][NM];            // E_i E_j B_ij, zero diagonal
+    float2 P1[NM][NM];           // (GE_ij, GE_ij): packed multiplier of (gamma_j, eta_j)
+    float2 P2[NM][NM];           // (-BE_ij, BE_ij): packed multiplier of (eta_j, gamma_j)
     float cst[NM], sst[NM];      // cos, sin of the equilibrium angle (reference frame)
     float ust[NM], vst[NM];      // u*, v*: off-diagonal network sums at the equilibrium (+ infinite bus)
     float dst[NM];               // equilibrium angles delta*_i (absolute)
@@ -82,26 +88,49 @@ struct SwingParams {
 };
 
 // sin(a) and cos(a) - 1 of a small deviation angle, without cancellation: the
-// Taylor series to degree 9 and 10 (truncation < 3e-9 for |a| <= 0.8), else the
-// reduced-argument evaluation above.
-__device__ __forceinline__ void sin_cosm1(float a, float* sn, float* cm1)
+// Taylor series to degree 9 and 10 (truncation < 3e-9 for |a| <= 0.8).
+__device__ __forceinline__ void sin_cosm1_small(float a, float* sn, float* cm1)
 {
     const float a2 = a * a;
-    if (fabsf(a) <= 0.8f) {
-        float ps = fmaf(a2, 2.7557319223985891e-6f, -1.9841269841269841e-4f);
-        ps = fmaf(ps, a2, 8.3333333333333333e-3f);
-        ps = fmaf(ps, a2, -1.6666666666666667e-1f);
-        *sn = fmaf(ps * a2, a, a);
-        float pc = fmaf(a2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
-        pc = fmaf(pc, a2, -1.3888888888888889e-3f);
-        pc = fmaf(pc, a2, 4.1666666666666667e-2f);
-        pc = fmaf(pc, a2, -0.5f);
-        *cm1 = pc * a2;
-    } else {
-        float c;
-        sincos_cw(a, sn, &c);
-        *cm1 = c - 1.0f;
-    }
+    float ps = fmaf(a2, 2.7557319223985891e-6f, -1.9841269841269841e-4f);
+    ps = fmaf(ps, a2, 8.3333333333333333e-3f);
+    ps = fmaf(ps, a2, -1.6666666666666667e-1f);
+    *sn = fmaf(ps * a2, a, a);
+    float pc = fmaf(a2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+    pc = fmaf(pc, a2, -1.3888888888888889e-3f);
+    pc = fmaf(pc, a2, 4.1666666666666667e-2f);
+    pc = fmaf(pc, a2, -0.5f);
+    *cm1 = pc * a2;
+}
+
+// Any deviation: the reduced-argument evaluation, cos - 1 = -2 sin^2(a/2).
+__device__ __forceinline__ void sin_cosm1_any(float a, float* sn, float* cm1)
+{
+    float c, sh, ch;
+    sincos_cw(a, sn, &c);
+    sincos_cw(0.5f * a, &sh, &ch);
+    *cm1 = -2.0f * sh * sh;
+}
+
+// Packed FP32 (two lanes per register pair) fused multiply-add of sm_100+:
+// d = a * b + c elementwise on (x, y) pairs.
+__device__ __forceinline__ unsigned long long f2pack(float x, float y)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+
+__device__ __forceinline__ void f2unpack(unsigned long long r, float& x, float& y)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
 // One step of the swing equations, integrated in deviation variables
@@ -158,18 +187,51 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
 #pragma unroll
         for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
         float ga[NM], et[NM];
+        bool big = false;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) {
-            float sn, cm1;
-            sin_cosm1(yd[j], &sn, &cm1);
-            ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
-            et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
+        for (int j = 0; j < NM; ++j) big = big || (fabsf(yd[j]) > 0.8f);
+        // warp-uniform choice: the series for the usual small deviations, the
+        // reduced-argument form for all machines when any lane swings far
+        if (__any_sync(__activemask(), big)) {
+#pragma unroll
+            for (int j = 0; j < NM; ++j) {
+                float sn, cm1;
+                sin_cosm1_any(yd[j], &sn, &cm1);
+                ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
+                et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NM; ++j) {
+                float sn, cm1;
+                sin_cosm1_small(yd[j], &sn, &cm1);
+                ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
+                et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
+            }
         }
         const float w0 = yw[0] * ref;
         ath = fmaf(b, p.omega_s * w0, ath);
+#if FMC_PACKED_FP32
+        unsigned long long ge2[NM], eg2[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+            ge2[j] = f2pack(ga[j], et[j]);
+            eg2[j] = f2pack(et[j], ga[j]);
+        }
+#endif
 #pragma unroll
         for (int i = 0; i < NM; ++i) {
             float du = 0.f, dv = 0.f;
+#if FMC_PACKED_FP32
+            unsigned long long acc = 0ull;
+#pragma unroll
+            for (int j = 0; j < NM; ++j) {
+                if (j == i) continue;
+                acc = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P1[i][j]), ge2[j], acc);
+                acc = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P2[i][j]), eg2[j], acc);
+            }
+            f2unpack(acc, du, dv);
+#else
 #pragma unroll
             for (int j = 0; j < NM; ++j) {
                 if (j == i) continue;
@@ -178,6 +240,7 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
                 dv = fmaf(p.GE[i][j], et[j], dv);
                 dv = fmaf(p.BE[i][j], ga[j], dv);
             }
+#endif
             float dpe = fmaf(p.cst[i], du, p.sst[i] * dv);
             dpe = fmaf(ga[i], p.ust[i] + du, dpe);
             dpe = fmaf(et[i], p.vst[i] + dv, dpe);
