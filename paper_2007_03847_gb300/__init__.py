@@ -22,7 +22,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libfastmc.so")
+# FASTMC_LIB may point at another build of the same library (A/B comparisons)
+LIB_PATH = os.environ.get("FASTMC_LIB") or os.path.join(HERE, "lib", "libfastmc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_READY, EBUSY, ECANCELLED, EUNSUPPORTED, ENOCONVERGE = range(10)
 LHS, SRS, LHS_MIDPOINT = 0, 1, 2

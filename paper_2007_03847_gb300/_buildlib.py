@@ -13,10 +13,12 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-CSRC = os.path.join(HERE, "csrc")
+CSRC = os.environ.get("FMC_CSRC") or os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
-OBJDIR = os.path.join(HERE, "_build")
-LIB = os.path.join(LIBDIR, "libfastmc.so")
+# FMC_BUILD_TAG builds a separately named copy (objects and library) of the sources in FMC_CSRC
+_TAG = os.environ.get("FMC_BUILD_TAG", "")
+OBJDIR = os.path.join(HERE, "_build" + _TAG)
+LIB = os.path.join(LIBDIR, f"libfastmc{_TAG}.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,6 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         os.path.join(os.path.dirname(HERE), "include", "fastmc.h")]
+    extra = os.environ.get("FMC_EXTRA_NVCC_FLAGS", "").split()
     jobs = []
     for src in sources:
         obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
@@ -58,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(job):
         src, obj = job
-        cmd = [nvcc] + _flags() + ["-c", src, "-o", obj]
+        cmd = [nvcc] + _flags() + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, r
 

@@ -339,23 +339,30 @@ static int make_map_bf16(fmc_ctx* ctx, CUtensorMap* m, const void* base, uint64_
 }
 
 // Tensor maps of the split operands: zeta [rows][d*Ks], phi [Nt][Kpad].
-static int make_contract_maps(fmc_ctx* ctx, CUtensorMap maps[4], int64_t rows, int d, int Ks, int Nt, int Kpad, int TN,
-                              int split)
+static int make_contract_maps_at(fmc_ctx* ctx, CUtensorMap maps[4], const void* zhi, const void* zlo, const void* phi_hi,
+                                 const void* phi_lo, int64_t rows, int d, int Ks, int Nt, int Kpad, int TN, int split)
 {
-    int rc = make_map_bf16(ctx, &maps[0], ctx->zeta_hi.ptr, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+    int rc = make_map_bf16(ctx, &maps[0], zhi, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
     if (rc) return rc;
-    rc = make_map_bf16(ctx, &maps[2], ctx->phi_hi.ptr, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
+    rc = make_map_bf16(ctx, &maps[2], phi_hi, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
     if (rc) return rc;
     if (split) {
-        rc = make_map_bf16(ctx, &maps[1], ctx->zeta_lo.ptr, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+        rc = make_map_bf16(ctx, &maps[1], zlo, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
         if (rc) return rc;
-        rc = make_map_bf16(ctx, &maps[3], ctx->phi_lo.ptr, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
+        rc = make_map_bf16(ctx, &maps[3], phi_lo, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
         if (rc) return rc;
     } else {
         maps[1] = maps[0];
         maps[3] = maps[2];
     }
     return FMC_OK;
+}
+
+static int make_contract_maps(fmc_ctx* ctx, CUtensorMap maps[4], int64_t rows, int d, int Ks, int Nt, int Kpad, int TN,
+                              int split)
+{
+    return make_contract_maps_at(ctx, maps, ctx->zeta_hi.ptr, ctx->zeta_lo.ptr, ctx->phi_hi.ptr, ctx->phi_lo.ptr, rows,
+                                 d, Ks, Nt, Kpad, TN, split);
 }
 
 extern "C" {
