@@ -194,6 +194,34 @@ int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, float* phi_dev, 
 int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
                         double dt, int32_t precision, float* dW_dev, void* stream);
 
+/*
+ * Allocation-free form of fmc_kle_reconstruct (the paper has no counterpart:
+ * this is a service to callers that cannot allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: a process that has reserved the GPU's
+ * memory for its own pool (so a fresh allocation would fail or fragment it), or
+ * a loop with a hard latency budget (cudaMalloc and cudaFree may synchronise the
+ * device).  This entry point allocates nothing.  Its working memory -- the split
+ * BF16 coefficients and basis and an error word (or the FP32 basis) -- is a
+ * fixed device array of FMC_NOALLOC_SCRATCH_BYTES bytes inside the library,
+ * present on every GPU that loads the library until the process exits.  The
+ * caller still passes the inputs and the output, with the same meaning, layout
+ * and results as fmc_kle_reconstruct.
+ *
+ * Limits and behaviour:
+ *   - A call needs 2*align256(count*d*round_up(K,8)*2) + 2*align256(Nt*round_up(K,32)*2)
+ *     + 256 bytes (BF16/BF16X3) or align256(K*Nt*4) bytes (F32); a larger call
+ *     returns FMC_EINVAL and says so in fmc_last_error.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents: calls
+ *     whose work overlaps on the GPU (different streams, or different host
+ *     threads) race.  Serialise them on one stream.
+ */
+#define FMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
+                                double dt, int32_t precision, float* dW_dev, void* stream);
+
 /* ---- equilibrium (Section V-A: "at equilibrium at t = 0") --------------------- */
 
 /*

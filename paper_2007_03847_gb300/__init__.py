@@ -92,6 +92,7 @@ def load_library():
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_kle_reconstruct_noalloc": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
             "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_moments_from_sums": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         }
@@ -241,6 +242,23 @@ def kle_reconstruct(zeta, d: int, K: int, T: float, dt: float, precision="f32", 
     if dW is None:
         dW = torch.empty((count, d, Nt), dtype=torch.float32, device="cuda")
     ctx.check(ctx.lib.fmc_kle_reconstruct(ctx.h, _ptr(zeta), count, d, K, T, dt, prec, _ptr(dW), _stream(stream)))
+    return dW
+
+
+def kle_reconstruct_noalloc(zeta, d: int, K: int, T: float, dt: float, precision="bf16x3", dW=None,
+                            ctx: Context | None = None, stream=None):
+    """fmc_kle_reconstruct_noalloc: the same increments as kle_reconstruct, computed with
+    the library's fixed scratch array instead of allocated working memory.  The
+    caller provides dW (or this wrapper creates it, which allocates through torch)."""
+    import torch
+    ctx = ctx or default_context()
+    count = zeta.shape[0]
+    Nt = int(round(T / dt))
+    prec = _PRECISION.get(precision, precision) if isinstance(precision, str) else precision
+    if dW is None:
+        dW = torch.empty((count, d, Nt), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.fmc_kle_reconstruct_noalloc(ctx.h, _ptr(zeta), count, d, K, T, dt, prec, _ptr(dW),
+                                                  _stream(stream)))
     return dW
 
 

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -365,6 +366,37 @@ static int make_contract_maps(fmc_ctx* ctx, CUtensorMap maps[4], int64_t rows, i
                                  d, Ks, Nt, Kpad, TN, split);
 }
 
+// ---- scratch of the allocation-free reconstruction -----------------------------
+// A fixed device array of this module serves as the only working memory of
+// fmc_kle_reconstruct_noalloc.  Host code may not use the array's name as a
+// device address: the address is obtained once per device, with that device
+// current, by cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FMC_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64];
+
+static int noalloc_scratch(fmc_ctx* ctx, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 64) return fail(ctx, FMC_EUNSUPPORTED, "device ordinal %d above 63", dev);
+    if (!g_noalloc_addr[dev]) {
+        int prev = -1;
+        FMC_CUDA(ctx, cudaGetDevice(&prev), "cudaGetDevice");
+        if (prev != dev) FMC_CUDA(ctx, cudaSetDevice(dev), "cudaSetDevice");
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (prev != dev) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return FMC_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 extern "C" {
 
 int fmc_create(fmc_ctx** out, int device, size_t mem_budget_bytes)
@@ -512,6 +544,68 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
     if ((rc = make_contract_maps(ctx, maps, count, d, Ks, Nt, Kpad, TN, split))) return rc;
     FMC_CUDA(ctx, cudaMemsetAsync(ctx->status.ptr, 0, 64, st), "memset");
     FMC_CUDA(ctx, launch_contract_tc(maps, count, d, Ks, nkb, Nt, TN, split, dW_dev, (int*)ctx->status.ptr + 1, st),
+             "tensor-core contraction");
+    return FMC_OK;
+}
+
+int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
+                                double dt, int32_t precision, float* dW_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (count < 1 || d < 1 || K < 1) return fail(ctx, FMC_EINVAL, "count, d, K must be >= 1");
+    if (!zeta_dev || !dW_dev) return fail(ctx, FMC_EINVAL, "NULL buffer");
+    int Nt = 0;
+    int rc = steps_of(ctx, T, dt, &Nt);
+    if (rc) return rc;
+    if (precision != FMC_PREC_F32 && precision != FMC_PREC_BF16 && precision != FMC_PREC_BF16X3)
+        return fail(ctx, FMC_EINVAL, "precision %d", precision);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Ks = round_up(K, 8);
+    const int Kpad = round_up(K, TC_BK);
+    // layout of the scratch array for this call
+    size_t need;
+    size_t o_zhi = 0, o_zlo = 0, o_phi_hi = 0, o_phi_lo = 0, o_status = 0, o_phi32 = 0;
+    if (precision == FMC_PREC_F32) {
+        need = align256((size_t)K * Nt * sizeof(float));
+    } else {
+        const size_t zb = align256((size_t)count * d * Ks * 2);
+        const size_t pb = align256((size_t)Nt * Kpad * 2);
+        o_zlo = zb;
+        o_phi_hi = 2 * zb;
+        o_phi_lo = 2 * zb + pb;
+        o_status = 2 * zb + 2 * pb;
+        need = o_status + 256;
+    }
+    if (need > (size_t)FMC_NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, FMC_EINVAL,
+                    "this reconstruction needs %zu bytes of working memory; the allocation-free form has %zu "
+                    "(use fmc_kle_reconstruct)",
+                    need, (size_t)FMC_NOALLOC_SCRATCH_BYTES);
+    if (count > (int64_t(1) << 31) - 256) return fail(ctx, FMC_EINVAL, "count too large for the tensor-core path");
+    unsigned char* base = nullptr;
+    if ((rc = noalloc_scratch(ctx, &base))) return rc;
+    if (precision == FMC_PREC_F32) {
+        float* phi32 = reinterpret_cast<float*>(base + o_phi32);
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, phi32, ctx->sms, st), "basis kernel");
+        FMC_CUDA(ctx, launch_sgemm_nn(count * d, Nt, K, zeta_dev, phi32, dW_dev, st), "sgemm kernel");
+        return FMC_OK;
+    }
+    const int split = (precision == FMC_PREC_BF16X3);
+    const int nkb = (Ks + TC_BK - 1) / TC_BK;
+    const int TN = 64;
+    void* zhi = base + o_zhi;
+    void* zlo = base + o_zlo;
+    void* phi_hi = base + o_phi_hi;
+    void* phi_lo = base + o_phi_lo;
+    int* status = reinterpret_cast<int*>(base + o_status);
+    FMC_CUDA(ctx, launch_split_rows(zeta_dev, count, d, K, Ks, zhi, zlo, st), "split");
+    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, Kpad, phi_hi, phi_lo, ctx->sms, st), "basis");
+    CUtensorMap maps[4];
+    if ((rc = make_contract_maps_at(ctx, maps, zhi, zlo, phi_hi, phi_lo, count, d, Ks, Nt, Kpad, TN, split)))
+        return rc;
+    // the array keeps the previous call's contents: the error word must start at zero
+    FMC_CUDA(ctx, cudaMemsetAsync(status, 0, 256, st), "memset");
+    FMC_CUDA(ctx, launch_contract_tc(maps, count, d, Ks, nkb, Nt, TN, split, dW_dev, status + 1, st),
              "tensor-core contraction");
     return FMC_OK;
 }
