@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=[None, "tol"],
+                    help="tol: LHS vs SRS (and precision forms) time to a stated error on E and Var")
+    ap.add_argument("--seeds", type=int, default=32)
     return ap.parse_args()
 
 
@@ -59,11 +62,16 @@ def workload(samples: int, horizon: float = 20.0):
 
 
 def algorithmic_flops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
-    """FP32 FMA-pipe work of one sample over one time step (FMA = 2 flop):
-    per RK stage 4n^2 (network products u, v) + 2n (Pe) + n d (forcing)
-    + 6n (speed/damping/RK accumulate/next-stage input); per step d (EM)."""
-    per_stage = 4 * n * n + 2 * n + n * d + 6 * n
-    return 2.0 * (integrator_stages * per_stage + d)
+    """FP32 work of one sample over one time step in the deviation form of the
+    swing equations, counted as FMA-pipe operations (each FMA, multiply or add
+    = one operation = 2 flop at the FMA rate).  Per RK stage and machine:
+    sin/cos series of the angle deviation 11, cos/sin expansion (gamma, eta) 4,
+    network products 4(n-1), electrical-power deviation 6, forcing d,
+    derivatives 5, RK accumulate and next-stage input 4; per step the state
+    update 2n and Euler-Maruyama plus stage forcing 6d."""
+    per_stage = n * (4 * (n - 1) + 30 + d)
+    ops = integrator_stages * per_stage + 2 * n + 6 * d
+    return 2.0 * ops
 
 
 class ClockSampler:
@@ -121,6 +129,24 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the
+    kernel sources still match the profiled ones (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "simulate_fused_kernel_ieee39_N65536.traffic.txt")
+    try:
+        kv = dict(line.split(None, 1) for line in open(path) if line.strip() and not line.startswith("#"))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in ("simulate_fused.cuh", "swing.cuh", "tc_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2007_03847_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != kv.get("source_sha256", "").strip():
+        return None
+    return float(kv["dram_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -194,10 +220,81 @@ def run_reference(args):
     return 0
 
 
+def run_tol_study(args):
+    """Time to a stated error on the expectation and variance trajectories.
+
+    Reference moments: an LHS design of 2^22 samples (blocks of 2^18 combined by
+    their shifted sums).  For N = 2^6 .. 2^16 and R seeds per N, the error of a
+    run is max_{t,s} |E_N - E_ref| / max sqrt(Var_ref) for the expectation and
+    max |Var_N - Var_ref| / max Var_ref for the variance; err(N) is the RMS over
+    the seeds.  Time to tolerance tau = device time of one run at the smallest N
+    with err(N) <= tau.  Forms: fused BF16x3 LHS (the chosen form), fused BF16x3
+    SRS, fused BF16 LHS, plain FP32 LHS.
+    """
+    import torch
+
+    import paper_2007_03847_gb300 as fmc
+    fmc.build()
+    ctx = fmc.Context(0)
+    base = workload(1 << 22, args.horizon)
+    # reference
+    blk = 1 << 18
+    S1 = S2 = shift = None
+    for k0 in range(0, base.N, blk):
+        a, b, sh = fmc.simulate_sums(base, k0, blk, ctx=ctx)
+        S1 = a if S1 is None else S1 + a
+        S2 = b if S2 is None else S2 + b
+        shift = sh
+    mref, vref = fmc.moments_from_sums(S1, S2, shift, base.N, ctx=ctx)
+    mref, vref = mref.cpu().numpy(), vref.cpu().numpy()
+    escale = float(np.sqrt(vref.max()))
+    vscale = float(vref.max())
+    forms = [("fused-bf16x3-LHS", "fused", "bf16x3", fs.LHS), ("fused-bf16x3-SRS", "fused", "bf16x3", fs.SRS),
+             ("fused-bf16-LHS", "fused", "bf16", fs.LHS), ("plain-f32-LHS", "plain", "f32", fs.LHS)]
+    Ns = [1 << e for e in range(6, 17)]
+    out = {"workload": WORKLOAD.replace("N=2^16", "N varied"), "reference_samples": base.N, "seeds": args.seeds,
+           "error_definition": "E: max|E_N-E_ref|/max sqrt(Var_ref); Var: max|Var_N-Var_ref|/max Var_ref; RMS over seeds",
+           "forms": {}}
+    for name, path, prec, samp in forms:
+        rows = []
+        for N in Ns:
+            errs_e, errs_v, times = [], [], []
+            for r in range(args.seeds):
+                sc = base.replace(N=N, seed=1000 + r, sampling=samp)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                m, v = fmc.simulate(sc, path=path, precision=prec, ctx=ctx)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+                m, v = m.cpu().numpy(), v.cpu().numpy()
+                errs_e.append(np.max(np.abs(m - mref)) / escale)
+                errs_v.append(np.max(np.abs(v - vref)) / vscale)
+            rows.append({"N": N, "err_E": float(np.sqrt(np.mean(np.square(errs_e)))),
+                         "err_Var": float(np.sqrt(np.mean(np.square(errs_v)))),
+                         "ms": float(np.median(times))})
+        # a single run below one wave of resident CTAs costs the same latency for
+        # any N; the throughput time charges N samples at the full-GPU rate
+        per_sample_ms = rows[-1]["ms"] / rows[-1]["N"]
+        ttt = {}
+        for tau in (1e-1, 3e-2, 1e-2, 3e-3):
+            for key in ("err_E", "err_Var"):
+                hit = next((r for r in rows if r[key] <= tau), None)
+                ttt[f"{key}<={tau:g}"] = None if hit is None else {
+                    "N": hit["N"], "latency_ms": hit["ms"], "throughput_ms": hit["N"] * per_sample_ms}
+        out["forms"][name] = {"rows": rows, "time_to_tol": ttt}
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.study == "tol":
+        return run_tol_study(args)
     import torch
     import torch.distributed as dist
 
@@ -214,16 +311,25 @@ def main():
     sms, gpu_name = ctx.info()
     path = args.path
     precision = args.precision or ("f32" if path == "plain" else "bf16x3")
-    sc = workload(args.samples, args.horizon)
+    # weak scaling: every rank simulates `samples` samples, its own block of one
+    # design of samples * world samples; the moment sums meet in one all-reduce
+    sc = workload(args.samples * world, args.horizon)
     n, Nt = sc.n, sc.Nt
-    units_per_step = sc.N * Nt * n
+    from paper_2007_03847_gb300.distributed import shard_range
+    k0, count = shard_range(sc.N, world, rank)
+    units_per_step = count * Nt * n
 
     # L2 is flushed between timed steps by writing a buffer larger than it
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        return fmc.simulate(sc, path=path, precision=precision, ctx=ctx)
+        if world == 1:
+            return fmc.simulate(sc, path=path, precision=precision, ctx=ctx)
+        S1, S2, shift = fmc.simulate_sums(sc, k0, count, path=path, precision=precision, ctx=ctx)
+        dist.all_reduce(S1)
+        dist.all_reduce(S2)
+        return fmc.moments_from_sums(S1, S2, shift, sc.N, ctx=ctx)
 
     for _ in range(args.warmup):
         step()
@@ -260,20 +366,23 @@ def main():
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     total_ms = float(t_max.item())
     ms_per_step = total_ms / args.steps
-    value = units_per_step * world / (ms_per_step / 1e3)
+    value = sc.N * Nt * n / (ms_per_step / 1e3)
 
     # roofline of the dominant kernel: FP32 FMA pipe
     kernel_ms = k_ms / max(1, k_launches)
-    flops_per_launch = algorithmic_flops_per_sample_step(n, sc.d) * sc.N * Nt
+    flops_per_launch = algorithmic_flops_per_sample_step(n, sc.d) * count * Nt
     achieved_tflops = flops_per_launch / (kernel_ms / 1e3) / 1e12
     mhz = clk.get("sm_mhz") or (measured_peaks() or {}).get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    traffic = profiled_traffic() if (path == "fused" and precision == "bf16x3" and sc.N == (1 << 16)
+                                     and Nt == 4000 and world == 1) else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak_tflops, "traffic": None,
+                "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                 "kernel": "simulate_fused_kernel" if path == "fused" else "simulate_plain_kernel",
                 "kernel_ms": kernel_ms,
                 "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (median SM clock "
-                             f"sampled during the timed region)"}
+                             f"sampled during the timed region); achieved counts the method's FP32 operations "
+                             f"({algorithmic_flops_per_sample_step(n, sc.d) / 2:.0f} per sample-step) at 2 flop each"}
 
     # end to end through the public API: scenario from host memory, moments read back
     e2e = None
@@ -291,7 +400,7 @@ def main():
             torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
         d2h = host_mean.numel() * 8 * 2
-        e2e = {"value": units_per_step * world / e2e_s, "unit": "machine-steps/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": sc.N * Nt * n / e2e_s, "unit": "machine-steps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     base = None
@@ -304,7 +413,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "f32" else f"f32+{precision}",
             "data": "synthetic (seeded system and LHS design)",
-            "config": {"workload": WORKLOAD, "path": path, "precision": precision, "samples_per_gpu": sc.N,
+            "config": {"workload": WORKLOAD, "path": path, "precision": precision, "samples_per_gpu": count,
                        "steps_per_sample": Nt, "machines": n, "disturbances": sc.d, "K": sc.K,
                        "l2": "flushed between timed steps (512 MB write)", "gpu": gpu_name, "sms": sms},
             "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline, "cpu_baseline": base,
