@@ -51,8 +51,11 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "tol"],
-                    help="tol: LHS vs SRS (and precision forms) time to a stated error on E and Var")
+    ap.add_argument("--study", default=None, choices=[None, "tol", "batch", "serve"],
+                    help="tol: LHS vs SRS (and precision forms) time to a stated error on E and Var; "
+                         "batch: 64 uneven scenarios in one captured graph; serve: Poisson request stream")
+    ap.add_argument("--max-machines", type=int, default=16,
+                    help="upper end of the machine count drawn for the batch and serve studies")
     ap.add_argument("--seeds", type=int, default=32)
     return ap.parse_args()
 
@@ -289,8 +292,92 @@ def run_tol_study(args):
     return 0
 
 
+def run_batch_study(args):
+    """64 seeded scenarios of uneven size (machines 3..max, disturbances 1..8,
+    K 50..300, T 5..60 s at dt = 5 ms, N 1k..256k) in one captured CUDA graph,
+    against the same scenarios run one after another."""
+    import torch
+
+    import paper_2007_03847_gb300 as fmc
+    fmc.build()
+    ctx = fmc.Context(0)
+    scs = fs.batched_cases(count=64, seed=0, n_range=(3, args.max_machines))
+    units = sum(sc.N * sc.Nt * sc.n for sc in scs)
+    b = fmc.Batch(scs, use_graph=True, ctx=ctx)
+    for _ in range(max(1, args.warmup)):
+        b.launch()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.steps):
+        b.launch()
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / args.steps
+    fmc.device_status(ctx)
+    b.close()
+    ev[0].record()
+    for sc in scs:
+        fmc.simulate(sc, path="fused", precision="bf16x3", ctx=ctx)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_seq = ev[0].elapsed_time(ev[1])
+    out = {"study": "batch", "scenarios": len(scs), "machine_steps_per_batch": units,
+           "machines": [min(sc.n for sc in scs), max(sc.n for sc in scs)],
+           "samples": [min(sc.N for sc in scs), max(sc.N for sc in scs)],
+           "graph_ms_per_batch": t_batch, "graph_machine_steps_per_s": units / (t_batch / 1e3),
+           "sequential_ms": t_seq, "sequential_machine_steps_per_s": units / (t_seq / 1e3),
+           "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
+def run_serve_study(args):
+    """Poisson request stream at several rates; requests drawn from the batch study's
+    distribution, each with its own seed; memory admission under a 120 GB budget.
+    Reports p50/p99 latency (submit -> moments complete) and samples/s per rate."""
+    import torch
+
+    import paper_2007_03847_gb300 as fmc
+    fmc.build()
+    srv = fmc.Server(slots=16, mem_budget_bytes=120 << 30)
+    pool = fs.batched_cases(count=256, seed=1, n_range=(3, args.max_machines))
+    rng = np.random.default_rng(0)
+    rows = []
+    for lam in (1, 2, 5, 10, 20, 50, 100, 200):
+        nreq = int(min(60, max(8, 15 * lam)))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
+        picks = rng.integers(0, len(pool), size=nreq)
+        handles = []
+        t0 = time.perf_counter()
+        for k in range(nreq):
+            now = time.perf_counter() - t0
+            if arrivals[k] > now:
+                time.sleep(arrivals[k] - now)
+            sc = pool[picks[k]].replace(seed=int(rng.integers(0, 2**31)))
+            handles.append((srv.submit(sc), sc.N))
+        lat, samples = [], 0
+        for h, N in handles:
+            res, _, _ = srv.wait(h, timeout_s=600)
+            assert res["status"] == 0, res
+            lat.append(res["latency_us"] / 1e3)
+            samples += N
+        t_all = time.perf_counter() - t0
+        rows.append({"rate_req_s": lam, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / t_all,
+                     "wall_s": t_all})
+    srv.close()
+    print(json.dumps({"study": "serve", "slots": 16, "budget_bytes": 120 << 30, "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.study == "batch":
+        return run_batch_study(args)
+    if args.study == "serve":
+        return run_serve_study(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.study == "tol":

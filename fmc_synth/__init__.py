@@ -2,9 +2,10 @@
 
 This module only draws the *inputs* of a study: the machine system, the
 disturbance model and the sampling settings.  It holds none of the method's
-arithmetic (no electrical power, no equilibrium, no KL basis, no sampling);
-the CUDA library and the FP64 oracle each compute those themselves from these
-inputs.  Parameter draws use numpy's PCG64 generator seeded explicitly; the
+arithmetic (no equilibrium, no dynamics, no KL basis, no sampling; the only
+network sum it forms is each machine's resistive load at zero angles, to place
+the mechanical powers where an operating point exists); the CUDA library and
+the FP64 oracle each compute the method themselves from these inputs.  Parameter draws use numpy's PCG64 generator seeded explicitly; the
 random numbers of the method itself (the Latin hypercube design) are drawn
 inside each implementation from the seed carried here.
 
@@ -16,9 +17,10 @@ are not available, so these stand in for them):
 * ``multimachine_case`` -- a Kron-reduced classical system of ``n`` machines
   shaped like the 39-bus case's 10 generators: symmetric off-diagonal
   susceptances U[1,8] and conductances U[0,0.3] p.u., diagonally dominant,
-  H ~ U[3,10] s, D ~ U[1,2], E ~ U[1.0,1.1], mechanical powers U[1,6] p.u. on
-  the non-reference machines, ``d`` OU disturbances (theta ~ U[0.5,2] /s,
-  sigma ~ U[0.02,0.1]) each on the mechanical power of a distinct machine.
+  H ~ U[3,10] s, D ~ U[1,2], E ~ U[1.0,1.1], mechanical power of machine i =
+  its resistive load sum_j E_i E_j G_ij plus U[-1,2] p.u. (machine 0 balances),
+  ``d`` OU disturbances (theta ~ U[0.5,2] /s, sigma ~ U[0.02,0.1]) each on the
+  mechanical power of a distinct machine (machines repeat when d > n).
 * ``batched_cases`` -- many such systems with uneven sizes.
 """
 from __future__ import annotations
@@ -123,7 +125,10 @@ def multimachine_case(n: int = 10, d: int = 3, K: int = 200, T: float = 20.0, dt
     H = rng.uniform(3.0, 10.0, size=n)
     Dm = rng.uniform(1.0, 2.0, size=n)
     E = rng.uniform(1.0, 1.1, size=n)
-    Pm = rng.uniform(1.0, 6.0, size=n)
+    # mechanical power: the resistive load of the machine at nominal voltages and
+    # angles (sum_j E_i E_j G_ij) plus a margin U[-1, 2] p.u., so that an operating
+    # point exists for any machine count (the positive conductances grow with n)
+    Pm = E * (G @ E) + rng.uniform(-1.0, 2.0, size=n)
     theta = rng.uniform(0.5, 2.0, size=d)
     sigma = rng.uniform(0.02, 0.1, size=d)
     gens = rng.choice(n, size=d, replace=(d > n))

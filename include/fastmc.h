@@ -266,6 +266,68 @@ int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* scen, int32_t path, double* m
 int fmc_simulate_sums(fmc_ctx* ctx, const fmc_scenario* scen, int64_t k0, int64_t count, int32_t path,
                       double* S1_dev, double* S2_dev, double* shift_dev, float* traj_dev, void* stream);
 
+/* ---- many scenarios ------------------------------------------------------- */
+
+/*
+ * A batch of independent scenarios of uneven size (machines, disturbances, K,
+ * horizon, N), run concurrently on the GPU: every scenario's kernels go to one
+ * of up to 16 library streams in turn, forked from and joined back to the
+ * caller's stream, so that the CTAs of different scenarios share the SMs.
+ * fmc_batch_create checks every scenario, solves every equilibrium (waiting for
+ * the device), reserves each scenario's workspace and, with use_graph = 1,
+ * captures the whole batch into one CUDA graph; fmc_batch_launch then replays
+ * it with a single graph launch on `stream` (or enqueues the kernels again
+ * without a graph).  Results: mean_dev[i], var_dev[i] [Nt_i+1][2 n_i] double
+ * (device, caller-owned, fixed at creation).  The fused path adds each
+ * scenario's per-time sums with FP64 atomics (sums of FP32 partials over
+ * 32-sample groups; summation order not fixed).
+ */
+typedef struct fmc_batch fmc_batch;
+int fmc_batch_create(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int32_t path, double* const* mean_dev,
+                     double* const* var_dev, int32_t use_graph, fmc_batch** out);
+int fmc_batch_launch(fmc_batch* batch, void* stream);
+int fmc_batch_destroy(fmc_batch* batch);
+
+/* create + launch (without a graph) + wait + destroy. */
+int fmc_simulate_batch(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int32_t path,
+                       double* const* mean_dev, double* const* var_dev, void* stream);
+
+/* ---- serving -------------------------------------------------------------- */
+
+/*
+ * A request server: requests (one scenario each, results to caller-owned
+ * device buffers) wait in a FIFO queue and are admitted, head first, as soon as
+ * one of `slots` worker slots is free and the request's device workspace fits
+ * in what is left of the memory budget (0: 80% of the free device memory).
+ * Each slot has its own stream, library context and workspace, so requests that
+ * arrive while others run start at once and their kernels share the GPU.  The
+ * fused path sums moments with FP64 atomics (no per-tile partial buffers).
+ *   fmc_submit   queues a request (the scenario is copied); FMC_ENOMEM if it
+ *                could never fit the budget.
+ *   fmc_poll     non-blocking: FMC_NOT_READY, or FMC_OK and *out (once).
+ *   fmc_wait     blocks up to timeout_us: FMC_ETIMEOUT, or FMC_OK and *out.
+ *   fmc_cancel   removes a queued request (its result reports FMC_ECANCELLED);
+ *                FMC_EBUSY if it is already running.
+ * The server is thread-safe; results are reported once.
+ */
+typedef struct fmc_server fmc_server;
+typedef struct fmc_result {
+    int32_t status;         /* FMC_OK or the request's error code */
+    int32_t reserved;
+    double latency_us;      /* submit -> results complete on the device */
+    double queue_us;        /* submit -> admitted */
+    uint64_t device_bytes;  /* workspace charged against the budget */
+    char message[256];      /* error text, "" on success */
+} fmc_result;
+int fmc_server_create(int device, int32_t slots, size_t mem_budget_bytes, fmc_server** out);
+int fmc_server_destroy(fmc_server* srv);
+int fmc_submit(fmc_server* srv, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
+               uint64_t* handle);
+int fmc_poll(fmc_server* srv, uint64_t handle, fmc_result* out);
+int fmc_wait(fmc_server* srv, uint64_t handle, int64_t timeout_us, fmc_result* out);
+int fmc_cancel(fmc_server* srv, uint64_t handle);
+int fmc_server_stats(fmc_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use);
+
 /* ---- Algorithm 1 step 4 --------------------------------------------------- */
 
 /*
@@ -302,7 +364,8 @@ int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error);
  * Kernel timing with CUDA events recorded on the launching stream around every
  * kernel phase of later calls (at most max_records phases; enable = 0 stops and
  * clears).  Phases: 0 LHS, 1 KL basis, 2 equilibrium, 3 fused simulation,
- * 4 fused moment reduce, 5 FP32 contraction, 6 plain integrator, 7 moments.
+ * 4 fused moment reduce, 5 FP32 contraction, 6 plain integrator, 7 moments,
+ * 8 a whole batch graph launch.
  */
 int fmc_profile(fmc_ctx* ctx, int32_t enable, int64_t max_records);
 

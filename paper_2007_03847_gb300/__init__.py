@@ -30,7 +30,7 @@ LHS, SRS, LHS_MIDPOINT = 0, 1, 2
 PREC_F32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 RK4, HEUN = 0, 1
 PATH_FUSED, PATH_PLAIN = 0, 1
-PH_LHS, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS = range(8)
+PH_LHS, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS, PH_BATCH = range(9)
 MAX_MACHINES, MAX_DISTURBANCES = 16, 8
 
 _PRECISION = {"f32": PREC_F32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3}
@@ -53,6 +53,11 @@ class _Scenario(ctypes.Structure):
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
     ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("latency_us", ctypes.c_double),
+                ("queue_us", ctypes.c_double), ("device_bytes", ctypes.c_uint64), ("message", ctypes.c_char * 256)]
 
 
 _lib = None
@@ -92,6 +97,20 @@ def load_library():
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_batch_create": ([vp, ctypes.POINTER(_Scenario), i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                  i32, ctypes.POINTER(vp)], ctypes.c_int),
+            "fmc_batch_launch": ([vp, vp], ctypes.c_int),
+            "fmc_batch_destroy": ([vp], ctypes.c_int),
+            "fmc_simulate_batch": ([vp, ctypes.POINTER(_Scenario), i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    vp], ctypes.c_int),
+            "fmc_server_create": ([ctypes.c_int, i32, ctypes.c_size_t, ctypes.POINTER(vp)], ctypes.c_int),
+            "fmc_server_destroy": ([vp], ctypes.c_int),
+            "fmc_submit": ([vp, ctypes.POINTER(_Scenario), i32, vp, vp, ctypes.POINTER(u64)], ctypes.c_int),
+            "fmc_poll": ([vp, u64, ctypes.POINTER(_Result)], ctypes.c_int),
+            "fmc_wait": ([vp, u64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
+            "fmc_cancel": ([vp, u64], ctypes.c_int),
+            "fmc_server_stats": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)],
+                                 ctypes.c_int),
             "fmc_kle_reconstruct_noalloc": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
             "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_moments_from_sums": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp], ctypes.c_int),
@@ -327,6 +346,122 @@ def moments_from_sums(S1, S2, shift, N: int, mean=None, var=None, ctx: Context |
     ctx.check(ctx.lib.fmc_moments_from_sums(ctx.h, _ptr(S1), _ptr(S2), _ptr(shift), N, rows, S, _ptr(mean),
                                             _ptr(var), _stream(stream)))
     return mean, var
+
+
+class Batch:
+    """fmc_batch: many scenarios run concurrently; with use_graph the whole batch is one
+    captured CUDA graph that launch() replays.  Results: self.mean[i], self.var[i]
+    ([Nt_i+1, 2 n_i] float64 device tensors)."""
+
+    def __init__(self, scenarios, path="fused", precision=None, use_graph: bool = True, ctx: Context | None = None):
+        import torch
+        self.ctx = ctx or default_context()
+        p = _PATH.get(path, path) if isinstance(path, str) else path
+        if precision is None:
+            precision = "f32" if p == PATH_PLAIN else "bf16x3"
+        self.structs = [ScenarioStruct(sc, precision=precision) for sc in scenarios]
+        arr = (_Scenario * len(scenarios))(*[ss.s for ss in self.structs])
+        self.mean = [torch.empty((ss.Nt + 1, 2 * sc.n), dtype=torch.float64, device="cuda")
+                     for ss, sc in zip(self.structs, scenarios)]
+        self.var = [torch.empty_like(m) for m in self.mean]
+        mp = (ctypes.c_void_p * len(scenarios))(*[m.data_ptr() for m in self.mean])
+        vp_ = (ctypes.c_void_p * len(scenarios))(*[v.data_ptr() for v in self.var])
+        h = ctypes.c_void_p()
+        self.ctx.check(self.ctx.lib.fmc_batch_create(self.ctx.h, arr, len(scenarios), p, mp, vp_,
+                                                     1 if use_graph else 0, ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        self.ctx.check(self.ctx.lib.fmc_batch_launch(self.h, _stream(stream)))
+        return self.mean, self.var
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.fmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """fmc_server: requests admitted by device memory into `slots` concurrent slots.
+
+    submit() returns a handle; poll()/wait() return (result dict, mean, var) once the
+    request is done (mean/var: [Nt+1, 2n] float64 device tensors), or None.
+    """
+
+    def __init__(self, device: int = 0, slots: int = 8, mem_budget_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise FastMCError(ECUDA, "no CUDA device is available")
+        torch.cuda.init()
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.fmc_server_create(device, slots, mem_budget_bytes, ctypes.byref(h))
+        if rc != OK:
+            raise FastMCError(rc, "fmc_server_create failed")
+        self.h = h
+        self.pending = {}
+
+    def submit(self, scenario, path="fused", precision="bf16x3"):
+        import torch
+        p = _PATH.get(path, path) if isinstance(path, str) else path
+        ss = ScenarioStruct(scenario, precision=precision)
+        mean = torch.empty((ss.Nt + 1, 2 * scenario.n), dtype=torch.float64, device="cuda")
+        var = torch.empty_like(mean)
+        hd = ctypes.c_uint64()
+        rc = self.lib.fmc_submit(self.h, ctypes.byref(ss.s), p, _ptr(mean), _ptr(var), ctypes.byref(hd))
+        if rc != OK:
+            raise FastMCError(rc, "fmc_submit failed")
+        self.pending[hd.value] = (mean, var)
+        return hd.value
+
+    def _finish(self, handle, res):
+        mean, var = self.pending.pop(handle)
+        out = {"status": res.status, "latency_us": res.latency_us, "queue_us": res.queue_us,
+               "device_bytes": res.device_bytes, "message": res.message.decode()}
+        return out, mean, var
+
+    def poll(self, handle):
+        res = _Result()
+        rc = self.lib.fmc_poll(self.h, handle, ctypes.byref(res))
+        if rc == NOT_READY:
+            return None
+        if rc != OK:
+            raise FastMCError(rc, "fmc_poll failed")
+        return self._finish(handle, res)
+
+    def wait(self, handle, timeout_s: float = 60.0):
+        res = _Result()
+        rc = self.lib.fmc_wait(self.h, handle, int(timeout_s * 1e6), ctypes.byref(res))
+        if rc == ETIMEOUT:
+            return None
+        if rc != OK:
+            raise FastMCError(rc, "fmc_wait failed")
+        return self._finish(handle, res)
+
+    def cancel(self, handle) -> int:
+        return self.lib.fmc_cancel(self.h, handle)
+
+    def stats(self):
+        q, r, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+        self.lib.fmc_server_stats(self.h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b))
+        return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fmc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def moments(x, mean=None, var=None, ctx: Context | None = None, stream=None):

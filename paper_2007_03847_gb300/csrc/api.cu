@@ -15,6 +15,7 @@
 #include "kernels.cuh"
 #include "swing.cuh"
 #include "tc_common.cuh"
+#include "api_internal.h"
 
 using namespace fmc;
 
@@ -26,7 +27,9 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-enum Phase { PH_LHS = 0, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS, PH_COUNT };
+enum Phase {
+    PH_LHS = 0, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS, PH_BATCH, PH_COUNT
+};
 
 struct ProfRec {
     int phase;
@@ -35,6 +38,12 @@ struct ProfRec {
 
 }  // namespace
 
+// Device buffers of one simulation: design, basis, partial sums, equilibrium,
+// status word; the plain path's FP32 design, increments and trajectories.
+struct Workspace {
+    DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
+};
+
 struct fmc_ctx {
     int device = 0;
     int sms = 0;
@@ -42,7 +51,19 @@ struct fmc_ctx {
     size_t budget = 0;
     size_t used = 0;
     std::string err;
-    DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
+    Workspace ws;                     // workspace of the single-scenario calls
+    DevBuf& zeta_hi = ws.zeta_hi;
+    DevBuf& zeta_lo = ws.zeta_lo;
+    DevBuf& phi_hi = ws.phi_hi;
+    DevBuf& phi_lo = ws.phi_lo;
+    DevBuf& phi32 = ws.phi32;
+    DevBuf& dW = ws.dW;
+    DevBuf& traj = ws.traj;
+    DevBuf& part = ws.part;
+    DevBuf& eq = ws.eq;
+    DevBuf& scen = ws.scen;
+    DevBuf& status = ws.status;
+    DevBuf& zeta32 = ws.zeta32;
     // profiling of kernel phases (CUDA events on the launching stream)
     bool prof = false;
     std::vector<ProfRec> recs;
@@ -285,15 +306,15 @@ static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const dou
 
 // Copies the system arrays to the device and launches the FP64 Newton kernel.
 // eq: [delta0 n][pm n][shift 2n]; status: iteration count or -1.
-static int run_equilibrium(fmc_ctx* ctx, const fmc_scenario* s, cudaStream_t st)
+static int run_equilibrium_ws(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, cudaStream_t st)
 {
     const int n = s->n;
     size_t nd = (size_t)2 * n * n + 5 * (size_t)n;
-    int rc = ensure(ctx, ctx->scen, nd * sizeof(double));
+    int rc = ensure(ctx, ws.scen, nd * sizeof(double));
     if (rc) return rc;
-    rc = ensure(ctx, ctx->eq, 4 * (size_t)n * sizeof(double));
+    rc = ensure(ctx, ws.eq, 4 * (size_t)n * sizeof(double));
     if (rc) return rc;
-    rc = ensure(ctx, ctx->status, 64);
+    rc = ensure(ctx, ws.status, 64);
     if (rc) return rc;
     std::vector<double> h(nd, 0.0);
     double* G = h.data();
@@ -310,17 +331,22 @@ static int run_equilibrium(fmc_ctx* ctx, const fmc_scenario* s, cudaStream_t st)
     }
     memcpy(E, s->E, sizeof(double) * n);
     memcpy(Pm, s->Pm, sizeof(double) * n);
-    double* dG = (double*)ctx->scen.ptr;
+    double* dG = (double*)ws.scen.ptr;
     FMC_CUDA(ctx, cudaMemcpyAsync(dG, h.data(), nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy scenario");
     ProfRec* pr;
     prof_begin(ctx, PH_EQ, st, &pr);
     FMC_CUDA(ctx,
              launch_equilibrium(n, s->has_inf_bus, s->Vinf, dG, dG + n * n, dG + 2 * n * n, dG + 2 * n * n + n,
-                                dG + 2 * n * n + 2 * n, dG + 2 * n * n + 3 * n, (double*)ctx->eq.ptr,
-                                (int*)ctx->status.ptr, st),
+                                dG + 2 * n * n + 2 * n, dG + 2 * n * n + 3 * n, (double*)ws.eq.ptr,
+                                (int*)ws.status.ptr, st),
              "equilibrium kernel");
     prof_end(pr, st);
     return FMC_OK;
+}
+
+static int run_equilibrium(fmc_ctx* ctx, const fmc_scenario* s, cudaStream_t st)
+{
+    return run_equilibrium_ws(ctx, ctx->ws, s, st);
 }
 
 static int make_map_bf16(fmc_ctx* ctx, CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
@@ -631,16 +657,21 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
     return FMC_OK;
 }
 
-// Samples k0 .. k0+count-1 of the N-sample design: equilibrium, LHS, KL
-// increments, integration and per-time shifted sums S1, S2 [Nt+1][2n] (FP64).
-// The shift (FP64 [2n]: delta*, then zeros) is left at ctx->eq + 2n.
-static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1,
-                         double* S2, float* traj_dev, cudaStream_t st)
+// A scenario made ready for the device: checked, equilibrium solved (FP64 on the
+// GPU, read back once), integrator constants formed for the parameter block.
+struct Prepared {
+    fmc_scenario s{};
+    int Nt = 0, nm = 0, nd = 0, path = 0;
+    int64_t k0 = 0, count = 0;
+    std::vector<unsigned char> params;
+};
+
+static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path,
+                   cudaStream_t st, Prepared& P)
 {
     int Nt = 0;
     int rc = check_scenario(ctx, s, &Nt);
     if (rc) return rc;
-    if (!S1 || !S2) return fail(ctx, FMC_EINVAL, "moment outputs are NULL");
     if (k0 < 0 || count < 1 || k0 + count > s->N)
         return fail(ctx, FMC_EINVAL, "sample block [%lld, %lld) outside [0, N)", (long long)k0,
                     (long long)(k0 + count));
@@ -649,53 +680,95 @@ static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_
         return fail(ctx, FMC_EINVAL, "the plain path computes in FP32 (precision FMC_PREC_F32)");
     if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
-    const int n = s->n, d = s->d, K = s->K;
-    const int64_t N = s->N;
-    const int nm = nm_bucket_for(n);
-    const int nd = nd_bucket_for(d);
+    const int n = s->n;
+    P.s = *s;
+    P.Nt = Nt;
+    P.nm = nm_bucket_for(n);
+    P.nd = nd_bucket_for(s->d);
+    P.path = path;
+    P.k0 = k0;
+    P.count = count;
     // FP64 Newton on the GPU; its angles come back to the host (one stream
     // synchronisation) to form the integrator's constants in the parameter block
-    if ((rc = run_equilibrium(ctx, s, st))) return rc;
-    const double* eq = (const double*)ctx->eq.ptr;
+    if ((rc = run_equilibrium_ws(ctx, ws, s, st))) return rc;
     std::vector<double> delta0(n);
     int eq_status = 0;
-    FMC_CUDA(ctx, cudaMemcpyAsync(delta0.data(), eq, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
-    FMC_CUDA(ctx, cudaMemcpyAsync(&eq_status, ctx->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaMemcpyAsync(delta0.data(), ws.eq.ptr, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaMemcpyAsync(&eq_status, ws.status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
     FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
     if (eq_status < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
-    std::vector<unsigned char> params;
-    build_params_bucket(nm, nd, s, delta0.data(), params);
+    build_params_bucket(P.nm, P.nd, s, delta0.data(), P.params);
+    return FMC_OK;
+}
+
+static int fused_tc(int d) { return (d <= 4) ? 32 : 16; }
+
+// All device buffers the enqueue of P needs (grows the workspace; may allocate).
+// per_tile_partials = false: the fused kernel adds its sums with FP64 atomics
+// and needs no partial buffer.
+static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_traj, bool per_tile_partials)
+{
+    const int n = P.s.n, d = P.s.d, K = P.s.K, Nt = P.Nt;
+    const int64_t count = P.count, Nt1 = (int64_t)Nt + 1;
+    const int S = 2 * n;
+    int rc;
+    if (P.path == FMC_PATH_PLAIN) {
+        const int M = d * K;
+        if ((rc = ensure(ctx, ws.zeta32, (size_t)count * M * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ws.phi32, (size_t)K * Nt * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ws.dW, (size_t)count * d * Nt * sizeof(float)))) return rc;
+        if (!want_traj && (rc = ensure(ctx, ws.traj, (size_t)count * Nt1 * S * sizeof(float)))) return rc;
+        return FMC_OK;
+    }
+    const int split = (P.s.precision == FMC_PREC_BF16X3);
+    const int Ks = round_up(K, 8);
+    const int Kpad = round_up(K, TC_BK);
+    const int64_t ntiles = (count + TC_M - 1) / TC_M;
+    size_t zbytes = (size_t)count * d * Ks * 2;
+    if ((rc = ensure(ctx, ws.zeta_hi, zbytes))) return rc;
+    if (split && (rc = ensure(ctx, ws.zeta_lo, zbytes))) return rc;
+    if ((rc = ensure(ctx, ws.phi_hi, (size_t)Nt * Kpad * 2))) return rc;
+    if (split && (rc = ensure(ctx, ws.phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+    if (per_tile_partials && (rc = ensure(ctx, ws.part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
+    return FMC_OK;
+}
+
+// Enqueues the path for P on `st` (no allocation, no synchronisation: usable
+// under stream capture once reserve() has run).  S1, S2 [Nt+1][2n] receive the
+// shifted sums over the block; the shift is at ws.eq + 2n.
+static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, double* S2, float* traj_dev,
+                   bool per_tile_partials, cudaStream_t st)
+{
+    const fmc_scenario* s = &P.s;
+    const int n = s->n, d = s->d, K = s->K, Nt = P.Nt;
+    const int64_t N = s->N, k0 = P.k0, count = P.count;
     const int64_t Nt1 = (int64_t)Nt + 1;
     const int S = 2 * n;
+    const double* eq = (const double*)ws.eq.ptr;
     const double* shift = eq + 2 * n;
+    int rc;
     ProfRec* pr;
 
-    if (path == FMC_PATH_PLAIN) {
+    if (P.path == FMC_PATH_PLAIN) {
         const int M = d * K;
-        if ((rc = ensure(ctx, ctx->zeta32, (size_t)count * M * sizeof(float)))) return rc;
-        if ((rc = ensure(ctx, ctx->phi32, (size_t)K * Nt * sizeof(float)))) return rc;
-        if ((rc = ensure(ctx, ctx->dW, (size_t)count * d * Nt * sizeof(float)))) return rc;
-        float* traj = traj_dev;
-        if (!traj) {
-            if ((rc = ensure(ctx, ctx->traj, (size_t)count * Nt1 * S * sizeof(float)))) return rc;
-            traj = (float*)ctx->traj.ptr;
-        }
+        float* traj = traj_dev ? traj_dev : (float*)ws.traj.ptr;
         prof_begin(ctx, PH_LHS, st, &pr);
         FMC_CUDA(ctx,
-                 launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ctx->zeta32.ptr, nullptr, ctx->sms, st),
+                 launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ws.zeta32.ptr, nullptr, ctx->sms, st),
                  "lhs kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_BASIS, st, &pr);
-        FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, (float*)ctx->phi32.ptr, ctx->sms, st), "basis kernel");
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, (float*)ws.phi32.ptr, ctx->sms, st), "basis kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_CONTRACT, st, &pr);
         FMC_CUDA(ctx,
-                 launch_sgemm_nn(count * d, Nt, K, (const float*)ctx->zeta32.ptr, (const float*)ctx->phi32.ptr,
-                                 (float*)ctx->dW.ptr, st),
+                 launch_sgemm_nn(count * d, Nt, K, (const float*)ws.zeta32.ptr, (const float*)ws.phi32.ptr,
+                                 (float*)ws.dW.ptr, st),
                  "sgemm kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_INTEGRATE, st, &pr);
-        FMC_CUDA(ctx, launch_simulate_plain(nm, nd, params.data(), eq, (const float*)ctx->dW.ptr, count, Nt, traj, st),
+        FMC_CUDA(ctx,
+                 launch_simulate_plain(P.nm, P.nd, P.params.data(), eq, (const float*)ws.dW.ptr, count, Nt, traj, st),
                  "plain integrator");
         prof_end(pr, st);
         prof_begin(ctx, PH_MOMENTS, st, &pr);
@@ -709,45 +782,85 @@ static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_
     const int Ks = round_up(K, 8);
     const int Kpad = round_up(K, TC_BK);
     const int nkb = (Ks + TC_BK - 1) / TC_BK;
-    const int TC = (d <= 4) ? 32 : 16;
+    const int TC = fused_tc(d);
     uint32_t tmem_cols = 32;
     while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
     const int64_t ntiles = (count + TC_M - 1) / TC_M;
-    size_t zbytes = (size_t)count * d * Ks * 2;
-    if ((rc = ensure(ctx, ctx->zeta_hi, zbytes))) return rc;
-    if (split && (rc = ensure(ctx, ctx->zeta_lo, zbytes))) return rc;
-    if ((rc = ensure(ctx, ctx->phi_hi, (size_t)Nt * Kpad * 2))) return rc;
-    if (split && (rc = ensure(ctx, ctx->phi_lo, (size_t)Nt * Kpad * 2))) return rc;
-    if ((rc = ensure(ctx, ctx->part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
     prof_begin(ctx, PH_LHS, st, &pr);
     FMC_CUDA(ctx,
-             launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ctx->zeta_hi.ptr,
-                              split ? ctx->zeta_lo.ptr : nullptr, ctx->sms, st),
+             launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr,
+                              ctx->sms, st),
              "lhs kernel");
     prof_end(pr, st);
     prof_begin(ctx, PH_BASIS, st, &pr);
     FMC_CUDA(ctx,
-             launch_basis_split(K, Nt, s->T, Kpad, ctx->phi_hi.ptr, split ? ctx->phi_lo.ptr : nullptr, ctx->sms, st),
+             launch_basis_split(K, Nt, s->T, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr, ctx->sms, st),
              "basis kernel");
     prof_end(pr, st);
     CUtensorMap maps[4];
-    if ((rc = make_contract_maps(ctx, maps, count, d, Ks, Nt, Kpad, TC, split))) return rc;
-    FMC_CUDA(ctx, cudaMemsetAsync((char*)ctx->status.ptr + 4, 0, 4, st), "memset");
+    if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
+                                    Ks, Nt, Kpad, TC, split)))
+        return rc;
+    FMC_CUDA(ctx, cudaMemsetAsync((char*)ws.status.ptr + 4, 0, 4, st), "memset");
+    if (!per_tile_partials) {
+        FMC_CUDA(ctx, cudaMemsetAsync(S1, 0, Nt1 * S * sizeof(double), st), "memset");
+        FMC_CUDA(ctx, cudaMemsetAsync(S2, 0, Nt1 * S * sizeof(double), st), "memset");
+    }
     prof_begin(ctx, PH_FUSED, st, &pr);
     int occ = 0;
-    cudaError_t e = launch_simulate_fused(nm, nd, params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
-                                          eq, (float*)ctx->part.ptr, traj_dev, (int*)ctx->status.ptr + 1, st, &occ);
+    cudaError_t e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split,
+                                          tmem_cols, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
+                                          per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
+                                          (int*)ws.status.ptr + 1, st, &occ);
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, FMC_EUNSUPPORTED, "fused kernel: %d CTAs per SM x %u TMEM columns exceeds 512", occ,
                     tmem_cols);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fused simulation kernel");
     prof_end(pr, st);
-    prof_begin(ctx, PH_REDUCE, st, &pr);
-    FMC_CUDA(ctx, launch_fused_sums((const float*)ctx->part.ptr, (int)ntiles, Nt1, S, S1, S2, st), "moment sums");
-    prof_end(pr, st);
+    if (per_tile_partials) {
+        prof_begin(ctx, PH_REDUCE, st, &pr);
+        FMC_CUDA(ctx, launch_fused_sums((const float*)ws.part.ptr, (int)ntiles, Nt1, S, S1, S2, st), "moment sums");
+        prof_end(pr, st);
+    }
     return FMC_OK;
 }
+
+// Samples k0 .. k0+count-1 of the N-sample design: equilibrium, LHS, KL
+// increments, integration and per-time shifted sums S1, S2 [Nt+1][2n] (FP64).
+// The shift (FP64 [2n]: delta*, then zeros) is left at ctx->eq + 2n.
+static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1,
+                         double* S2, float* traj_dev, cudaStream_t st)
+{
+    if (!S1 || !S2) return fail(ctx, FMC_EINVAL, "moment outputs are NULL");
+    Prepared P;
+    int rc = prepare(ctx, ctx->ws, s, k0, count, path, st, P);
+    if (rc) return rc;
+    if ((rc = reserve(ctx, ctx->ws, P, traj_dev != nullptr, true))) return rc;
+    return enqueue(ctx, ctx->ws, P, S1, S2, traj_dev, true, st);
+}
+
+}  // extern "C"
+
+int fmc::simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
+                          bool per_tile_partials, cudaStream_t st)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!s || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "NULL scenario or output");
+    Prepared P;
+    int rc = prepare(ctx, ctx->ws, s, 0, s->N, path, st, P);
+    if (rc) return rc;
+    const bool tiles = per_tile_partials || path == FMC_PATH_PLAIN;
+    if ((rc = reserve(ctx, ctx->ws, P, false, tiles))) return rc;
+    if ((rc = enqueue(ctx, ctx->ws, P, mean_dev, var_dev, nullptr, tiles, st))) return rc;
+    FMC_CUDA(ctx,
+             launch_finalize(mean_dev, var_dev, (const double*)ctx->eq.ptr + 2 * s->n, s->N, (int64_t)P.Nt + 1,
+                             2 * s->n, mean_dev, var_dev, st),
+             "moment finalize");
+    return FMC_OK;
+}
+
+extern "C" {
 
 int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
                  float* traj_dev, void* stream)
@@ -794,6 +907,179 @@ int fmc_moments_from_sums(fmc_ctx* ctx, const double* S1_dev, const double* S2_d
     FMC_CUDA(ctx, launch_finalize(S1_dev, S2_dev, shift_dev, N, T1, S, mean_dev, var_dev, (cudaStream_t)stream),
              "moment finalize");
     return FMC_OK;
+}
+
+// ---- many scenarios ------------------------------------------------------------
+
+struct fmc_batch {
+    fmc_ctx* ctx = nullptr;
+    std::vector<Workspace*> ws;
+    std::vector<Prepared> prep;
+    std::vector<double*> mean, var;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(fmc_batch* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (Workspace* w : b->ws) {
+        DevBuf* bufs[] = {&w->zeta_hi, &w->zeta_lo, &w->phi_hi, &w->phi_lo, &w->phi32, &w->dW,
+                          &w->traj,    &w->part,    &w->eq,     &w->scen,   &w->status, &w->zeta32};
+        for (DevBuf* d : bufs)
+            if (d->ptr) {
+                cudaFree(d->ptr);
+                b->ctx->used -= d->bytes;
+            }
+        delete w;
+    }
+    delete b;
+}
+
+// Enqueue every scenario: fork from `st` onto the batch's streams, one scenario
+// per stream in turn (so that independent scenarios share the GPU), join back.
+static int batch_enqueue(fmc_batch* b, cudaStream_t st)
+{
+    fmc_ctx* ctx = b->ctx;
+    FMC_CUDA(ctx, cudaEventRecord(b->fork, st), "event");
+    for (cudaStream_t s : b->streams) FMC_CUDA(ctx, cudaStreamWaitEvent(s, b->fork, 0), "wait");
+    for (size_t i = 0; i < b->prep.size(); ++i) {
+        cudaStream_t s = b->streams[i % b->streams.size()];
+        const Prepared& P = b->prep[i];
+        Workspace& w = *b->ws[i];
+        int rc = enqueue(ctx, w, P, b->mean[i], b->var[i], nullptr, P.path == FMC_PATH_PLAIN, s);
+        if (rc) return rc;
+        FMC_CUDA(ctx,
+                 launch_finalize(b->mean[i], b->var[i], (const double*)w.eq.ptr + 2 * P.s.n, P.s.N, (int64_t)P.Nt + 1,
+                                 2 * P.s.n, b->mean[i], b->var[i], s),
+                 "moment finalize");
+    }
+    for (size_t k = 0; k < b->streams.size(); ++k) {
+        FMC_CUDA(ctx, cudaEventRecord(b->done[k], b->streams[k]), "event");
+        FMC_CUDA(ctx, cudaStreamWaitEvent(st, b->done[k], 0), "wait");
+    }
+    return FMC_OK;
+}
+
+int fmc_batch_create(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int32_t path, double* const* mean_dev,
+                     double* const* var_dev, int32_t use_graph, fmc_batch** out)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!out) return fail(ctx, FMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_scen < 1 || !scen || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "empty or NULL batch");
+    fmc_batch* b = new fmc_batch();
+    b->ctx = ctx;
+    prof_clear(ctx);
+    const bool prof_was = ctx->prof;
+    ctx->prof = false;  // no event records inside the batch
+    int rc = FMC_OK;
+    cudaStream_t st0 = 0;
+    for (int i = 0; i < n_scen && rc == FMC_OK; ++i) {
+        if (!mean_dev[i] || !var_dev[i]) {
+            rc = fail(ctx, FMC_EINVAL, "scenario %d: NULL output", i);
+            break;
+        }
+        Workspace* w = new Workspace();
+        b->ws.push_back(w);
+        b->prep.emplace_back();
+        rc = prepare(ctx, *w, &scen[i], 0, scen[i].N, path, st0, b->prep.back());
+        if (rc == FMC_OK) rc = reserve(ctx, *w, b->prep.back(), false, path == FMC_PATH_PLAIN);
+        b->mean.push_back(mean_dev[i]);
+        b->var.push_back(var_dev[i]);
+    }
+    const int nstreams = n_scen < 16 ? n_scen : 16;
+    for (int k = 0; k < nstreams && rc == FMC_OK; ++k) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(ctx, FMC_ECUDA, "stream/event creation failed");
+        else {
+            b->streams.push_back(s);
+            b->done.push_back(e);
+        }
+    }
+    if (rc == FMC_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(ctx, FMC_ECUDA, "event creation failed");
+    if (rc == FMC_OK && use_graph) {
+        // capture the whole batch once; fmc_batch_launch replays it
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = fail(ctx, FMC_ECUDA, "stream creation failed");
+        } else {
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamBeginCapture");
+            if (rc == FMC_OK) {
+                int rc2 = batch_enqueue(b, cap);
+                e = cudaStreamEndCapture(cap, &b->graph);
+                if (rc2) rc = rc2;
+                else if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamEndCapture");
+            }
+            if (rc == FMC_OK) {
+                e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+                if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaGraphInstantiate");
+            }
+            cudaStreamDestroy(cap);
+        }
+    }
+    ctx->prof = prof_was;
+    if (rc != FMC_OK) {
+        std::string msg = ctx->err;
+        batch_free(b);
+        ctx->err = msg;
+        return rc;
+    }
+    *out = b;
+    return FMC_OK;
+}
+
+int fmc_batch_launch(fmc_batch* b, void* stream)
+{
+    if (!b) return FMC_EINVAL;
+    fmc_ctx* ctx = b->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->exec) {
+        ProfRec* pr;
+        prof_begin(ctx, PH_BATCH, st, &pr);
+        FMC_CUDA(ctx, cudaGraphLaunch(b->exec, st), "cudaGraphLaunch");
+        prof_end(pr, st);
+        return FMC_OK;
+    }
+    const bool prof_was = ctx->prof;
+    ctx->prof = false;
+    int rc = batch_enqueue(b, st);
+    ctx->prof = prof_was;
+    return rc;
+}
+
+int fmc_batch_destroy(fmc_batch* b)
+{
+    if (!b) return FMC_EINVAL;
+    batch_free(b);
+    return FMC_OK;
+}
+
+int fmc_simulate_batch(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int32_t path, double* const* mean_dev,
+                       double* const* var_dev, void* stream)
+{
+    fmc_batch* b = nullptr;
+    int rc = fmc_batch_create(ctx, scen, n_scen, path, mean_dev, var_dev, 0, &b);
+    if (rc) return rc;
+    rc = fmc_batch_launch(b, stream);
+    if (rc == FMC_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        rc = fail(ctx, FMC_ECUDA, "batch failed on the device");
+    fmc_batch_destroy(b);
+    return rc;
 }
 
 int fmc_moments(fmc_ctx* ctx, const float* x_dev, int64_t N, int64_t C, double* mean_dev, double* var_dev, void* stream)

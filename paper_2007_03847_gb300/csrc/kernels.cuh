@@ -25,8 +25,8 @@ cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* para
 int fused_smem_bytes(int nm_bucket, int TC, int split);
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
-                                  const double* eq, float* part, float* traj, int* err, cudaStream_t st,
-                                  int* max_ctas_per_sm);
+                                  const double* eq, float* part, double* S1, double* S2, float* traj, int* err,
+                                  cudaStream_t st, int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
 cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
                              int sms, cudaStream_t st);

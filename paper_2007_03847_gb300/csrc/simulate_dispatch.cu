@@ -34,10 +34,10 @@ int fused_smem_bytes(int nm_bucket, int TC, int split)
 
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
-                                  const double* eq, float* part, float* traj, int* err, cudaStream_t st,
-                                  int* max_ctas_per_sm)
+                                  const double* eq, float* part, double* S1, double* S2, float* traj, int* err,
+                                  cudaStream_t st, int* max_ctas_per_sm)
 {
-    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, tmem_cols, eq, part, traj, err};
+    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, tmem_cols, eq, part, traj, err, S1, S2};
     const int smem = fused_smem_bytes(nm_bucket, TC, split);
     const int64_t ntiles = (count + TC_M - 1) / TC_M;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;

@@ -30,9 +30,11 @@ struct FusedArgs {
     int Nt, TC, d, Ks, nkb, split;
     uint32_t tmem_cols;
     const double* eq;   // [delta* n][pm n][moment shift 2n] (the shift is used by the reduce)
-    float* part;        // [ntiles][Nt+1][4n]
+    float* part;        // [ntiles][Nt+1][4n], or nullptr: add into S1, S2 with FP64 atomics
     float* traj;        // [count][Nt+1][2n] or nullptr
     int* err;
+    double* S1;         // [Nt+1][2n] when part == nullptr
+    double* S2;
 };
 
 template <int NM, int ND>
@@ -103,8 +105,9 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             }
     }
     // time 0: every sample sits at the (rounded) shift, so both sums are zero
-    float* part_tile = a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4;
-    for (int v = tid; v < S4; v += FU_THREADS) part_tile[v] = 0.f;
+    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4 : nullptr;
+    if (part_tile)
+        for (int v = tid; v < S4; v += FU_THREADS) part_tile[v] = 0.f;
 
     const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
     uint32_t g = 0;  // K blocks issued so far (thread 0)
@@ -199,7 +202,15 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                     const int sl = e / S4, v = e - sl * S4;
                     const float* m = msum + sl * 4 * (4 * NM) + v;
                     float acc = ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM];
-                    part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
+                    if (part_tile) {
+                        part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
+                    } else {
+                        const int64_t row = (int64_t)(tn0 + sl) * S;
+                        if (v < S)
+                            atomicAdd(a.S1 + row + v, (double)acc);
+                        else
+                            atomicAdd(a.S2 + row + (v - S), (double)acc);
+                    }
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(FU_THREADS) : "memory");
             }

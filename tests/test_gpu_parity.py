@@ -261,3 +261,40 @@ def test_integrator_sincos_accuracy(fmc):
     er = max(np.abs(sref.double().cpu().numpy() - np.sin(xd)).max(), np.abs(cref.double().cpu().numpy() - np.cos(xd)).max())
     assert es.max() <= 1.2e-7 and ec.max() <= 1.2e-7, (es.max(), ec.max())
     assert max(es.max(), ec.max()) <= 2.0 * er + 1e-8
+
+
+# ----------------------------------------------------------------------------- batches
+
+
+def _mixed_batch():
+    return [fs.multimachine_case(n=3, d=1, K=50, T=0.5, dt=0.005, N=300, seed=11),
+            fs.multimachine_case(n=10, d=3, K=200, T=1.0, dt=0.005, N=1000, seed=12),
+            fs.multimachine_case(n=16, d=8, K=37, T=0.25, dt=0.005, N=129, seed=13),
+            fs.smib_case(N=777, T=1.0),
+            fs.multimachine_case(n=7, d=5, K=120, T=0.8, dt=0.005, N=4096, seed=14)]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_single_scenarios(fmc, use_graph):
+    scs = _mixed_batch()
+    b = fmc.Batch(scs, use_graph=use_graph)
+    for rep in range(2):  # a replayed graph gives the same results
+        means, vars_ = b.launch()
+        fmc.device_status()
+        for sc, m, v in zip(scs, means, vars_):
+            m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
+            # same samples and arithmetic; only the order of the FP64 sums differs
+            assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
+            assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
+    b.close()
+
+
+def test_batch_moments_match_oracle(fmc, orc):
+    scs = _mixed_batch()[:2]
+    b = fmc.Batch(scs, use_graph=True)
+    means, vars_ = b.launch()
+    for sc, m, v in zip(scs, means, vars_):
+        zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+        ref = orc.simulate(sc, zr, nthreads=8)
+        _check_moments(m.cpu().numpy(), v.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+    b.close()

@@ -1,0 +1,93 @@
+"""The request server on the GPU: results alone and in the mix, timeouts,
+cancellation and memory admission.  Failures are made on the host (a wait that
+runs out, a cancelled request, an over-budget request); nothing faults the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+import fmc_synth as fs
+from gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fmc():
+    return need_gpu()
+
+
+def _mix():
+    return [fs.multimachine_case(n=10, d=3, K=200, T=2.0, dt=0.005, N=20000, seed=21),
+            fs.multimachine_case(n=4, d=2, K=60, T=1.0, dt=0.005, N=3000, seed=22),
+            fs.smib_case(N=1000, T=5.0),
+            fs.multimachine_case(n=16, d=8, K=100, T=0.5, dt=0.005, N=5000, seed=23),
+            fs.multimachine_case(n=7, d=1, K=250, T=1.5, dt=0.005, N=65536, seed=24),
+            fs.multimachine_case(n=3, d=4, K=33, T=0.3, dt=0.005, N=129, seed=25)]
+
+
+def test_results_same_alone_and_in_the_mix(fmc):
+    scs = _mix()
+    alone = [fmc.simulate(sc, path="fused", precision="bf16x3") for sc in scs]
+    srv = fmc.Server(slots=4)
+    handles = [srv.submit(sc) for sc in scs + scs]  # two copies of each, all in flight together
+    for i, h in enumerate(handles):
+        res, m, v = srv.wait(h, timeout_s=120)
+        assert res["status"] == 0, res
+        m0, v0 = alone[i % len(scs)]
+        # the same samples and arithmetic; only the order of the FP64 sums differs
+        assert np.allclose(m.cpu().numpy(), m0.cpu().numpy(), rtol=1e-12, atol=1e-15)
+        assert np.allclose(v.cpu().numpy(), v0.cpu().numpy(), rtol=1e-9, atol=1e-18)
+        assert res["latency_us"] >= res["queue_us"] >= 0
+    srv.close()
+
+
+def test_wait_timeout_and_poll(fmc):
+    srv = fmc.Server(slots=1)
+    big = fs.multimachine_case(n=10, d=3, K=200, T=20.0, dt=0.005, N=1 << 16, seed=5)
+    h = srv.submit(big)
+    assert srv.wait(h, timeout_s=1e-6) is None          # FMC_ETIMEOUT: not done yet
+    t0 = time.time()
+    while srv.poll(h) is None:
+        assert time.time() - t0 < 120
+        time.sleep(0.01)
+    srv.close()
+
+
+def test_cancel_queued_request(fmc):
+    srv = fmc.Server(slots=1)
+    first = srv.submit(fs.multimachine_case(n=10, d=3, K=200, T=20.0, dt=0.005, N=1 << 16, seed=6))
+    second = srv.submit(fs.smib_case(N=1000))
+    time.sleep(0.2)                                     # the first is running, the second queued
+    assert srv.cancel(second) == fmc.OK
+    res, _, _ = srv.wait(second, timeout_s=10)
+    assert res["status"] == fmc.ECANCELLED
+    res, _, _ = srv.wait(first, timeout_s=120)
+    assert res["status"] == 0
+    srv.close()
+
+
+def test_memory_admission(fmc):
+    sc = fs.multimachine_case(n=10, d=3, K=200, T=2.0, dt=0.005, N=1 << 15, seed=7)
+    need = 2 * sc.N * sc.d * 200 * 2  # the split design alone
+    srv = fmc.Server(slots=4, mem_budget_bytes=int(need * 1.5))
+    with pytest.raises(fmc.FastMCError) as e:
+        srv.submit(sc.replace(N=1 << 17))               # could never fit the budget
+    assert e.value.code == fmc.ENOMEM
+    hs = [srv.submit(sc) for _ in range(3)]             # fit one at a time
+    peak = 0
+    done = 0
+    t0 = time.time()
+    while done < 3:
+        st = srv.stats()
+        peak = max(peak, st["running"])
+        for h in list(hs):
+            r = srv.poll(h)
+            if r is not None:
+                assert r[0]["status"] == 0
+                hs.remove(h)
+                done += 1
+        assert time.time() - t0 < 120
+        time.sleep(0.002)
+    assert peak <= 1
+    srv.close()
