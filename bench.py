@@ -49,19 +49,28 @@ def parse():
     ap.add_argument("--precision", default=None, choices=[None, "bf16x3", "bf16", "f32"])
     ap.add_argument("--samples", type=int, default=1 << 16)
     ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
+    ap.add_argument("--machines", type=int, default=10, help="machines of the system (17..52: large-system kernel)")
+    ap.add_argument("--disturbances", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "tol", "batch", "serve"],
                     help="tol: LHS vs SRS (and precision forms) time to a stated error on E and Var; "
                          "batch: 64 uneven scenarios in one captured graph; serve: Poisson request stream")
-    ap.add_argument("--max-machines", type=int, default=16,
+    ap.add_argument("--max-machines", type=int, default=50,
                     help="upper end of the machine count drawn for the batch and serve studies")
     ap.add_argument("--seeds", type=int, default=32)
     return ap.parse_args()
 
 
-def workload(samples: int, horizon: float = 20.0):
-    return fs.multimachine_case(n=10, d=3, K=200, T=horizon, dt=0.005, N=samples, seed=0)
+def workload(samples: int, horizon: float = 20.0, machines: int = 10, disturbances: int = 3):
+    return fs.multimachine_case(n=machines, d=disturbances, K=200, T=horizon, dt=0.005, N=samples, seed=0)
+
+
+def workload_name(args) -> str:
+    if args.machines == 10 and args.disturbances == 3 and args.samples == (1 << 16) and args.horizon == 20.0:
+        return WORKLOAD
+    return (f"classical {args.machines}-machine system (39-bus-shaped draws), {args.disturbances} OU disturbances, "
+            f"K=200, T={args.horizon:g}s, dt=5ms, N={args.samples}, LHS")
 
 
 def algorithmic_flops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
@@ -400,7 +409,7 @@ def main():
     precision = args.precision or ("f32" if path == "plain" else "bf16x3")
     # weak scaling: every rank simulates `samples` samples, its own block of one
     # design of samples * world samples; the moment sums meet in one all-reduce
-    sc = workload(args.samples * world, args.horizon)
+    sc = workload(args.samples * world, args.horizon, args.machines, args.disturbances)
     n, Nt = sc.n, sc.Nt
     from paper_2007_03847_gb300.distributed import shard_range
     k0, count = shard_range(sc.N, world, rank)
@@ -462,10 +471,11 @@ def main():
     mhz = clk.get("sm_mhz") or (measured_peaks() or {}).get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
     traffic = profiled_traffic() if (path == "fused" and precision == "bf16x3" and sc.N == (1 << 16)
-                                     and Nt == 4000 and world == 1) else None
+                                     and Nt == 4000 and n == 10 and world == 1) else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
-                "kernel": "simulate_fused_kernel" if path == "fused" else "simulate_plain_kernel",
+                "kernel": ("simulate_wide_kernel" if n > 16 else "simulate_fused_kernel") if path == "fused"
+                          else "simulate_plain_kernel",
                 "kernel_ms": kernel_ms,
                 "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (median SM clock "
                              f"sampled during the timed region); achieved counts the method's FP32 operations "
@@ -500,7 +510,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "f32" else f"f32+{precision}",
             "data": "synthetic (seeded system and LHS design)",
-            "config": {"workload": WORKLOAD, "path": path, "precision": precision, "samples_per_gpu": count,
+            "config": {"workload": workload_name(args), "path": path, "precision": precision, "samples_per_gpu": count,
                        "steps_per_sample": Nt, "machines": n, "disturbances": sc.d, "K": sc.K,
                        "l2": "flushed between timed steps (512 MB write)", "gpu": gpu_name, "sms": sms},
             "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline, "cpu_baseline": base,

@@ -69,7 +69,8 @@ extern "C" {
 #define FMC_PATH_PLAIN 1    /* unfused FP32: increments and trajectories through HBM */
 
 /* ---- limits of this build -------------------------------------------------- */
-#define FMC_MAX_MACHINES 16
+#define FMC_MAX_MACHINES 52        /* fused path (17..52 machines: four warps per sample) */
+#define FMC_MAX_MACHINES_PLAIN 16  /* plain FP32 path */
 #define FMC_MAX_DISTURBANCES 8
 
 typedef struct fmc_ctx fmc_ctx;
@@ -95,7 +96,7 @@ typedef struct fmc_ctx fmc_ctx;
  * All arrays are host memory, read during the call.
  */
 typedef struct fmc_scenario {
-    int32_t n;              /* machines, 1..FMC_MAX_MACHINES */
+    int32_t n;              /* machines, 1..FMC_MAX_MACHINES (FMC_MAX_MACHINES_PLAIN on the plain path) */
     int32_t d;              /* disturbances = Wiener processes, 1..FMC_MAX_DISTURBANCES */
     int32_t K;              /* KL terms per Wiener process, >= 1 */
     int32_t sampling;       /* FMC_LHS, FMC_SRS or FMC_LHS_MIDPOINT */

@@ -31,7 +31,7 @@ PREC_F32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 RK4, HEUN = 0, 1
 PATH_FUSED, PATH_PLAIN = 0, 1
 PH_LHS, PH_BASIS, PH_EQ, PH_FUSED, PH_REDUCE, PH_CONTRACT, PH_INTEGRATE, PH_MOMENTS, PH_BATCH = range(9)
-MAX_MACHINES, MAX_DISTURBANCES = 16, 8
+MAX_MACHINES, MAX_MACHINES_PLAIN, MAX_DISTURBANCES = 52, 16, 8
 
 _PRECISION = {"f32": PREC_F32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3}
 _PATH = {"fused": PATH_FUSED, "plain": PATH_PLAIN}

@@ -42,6 +42,7 @@ struct ProfRec {
 // status word; the plain path's FP32 design, increments and trajectories.
 struct Workspace {
     DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
+    DevBuf wconst;  // constant block of the large-system kernel
 };
 
 struct fmc_ctx {
@@ -64,6 +65,7 @@ struct fmc_ctx {
     DevBuf& scen = ws.scen;
     DevBuf& status = ws.status;
     DevBuf& zeta32 = ws.zeta32;
+    DevBuf& wconst = ws.wconst;
     // profiling of kernel phases (CUDA events on the launching stream)
     bool prof = false;
     std::vector<ProfRec> recs;
@@ -304,6 +306,50 @@ static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const dou
     }
 }
 
+// Constant block of the large-system kernel (layout at wide_const_floats): the
+// same deviation-form constants as build_params, with the network matrices
+// arranged [j][h][k] for machine i = h + 4k.
+static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, std::vector<float>& out)
+{
+    const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
+    out.assign(wide_const_floats(n, nmt, d), 0.f);
+    float* GE = out.data();
+    float* BE = GE + n * 4 * nmtp;
+    float* pm = BE + n * 4 * nmtp;
+    const bool rel = !s->has_inf_bus;
+    std::vector<double> c(n), sn(n);
+    for (int j = 0; j < n; ++j) {
+        double a = rel ? delta0[j] - delta0[0] : delta0[j];
+        c[j] = std::cos(a);
+        sn[j] = std::sin(a);
+    }
+    for (int i = 0; i < n; ++i) {
+        const int h = i % 4, k = i / 4;
+        double u = 0.0, v = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double ge = s->E[i] * s->E[j] * s->G[i * n + j];
+            double be = s->E[i] * s->E[j] * s->B[i * n + j];
+            GE[(j * 4 + h) * nmtp + k] = (float)ge;
+            BE[(j * 4 + h) * nmtp + k] = (float)be;
+            u += ge * c[j] - be * sn[j];
+            v += ge * sn[j] + be * c[j];
+        }
+        if (s->has_inf_bus) {
+            u += s->E[i] * s->Vinf * s->Ginf[i];
+            v += s->E[i] * s->Vinf * s->Binf[i];
+        }
+        pm[0 * g4 + i] = (float)c[i];
+        pm[1 * g4 + i] = (float)sn[i];
+        pm[2 * g4 + i] = (float)u;
+        pm[3 * g4 + i] = (float)v;
+        pm[4 * g4 + i] = (float)delta0[i];
+        pm[5 * g4 + i] = (float)(1.0 / (2.0 * s->H[i]));
+        pm[6 * g4 + i] = (float)s->D[i];
+        for (int q = 0; q < d; ++q) pm[(7 + q) * g4 + i] = (float)s->inject[i * d + q];
+    }
+}
+
 // Copies the system arrays to the device and launches the FP64 Newton kernel.
 // eq: [delta0 n][pm n][shift 2n]; status: iteration count or -1.
 static int run_equilibrium_ws(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, cudaStream_t st)
@@ -469,8 +515,9 @@ int fmc_destroy(fmc_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     prof_clear(ctx);
-    DevBuf* bufs[] = {&ctx->zeta_hi, &ctx->zeta_lo, &ctx->phi_hi, &ctx->phi_lo, &ctx->phi32, &ctx->dW,
-                      &ctx->traj,    &ctx->part,    &ctx->eq,     &ctx->scen,   &ctx->status, &ctx->zeta32};
+    DevBuf* bufs[] = {&ctx->zeta_hi, &ctx->zeta_lo, &ctx->phi_hi, &ctx->phi_lo, &ctx->phi32,  &ctx->dW,
+                      &ctx->traj,    &ctx->part,    &ctx->eq,     &ctx->scen,   &ctx->status, &ctx->zeta32,
+                      &ctx->wconst};
     for (DevBuf* b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     delete ctx;
@@ -662,6 +709,7 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
 struct Prepared {
     fmc_scenario s{};
     int Nt = 0, nm = 0, nd = 0, path = 0;
+    int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
 };
@@ -681,9 +729,13 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
     const int n = s->n;
+    if (path == FMC_PATH_PLAIN && n > FMC_MAX_MACHINES_PLAIN)
+        return fail(ctx, FMC_EUNSUPPORTED, "the plain path handles up to %d machines (n = %d)",
+                    FMC_MAX_MACHINES_PLAIN, n);
     P.s = *s;
     P.Nt = Nt;
     P.nm = nm_bucket_for(n);
+    P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
     P.nd = nd_bucket_for(s->d);
     P.path = path;
     P.k0 = k0;
@@ -697,6 +749,17 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     FMC_CUDA(ctx, cudaMemcpyAsync(&eq_status, ws.status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
     FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
     if (eq_status < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    if (P.nmt > 0) {
+        // constants of the large-system kernel go to the device once, here
+        // (outside any stream capture)
+        std::vector<float> wc;
+        build_wide_consts(s, delta0.data(), P.nmt, wc);
+        if ((rc = ensure(ctx, ws.wconst, wc.size() * sizeof(float)))) return rc;
+        FMC_CUDA(ctx, cudaMemcpyAsync(ws.wconst.ptr, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice, st),
+                 "copy constants");
+        FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+        return FMC_OK;
+    }
     build_params_bucket(P.nm, P.nd, s, delta0.data(), P.params);
     return FMC_OK;
 }
@@ -808,10 +871,39 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     }
     prof_begin(ctx, PH_FUSED, st, &pr);
     int occ = 0;
-    cudaError_t e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split,
-                                          tmem_cols, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
-                                          per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
-                                          (int*)ws.status.ptr + 1, st, &occ);
+    cudaError_t e;
+    if (P.nmt > 0) {
+        WideArgs wa{};
+        wa.count = count;
+        wa.Nt = Nt;
+        wa.TC = TC;
+        wa.d = d;
+        wa.Ks = Ks;
+        wa.nkb = nkb;
+        wa.split = split;
+        wa.n = n;
+        wa.tmem_cols = tmem_cols;
+        wa.integrator = s->integrator;
+        wa.rel = s->has_inf_bus ? 0 : 1;
+        wa.omega_s = (float)s->omega_s;
+        wa.dt = (float)s->dt;
+        for (int q = 0; q < d; ++q) {
+            wa.ou_a[q] = (float)(1.0 - s->theta[q] * s->dt);
+            wa.ou_s[q] = (float)s->sigma[q];
+        }
+        wa.consts = (const float*)ws.wconst.ptr;
+        wa.part = per_tile_partials ? (float*)ws.part.ptr : nullptr;
+        wa.S1 = per_tile_partials ? nullptr : S1;
+        wa.S2 = per_tile_partials ? nullptr : S2;
+        wa.traj = traj_dev;
+        wa.err = (int*)ws.status.ptr + 1;
+        e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
+    } else {
+        e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
+                                  eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
+                                  per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
+                                  (int*)ws.status.ptr + 1, st, &occ);
+    }
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)
         return fail(ctx, FMC_EUNSUPPORTED, "fused kernel: %d CTAs per SM x %u TMEM columns exceeds 512", occ,
@@ -933,8 +1025,9 @@ static void batch_free(fmc_batch* b)
     if (b->fork) cudaEventDestroy(b->fork);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (Workspace* w : b->ws) {
-        DevBuf* bufs[] = {&w->zeta_hi, &w->zeta_lo, &w->phi_hi, &w->phi_lo, &w->phi32, &w->dW,
-                          &w->traj,    &w->part,    &w->eq,     &w->scen,   &w->status, &w->zeta32};
+        DevBuf* bufs[] = {&w->zeta_hi, &w->zeta_lo, &w->phi_hi, &w->phi_lo, &w->phi32,  &w->dW,
+                          &w->traj,    &w->part,    &w->eq,     &w->scen,   &w->status, &w->zeta32,
+                          &w->wconst};
         for (DevBuf* d : bufs)
             if (d->ptr) {
                 cudaFree(d->ptr);

@@ -35,6 +35,39 @@ cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, d
 cudaError_t launch_finalize(const double* S1, const double* S2, const double* shift, int64_t N, int64_t Nt1, int S,
                             double* mean, double* var, cudaStream_t st);
 
+// Fused kernel for 17..52 machines (four warps per sample group).  Machine
+// slots per thread NMT in {5, 7, 10, 13}: n <= 4 NMT.
+struct WideArgs {
+    int64_t count;
+    int Nt, TC, d, Ks, nkb, split, n;
+    uint32_t tmem_cols;
+    int integrator, rel;
+    float omega_s, dt;
+    float ou_a[8], ou_s[8];
+    const float* consts;  // device copy of the constant block (wide_const_floats floats)
+    float* part;          // [tiles][Nt+1][4n], or nullptr: add into S1, S2 with FP64 atomics
+    double* S1;           // [Nt+1][2n] when part == nullptr
+    double* S2;
+    float* traj;          // [count][Nt+1][2n] or nullptr
+    int* err;
+};
+
+__host__ __device__ constexpr int wide_nmtp(int nmt) { return (nmt + 3) & ~3; }
+
+// Constant block of the wide kernel (floats):
+//   GE [n][4][NMTP], BE [n][4][NMTP]: entry (j, h, k) = E_i E_j G_ij (resp. B_ij)
+//     for machine i = h + 4k, zero on the diagonal and for padded i;
+//   then seven rows of 4 NMT per machine: cos D*, sin D*, u*, v*, delta*, 1/(2H), D;
+//   then the injection map, d rows of 4 NMT.
+__host__ __device__ inline int wide_const_floats(int n, int nmt, int d)
+{
+    return 2 * n * 4 * wide_nmtp(nmt) + (7 + d) * 4 * nmt;
+}
+
+int wide_nmt_for(int n);
+cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
+                                 int* max_ctas_per_sm);
+
 cudaError_t launch_sincos_probe(const float* x, int64_t n, float* s_cw, float* c_cw, float* s_ref, float* c_ref,
                                 cudaStream_t st);
 

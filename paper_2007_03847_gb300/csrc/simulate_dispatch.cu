@@ -20,6 +20,32 @@ cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int
 cudaError_t launch_fused_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
 cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
 
+cudaError_t launch_wide_nmt5(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt7(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt10(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt13(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+
+int wide_nmt_for(int n)
+{
+    static const int slots[] = {5, 7, 10, 13};
+    for (int m : slots)
+        if (n <= 4 * m) return m;
+    return -1;
+}
+
+cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
+                                 int* max_ctas_per_sm)
+{
+    if (a.n > 4 * nmt || a.d > nd) return cudaErrorInvalidValue;
+    switch (nmt) {
+        case 5: return launch_wide_nmt5(nd, maps, a, st, max_ctas_per_sm);
+        case 7: return launch_wide_nmt7(nd, maps, a, st, max_ctas_per_sm);
+        case 10: return launch_wide_nmt10(nd, maps, a, st, max_ctas_per_sm);
+        case 13: return launch_wide_nmt13(nd, maps, a, st, max_ctas_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 int fused_smem_bytes(int nm_bucket, int TC, int split)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);

@@ -1,0 +1,411 @@
+// Algorithm 1 steps 2-4 fused for systems too large to keep one sample's whole
+// state in one thread (17..52 machines).
+//
+// One CTA = 128 samples = 128 TMEM lanes, 16 warps.  Warp (q, h) = (w mod 4,
+// w / 4) integrates the machines i = h + 4k (k < NMT) of the 32 samples whose
+// TMEM lanes it may read (subpartition q), so four warps share every sample and
+// each thread holds a quarter of its sample's state.  The KL contraction into
+// TMEM is the fused kernel's (one thread issues TMA loads and tcgen05.mma per
+// time chunk); all four warps of a sample group read the same increments and
+// advance the OU disturbances redundantly.
+//
+// Per RK stage every thread publishes, for its machines, the deviations
+//   gamma_i = cos(D*_i + Delta_i) - cos D*_i,  eta_i = sin(D*_i + Delta_i) - sin D*_i
+// of the stage input to shared memory (double-buffered, so one named barrier of
+// the 128 threads of a sample group per stage suffices), then accumulates the
+// network sums of its machines over all machines j, reading (gamma_j, eta_j)
+// once per j.  The network matrices sit in shared memory laid out
+// [j][h][k] (k padded to a multiple of 4) so that a warp reads its column slice
+// with broadcast 16-byte loads.  The arithmetic per machine is that of
+// swing_step (deviation form around the FP64 equilibrium, diagonal excluded).
+#pragma once
+
+#include "fmc_common.cuh"
+#include "kernels.cuh"
+#include "swing.cuh"
+#include "tc_common.cuh"
+
+namespace fmc {
+
+constexpr int WI_THREADS = 512;
+constexpr int WI_MS = 4;  // steps between flushes of the moment buffer
+
+template <int NMT>
+__host__ __device__ inline int wide_mom_floats()
+{
+    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 4 * NMT;
+}
+
+// sin and cos - 1 of a deviation, rotated into (gamma, eta) about the equilibrium.
+__device__ __forceinline__ float2 wide_gamma_eta(float x, float cs, float ss, bool big)
+{
+    float sn, cm1;
+    if (big)
+        sin_cosm1_any(x, &sn, &cm1);
+    else
+        sin_cosm1_small(x, &sn, &cm1);
+    return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
+}
+
+template <int NMT, int ND>
+__global__ void __launch_bounds__(WI_THREADS, 1)
+    simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                         const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                         const __grid_constant__ WideArgs a)
+{
+    constexpr int NMTP = wide_nmtp(NMT);
+    constexpr int G4 = 4 * NMT;
+    constexpr int WROW = 2 * NMT + 1;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t bars[5];  // full[2], freed[2], done
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int q = warp & 3, h = warp >> 2;
+    const int n = a.n, d = a.d, S = 2 * n, S4 = 4 * n;
+    const int r = 32 * q + lane;  // sample row within the tile = TMEM lane
+    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int64_t srow = row0 + r;
+    const bool active = srow < a.count;
+    const int TC = a.TC;
+
+    // shared memory: [ring | moment buffers] [gamma/eta x2] [w0 x2] [constants]
+    TcRing ring;
+    ring.a_bytes = TC_M * 64;
+    ring.b_bytes = TC * 64;
+    ring.split = a.split;
+    const uint32_t stage_bytes = (ring.a_bytes + ring.b_bytes) * (a.split ? 2 : 1);
+    ring.stage[0] = smem;
+    ring.stage[1] = smem + stage_bytes;
+    ring.full = &bars[0];
+    ring.freed = &bars[2];
+    const uint32_t mom_bytes = (uint32_t)wide_mom_floats<NMT>() * 4u;
+    const uint32_t u_bytes = ((2 * stage_bytes > mom_bytes ? 2 * stage_bytes : mom_bytes) + 1023u) & ~1023u;
+    float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;   // [32][WROW] per warp
+    float* msum = reinterpret_cast<float*>(smem) + 16 * 32 * WROW;     // [WI_MS][q][h][4 NMT]
+    float2* gh = reinterpret_cast<float2*>(smem + u_bytes);            // [2][n][128]
+    float* w0buf = reinterpret_cast<float*>(gh + 2 * n * 128);         // [2][128]
+    float* cst_s = w0buf + 256;
+    const int nconst = wide_const_floats(n, NMT, d);
+    for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[e];
+    const float* GEs = cst_s;
+    const float* BEs = cst_s + n * 4 * NMTP;
+    const float* pm = cst_s + 2 * n * 4 * NMTP;
+    const float* c_cst = pm;
+    const float* c_sst = pm + G4;
+    const float* c_ust = pm + 2 * G4;
+    const float* c_vst = pm + 3 * G4;
+    const float* c_dst = pm + 4 * G4;
+    const float* c_i2h = pm + 5 * G4;
+    const float* c_D = pm + 6 * G4;
+    const float* c_inj = pm + 7 * G4;  // [d][4 NMT]
+
+    if (tid == 0) {
+        prefetch_tmap(&mAh);
+        prefetch_tmap(&mBh);
+        for (int b = 0; b < 5; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+
+    float del[NMT], w[NMT], theta = 0.f;  // deviations from the equilibrium
+    float x0[ND];
+#pragma unroll
+    for (int k = 0; k < NMT; ++k) {
+        del[k] = 0.f;
+        w[k] = 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < ND; ++e) x0[e] = 0.f;
+
+    const int64_t trow = 2 * (int64_t)n;
+    float* traj = (a.traj != nullptr && active) ? a.traj + srow * (int64_t)(a.Nt + 1) * trow : nullptr;
+    if (traj) {
+#pragma unroll
+        for (int k = 0; k < NMT; ++k) {
+            const int i = h + 4 * k;
+            if (i < n) {
+                traj[i] = c_dst[i];
+                traj[n + i] = 0.f;
+            }
+        }
+    }
+    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4 : nullptr;
+    if (part_tile)
+        for (int v = tid; v < S4; v += WI_THREADS) part_tile[v] = 0.f;
+
+    // stage-0 input of the first step: every deviation is zero
+    int gb = 0;
+#pragma unroll
+    for (int k = 0; k < NMT; ++k) {
+        const int i = h + 4 * k;
+        if (i < n) gh[i * 128 + r] = make_float2(0.f, 0.f);
+    }
+    if (h == 0) w0buf[r] = 0.f;
+
+    const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
+    uint32_t g = 0;
+    const int J = d * a.nkb;
+    const float dt = a.dt;
+    const bool rk4 = (a.integrator == FMC_RK4);
+    const int nst = rk4 ? 4 : 2;
+    const float ref = a.rel ? 1.f : 0.f;
+    const float hh = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
+
+    for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
+        // ---- tensor cores: dW of this chunk into TMEM ----
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            bool ok = ring_load(ring, g, &mAh, &mAl, &mBh, &mBl, 0, (int)row0, 0, n0);
+            for (int j = 0; j < J && ok; ++j) {
+                if (j + 1 < J) {
+                    const int w1 = (j + 1) / a.nkb, kb1 = (j + 1) % a.nkb;
+                    ok = ring_load(ring, g + j + 1, &mAh, &mAl, &mBh, &mBl, w1 * a.Ks + kb1 * TC_BK, (int)row0,
+                                   kb1 * TC_BK, n0);
+                }
+                const int wj = j / a.nkb, kbj = j % a.nkb;
+                if (ok) ok = ring_mma(ring, g + j, tmem + (uint32_t)(wj * TC), idesc, kbj == 0);
+            }
+            g += (uint32_t)J;
+            if (ok) {
+                umma_commit(&bars[4]);
+            } else {
+                abort_flag = 1;
+                atomicExch(a.err, DEV_TIMEOUT_TMA);
+            }
+        }
+        __syncthreads();
+        bool ok = (abort_flag == 0);
+        if (ok && !mbar_wait(&bars[4], (uint32_t)c & 1u)) {
+            ok = false;
+            atomicExch(a.err, DEV_TIMEOUT_MMA);
+        }
+        if (!__syncthreads_and(ok)) break;
+        tc_fence_after();
+
+        // ---- FP32 pipes: integrate this chunk ----
+        const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
+        for (int s = 0; s < steps; ++s) {
+            float dw[ND], x1[ND];
+#pragma unroll
+            for (int e = 0; e < ND; ++e) dw[e] = 0.f;
+#pragma unroll
+            for (int e = 0; e < ND; ++e)
+                if (e < d) dw[e] = tmem_ld1(lane_addr + (uint32_t)(e * TC + s));
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < ND; ++e) x1[e] = fmaf(a.ou_a[e], x0[e], a.ou_s[e] * dw[e]);
+
+            float ad[NMT], aw[NMT], yw[NMT];
+            float ath = 0.f;
+#pragma unroll
+            for (int k = 0; k < NMT; ++k) {
+                yw[k] = w[k];
+                ad[k] = 0.f;
+                aw[k] = 0.f;
+            }
+#pragma unroll 1
+            for (int st = 0; st < nst; ++st) {
+                float b, cn, xw;
+                if (rk4) {
+                    b = (st == 1 || st == 2) ? 2.f : 1.f;
+                    cn = (st == 2) ? dt : 0.5f * dt;
+                    xw = (st == 0) ? 0.f : ((st == 3) ? 1.f : 0.5f);
+                } else {
+                    b = 1.f;
+                    cn = dt;
+                    xw = (st == 0) ? 0.f : 1.f;
+                }
+                // the group's (gamma, eta) of this stage's input are complete
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + q) : "memory");
+                const float2* ghc = gh + gb * n * 128 + r;
+                float du[NMT], dv[NMT];
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    du[k] = 0.f;
+                    dv[k] = 0.f;
+                }
+#pragma unroll 2
+                for (int j = 0; j < n; ++j) {
+                    const float2 gej = ghc[j * 128];
+                    const float4* g4 = reinterpret_cast<const float4*>(GEs + (j * 4 + h) * NMTP);
+                    const float4* b4 = reinterpret_cast<const float4*>(BEs + (j * 4 + h) * NMTP);
+#pragma unroll
+                    for (int k4 = 0; k4 < NMTP / 4; ++k4) {
+                        const float4 gv = g4[k4], bv = b4[k4];
+                        const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+                        const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const int k = 4 * k4 + kk;
+                            if (k < NMT) {
+                                du[k] = fmaf(gg[kk], gej.x, du[k]);
+                                du[k] = fmaf(-bb[kk], gej.y, du[k]);
+                                dv[k] = fmaf(gg[kk], gej.y, dv[k]);
+                                dv[k] = fmaf(bb[kk], gej.x, dv[k]);
+                            }
+                        }
+                    }
+                }
+                const float w0 = w0buf[gb * 128 + r] * ref;
+                float xs[ND];
+#pragma unroll
+                for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
+                const bool pub = (st + 1 < nst);
+                float2* ghn = gh + (gb ^ 1) * n * 128 + r;
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    const int i = h + 4 * k;
+                    const float2 ge = ghc[(i < n ? i : 0) * 128];
+                    const float cs = c_cst[i], ss = c_sst[i];
+                    float dpe = fmaf(cs, du[k], ss * dv[k]);
+                    dpe = fmaf(ge.x, c_ust[i] + du[k], dpe);
+                    dpe = fmaf(ge.y, c_vst[i] + dv[k], dpe);
+                    float f = 0.f;
+#pragma unroll
+                    for (int e = 0; e < ND; ++e)
+                        if (e < d) f = fmaf(c_inj[e * G4 + i], xs[e], f);
+                    const float kd = a.omega_s * (yw[k] - w0);
+                    const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
+                    ad[k] = fmaf(b, kd, ad[k]);
+                    aw[k] = fmaf(b, kw, aw[k]);
+                    const float yd = fmaf(cn, kd, del[k]);
+                    yw[k] = fmaf(cn, kw, w[k]);
+                    if (pub) {
+                        // the next stage's input of machine i
+                        const bool big = __any_sync(0xffffffffu, i < n && fabsf(yd) > 0.8f);
+                        if (i < n) ghn[i * 128] = wide_gamma_eta(yd, cs, ss, big);
+                    }
+                }
+                if (pub && h == 0) w0buf[(gb ^ 1) * 128 + r] = yw[0];
+                ath = fmaf(b, a.omega_s * w0, ath);
+                if (pub) gb ^= 1;
+            }
+#pragma unroll
+            for (int k = 0; k < NMT; ++k) {
+                del[k] = fmaf(hh, ad[k], del[k]);
+                w[k] = fmaf(hh, aw[k], w[k]);
+            }
+            theta = fmaf(hh, ath, theta);
+#pragma unroll
+            for (int e = 0; e < ND; ++e) x0[e] = x1[e];
+            // stage-0 input of the next step
+            {
+                float2* ghn = gh + (gb ^ 1) * n * 128 + r;
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    const int i = h + 4 * k;
+                    const bool big = __any_sync(0xffffffffu, i < n && fabsf(del[k]) > 0.8f);
+                    if (i < n) ghn[i * 128] = wide_gamma_eta(del[k], c_cst[i], c_sst[i], big);
+                }
+                if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
+                gb ^= 1;
+            }
+
+            const int tn = n0 + s + 1;  // grid index of the new state
+            if (traj) {
+                float* o = traj + (int64_t)tn * trow;
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    const int i = h + 4 * k;
+                    if (i < n) {
+                        o[i] = (theta + del[k]) + c_dst[i];
+                        o[n + i] = w[k];
+                    }
+                }
+            }
+            // ---- moments: per warp, 32 samples x own machines ----
+            float* myrow = wbuf + lane * WROW;
+#pragma unroll
+            for (int k = 0; k < NMT; ++k) {
+                myrow[k] = active ? theta + del[k] : 0.f;
+                myrow[NMT + k] = active ? w[k] : 0.f;
+            }
+            __syncwarp();
+            const int ms = s % WI_MS;
+            if (lane < 2 * NMT) {
+                float s1 = 0.f, s2 = 0.f;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    float v = wbuf[rr * WROW + lane];
+                    s1 += v;
+                    s2 = fmaf(v, v, s2);
+                }
+                float* slot = msum + ((ms * 4 + q) * 4 + h) * G4;
+                slot[lane] = s1;
+                slot[2 * NMT + lane] = s2;
+            }
+            __syncwarp();
+            if (ms == WI_MS - 1 || s == steps - 1) {
+                __syncthreads();
+                const int nsl = ms + 1;
+                const int tn0 = tn - ms;
+                for (int e = tid; e < nsl * S4; e += WI_THREADS) {
+                    const int sl = e / S4, v = e - sl * S4;
+                    // v = kind * 2n + state; state < n is delta_i, else omega_(state - n)
+                    const int kind = v >= S ? 1 : 0;
+                    const int stt = v - kind * S;
+                    const int isw = stt >= n ? 1 : 0;
+                    const int i = stt - isw * n;
+                    const int col = kind * 2 * NMT + isw * NMT + (i >> 2);
+                    const float* m = msum + (sl * 16 + (i & 3)) * G4 + col;
+                    const float acc = ((m[0] + m[4 * G4]) + m[8 * G4]) + m[12 * G4];
+                    if (part_tile) {
+                        part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
+                    } else {
+                        const int64_t rowt = (int64_t)(tn0 + sl) * S;
+                        if (kind == 0)
+                            atomicAdd(a.S1 + rowt + stt, (double)acc);
+                        else
+                            atomicAdd(a.S2 + rowt + stt, (double)acc);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// Dynamic shared memory of the kernel (bytes), alignment slack included.
+template <int NMT>
+inline int wide_smem_bytes(int TC, int split, int n, int d)
+{
+    const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
+    const int mom = wide_mom_floats<NMT>() * 4;
+    const int u = ((2 * stage > mom ? 2 * stage : mom) + 1023) & ~1023;
+    return 1024 + u + 2 * n * 128 * 8 + 256 * 4 + wide_const_floats(n, NMT, d) * 4;
+}
+
+template <int NMT, int ND>
+cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ_out)
+{
+    auto kern = simulate_wide_kernel<NMT, ND>;
+    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WI_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    *occ_out = occ;
+    if (occ < 1 || (uint32_t)occ * a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
+    const int64_t ntiles = (a.count + TC_M - 1) / TC_M;
+    if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)ntiles, WI_THREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    return cudaGetLastError();
+}
+
+}  // namespace fmc

@@ -56,9 +56,11 @@ def test_wait_timeout_and_poll(fmc):
 
 def test_cancel_queued_request(fmc):
     srv = fmc.Server(slots=1)
-    first = srv.submit(fs.multimachine_case(n=10, d=3, K=200, T=20.0, dt=0.005, N=1 << 16, seed=6))
+    # the first request runs for about two seconds on one slot, so the second
+    # is still queued when it is cancelled
+    first = srv.submit(fs.multimachine_case(n=10, d=3, K=200, T=60.0, dt=0.005, N=1 << 20, seed=6))
     second = srv.submit(fs.smib_case(N=1000))
-    time.sleep(0.2)                                     # the first is running, the second queued
+    time.sleep(0.05)
     assert srv.cancel(second) == fmc.OK
     res, _, _ = srv.wait(second, timeout_s=10)
     assert res["status"] == fmc.ECANCELLED

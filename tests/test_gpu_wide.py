@@ -1,0 +1,115 @@
+"""GPU parity of the large-system fused kernel (17..52 machines, four warps per
+sample group) against the FP64 oracle.
+
+Same tolerances as the other simulation parity tests: trajectories within 1e-4
+normwise relative error on delta and on omega separately, moments within 1e-5.
+Machine counts cover every slot bucket (n <= 20, 28, 40, 52) with full and
+ragged last machine groups; sample counts leave a ragged last tile.
+"""
+import numpy as np
+import pytest
+
+import fmc_synth as fs
+from gpu_common import need_gpu, normwise_rel, traj_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fmc():
+    return need_gpu()
+
+
+def _check_moments(m, v, rm, rv, n, tol=1e-5):
+    for sl in (slice(0, n), slice(n, 2 * n)):
+        scale = np.max(np.sqrt(rm[:, sl] ** 2 + rv[:, sl]))
+        assert np.max(np.abs(m[:, sl] - rm[:, sl])) <= tol * scale
+        assert normwise_rel(v[:, sl], rv[:, sl]) <= tol
+
+
+CASES = {
+    "n17_d1": dict(n=17, d=1, K=30, T=0.5, dt=0.005, N=131, seed=21),
+    "n28_d3": dict(n=28, d=3, K=40, T=0.5, dt=0.005, N=200, seed=22),
+    "n37_d5": dict(n=37, d=5, K=23, T=0.333, dt=0.003, N=129, seed=23),
+    "n50_d8": dict(n=50, d=8, K=16, T=0.2, dt=0.005, N=257, seed=24),
+    "n52_d2": dict(n=52, d=2, K=50, T=0.3, dt=0.005, N=128, seed=25),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_wide_trajectories_and_moments(fmc, orc, case):
+    sc = fs.multimachine_case(**CASES[case])
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    fmc.device_status()
+    zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+    ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_wide_heun(fmc, orc):
+    sc = fs.multimachine_case(**CASES["n28_d3"]).replace(integrator=fs.HEUN)
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+    ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_wide_sums_without_trajectories_match(fmc):
+    # the moment path alone (no trajectory buffer) gives the same moments
+    sc = fs.multimachine_case(**CASES["n37_d5"])
+    m1, v1, _ = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    m2, v2 = fmc.simulate(sc, path="fused", precision="bf16x3")
+    assert np.array_equal(m1.cpu().numpy(), m2.cpu().numpy())
+    assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
+
+
+def test_wide_sigma_zero_stays_at_equilibrium(fmc, orc):
+    sc = fs.multimachine_case(n=40, d=4, K=50, T=1.0, dt=0.005, N=256, seed=5).replace(sigma=np.zeros(4))
+    mean, var = fmc.simulate(sc, path="fused")
+    d0, _, _ = orc.equilibrium(sc)
+    m = mean.cpu().numpy()
+    assert np.max(np.abs(m[:, :40] - d0)) < 1e-5
+    assert np.max(np.abs(m[:, 40:])) < 1e-6
+    assert np.max(var.cpu().numpy()) < 1e-10
+
+
+def test_wide_sample_blocks_add_up(fmc, orc):
+    # two blocks of the same design through the sums entry point = the whole design
+    sc = fs.multimachine_case(**CASES["n50_d8"])
+    zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+    ref = orc.simulate(sc, zr, nthreads=8)
+    a1, a2, shift = fmc.simulate_sums(sc, 0, 129)
+    b1, b2, _ = fmc.simulate_sums(sc, 129, sc.N - 129)
+    S1 = (a1 + b1).cpu().numpy()
+    S2 = (a2 + b2).cpu().numpy()
+    sh = shift.cpu().numpy()
+    N = sc.N
+    mean = sh[None, :] + S1 / N
+    var = (S2 - S1 * S1 / N) / (N - 1)
+    _check_moments(mean, var, ref["mean"], ref["var"], sc.n)
+
+
+def test_wide_plain_path_is_refused(fmc):
+    sc = fs.multimachine_case(n=20, d=2, K=10, T=0.1, dt=0.005, N=64)
+    with pytest.raises(fmc.FastMCError) as e:
+        fmc.simulate(sc, path="plain")
+    assert e.value.code == 8
+
+
+def test_wide_in_a_batch(fmc):
+    scs = [fs.multimachine_case(n=3, d=1, K=50, T=0.5, dt=0.005, N=300, seed=31),
+           fs.multimachine_case(n=45, d=6, K=60, T=0.4, dt=0.005, N=1000, seed=32),
+           fs.multimachine_case(n=10, d=3, K=200, T=0.5, dt=0.005, N=700, seed=33),
+           fs.multimachine_case(n=21, d=8, K=20, T=0.25, dt=0.005, N=129, seed=34)]
+    b = fmc.Batch(scs, use_graph=True)
+    means, vars_ = b.launch()
+    fmc.device_status()
+    for sc, m, v in zip(scs, means, vars_):
+        m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
+        assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
+        assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
+    b.close()
