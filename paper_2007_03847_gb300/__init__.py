@@ -96,6 +96,7 @@ def load_library():
             "fmc_profile": ([vp, i32, i64], ctypes.c_int),
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "fmc_set_kernel_policy": ([vp, ctypes.c_int32], ctypes.c_int),
             "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_batch_create": ([vp, ctypes.POINTER(_Scenario), i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                   i32, ctypes.POINTER(vp)], ctypes.c_int),
@@ -506,6 +507,16 @@ def test_sincos(x, ctx: Context | None = None, stream=None):
     outs = [torch.empty_like(x) for _ in range(4)]
     ctx.check(ctx.lib.fmc_test_sincos(ctx.h, _ptr(x), x.numel(), *[_ptr(o) for o in outs], _stream(stream)))
     return outs
+
+
+KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT = 0, 1, 2
+_KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT}
+
+
+def set_kernel_policy(policy, ctx: Context | None = None) -> None:
+    """Fused-path kernel for later single-scenario calls: "auto", "per_sample" or "split"."""
+    ctx = ctx or default_context()
+    ctx.check(ctx.lib.fmc_set_kernel_policy(ctx.h, _KERNEL.get(policy, policy)))
 
 
 def fused_occupancy(ctx: Context | None = None) -> int:

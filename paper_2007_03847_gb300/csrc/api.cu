@@ -71,6 +71,7 @@ struct fmc_ctx {
     std::vector<ProfRec> recs;
     size_t prof_cap = 0;
     int last_fused_ctas_per_sm = 0;
+    int kernel_policy = FMC_KERNEL_AUTO;
 };
 
 static thread_local std::string g_create_err;
@@ -710,12 +711,13 @@ struct Prepared {
     fmc_scenario s{};
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
+    bool exclusive = true;  // the launch has the GPU to itself (see fused_tc)
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
 };
 
 static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path,
-                   cudaStream_t st, Prepared& P)
+                   cudaStream_t st, Prepared& P, bool exclusive = true)
 {
     int Nt = 0;
     int rc = check_scenario(ctx, s, &Nt);
@@ -735,7 +737,18 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     P.s = *s;
     P.Nt = Nt;
     P.nm = nm_bucket_for(n);
-    P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
+    P.exclusive = exclusive;
+    // four warps per sample for systems above 16 machines (or on request)
+    const int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
+    if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_PER_SAMPLE && P.nm < 0)
+        return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
+                    FMC_MAX_MACHINES_PLAIN, n);
+    if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_SPLIT)
+        P.nmt = wide_nmt_for(n);
+    else if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_PER_SAMPLE)
+        P.nmt = 0;
+    else
+        P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
     P.nd = nd_bucket_for(s->d);
     P.path = path;
     P.k0 = k0;
@@ -764,7 +777,26 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     return FMC_OK;
 }
 
-static int fused_tc(int d) { return (d <= 4) ? 32 : 16; }
+// Time chunk TC of the fused kernels.  A CTA's accumulator holds d x TC FP32
+// TMEM columns (512 per SM), and every chunk boundary reloads the CTA's design
+// tile through the shared-memory ring (a latency the CTA waits out).  When the
+// GPU is the call's alone and the tiles need fewer than four CTAs per SM, each
+// CTA may take more columns, so the chunk grows (up to 256 steps) and the
+// boundaries become rarer; launches that share the GPU (batches, the server)
+// keep 128 columns per CTA.
+static int fused_tc(int d, int64_t ntiles, int sms, bool wide, bool exclusive)
+{
+    int per_sm = 4;
+    if (exclusive) {
+        const int64_t need = (ntiles + sms - 1) / sms;
+        per_sm = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
+    }
+    const int cols = 512 / per_sm;
+    // the large-system kernel's shared memory leaves room for a ring of 128-step chunks
+    int TC = wide ? 128 : 256;
+    while (TC > 16 && d * TC > cols) TC >>= 1;
+    return TC;
+}
 
 // All device buffers the enqueue of P needs (grows the workspace; may allocate).
 // per_tile_partials = false: the fused kernel adds its sums with FP64 atomics
@@ -845,10 +877,10 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     const int Ks = round_up(K, 8);
     const int Kpad = round_up(K, TC_BK);
     const int nkb = (Ks + TC_BK - 1) / TC_BK;
-    const int TC = fused_tc(d);
+    const int64_t ntiles = (count + TC_M - 1) / TC_M;
+    const int TC = fused_tc(d, ntiles, ctx->sms, P.nmt > 0, P.exclusive);
     uint32_t tmem_cols = 32;
     while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
-    const int64_t ntiles = (count + TC_M - 1) / TC_M;
     prof_begin(ctx, PH_LHS, st, &pr);
     FMC_CUDA(ctx,
              launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr,
@@ -940,7 +972,7 @@ int fmc::simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, dou
     if (!ctx) return FMC_EINVAL;
     if (!s || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "NULL scenario or output");
     Prepared P;
-    int rc = prepare(ctx, ctx->ws, s, 0, s->N, path, st, P);
+    int rc = prepare(ctx, ctx->ws, s, 0, s->N, path, st, P, false);  // requests of the server share the GPU
     if (rc) return rc;
     const bool tiles = per_tile_partials || path == FMC_PATH_PLAIN;
     if ((rc = reserve(ctx, ctx->ws, P, false, tiles))) return rc;
@@ -1085,7 +1117,7 @@ int fmc_batch_create(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int
         Workspace* w = new Workspace();
         b->ws.push_back(w);
         b->prep.emplace_back();
-        rc = prepare(ctx, *w, &scen[i], 0, scen[i].N, path, st0, b->prep.back());
+        rc = prepare(ctx, *w, &scen[i], 0, scen[i].N, path, st0, b->prep.back(), false);  // scenarios share the GPU
         if (rc == FMC_OK) rc = reserve(ctx, *w, b->prep.back(), false, path == FMC_PATH_PLAIN);
         b->mean.push_back(mean_dev[i]);
         b->var.push_back(var_dev[i]);
@@ -1248,6 +1280,15 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
         return fail(ctx, FMC_EINVAL, "bad arguments");
     FMC_CUDA(ctx, launch_sincos_probe(x_dev, n, s_dev, c_dev, s_ref_dev, c_ref_dev, (cudaStream_t)stream),
              "sincos probe");
+    return FMC_OK;
+}
+
+int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (policy != FMC_KERNEL_AUTO && policy != FMC_KERNEL_PER_SAMPLE && policy != FMC_KERNEL_SPLIT)
+        return fail(ctx, FMC_EINVAL, "kernel policy %d", policy);
+    ctx->kernel_policy = policy;
     return FMC_OK;
 }
 

@@ -43,9 +43,8 @@ __global__ void __launch_bounds__(128) contract_tc_kernel(const __grid_constant_
     r.a_bytes = TC_M * 64;
     r.b_bytes = a.TN * 64;
     r.split = a.split;
-    const uint32_t stage_bytes = (r.a_bytes + r.b_bytes) * (a.split ? 2 : 1);
-    r.stage[0] = smem;
-    r.stage[1] = smem + stage_bytes;
+    r.base = smem;
+    r.ns = 2;
     r.full = &bars[0];
     r.freed = &bars[2];
 

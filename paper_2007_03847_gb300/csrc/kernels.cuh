@@ -22,7 +22,7 @@ cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G,
                                cudaStream_t st);
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
                                   int64_t count, int Nt, float* traj, cudaStream_t st);
-int fused_smem_bytes(int nm_bucket, int TC, int split);
+int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm);
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
                                   const double* eq, float* part, double* S1, double* S2, float* traj, int* err,
@@ -35,11 +35,13 @@ cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, d
 cudaError_t launch_finalize(const double* S1, const double* S2, const double* shift, int64_t N, int64_t Nt1, int S,
                             double* mean, double* var, cudaStream_t st);
 
-// Fused kernel for 17..52 machines (four warps per sample group).  Machine
-// slots per thread NMT in {5, 7, 10, 13}: n <= 4 NMT.
+// Fused kernel with four warps per sample group: 17..52 machines, or few
+// samples of any system.  Machine slots per thread NMT in {1, 2, 3, 4, 5, 7,
+// 10, 13}: n <= 4 NMT.
 struct WideArgs {
     int64_t count;
     int Nt, TC, d, Ks, nkb, split, n;
+    int ns;  // ring stages (set by the launcher)
     uint32_t tmem_cols;
     int integrator, rel;
     float omega_s, dt;

@@ -20,6 +20,10 @@ cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int
 cudaError_t launch_fused_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, cudaStream_t, int*);
 cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, cudaStream_t);
 
+cudaError_t launch_wide_nmt1(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt2(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt3(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
+cudaError_t launch_wide_nmt4(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
 cudaError_t launch_wide_nmt5(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
 cudaError_t launch_wide_nmt7(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
 cudaError_t launch_wide_nmt10(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
@@ -27,7 +31,7 @@ cudaError_t launch_wide_nmt13(int, const CUtensorMap*, const WideArgs&, cudaStre
 
 int wide_nmt_for(int n)
 {
-    static const int slots[] = {5, 7, 10, 13};
+    static const int slots[] = {1, 2, 3, 4, 5, 7, 10, 13};
     for (int m : slots)
         if (n <= 4 * m) return m;
     return -1;
@@ -38,6 +42,10 @@ cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const
 {
     if (a.n > 4 * nmt || a.d > nd) return cudaErrorInvalidValue;
     switch (nmt) {
+        case 1: return launch_wide_nmt1(nd, maps, a, st, max_ctas_per_sm);
+        case 2: return launch_wide_nmt2(nd, maps, a, st, max_ctas_per_sm);
+        case 3: return launch_wide_nmt3(nd, maps, a, st, max_ctas_per_sm);
+        case 4: return launch_wide_nmt4(nd, maps, a, st, max_ctas_per_sm);
         case 5: return launch_wide_nmt5(nd, maps, a, st, max_ctas_per_sm);
         case 7: return launch_wide_nmt7(nd, maps, a, st, max_ctas_per_sm);
         case 10: return launch_wide_nmt10(nd, maps, a, st, max_ctas_per_sm);
@@ -46,16 +54,27 @@ cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const
     }
 }
 
-int fused_smem_bytes(int nm_bucket, int TC, int split)
+// Ring stages of the fused kernel: as many as a CTA's share of the SM's shared
+// memory holds (2..TC_MAX_STAGES), so that more of a chunk's loads are in flight.
+int fused_ring_stages(int TC, int split, int max_ctas_per_sm)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
-    const int ring = 2 * stage;
+    int share = 233472 / max_ctas_per_sm - 2048;  // per CTA: 1 KB reserved, 1 KB static
+    if (share > TC_SMEM_DYN_MAX) share = TC_SMEM_DYN_MAX;
+    int ns = (share - 1024) / stage;
+    return ns < 2 ? 2 : (ns > TC_MAX_STAGES ? TC_MAX_STAGES : ns);
+}
+
+int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm)
+{
+    const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
+    const int ring = fused_ring_stages(TC, split, max_ctas_per_sm) * stage;
     const int mom = (4 * 32 * (2 * nm_bucket + 1) + FU_MS * 4 * 4 * nm_bucket) * 4;
     int need = (ring > mom ? ring : mom) + 1024;
-    // at most four CTAs per SM (233472 bytes of shared memory per SM, 1 KB
-    // reserved per CTA): each CTA then owns a quarter of the 512 TMEM columns
-    const int floor4 = 233472 / 5 - 1024 + 64;
-    return need > floor4 ? need : floor4;
+    // at most max_ctas_per_sm CTAs per SM (233472 bytes of shared memory per SM,
+    // 1 KB reserved per CTA), so that their TMEM columns fit the SM's 512
+    const int floor = 233472 / (max_ctas_per_sm + 1) - 1024 + 64;
+    return need > floor ? need : floor;
 }
 
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
@@ -63,8 +82,10 @@ cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* para
                                   const double* eq, float* part, double* S1, double* S2, float* traj, int* err,
                                   cudaStream_t st, int* max_ctas_per_sm)
 {
-    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, tmem_cols, eq, part, traj, err, S1, S2};
-    const int smem = fused_smem_bytes(nm_bucket, TC, split);
+    const int cap = (int)(512u / tmem_cols) < 4 ? (int)(512u / tmem_cols) : 4;
+    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, fused_ring_stages(TC, split, cap), tmem_cols, eq, part, traj,
+                err, S1, S2};
+    const int smem = fused_smem_bytes(nm_bucket, TC, split, cap);
     const int64_t ntiles = (count + TC_M - 1) / TC_M;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
     switch (nm_bucket) {

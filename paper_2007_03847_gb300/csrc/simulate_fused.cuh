@@ -28,6 +28,7 @@ constexpr int FU_MS = 8;  // steps between flushes of the moment buffer
 struct FusedArgs {
     int64_t count;
     int Nt, TC, d, Ks, nkb, split;
+    int ns;             // ring stages
     uint32_t tmem_cols;
     const double* eq;   // [delta* n][pm n][moment shift 2n] (the shift is used by the reduce)
     float* part;        // [ntiles][Nt+1][4n], or nullptr: add into S1, S2 with FP64 atomics
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bars[5];  // full[2], freed[2], done
+    __shared__ uint64_t bars[2 * TC_MAX_STAGES + 1];  // full[ns], freed[ns], done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -61,11 +62,11 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     r.a_bytes = TC_M * 64;
     r.b_bytes = TC * 64;
     r.split = a.split;
-    const uint32_t stage_bytes = (r.a_bytes + r.b_bytes) * (a.split ? 2 : 1);
-    r.stage[0] = smem;
-    r.stage[1] = smem + stage_bytes;
+    r.base = smem;
+    r.ns = (uint32_t)a.ns;
     r.full = &bars[0];
-    r.freed = &bars[2];
+    r.freed = &bars[TC_MAX_STAGES];
+    uint64_t* done = &bars[2 * TC_MAX_STAGES];
     const int WROW = 2 * NM + 1;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;           // [32][WROW] per warp
     float* msum = reinterpret_cast<float*>(smem) + 4 * 32 * WROW;              // [FU_MS][4][4*NM]
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     if (tid == 0) {
         prefetch_tmap(&mAh);
         prefetch_tmap(&mBh);
-        for (int b = 0; b < 5; ++b) mbar_init(&bars[b], 1);
+        for (int b = 0; b < 2 * TC_MAX_STAGES + 1; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             }
             g += (uint32_t)J;
             if (ok) {
-                umma_commit(&bars[4]);
+                umma_commit(done);
             } else {
                 abort_flag = 1;
                 atomicExch(a.err, DEV_TIMEOUT_TMA);
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         }
         __syncthreads();
         bool ok = (abort_flag == 0);
-        if (ok && !mbar_wait(&bars[4], (uint32_t)c & 1u)) {
+        if (ok && !mbar_wait(done, (uint32_t)c & 1u)) {
             ok = false;
             atomicExch(a.err, DEV_TIMEOUT_MMA);
         }
@@ -183,13 +184,23 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             __syncwarp();
             const int ms = s % FU_MS;
             if (lane < S) {
-                float s1 = 0.f, s2 = 0.f;
-#pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) {
-                    float v = wbuf[rr * WROW + lane];
-                    s1 += v;
-                    s2 = fmaf(v, v, s2);
+                // four interleaved partial sums (shorter dependency chains), combined in a fixed order
+                float s1a = 0.f, s1b = 0.f, s1c = 0.f, s1d = 0.f, s2a = 0.f, s2b = 0.f, s2c = 0.f, s2d = 0.f;
+#pragma unroll
+                for (int rr = 0; rr < 32; rr += 4) {
+                    const float v0 = wbuf[rr * WROW + lane], v1 = wbuf[(rr + 1) * WROW + lane];
+                    const float v2 = wbuf[(rr + 2) * WROW + lane], v3 = wbuf[(rr + 3) * WROW + lane];
+                    s1a += v0;
+                    s1b += v1;
+                    s1c += v2;
+                    s1d += v3;
+                    s2a = fmaf(v0, v0, s2a);
+                    s2b = fmaf(v1, v1, s2b);
+                    s2c = fmaf(v2, v2, s2c);
+                    s2d = fmaf(v3, v3, s2d);
                 }
+                const float s1 = (s1a + s1b) + (s1c + s1d);
+                const float s2 = (s2a + s2b) + (s2c + s2d);
                 msum[(ms * 4 + warp) * (4 * NM) + lane] = s1;
                 msum[(ms * 4 + warp) * (4 * NM) + S + lane] = s2;
             }

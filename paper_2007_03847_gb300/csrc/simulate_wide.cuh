@@ -1,5 +1,5 @@
 // Algorithm 1 steps 2-4 fused for systems too large to keep one sample's whole
-// state in one thread (17..52 machines).
+// state in one thread (17..52 machines); smaller systems on request.
 //
 // One CTA = 128 samples = 128 TMEM lanes, 16 warps.  Warp (q, h) = (w mod 4,
 // w / 4) integrates the machines i = h + 4k (k < NMT) of the 32 samples whose
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     constexpr int WROW = 2 * NMT + 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bars[5];  // full[2], freed[2], done
+    __shared__ uint64_t bars[2 * TC_MAX_STAGES + 1];  // full[ns], freed[ns], done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -77,12 +77,14 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     ring.b_bytes = TC * 64;
     ring.split = a.split;
     const uint32_t stage_bytes = (ring.a_bytes + ring.b_bytes) * (a.split ? 2 : 1);
-    ring.stage[0] = smem;
-    ring.stage[1] = smem + stage_bytes;
+    ring.base = smem;
+    ring.ns = (uint32_t)a.ns;
     ring.full = &bars[0];
-    ring.freed = &bars[2];
+    ring.freed = &bars[TC_MAX_STAGES];
+    uint64_t* done = &bars[2 * TC_MAX_STAGES];
     const uint32_t mom_bytes = (uint32_t)wide_mom_floats<NMT>() * 4u;
-    const uint32_t u_bytes = ((2 * stage_bytes > mom_bytes ? 2 * stage_bytes : mom_bytes) + 1023u) & ~1023u;
+    const uint32_t ring_bytes = (uint32_t)a.ns * stage_bytes;
+    const uint32_t u_bytes = ((ring_bytes > mom_bytes ? ring_bytes : mom_bytes) + 1023u) & ~1023u;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;   // [32][WROW] per warp
     float* msum = reinterpret_cast<float*>(smem) + 16 * 32 * WROW;     // [WI_MS][q][h][4 NMT]
     float2* gh = reinterpret_cast<float2*>(smem + u_bytes);            // [2][n][128]
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     if (tid == 0) {
         prefetch_tmap(&mAh);
         prefetch_tmap(&mBh);
-        for (int b = 0; b < 5; ++b) mbar_init(&bars[b], 1);
+        for (int b = 0; b < 2 * TC_MAX_STAGES + 1; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             }
             g += (uint32_t)J;
             if (ok) {
-                umma_commit(&bars[4]);
+                umma_commit(done);
             } else {
                 abort_flag = 1;
                 atomicExch(a.err, DEV_TIMEOUT_TMA);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
         }
         __syncthreads();
         bool ok = (abort_flag == 0);
-        if (ok && !mbar_wait(&bars[4], (uint32_t)c & 1u)) {
+        if (ok && !mbar_wait(done, (uint32_t)c & 1u)) {
             ok = false;
             atomicExch(a.err, DEV_TIMEOUT_MMA);
         }
@@ -382,19 +384,25 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 
 // Dynamic shared memory of the kernel (bytes), alignment slack included.
 template <int NMT>
-inline int wide_smem_bytes(int TC, int split, int n, int d)
+inline int wide_smem_bytes(int TC, int split, int n, int d, int ns)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
     const int mom = wide_mom_floats<NMT>() * 4;
-    const int u = ((2 * stage > mom ? 2 * stage : mom) + 1023) & ~1023;
+    const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
     return 1024 + u + 2 * n * 128 * 8 + 256 * 4 + wide_const_floats(n, NMT, d) * 4;
 }
 
 template <int NMT, int ND>
-cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ_out)
+cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStream_t st, int* occ_out)
 {
     auto kern = simulate_wide_kernel<NMT, ND>;
-    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d);
+    // as many ring stages as the shared memory left by the other buffers holds
+    WideArgs a = args;
+    a.ns = 2;
+    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d, a.ns + 1) <= TC_SMEM_DYN_MAX)
+        ++a.ns;
+    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d, a.ns);
+    if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int occ = 0;

@@ -174,16 +174,26 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // ---------------------------------------------------------------------------
 // One [128 x TN] block of dW for disturbance w accumulated into TMEM:
 //   D[r][c] = sum_k Z[row0 + r][w*Ks + k] * Phi[col0 + c][k],   k < nkb*32,
-// streamed through a two-stage shared-memory ring in K blocks of 32.  Issued by
-// a single thread.  `g` counts K blocks over the kernel's lifetime and selects
-// the ring stage and mbarrier parities.  Returns false if a bounded wait gave up.
+// streamed through an ns-stage shared-memory ring in K blocks of 32 (ns - 1
+// loads in flight while the tensor cores consume one).  Issued by a single
+// thread.  `g` counts K blocks over the kernel's lifetime and selects the ring
+// stage (g mod ns) and the mbarrier parities.  Returns false if a bounded wait
+// gave up.
 // ---------------------------------------------------------------------------
+constexpr int TC_MAX_STAGES = 8;
+
+// Dynamic shared memory a fused kernel may request: the opt-in maximum per
+// block (227 KB) less the kernels' static shared memory (1 KB with the
+// alignment of the dynamic array) and a margin.
+constexpr int TC_SMEM_DYN_MAX = 227 * 1024 - 2048;
+
 struct TcRing {
-    uint8_t* stage[2];      // each: A_hi | A_lo | B_hi | B_lo
-    uint64_t* full;         // [2]
-    uint64_t* freed;        // [2]
+    uint8_t* base;          // ns stages, each: A_hi | A_lo | B_hi | B_lo
+    uint64_t* full;         // [ns]
+    uint64_t* freed;        // [ns]
     uint32_t a_bytes;       // 128 rows x 64 B
     uint32_t b_bytes;       // TN rows x 64 B
+    uint32_t ns;            // stages, 2..TC_MAX_STAGES
     int split;              // 1 for BF16x3 (hi/lo operands present)
 };
 
@@ -196,12 +206,12 @@ __device__ __forceinline__ bool ring_load(const TcRing& r, uint32_t g, const CUt
                                           const CUtensorMap* mBh, const CUtensorMap* mBl, int ax, int ay, int bx,
                                           int by)
 {
-    const uint32_t st = g & 1u;
-    const uint32_t fill = g >> 1;
+    const uint32_t st = g % r.ns;
+    const uint32_t fill = g / r.ns;
     if (fill >= 1) {
         if (!mbar_wait(&r.freed[st], (fill - 1) & 1u)) return false;
     }
-    uint8_t* base = r.stage[st];
+    uint8_t* base = r.base + st * ring_stage_bytes(r);
     mbar_arrive_expect_tx(&r.full[st], ring_stage_bytes(r));
     tma_load_2d(base, mAh, ax, ay, &r.full[st]);
     tma_load_2d(base + r.a_bytes * (r.split ? 2 : 1), mBh, bx, by, &r.full[st]);
@@ -214,11 +224,11 @@ __device__ __forceinline__ bool ring_load(const TcRing& r, uint32_t g, const CUt
 
 __device__ __forceinline__ bool ring_mma(const TcRing& r, uint32_t g, uint32_t d_tmem, uint32_t idesc, bool first)
 {
-    const uint32_t st = g & 1u;
-    const uint32_t fill = g >> 1;
+    const uint32_t st = g % r.ns;
+    const uint32_t fill = g / r.ns;
     if (!mbar_wait(&r.full[st], fill & 1u)) return false;
     tc_fence_after();
-    uint8_t* base = r.stage[st];
+    uint8_t* base = r.base + st * ring_stage_bytes(r);
     const uint32_t a_hi = smem_u32(base);
     const uint32_t b_hi = smem_u32(base + r.a_bytes * (r.split ? 2 : 1));
     const uint32_t a_lo = a_hi + r.a_bytes;

@@ -31,6 +31,19 @@ def fmc():
     return need_gpu()
 
 
+@pytest.fixture(params=["per_sample", "split"])
+def kernel(fmc, request):
+    """Runs a test with each fused kernel forced, then restores the automatic choice."""
+    fmc.set_kernel_policy(request.param)
+    yield request.param
+    fmc.set_kernel_policy("auto")
+
+
+def _batch_kernel(fmc, sc):
+    # the kernel a batch (shared GPU) takes for this scenario
+    fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
+
+
 def _zeta_tol(zref):
     z = np.asarray(zref, dtype=np.float64)
     ulp = np.spacing(np.abs(z).astype(np.float32)).astype(np.float64)
@@ -147,9 +160,17 @@ def _small_cases():
     }
 
 
-@pytest.mark.parametrize("path,precision", [("plain", "f32"), ("fused", "bf16x3")])
 @pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8"])
-def test_simulate_trajectories_and_moments(fmc, orc, path, precision, case):
+def test_simulate_trajectories_and_moments_plain(fmc, orc, case):
+    _trajectories_and_moments(fmc, orc, "plain", "f32", case)
+
+
+@pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8"])
+def test_simulate_trajectories_and_moments_fused(fmc, orc, kernel, case):
+    _trajectories_and_moments(fmc, orc, "fused", "bf16x3", case)
+
+
+def _trajectories_and_moments(fmc, orc, path, precision, case):
     sc = _small_cases()[case]
     mean, var, traj = fmc.simulate(sc, path=path, precision=precision, want_traj=True)
     fmc.device_status()
@@ -160,7 +181,7 @@ def test_simulate_trajectories_and_moments(fmc, orc, path, precision, case):
     _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
 
 
-def test_simulate_bf16_error_is_stated(fmc, orc):
+def test_simulate_bf16_error_is_stated(fmc, orc, kernel):
     # BF16 contraction: trajectories carry the 2^-9 rounding of zeta and phi
     sc = _small_cases()["mm10"]
     mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16", want_traj=True)
@@ -170,7 +191,25 @@ def test_simulate_bf16_error_is_stated(fmc, orc):
     assert ed <= 2e-2 and ew <= 2e-2, (ed, ew)
 
 
-def test_heun_integrator(fmc, orc):
+@pytest.mark.parametrize("tiles_per_sm", [1, 2, 3])
+@pytest.mark.parametrize("d", [1, 3, 6])
+def test_chunk_length_follows_the_tiles(fmc, orc, tiles_per_sm, d):
+    # The time chunk grows when few CTAs share an SM (one, two, or four per SM
+    # give 512, 256 or 128 TMEM columns per CTA): sample counts just under each
+    # boundary, a horizon that is not a multiple of any chunk length.
+    sms, _ = fmc.default_context().info()
+    N = 128 * sms * tiles_per_sm - 37
+    sc = fs.multimachine_case(n=4, d=d, K=24, T=0.305, dt=0.005, N=N, seed=40 + d)
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    fmc.device_status()
+    zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+    ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_heun_integrator(fmc, orc, kernel):
     sc = _small_cases()["mm10"].replace(integrator=fs.HEUN)
     mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
     zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
@@ -186,7 +225,7 @@ def test_single_sample_variance_nan(fmc):
     assert np.all(np.isnan(v))
 
 
-def test_sigma_zero_stays_at_equilibrium(fmc, orc):
+def test_sigma_zero_stays_at_equilibrium(fmc, orc, kernel):
     sc = fs.multimachine_case(n=10, d=3, K=50, T=1.0, dt=0.005, N=256).replace(sigma=np.zeros(3))
     mean, var = fmc.simulate(sc, path="fused")
     d0, _, _ = orc.equilibrium(sc)
@@ -282,8 +321,10 @@ def test_batch_equals_single_scenarios(fmc, use_graph):
         means, vars_ = b.launch()
         fmc.device_status()
         for sc, m, v in zip(scs, means, vars_):
+            _batch_kernel(fmc, sc)
             m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
-            # same samples and arithmetic; only the order of the FP64 sums differs
+            fmc.set_kernel_policy("auto")
+            # same samples, kernel and arithmetic; only the order of the FP64 sums differs
             assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
             assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
     b.close()

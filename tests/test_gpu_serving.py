@@ -28,7 +28,13 @@ def _mix():
 
 def test_results_same_alone_and_in_the_mix(fmc):
     scs = _mix()
-    alone = [fmc.simulate(sc, path="fused", precision="bf16x3") for sc in scs]
+    # alone: the same kernel as the server's (a shared GPU takes the per-sample
+    # kernel for these sizes)
+    fmc.set_kernel_policy("per_sample")
+    try:
+        alone = [fmc.simulate(sc, path="fused", precision="bf16x3") for sc in scs]
+    finally:
+        fmc.set_kernel_policy("auto")
     srv = fmc.Server(slots=4)
     handles = [srv.submit(sc) for sc in scs + scs]  # two copies of each, all in flight together
     for i, h in enumerate(handles):

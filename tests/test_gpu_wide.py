@@ -93,6 +93,17 @@ def test_wide_sample_blocks_add_up(fmc, orc):
     _check_moments(mean, var, ref["mean"], ref["var"], sc.n)
 
 
+def test_per_sample_kernel_refuses_large_systems(fmc):
+    sc = fs.multimachine_case(n=20, d=2, K=10, T=0.1, dt=0.005, N=64)
+    fmc.set_kernel_policy("per_sample")
+    try:
+        with pytest.raises(fmc.FastMCError) as e:
+            fmc.simulate(sc)
+        assert e.value.code == 8
+    finally:
+        fmc.set_kernel_policy("auto")
+
+
 def test_wide_plain_path_is_refused(fmc):
     sc = fs.multimachine_case(n=20, d=2, K=10, T=0.1, dt=0.005, N=64)
     with pytest.raises(fmc.FastMCError) as e:
@@ -109,7 +120,10 @@ def test_wide_in_a_batch(fmc):
     means, vars_ = b.launch()
     fmc.device_status()
     for sc, m, v in zip(scs, means, vars_):
+        # the kernel the batch takes for this scenario on a shared GPU
+        fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
         m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
+        fmc.set_kernel_policy("auto")
         assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
         assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
     b.close()
