@@ -28,7 +28,10 @@ __global__ void __launch_bounds__(128) contract_tc_kernel(const __grid_constant_
                                                           const __grid_constant__ CUtensorMap mBl, ContractArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1 KB alignment by an offset from the shared array itself (not through an
+    // integer round trip), so that every access through these pointers stays a
+    // shared-memory access rather than a generic one
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ uint64_t bars[5];  // full[2], freed[2], done
     __shared__ uint32_t tmem_base;
     __shared__ int ok_flag;

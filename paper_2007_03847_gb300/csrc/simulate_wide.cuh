@@ -54,10 +54,15 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                          const __grid_constant__ WideArgs a)
 {
     constexpr int NMTP = wide_nmtp(NMT);
+    constexpr int KP = NMT > 10 ? 8 : NMT;  // machine slots per pass over the network sum
+    constexpr int JU = NMT > 7 ? 1 : 2;      // unrolling of the loop over j (registers permitting)
     constexpr int G4 = 4 * NMT;
     constexpr int WROW = 2 * NMT + 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1 KB alignment by an offset from the shared array itself (not through an
+    // integer round trip), so that every access through these pointers stays a
+    // shared-memory access rather than a generic one
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ uint64_t bars[2 * TC_MAX_STAGES + 1];  // full[ns], freed[ns], done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -232,62 +237,72 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 // the group's (gamma, eta) of this stage's input are complete
                 asm volatile("bar.sync %0, 128;" ::"r"(1 + q) : "memory");
                 const float2* ghc = gh + gb * n * 128 + r;
-                float du[NMT], dv[NMT];
-#pragma unroll
-                for (int k = 0; k < NMT; ++k) {
-                    du[k] = 0.f;
-                    dv[k] = 0.f;
-                }
-#pragma unroll 2
-                for (int j = 0; j < n; ++j) {
-                    const float2 gej = ghc[j * 128];
-                    const float4* g4 = reinterpret_cast<const float4*>(GEs + (j * 4 + h) * NMTP);
-                    const float4* b4 = reinterpret_cast<const float4*>(BEs + (j * 4 + h) * NMTP);
-#pragma unroll
-                    for (int k4 = 0; k4 < NMTP / 4; ++k4) {
-                        const float4 gv = g4[k4], bv = b4[k4];
-                        const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
-                        const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const int k = 4 * k4 + kk;
-                            if (k < NMT) {
-                                du[k] = fmaf(gg[kk], gej.x, du[k]);
-                                du[k] = fmaf(-bb[kk], gej.y, du[k]);
-                                dv[k] = fmaf(gg[kk], gej.y, dv[k]);
-                                dv[k] = fmaf(bb[kk], gej.x, dv[k]);
-                            }
-                        }
-                    }
-                }
                 const float w0 = w0buf[gb * 128 + r] * ref;
                 float xs[ND];
 #pragma unroll
                 for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
                 const bool pub = (st + 1 < nst);
                 float2* ghn = gh + (gb ^ 1) * n * 128 + r;
+                // KP machine slots per pass over j: one pass up to 10 slots; two
+                // passes above, so that fewer network sums are live at once
 #pragma unroll
-                for (int k = 0; k < NMT; ++k) {
-                    const int i = h + 4 * k;
-                    const float2 ge = ghc[(i < n ? i : 0) * 128];
-                    const float cs = c_cst[i], ss = c_sst[i];
-                    float dpe = fmaf(cs, du[k], ss * dv[k]);
-                    dpe = fmaf(ge.x, c_ust[i] + du[k], dpe);
-                    dpe = fmaf(ge.y, c_vst[i] + dv[k], dpe);
-                    float f = 0.f;
+                for (int k0 = 0; k0 < NMT; k0 += KP) {
+                    float du[KP], dv[KP];
 #pragma unroll
-                    for (int e = 0; e < ND; ++e)
-                        if (e < d) f = fmaf(c_inj[e * G4 + i], xs[e], f);
-                    const float kd = a.omega_s * (yw[k] - w0);
-                    const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
-                    ad[k] = fmaf(b, kd, ad[k]);
-                    aw[k] = fmaf(b, kw, aw[k]);
-                    const float yd = fmaf(cn, kd, del[k]);
-                    yw[k] = fmaf(cn, kw, w[k]);
-                    if (pub) {
-                        // the next stage's input of machine i
-                        const bool big = __any_sync(0xffffffffu, i < n && fabsf(yd) > 0.8f);
-                        if (i < n) ghn[i * 128] = wide_gamma_eta(yd, cs, ss, big);
+                    for (int k = 0; k < KP; ++k) {
+                        du[k] = 0.f;
+                        dv[k] = 0.f;
+                    }
+#pragma unroll JU
+                    for (int j = 0; j < n; ++j) {
+                        const float2 gej = ghc[j * 128];
+                        const float4* g4 = reinterpret_cast<const float4*>(GEs + (j * 4 + h) * NMTP + k0);
+                        const float4* b4 = reinterpret_cast<const float4*>(BEs + (j * 4 + h) * NMTP + k0);
+#pragma unroll
+                        for (int k4 = 0; k4 < (KP + 3) / 4; ++k4) {
+                            if (k0 + 4 * k4 < NMT) {
+                                const float4 gv = g4[k4], bv = b4[k4];
+                                const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+                                const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    const int k = 4 * k4 + kk;
+                                    if (k < KP && k0 + k < NMT) {
+                                        du[k] = fmaf(gg[kk], gej.x, du[k]);
+                                        du[k] = fmaf(-bb[kk], gej.y, du[k]);
+                                        dv[k] = fmaf(gg[kk], gej.y, dv[k]);
+                                        dv[k] = fmaf(bb[kk], gej.x, dv[k]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int kq = 0; kq < KP; ++kq) {
+                        const int k = k0 + kq;
+                        if (k < NMT) {
+                            const int i = h + 4 * k;
+                            const float2 ge = ghc[(i < n ? i : 0) * 128];
+                            const float cs = c_cst[i], ss = c_sst[i];
+                            float dpe = fmaf(cs, du[kq], ss * dv[kq]);
+                            dpe = fmaf(ge.x, c_ust[i] + du[kq], dpe);
+                            dpe = fmaf(ge.y, c_vst[i] + dv[kq], dpe);
+                            float f = 0.f;
+#pragma unroll
+                            for (int e = 0; e < ND; ++e)
+                                if (e < d) f = fmaf(c_inj[e * G4 + i], xs[e], f);
+                            const float kd = a.omega_s * (yw[k] - w0);
+                            const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
+                            ad[k] = fmaf(b, kd, ad[k]);
+                            aw[k] = fmaf(b, kw, aw[k]);
+                            const float yd = fmaf(cn, kd, del[k]);
+                            yw[k] = fmaf(cn, kw, w[k]);
+                            if (pub) {
+                                // the next stage's input of machine i
+                                const bool big = __any_sync(0xffffffffu, i < n && fabsf(yd) > 0.8f);
+                                if (i < n) ghn[i * 128] = wide_gamma_eta(yd, cs, ss, big);
+                            }
+                        }
                     }
                 }
                 if (pub && h == 0) w0buf[(gb ^ 1) * 128 + r] = yw[0];
