@@ -37,6 +37,9 @@ LHS_MIDPOINT = 2
 RK4 = 0
 HEUN = 1
 
+BASIS_SINE = 0    # Brownian eigenbasis
+BASIS_COSINE = 1  # the paper's cosine white-noise basis
+
 
 @dataclasses.dataclass
 class Scenario:
@@ -65,6 +68,7 @@ class Scenario:
     Vinf: float = 1.0
     sampling: int = LHS
     integrator: int = RK4
+    basis: int = BASIS_SINE
 
     @property
     def Nt(self) -> int:

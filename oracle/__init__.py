@@ -13,14 +13,20 @@ Functions and the passages they follow:
   Algorithm 1 step 1.
 * ``ppnd16``                  -- inverse normal CDF, Wichura AS 241 (1988).
 * ``kl_increment_basis``, ``kl_path_basis``, ``kle_reconstruct`` -- Eqs. (kl),
-  (kle), (eqkl); Algorithm 1 step 2.
+  (kle), (eqkl); Algorithm 1 step 2.  Two bases: the Brownian eigenbasis (the
+  Karhunen-Loeve basis of min(s, t)) and the paper's cosine basis, Eq. (klb2).
+* ``em_normal``, ``em_increments``, ``simulate_em`` -- the traditional Monte
+  Carlo the paper compares against (Section V-B): Eq. (distito) with a fresh
+  normal per step.
 * ``electrical_power``, ``equilibrium`` -- Eqs. (state)/(algebra) for the
   classical model; equilibrium at t = 0 as in Section V-A.
 * ``simulate``                -- Algorithm 1 steps 2-4.
 * ``moments_twopass``         -- Algorithm 1 step 4.
 
 Pins (tests/test_oracle_*.py): Philox known-answer vectors, every LHS stratum
-hit once, Phi(Phi^-1(p)) = p, the KL variance identity at t = T, the OU and
+hit once, Phi(Phi^-1(p)) = p, the KL variance identity at t = T (and W(T)
+exact for the cosine basis, its bridge-tail bound), the per-step normals as
+Philox words through scipy's inverse CDF, the exact EM-OU variance, the OU and
 Lyapunov closed forms, constant equilibrium, RK4 order, product vs pairwise
 electrical power.  End-to-end moments of the nonlinear multi-machine system
 have no published values: parity unpinned beyond those invariants.
@@ -64,7 +70,8 @@ class _System(ctypes.Structure):
         ("G", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Ginf", ctypes.c_void_p), ("Binf", ctypes.c_void_p),
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
-        ("init_delta", ctypes.c_void_p),
+        ("init_delta", ctypes.c_void_p), ("basis", ctypes.c_int32), ("em", ctypes.c_int32),
+        ("em_seed", ctypes.c_uint64), ("em_k0", ctypes.c_int64),
     ]
 
 
@@ -87,6 +94,14 @@ def _load():
             lib.oracle_kl_increment_basis.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                       ctypes.c_void_p]
             lib.oracle_kl_path_basis.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]
+            lib.oracle_em_increments.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_double, ctypes.c_void_p]
+            lib.oracle_em_normal.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+            lib.oracle_em_normal.restype = ctypes.c_double
+            lib.oracle_kl_increment_basis_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                         ctypes.c_int32, ctypes.c_void_p]
+            lib.oracle_kl_path_basis_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                    ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_kle_reconstruct.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_electrical_power.argtypes = [ctypes.POINTER(_System), ctypes.c_void_p, ctypes.c_void_p,
@@ -142,22 +157,26 @@ def lhs_sample(seed: int, N: int, M: int, mode: int = LHS, k0: int = 0, count: i
     return (zeta, strata) if with_strata else zeta
 
 
-def kl_increment_basis(K: int, T: float, Nt: int) -> np.ndarray:
+BASIS_SINE = 0    # Brownian eigenbasis (the Karhunen-Loeve basis of min(s, t))
+BASIS_COSINE = 1  # the paper's Eq. (klb2)
+
+
+def kl_increment_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndarray:
     phi = np.zeros((K, Nt), dtype=np.float64)
-    _load().oracle_kl_increment_basis(K, T, Nt, _ptr(phi))
+    _load().oracle_kl_increment_basis_ex(basis, K, T, Nt, _ptr(phi))
     return phi
 
 
-def kl_path_basis(K: int, T: float, Nt: int) -> np.ndarray:
+def kl_path_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndarray:
     psi = np.zeros((K, Nt + 1), dtype=np.float64)
-    _load().oracle_kl_path_basis(K, T, Nt, _ptr(psi))
+    _load().oracle_kl_path_basis_ex(basis, K, T, Nt, _ptr(psi))
     return psi
 
 
-def kle_reconstruct(zeta: np.ndarray, d: int, K: int, T: float, Nt: int) -> np.ndarray:
+def kle_reconstruct(zeta: np.ndarray, d: int, K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndarray:
     zeta = np.ascontiguousarray(zeta, dtype=np.float64)
     count = zeta.shape[0]
-    phi = kl_increment_basis(K, T, Nt)
+    phi = kl_increment_basis(K, T, Nt, basis)
     dW = np.zeros((count, d, Nt), dtype=np.float64)
     _load().oracle_kle_reconstruct(_ptr(zeta), count, d, K, _ptr(phi), Nt, _ptr(dW))
     return dW
@@ -180,6 +199,7 @@ class _Holder:
         s.has_inf_bus = 1 if sc.has_inf_bus else 0
         s.integrator = int(sc.integrator if integrator is None else integrator)
         s.Vinf = float(sc.Vinf)
+        s.basis = int(getattr(sc, "basis", BASIS_SINE))
         if init_delta is not None:
             self.arrays["init_delta"] = f(init_delta)
         for name, arr in self.arrays.items():
@@ -217,6 +237,12 @@ def simulate(sc, zeta: np.ndarray, *, want_traj: bool = False, want_dW: bool = F
     initial state (speeds still start at zero).
     """
     h = _Holder(sc, integrator, init_delta)
+    return _simulate_holder(h, sc, zeta, want_traj=want_traj, want_dW=want_dW, want_moments=want_moments,
+                            pe_form=pe_form, nthreads=nthreads)
+
+
+def _simulate_holder(h, sc, zeta, *, want_traj: bool = False, want_dW: bool = False, want_moments: bool = True,
+                     pe_form: int = PE_PAIRWISE, nthreads: int = 1):
     zeta = np.ascontiguousarray(zeta, dtype=np.float64)
     S = zeta.shape[0]
     assert zeta.shape[1] == sc.d * sc.K
@@ -237,6 +263,28 @@ def simulate(sc, zeta: np.ndarray, *, want_traj: bool = False, want_dW: bool = F
     if want_moments:
         out["mean"], out["var"] = mean, var
     return out
+
+
+def em_increments(seed: int, k0: int, count: int, d: int, Nt: int, dt: float) -> np.ndarray:
+    """The "traditional MCs" increments (Eq. distito, fresh normal per step): dW [count, d, Nt]."""
+    dW = np.zeros((count, d, Nt), dtype=np.float64)
+    _load().oracle_em_increments(seed, k0, count, d, Nt, dt, _ptr(dW))
+    return dW
+
+
+def em_normal(seed: int, k: int, w: int, n: int) -> float:
+    return float(_load().oracle_em_normal(seed, k, w, n))
+
+
+def simulate_em(sc, k0: int = 0, count: int | None = None, **kw):
+    """``simulate`` with the per-step normal increments of samples k0..k0+count-1
+    (the paper's traditional Monte Carlo) instead of the KL expansion."""
+    count = sc.N - k0 if count is None else count
+    integrator = kw.pop("integrator", None)
+    init_delta = kw.pop("init_delta", None)
+    h = _Holder(sc, integrator, init_delta)
+    h.s.em, h.s.em_seed, h.s.em_k0 = 1, int(sc.seed), int(k0)
+    return _simulate_holder(h, sc, np.zeros((count, sc.d * sc.K)), **kw)
 
 
 def ou_em(dW: np.ndarray, dt: float, theta: float, sigma: float) -> np.ndarray:

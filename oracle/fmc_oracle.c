@@ -217,6 +217,35 @@ int oracle_lhs_sample(uint64_t seed, int64_t N, int64_t k0, int64_t count, int32
 }
 
 /* ------------------------------------------------------------------------- */
+/* The paper's "traditional MCs" (Section V-B): the disturbance advanced by the
+ * scheme of Eq. (distito) with a fresh standard normal per step, i.e. Wiener
+ * increments dW = sqrt(dt) zeta_{k,w,n} instead of a KL expansion.  The normal
+ * of (sample k, disturbance w, step n) is Phi^-1(u), u = (r + 1/2) 2^-32 with
+ * r = Philox(key = seed, counter = (k, n, 256, w / 4)) word (w mod 4).        */
+/* ------------------------------------------------------------------------- */
+#define ORACLE_TAG_EM 256u
+
+double oracle_em_normal(uint64_t seed, int64_t k, int32_t w, int32_t n)
+{
+    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)n, ORACLE_TAG_EM, (uint32_t)(w / 4)};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    double u = ((double)out[w % 4] + 0.5) * (1.0 / 4294967296.0);
+    return oracle_ppnd16(u);
+}
+
+/* dW [count][d][Nt] of samples k0..k0+count-1. */
+void oracle_em_increments(uint64_t seed, int64_t k0, int64_t count, int32_t d, int32_t Nt, double dt, double* dW)
+{
+    double sq = sqrt(dt);
+    for (int64_t s = 0; s < count; ++s)
+        for (int32_t w = 0; w < d; ++w)
+            for (int32_t n = 0; n < Nt; ++n)
+                dW[(s * d + w) * (int64_t)Nt + n] = sq * oracle_em_normal(seed, k0 + s, w, n);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Algorithm 1 step 2, Eqs. (kl)/(kle): truncated KL expansion of a standard
  * Wiener process on [0,T] with the Brownian eigenbasis,
  *   W(t) = sum_{k=1..K} zeta_k c_k sin(a_k t),  a_k = (k-1/2) pi / T,
@@ -238,6 +267,32 @@ void oracle_kl_increment_basis(int32_t K, double T, int32_t Nt, double* phi)
     }
 }
 
+/* The paper's own basis of Eq. (klb2): m_1(t) = 1/sqrt(T), m_j(t) = sqrt(2/T)
+ * cos((j-1) pi t / T) for j >= 2, an orthonormal basis of white noise on [0, T].
+ * Integrated from 0, as Eq. (kl) does: M_1(t) = t / sqrt(T) and
+ * M_j(t) = sqrt(2T) / ((j-1) pi) sin((j-1) pi t / T); the increments are the
+ * plain differences M_j(t_{n+1}) - M_j(t_n).                                 */
+static double cos_basis_integral(int32_t j, double T, double t)
+{
+    if (j == 1) return t / sqrt(T);
+    double a = (double)(j - 1) * ORACLE_PI / T;
+    return sqrt(2.0 * T) / ((double)(j - 1) * ORACLE_PI) * sin(a * t);
+}
+
+/* basis 0: the Brownian eigenbasis above; basis 1: Eq. (klb2). */
+void oracle_kl_increment_basis_ex(int32_t basis, int32_t K, double T, int32_t Nt, double* phi)
+{
+    if (basis == 0) {
+        oracle_kl_increment_basis(K, T, Nt, phi);
+        return;
+    }
+    double dt = T / (double)Nt;
+    for (int32_t j = 1; j <= K; ++j)
+        for (int32_t n = 0; n < Nt; ++n)
+            phi[(int64_t)(j - 1) * Nt + n] =
+                cos_basis_integral(j, T, (double)(n + 1) * dt) - cos_basis_integral(j, T, (double)n * dt);
+}
+
 /* W(t_n) itself (not used on the path; a pin for the covariance of the basis). */
 void oracle_kl_path_basis(int32_t K, double T, int32_t Nt, double* psi)
 {
@@ -248,6 +303,18 @@ void oracle_kl_path_basis(int32_t K, double T, int32_t Nt, double* psi)
         for (int32_t n = 0; n <= Nt; ++n)
             psi[(int64_t)(k - 1) * (Nt + 1) + n] = c * sin(a * (double)n * dt);
     }
+}
+
+void oracle_kl_path_basis_ex(int32_t basis, int32_t K, double T, int32_t Nt, double* psi)
+{
+    if (basis == 0) {
+        oracle_kl_path_basis(K, T, Nt, psi);
+        return;
+    }
+    double dt = T / (double)Nt;
+    for (int32_t j = 1; j <= K; ++j)
+        for (int32_t n = 0; n <= Nt; ++n)
+            psi[(int64_t)(j - 1) * (Nt + 1) + n] = cos_basis_integral(j, T, (double)n * dt);
 }
 
 /* Eq. (eqkl) as increments: dW[s][w][n] = sum_k zeta[s][w*K + k] phi[k][n]. */
@@ -307,6 +374,10 @@ typedef struct oracle_system {
     const double* sigma; /* [d] OU diffusion, p.u./sqrt(s) */
     const double* inject;/* [n*d] how disturbance w enters machine i's power */
     const double* init_delta; /* [n] initial angles instead of the equilibrium, or NULL */
+    int32_t basis;       /* 0: Brownian eigenbasis (sine), 1: Eq. (klb2) (cosine) */
+    int32_t em;          /* 1: per-step normal increments (Eq. distito), not the KL expansion */
+    uint64_t em_seed;    /* Philox key of those normals */
+    int64_t em_k0;       /* index of the first simulated sample */
 } oracle_system;
 
 /* Electrical power, textbook pairwise form:
@@ -556,13 +627,17 @@ static void* sim_worker(void* arg)
     ws_alloc(&w, n, d, Nt);
     double* traj_local = (double*)malloc(sizeof(double) * cols);
     for (int64_t smp = job->s0; smp < job->s1; ++smp) {
-        const double* z = job->zeta + smp * (int64_t)d * K;
-        for (int q = 0; q < d; ++q)
-            for (int step = 0; step < Nt; ++step) {
-                double acc = 0.0;
-                for (int k = 0; k < K; ++k) acc += z[q * K + k] * job->phi[(int64_t)k * Nt + step];
-                w.dW[(int64_t)q * Nt + step] = acc;
-            }
+        if (s->em) {
+            oracle_em_increments(s->em_seed, s->em_k0 + smp, 1, d, Nt, s->dt, w.dW);
+        } else {
+            const double* z = job->zeta + smp * (int64_t)d * K;
+            for (int q = 0; q < d; ++q)
+                for (int step = 0; step < Nt; ++step) {
+                    double acc = 0.0;
+                    for (int k = 0; k < K; ++k) acc += z[q * K + k] * job->phi[(int64_t)k * Nt + step];
+                    w.dW[(int64_t)q * Nt + step] = acc;
+                }
+        }
         if (job->dW_out) memcpy(job->dW_out + smp * (int64_t)d * Nt, w.dW, sizeof(double) * (size_t)d * Nt);
         double* traj = job->traj_out ? job->traj_out + smp * cols : traj_local;
         simulate_one(s, job->delta0, job->pm_eq, &w, job->pe_form, traj);
@@ -589,7 +664,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
     if (nthreads > count) nthreads = (int32_t)count;
     int64_t cols = (int64_t)(Nt + 1) * 2 * n;
     double* phi = (double*)malloc(sizeof(double) * (size_t)s->K * Nt);
-    oracle_kl_increment_basis(s->K, s->T, Nt, phi);
+    oracle_kl_increment_basis_ex(s->basis, s->K, s->T, Nt, phi);
     double* delta0 = (double*)malloc(sizeof(double) * n);
     double* pm_eq = (double*)malloc(sizeof(double) * n);
     if (oracle_equilibrium(s, delta0, pm_eq) < 0) {

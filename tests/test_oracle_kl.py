@@ -76,3 +76,53 @@ def test_empirical_increment_covariance(orc):
     # time average is about the closed-form remainder (2T/pi^2) psi_1(K + 1/2)
     rem = 2.0 * T / np.pi**2 * polygamma(1, 400 + 0.5)
     assert 0.5 * rem < (T / Nt - v400) < 1.5 * rem
+
+
+# ----------------------------------------------------------------------------- the paper's cosine basis
+# Eq. (klb2): m_1 = 1/sqrt(T), m_j = sqrt(2/T) cos((j-1) pi t / T).  Integrated,
+# the first term is t/sqrt(T) and the others are the Karhunen-Loeve expansion of
+# the Brownian bridge, whose variance is t (1 - t/T); so W_K(T) is exact for
+# every K, Var W_K(t) -> t from below, and the bridge tail after K - 1 terms is
+# at most (2T/pi^2) psi_1(K) (trigamma).
+
+
+@pytest.mark.parametrize("K,T", [(1, 1.0), (2, 3.0), (6, 60.0), (100, 10.0)])
+def test_cosine_basis_exact_at_horizon(orc, K, T):
+    Nt = 24
+    psi = orc.kl_path_basis(K, T, Nt, orc.BASIS_COSINE)
+    assert abs(np.sum(psi[:, Nt] ** 2) - T) < 1e-12 * T
+    assert abs(psi[0, Nt] - np.sqrt(T)) < 1e-14 * np.sqrt(T)
+
+
+@pytest.mark.parametrize("K", [1, 2, 17, 300])
+def test_cosine_basis_variance_below_t_within_bridge_tail(orc, K):
+    T, Nt = 10.0, 400
+    psi = orc.kl_path_basis(K, T, Nt, orc.BASIS_COSINE)
+    t = np.linspace(0.0, T, Nt + 1)
+    rem = t - np.sum(psi**2, axis=0)
+    assert rem.min() > -1e-12
+    assert rem.max() <= 2.0 * T / np.pi**2 * polygamma(1, K) + 1e-12
+    if K == 1:  # only the linear term: the bridge variance is missing entirely
+        assert np.allclose(rem, t * (1 - t / T), rtol=0, atol=1e-12)
+
+
+def test_cosine_basis_covariance_tends_to_min(orc):
+    K, T, Nt = 20000, 10.0, 20
+    psi = orc.kl_path_basis(K, T, Nt, orc.BASIS_COSINE)
+    t = np.linspace(0, T, Nt + 1)
+    cov = psi.T @ psi
+    assert np.max(np.abs(cov - np.minimum.outer(t, t))) <= 2.0 * T / np.pi**2 * polygamma(1, K) + 1e-12
+
+
+def test_cosine_basis_increments(orc):
+    K, T, Nt = 40, 5.0, 250
+    phi = orc.kl_increment_basis(K, T, Nt, orc.BASIS_COSINE)
+    psi = orc.kl_path_basis(K, T, Nt, orc.BASIS_COSINE)
+    assert np.allclose(phi, np.diff(psi, axis=1), rtol=0, atol=1e-14)
+    # the constant white-noise mode contributes dt/sqrt(T) per step; every
+    # oscillating mode integrates to zero over [0, T]
+    # (a difference of two values up to sqrt(T): a few ulps of sqrt(T) absolute)
+    assert np.allclose(phi[0], (T / Nt) / np.sqrt(T), rtol=0, atol=8 * np.finfo(float).eps * np.sqrt(T))
+    assert np.max(np.abs(phi[1:].sum(axis=1))) < 1e-13
+    # differs from the Brownian eigenbasis
+    assert np.max(np.abs(phi - orc.kl_increment_basis(K, T, Nt))) > 1e-3
