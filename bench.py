@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--disturbances", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=[None, "tol", "batch", "serve"],
+    ap.add_argument("--study", default=None, choices=[None, "tol", "batch", "serve", "dn"],
                     help="tol: LHS vs SRS (and precision forms) time to a stated error on E and Var; "
-                         "batch: 64 uneven scenarios in one captured graph; serve: Poisson request stream")
+                         "batch: 64 uneven scenarios in one captured graph; serve: Poisson request stream; "
+                         "dn: the paper's convergence experiment (generator trip, RMS frequency deviation, D(N))")
+    ap.add_argument("--dn-max", type=int, default=1000, help="largest N of the dn study")
     ap.add_argument("--max-machines", type=int, default=50,
                     help="upper end of the machine count drawn for the batch and serve studies")
     ap.add_argument("--seeds", type=int, default=32)
@@ -241,7 +243,11 @@ def run_tol_study(args):
     max |Var_N - Var_ref| / max Var_ref for the variance; err(N) is the RMS over
     the seeds.  Time to tolerance tau = device time of one run at the smallest N
     with err(N) <= tau.  Forms: fused BF16x3 LHS (the chosen form), fused BF16x3
-    SRS, fused BF16 LHS, plain FP32 LHS.
+    SRS, fused BF16 LHS, plain FP32 LHS, and the paper's traditional Monte Carlo
+    (a fresh normal per step, no KL expansion).  The traditional Monte Carlo
+    converges to the untruncated process, so its errors are taken against a
+    reference of its own (2^22 samples); the distance between the two references
+    (the KL truncation at this K) is reported beside them.
     """
     import torch
 
@@ -249,23 +255,33 @@ def run_tol_study(args):
     fmc.build()
     ctx = fmc.Context(0)
     base = workload(1 << 22, args.horizon)
-    # reference
+    # references: 2^22 samples in blocks of 2^18 combined by their shifted sums
     blk = 1 << 18
-    S1 = S2 = shift = None
-    for k0 in range(0, base.N, blk):
-        a, b, sh = fmc.simulate_sums(base, k0, blk, ctx=ctx)
-        S1 = a if S1 is None else S1 + a
-        S2 = b if S2 is None else S2 + b
-        shift = sh
-    mref, vref = fmc.moments_from_sums(S1, S2, shift, base.N, ctx=ctx)
-    mref, vref = mref.cpu().numpy(), vref.cpu().numpy()
+
+    def reference(sampling):
+        sc0 = base.replace(sampling=sampling)
+        S1 = S2 = shift = None
+        for k0 in range(0, sc0.N, blk):
+            a, b, sh = fmc.simulate_sums(sc0, k0, blk, ctx=ctx)
+            S1 = a if S1 is None else S1 + a
+            S2 = b if S2 is None else S2 + b
+            shift = sh
+        m, v = fmc.moments_from_sums(S1, S2, shift, sc0.N, ctx=ctx)
+        return m.cpu().numpy(), v.cpu().numpy()
+
+    refs = {fs.LHS: reference(fs.LHS), fs.SRS_EM: reference(fs.SRS_EM)}
+    mref, vref = refs[fs.LHS]
     escale = float(np.sqrt(vref.max()))
     vscale = float(vref.max())
     forms = [("fused-bf16x3-LHS", "fused", "bf16x3", fs.LHS), ("fused-bf16x3-SRS", "fused", "bf16x3", fs.SRS),
-             ("fused-bf16-LHS", "fused", "bf16", fs.LHS), ("plain-f32-LHS", "plain", "f32", fs.LHS)]
+             ("fused-bf16-LHS", "fused", "bf16", fs.LHS), ("plain-f32-LHS", "plain", "f32", fs.LHS),
+             ("fused-SRS_EM (traditional Monte Carlo)", "fused", "bf16x3", fs.SRS_EM)]
     Ns = [1 << e for e in range(6, 17)]
+    mem, vem = refs[fs.SRS_EM]
     out = {"workload": WORKLOAD.replace("N=2^16", "N varied"), "reference_samples": base.N, "seeds": args.seeds,
            "error_definition": "E: max|E_N-E_ref|/max sqrt(Var_ref); Var: max|Var_N-Var_ref|/max Var_ref; RMS over seeds",
+           "kl_truncation_between_references": {"E": float(np.max(np.abs(mem - mref)) / escale),
+                                                "Var": float(np.max(np.abs(vem - vref)) / vscale)},
            "forms": {}}
     for name, path, prec, samp in forms:
         rows = []
@@ -281,8 +297,9 @@ def run_tol_study(args):
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b))
                 m, v = m.cpu().numpy(), v.cpu().numpy()
-                errs_e.append(np.max(np.abs(m - mref)) / escale)
-                errs_v.append(np.max(np.abs(v - vref)) / vscale)
+                mr, vr = refs[fs.SRS_EM] if samp == fs.SRS_EM else refs[fs.LHS]
+                errs_e.append(np.max(np.abs(m - mr)) / escale)
+                errs_v.append(np.max(np.abs(v - vr)) / vscale)
             rows.append({"N": N, "err_E": float(np.sqrt(np.mean(np.square(errs_e)))),
                          "err_Var": float(np.sqrt(np.mean(np.square(errs_v)))),
                          "ms": float(np.median(times))})
@@ -343,9 +360,13 @@ def run_batch_study(args):
 
 
 def run_serve_study(args):
-    """Poisson request stream at several rates; requests drawn from the batch study's
-    distribution, each with its own seed; memory admission under a 120 GB budget.
-    Reports p50/p99 latency (submit -> moments complete) and samples/s per rate."""
+    """Poisson request stream at several rates.  Each request draws a scenario from
+    the batch study's distribution, its own seed and a target error on E and Var
+    (tol_E in {1e-2, 3e-3}, tol_Var in {3e-2, 1e-2}, the normalisation of the
+    convergence study); the server grows four independent designs from 256
+    samples each until the targets are met (at most 2^20 samples).  Memory
+    admission under a 120 GB budget.  Reports p50/p99 latency (submit -> moments
+    complete), samples/s and machine-steps/s per rate."""
     import torch
 
     import paper_2007_03847_gb300 as fmc
@@ -364,25 +385,90 @@ def run_serve_study(args):
             now = time.perf_counter() - t0
             if arrivals[k] > now:
                 time.sleep(arrivals[k] - now)
-            sc = pool[picks[k]].replace(seed=int(rng.integers(0, 2**31)))
-            handles.append((srv.submit(sc), sc.N))
-        lat, samples = [], 0
-        for h, N in handles:
-            res, _, _ = srv.wait(h, timeout_s=600)
+            sc = pool[picks[k]].replace(seed=int(rng.integers(0, 2**31)), N=256)
+            tol_E = float(rng.choice([1e-2, 3e-3]))
+            tol_V = float(rng.choice([3e-2, 1e-2]))
+            handles.append((srv.submit(sc, tol_E=tol_E, tol_Var=tol_V, max_N=1 << 20), sc))
+        lat, samples, msteps, met = [], 0, 0, 0
+        for h, sc in handles:
+            res, _, _ = srv.wait(h, timeout_s=900)
             assert res["status"] == 0, res
             lat.append(res["latency_us"] / 1e3)
-            samples += N
+            samples += res["n_used"]
+            msteps += res["n_used"] * sc.Nt * sc.n
+            met += int(res["target_met"])
         t_all = time.perf_counter() - t0
-        rows.append({"rate_req_s": lam, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / t_all,
-                     "wall_s": t_all})
+        rows.append({"rate_req_s": lam, "requests": nreq, "targets_met": met,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "samples_per_s": samples / t_all, "machine_steps_per_s": msteps / t_all, "wall_s": t_all})
     srv.close()
-    print(json.dumps({"study": "serve", "slots": 16, "budget_bytes": 120 << 30, "rows": rows}))
+    print(json.dumps({"study": "serve", "slots": 16, "budget_bytes": 120 << 30, "replicates": 4,
+                      "initial_samples_per_design": 256, "max_samples": 1 << 20, "rows": rows}))
+    return 0
+
+
+def run_dn_study(args):
+    """The paper's convergence experiment (Section V-B, Table II) on the 10-machine
+    system: the generator with the largest mechanical power trips at t = 1 s (its
+    mechanical power is lost; the classical model keeps it electrically connected),
+    the response function is the RMS of the system (centre-of-inertia) frequency
+    deviation over 60 s, and for N = 1..dn_max a fresh design of N samples gives
+    E[RRF](N) and Var[RRF](N).  The degree of convergence D(N) is max - min of the
+    estimate over N-4..N.  Methods: LHS with K = 6 KL terms per disturbance (the
+    paper's setting) and K = 200, and the traditional Monte Carlo (a fresh normal
+    per step).  Reported: D at dn_max for each method and the smallest N at which
+    each KL/LHS method's D falls to the traditional Monte Carlo's D(dn_max)."""
+    import paper_2007_03847_gb300 as fmc
+    fmc.build()
+    ctx = fmc.Context(0)
+    base = fs.multimachine_case(n=10, d=3, K=6, T=60.0, dt=0.005, N=1, seed=0)
+    k = int(np.argmax(base.Pm[1:])) + 1          # not the balancing machine 0
+    base = base.replace(event_machine=k, event_time=1.0, event_dpm=-float(base.Pm[k]))
+    methods = [("LHS, K=6", dict(K=6, sampling=fs.LHS)), ("LHS, K=200", dict(K=200, sampling=fs.LHS)),
+               ("traditional Monte Carlo", dict(K=6, sampling=fs.SRS_EM))]
+    Nmax = args.dn_max
+    out = {"study": "dn", "system": "10-machine (39-bus-shaped draws), 3 OU disturbances, T = 60 s, dt = 5 ms",
+           "event": {"machine": k, "time_s": 1.0, "dPm": -float(base.Pm[k])},
+           "response": "RMS over 60 s of the centre-of-inertia speed deviation (p.u.)", "N_max": Nmax,
+           "methods": {}}
+    curves = {}
+    t0 = time.perf_counter()
+    for name, kw in methods:
+        E = np.full(Nmax + 1, np.nan)
+        V = np.full(Nmax + 1, np.nan)
+        for N in range(1, Nmax + 1):
+            sc = base.replace(N=N, seed=7919 * N + 17, **kw)
+            rrf, _, _ = fmc.simulate_rrf(sc, path="fused", precision="bf16x3", ctx=ctx)
+            E[N], V[N] = rrf.cpu().numpy()
+        dE = np.full(Nmax + 1, np.nan)
+        dV = np.full(Nmax + 1, np.nan)
+        for N in range(6, Nmax + 1):
+            dE[N] = np.max(E[N - 4:N + 1]) - np.min(E[N - 4:N + 1])
+            dV[N] = np.max(V[N - 4:N + 1]) - np.min(V[N - 4:N + 1])
+        curves[name] = (E, V, dE, dV)
+    mc = curves["traditional Monte Carlo"]
+    for name, (E, V, dE, dV) in curves.items():
+        hitE = next((N for N in range(6, Nmax + 1) if dE[N] <= mc[2][Nmax]), None)
+        hitV = next((N for N in range(6, Nmax + 1) if dV[N] <= mc[3][Nmax]), None)
+        out["methods"][name] = {
+            "E_RRF_at_Nmax": float(E[Nmax]), "Var_RRF_at_Nmax": float(V[Nmax]),
+            "D_E_at_Nmax": float(dE[Nmax]), "D_Var_at_Nmax": float(dV[Nmax]),
+            "N_to_reach_MC_D_E": hitE, "N_to_reach_MC_D_Var": hitV,
+            "sample_ratio_E": None if hitE is None else Nmax / hitE,
+            "sample_ratio_Var": None if hitV is None else Nmax / hitV,
+            "D_E": [float(x) for x in dE[6::max(1, Nmax // 100)]],
+            "D_Var": [float(x) for x in dV[6::max(1, Nmax // 100)]],
+        }
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+    ctx.close()
     return 0
 
 
 def main():
     args = parse()
+    if args.study == "dn":
+        return run_dn_study(args)
     if args.study == "batch":
         return run_batch_study(args)
     if args.study == "serve":

@@ -33,6 +33,7 @@ import numpy as np
 LHS = 0
 SRS = 1
 LHS_MIDPOINT = 2
+SRS_EM = 3  # the paper's traditional Monte Carlo: a fresh normal per step (no KL expansion)
 
 RK4 = 0
 HEUN = 1
@@ -69,6 +70,15 @@ class Scenario:
     sampling: int = LHS
     integrator: int = RK4
     basis: int = BASIS_SINE
+    # an event in the style of the paper's generator trip: from t = event_time on
+    # (rounded to the grid) machine event_machine's mechanical power changes by
+    # event_dpm p.u.; None: no event
+    event_machine: int | None = None
+    event_time: float = 0.0
+    event_dpm: float = 0.0
+    # general Ito disturbances (one dict per disturbance, see ito_* below), or
+    # None: every disturbance is Ornstein-Uhlenbeck with theta, sigma
+    ito: list | None = None
 
     @property
     def Nt(self) -> int:
@@ -83,6 +93,36 @@ class Scenario:
 
     def machine_steps(self) -> int:
         return int(self.N) * self.Nt * self.n
+
+
+# One-dimensional Ito processes of the paper's Table I (unit rate) and the wind
+# model it identifies (Eq. windito): drift m0 + m1 x + m2 x^2; diffusion either
+# s0 + s1 x + s2 x^2 (kind 1) or the square root of v0 + v1 x + v2 x^2 + v3 |x - a|
+# (kind 2); x0 = the start (the mean of the stationary law, or the drift's
+# stable root).
+def ito_gaussian(a: float, b: float) -> dict:
+    return dict(kind=2, m=(a, -1.0, 0.0), v=(2.0 * b, 0.0, 0.0, 0.0), a=0.0, x0=a)
+
+
+def ito_beta(a: float, b: float) -> dict:
+    return dict(kind=2, m=(a / (a + b), -1.0, 0.0), v=(0.0, 2.0 / (a + b), -2.0 / (a + b), 0.0), a=0.0,
+                x0=a / (a + b))
+
+
+def ito_gamma(a: float, b: float) -> dict:
+    return dict(kind=2, m=(a / b, -1.0, 0.0), v=(0.0, 2.0 / b, 0.0, 0.0), a=0.0, x0=a / b)
+
+
+def ito_laplace(a: float, b: float) -> dict:
+    return dict(kind=2, m=(a, -1.0, 0.0), v=(2.0 * b * b, 0.0, 0.0, 2.0 * b), a=a, x0=a)
+
+
+def ito_wind() -> dict:
+    m = (0.0535, -0.0899, 0.0349)
+    # the stable root of the drift (where it decreases)
+    r = np.roots([m[2], m[1], m[0]])
+    x0 = float(min(r.real))
+    return dict(kind=1, m=m, s=(-0.410, 0.919, -0.505), a=0.0, x0=x0)
 
 
 def _f64(a) -> np.ndarray:

@@ -54,6 +54,10 @@ extern "C" {
 #define FMC_LHS 0           /* Latin hypercube: stratum pi_i(k), uniform inside */
 #define FMC_SRS 1           /* simple random sampling: p = u */
 #define FMC_LHS_MIDPOINT 2  /* Latin hypercube at the stratum midpoint */
+#define FMC_SRS_EM 3        /* the paper's traditional Monte Carlo (Section V-B): a fresh normal per
+                               step and disturbance, dW = sqrt(dt) Phi^-1(u) with u from Philox
+                               counter (k, n, 256, w/4) word w mod 4 -- Eq. (distito); no KL
+                               expansion, K and the precision are not used */
 
 /* ---- contraction precision of the KL reconstruction ------------------------- */
 #define FMC_PREC_F32 0      /* FP32 SIMT (the plain form) */
@@ -63,6 +67,10 @@ extern "C" {
 /* ---- integrators for the swing equations --------------------------------- */
 #define FMC_RK4 0
 #define FMC_HEUN 1
+
+/* ---- KL bases ------------------------------------------------------------ */
+#define FMC_BASIS_SINE 0    /* eigenbasis of min(s,t): the Karhunen-Loeve expansion of W */
+#define FMC_BASIS_COSINE 1  /* the paper's Eq. (klb2): constant + cosine white-noise modes */
 
 /* ---- simulation paths --------------------------------------------------- */
 #define FMC_PATH_FUSED 0    /* one kernel: contraction in TMEM -> integrator -> moment partials */
@@ -95,6 +103,32 @@ typedef struct fmc_ctx fmc_ctx;
  * (its Pm is replaced by the balance).
  * All arrays are host memory, read during the call.
  */
+/*
+ * A general one-dimensional Ito disturbance (Section II, Table I; the wind model
+ * of Eq. windito):  d xi = mu(xi) dt + sigma(xi) dW,  xi(0) = x0,
+ *   mu(x) = m[0] + m[1] x + m[2] x^2,
+ *   kind FMC_ITO_POLY: sigma(x)   = s[0] + s[1] x + s[2] x^2,
+ *   kind FMC_ITO_SQRT: sigma(x)^2 = v[0] + v[1] x + v[2] x^2 + v[3] |x - a|  (sigma = 0 where negative),
+ *   kind FMC_ITO_OU:   the scenario's theta/sigma (mu = -theta x, sigma const, x0 = 0).
+ * The system is at equilibrium with the disturbance at x0 (the power balance sees
+ * inject * (xi - x0)).  Advanced by the scheme of Eq. (distito); with KL paths
+ * (smooth, so converging to the Stratonovich solution) the drift carries
+ * -sigma sigma'/2 so that the limit is the Ito process; with per-step normals
+ * (FMC_SRS_EM) it does not.
+ */
+#define FMC_ITO_OU 0
+#define FMC_ITO_POLY 1
+#define FMC_ITO_SQRT 2
+typedef struct fmc_ito {
+    int32_t kind;
+    int32_t reserved;
+    double m[3];
+    double s[3];
+    double v[4];
+    double a;
+    double x0;
+} fmc_ito;
+
 typedef struct fmc_scenario {
     int32_t n;              /* machines, 1..FMC_MAX_MACHINES (FMC_MAX_MACHINES_PLAIN on the plain path) */
     int32_t d;              /* disturbances = Wiener processes, 1..FMC_MAX_DISTURBANCES */
@@ -107,7 +141,7 @@ typedef struct fmc_scenario {
     int32_t precision;      /* FMC_PREC_* of the KL contraction */
     int32_t integrator;     /* FMC_RK4 or FMC_HEUN */
     int32_t has_inf_bus;    /* 0 or 1 */
-    int32_t reserved0;
+    int32_t basis;          /* FMC_BASIS_SINE (default) or FMC_BASIS_COSINE */
     double omega_s;         /* synchronous speed, rad/s */
     double Vinf;            /* infinite-bus voltage */
     const double* G;        /* [n][n] conductance */
@@ -121,6 +155,15 @@ typedef struct fmc_scenario {
     const double* theta;    /* [d] OU rates, 1/s */
     const double* sigma;    /* [d] OU diffusion coefficients */
     const double* inject;   /* [n][d] weight of disturbance w in machine i's power balance */
+    /* An event in the style of the paper's generator trip (Section V-A): from grid
+     * step round(event_time/dt) on, machine event_machine's mechanical power
+     * changes by event_dpm p.u. (negative: generation lost), for whole steps.
+     * event_machine < 0: none.  It takes a disturbance slot: d <= 7 with an event. */
+    int32_t event_machine;
+    int32_t reserved1;
+    double event_time;      /* s */
+    double event_dpm;       /* p.u. */
+    const fmc_ito* ito;     /* [d] disturbance models, or NULL: all Ornstein-Uhlenbeck (theta, sigma) */
 } fmc_scenario;
 
 /* ---- context ------------------------------------------------------------- */
@@ -174,13 +217,16 @@ int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int
 /* ---- Algorithm 1 step 2: KL reconstruction (Eqs. kl, kle, eqkl) --------------- */
 
 /*
- * Increment basis of the truncated Brownian KL expansion on the grid
- * t_n = n T/Nt:  phi[k][n] = c_k (sin(a_k t_{n+1}) - sin(a_k t_n)),
- * a_k = (k+1/2) pi / T, c_k = sqrt(2T)/((k+1/2) pi), k = 0..K-1 (0-based).
+ * Increment basis of the truncated KL expansion on the grid t_n = n T/Nt,
+ * k = 0..K-1 (0-based):
+ *   FMC_BASIS_SINE   (Brownian eigenbasis): phi[k][n] = c_k (sin(a_k t_{n+1}) - sin(a_k t_n)),
+ *                    a_k = (k+1/2) pi / T, c_k = sqrt(2T)/((k+1/2) pi);
+ *   FMC_BASIS_COSINE (Eq. klb2, integrated): phi[0][n] = dt/sqrt(T), and for k >= 1
+ *                    c_k (sin(a_k t_{n+1}) - sin(a_k t_n)), a_k = k pi / T, c_k = sqrt(2T)/(k pi).
  * Computed in FP64 on the GPU and rounded:  phi_dev [K][Nt] float.
- * Errors: FMC_EINVAL if K < 1, Nt < 1 or T <= 0.
+ * Errors: FMC_EINVAL if K < 1, Nt < 1, T <= 0 or an unknown basis.
  */
-int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, float* phi_dev, void* stream);
+int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, int32_t basis, float* phi_dev, void* stream);
 
 /*
  * Increments of the reconstructed Wiener paths of `count` samples:
@@ -274,8 +320,9 @@ int fmc_simulate_sums(fmc_ctx* ctx, const fmc_scenario* scen, int64_t k0, int64_
  * horizon, N), run concurrently on the GPU: every scenario's kernels go to one
  * of up to 16 library streams in turn, forked from and joined back to the
  * caller's stream, so that the CTAs of different scenarios share the SMs.
- * fmc_batch_create checks every scenario, solves every equilibrium (waiting for
- * the device), reserves each scenario's workspace and, with use_graph = 1,
+ * fmc_batch_create copies and checks every scenario (the caller's arrays may go
+ * away afterwards), solves every equilibrium (waiting for the device), reserves
+ * each scenario's workspace and, with use_graph = 1,
  * captures the whole batch into one CUDA graph; fmc_batch_launch then replays
  * it with a single graph launch on `stream` (or enqueues the kernels again
  * without a graph).  Results: mean_dev[i], var_dev[i] [Nt_i+1][2 n_i] double
@@ -314,20 +361,53 @@ int fmc_simulate_batch(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, i
 typedef struct fmc_server fmc_server;
 typedef struct fmc_result {
     int32_t status;         /* FMC_OK or the request's error code */
-    int32_t reserved;
+    int32_t replicates;     /* independent designs behind the moments (1 without a target) */
     double latency_us;      /* submit -> results complete on the device */
     double queue_us;        /* submit -> admitted */
     uint64_t device_bytes;  /* workspace charged against the budget */
+    int64_t n_used;         /* samples simulated for the reported moments */
+    double err_E;           /* estimated error of the expectations (targets only, else -1) */
+    double err_Var;         /* estimated error of the variances (targets only, else -1) */
+    int32_t target_met;     /* 1 if both targets were reached (targets only) */
+    int32_t reserved;
     char message[256];      /* error text, "" on success */
 } fmc_result;
 int fmc_server_create(int device, int32_t slots, size_t mem_budget_bytes, fmc_server** out);
 int fmc_server_destroy(fmc_server* srv);
 int fmc_submit(fmc_server* srv, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
                uint64_t* handle);
+/*
+ * A request with a target error instead of a sample count.  The server runs
+ * R = 4 independent Latin hypercube designs (seeds derived from the scenario's)
+ * of n samples each, starting at n = scen->N, and estimates the error of the
+ * pooled moments from the spread of the replicates:
+ *   err_E   = max_{t,s} sd_r(E_r) / sqrt(R) / max_{t,s} sqrt(Var),
+ *   err_Var = max_{t,s} sd_r(Var_r) / sqrt(R) / max_{t,s} Var
+ * (the normalisation of the error the convergence study reports).  While a
+ * target (> 0) is missed and 4 R n <= max_N, n grows fourfold and the designs
+ * are drawn again.  The result holds the pooled moments (replicate averages) of
+ * the last round, n_used = R n, the error estimates and target_met.  Only
+ * Latin hypercube and simple random sampling take targets.
+ */
+int fmc_submit_target(fmc_server* srv, const fmc_scenario* scen, int32_t path, double tol_E, double tol_Var,
+                      int64_t max_N, double* mean_dev, double* var_dev, uint64_t* handle);
 int fmc_poll(fmc_server* srv, uint64_t handle, fmc_result* out);
 int fmc_wait(fmc_server* srv, uint64_t handle, int64_t timeout_us, fmc_result* out);
 int fmc_cancel(fmc_server* srv, uint64_t handle);
 int fmc_server_stats(fmc_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use);
+
+/*
+ * The paper's response function (Section V-B), per sample: the RMS over the
+ * horizon of the system frequency deviation, taken as the centre-of-inertia
+ * speed deviation omega_coi = sum_i H_i domega_i / sum_i H_i on the grid,
+ *   RRF = sqrt( (1/Nt) sum_{n=1..Nt} omega_coi(t_n)^2 )   (p.u.),
+ * and its expectation and unbiased variance over the N samples:
+ *   rrf_dev [2] FP64 (device): E[RRF], Var[RRF].
+ * Runs the whole scenario like fmc_simulate; mean_dev / var_dev [Nt+1][2n]
+ * receive the moment trajectories too, or may be NULL.
+ */
+int fmc_simulate_rrf(fmc_ctx* ctx, const fmc_scenario* scen, int32_t path, double* rrf_dev, double* mean_dev,
+                     double* var_dev, void* stream);
 
 /* ---- Algorithm 1 step 4 --------------------------------------------------- */
 

@@ -62,6 +62,29 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Ito(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("m0", ctypes.c_double), ("m1", ctypes.c_double),
+                ("m2", ctypes.c_double), ("s0", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double),
+                ("v0", ctypes.c_double), ("v1", ctypes.c_double), ("v2", ctypes.c_double), ("v3", ctypes.c_double),
+                ("a", ctypes.c_double), ("x0", ctypes.c_double)]
+
+
+def _ito_struct(spec) -> _Ito:
+    """spec: dict(kind=1|2, m=(m0, m1, m2), s=(s0, s1, s2) | v=(v0, v1, v2, v3), a=..., x0=...), or None (OU)."""
+    it = _Ito()
+    if spec is None:
+        return it
+    it.kind = int(spec["kind"])
+    it.m0, it.m1, it.m2 = (float(c) for c in spec["m"])
+    if it.kind == 1:
+        it.s0, it.s1, it.s2 = (float(c) for c in spec["s"])
+    else:
+        it.v0, it.v1, it.v2, it.v3 = (float(c) for c in spec["v"])
+    it.a = float(spec.get("a", 0.0))
+    it.x0 = float(spec.get("x0", 0.0))
+    return it
+
+
 class _System(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int32), ("d", ctypes.c_int32), ("K", ctypes.c_int32), ("Nt", ctypes.c_int32),
@@ -71,7 +94,8 @@ class _System(ctypes.Structure):
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
         ("init_delta", ctypes.c_void_p), ("basis", ctypes.c_int32), ("em", ctypes.c_int32),
-        ("em_seed", ctypes.c_uint64), ("em_k0", ctypes.c_int64),
+        ("em_seed", ctypes.c_uint64), ("em_k0", ctypes.c_int64), ("event_machine", ctypes.c_int32),
+        ("event_step", ctypes.c_int32), ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p),
     ]
 
 
@@ -98,6 +122,8 @@ def _load():
                                                  ctypes.c_int32, ctypes.c_double, ctypes.c_void_p]
             lib.oracle_em_normal.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
             lib.oracle_em_normal.restype = ctypes.c_double
+            lib.oracle_ito_paths.argtypes = [ctypes.POINTER(_Ito), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_kl_increment_basis_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                          ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_kl_path_basis_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -109,7 +135,7 @@ def _load():
             lib.oracle_equilibrium.argtypes = [ctypes.POINTER(_System), ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_equilibrium.restype = ctypes.c_int
             lib.oracle_simulate.argtypes = [ctypes.POINTER(_System), ctypes.c_void_p, ctypes.c_int64,
-                                            ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 6
+                                            ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 7
             lib.oracle_simulate.restype = ctypes.c_int
             lib.oracle_ou_em.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
@@ -200,6 +226,14 @@ class _Holder:
         s.integrator = int(sc.integrator if integrator is None else integrator)
         s.Vinf = float(sc.Vinf)
         s.basis = int(getattr(sc, "basis", BASIS_SINE))
+        ev = getattr(sc, "event_machine", -1)
+        s.event_machine = int(ev if ev is not None else -1)
+        s.event_step = int(round(float(getattr(sc, "event_time", 0.0)) / float(sc.dt)))
+        s.event_dpm = float(getattr(sc, "event_dpm", 0.0))
+        specs = getattr(sc, "ito", None)
+        if specs is not None:
+            self.ito = (_Ito * sc.d)(*[_ito_struct(sp) for sp in specs])
+            s.ito = ctypes.cast(self.ito, ctypes.c_void_p)
         if init_delta is not None:
             self.arrays["init_delta"] = f(init_delta)
         for name, arr in self.arrays.items():
@@ -252,8 +286,9 @@ def _simulate_holder(h, sc, zeta, *, want_traj: bool = False, want_dW: bool = Fa
     traj = np.zeros((S, Nt + 1, 2 * n)) if want_traj else None
     mean = np.zeros((Nt + 1, 2 * n)) if want_moments else None
     var = np.zeros((Nt + 1, 2 * n)) if want_moments else None
+    rrf = np.zeros(S)
     rc = _load().oracle_simulate(ctypes.byref(h.s), _ptr(zeta), S, pe_form, nthreads, _ptr(out["delta0"]),
-                                 _ptr(out["pm_eq"]), _ptr(dW), _ptr(traj), _ptr(mean), _ptr(var))
+                                 _ptr(out["pm_eq"]), _ptr(dW), _ptr(traj), _ptr(mean), _ptr(var), _ptr(rrf))
     if rc != 0:
         raise RuntimeError(f"oracle_simulate failed ({rc})")
     if want_dW:
@@ -262,6 +297,8 @@ def _simulate_holder(h, sc, zeta, *, want_traj: bool = False, want_dW: bool = Fa
         out["traj"] = traj
     if want_moments:
         out["mean"], out["var"] = mean, var
+    # the response function of every sample (RMS centre-of-inertia speed deviation)
+    out["rrf"] = rrf
     return out
 
 
@@ -285,6 +322,18 @@ def simulate_em(sc, k0: int = 0, count: int | None = None, **kw):
     h = _Holder(sc, integrator, init_delta)
     h.s.em, h.s.em_seed, h.s.em_k0 = 1, int(sc.seed), int(k0)
     return _simulate_holder(h, sc, np.zeros((count, sc.d * sc.K)), **kw)
+
+
+def ito_paths(spec, dW: np.ndarray, dt: float, stratonovich: bool) -> np.ndarray:
+    """Paths x [S, Nt+1] of a general disturbance (Table I / Eq. windito) driven by
+    increments dW [S, Nt]; stratonovich: subtract sigma sigma'/2 from the drift
+    (increments of a smooth KL path)."""
+    dW = np.ascontiguousarray(dW, dtype=np.float64)
+    S, Nt = dW.shape
+    x = np.zeros((S, Nt + 1))
+    it = _ito_struct(spec)
+    _load().oracle_ito_paths(ctypes.byref(it), _ptr(dW), S, Nt, dt, 1 if stratonovich else 0, _ptr(x))
+    return x
 
 
 def ou_em(dW: np.ndarray, dt: float, theta: float, sigma: float) -> np.ndarray:

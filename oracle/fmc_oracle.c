@@ -348,6 +348,66 @@ void oracle_ou_em(const double* dW, int64_t count, int32_t Nt, double dt, double
 }
 
 /* ------------------------------------------------------------------------- */
+/* General one-dimensional Ito disturbances (Section II, Table I; the wind model
+ * of Eq. windito): d xi = mu(xi) dt + sigma(xi) dW with
+ *   mu(x)       = m0 + m1 x + m2 x^2,
+ *   kind 1:  sigma(x)   = s0 + s1 x + s2 x^2                 (Eq. windito),
+ *   kind 2:  sigma(x)^2 = v0 + v1 x + v2 x^2 + v3 |x - a|    (Table I; sigma = 0 where negative),
+ * started at x(0) = x0.  Advanced by the scheme of Eq. (distito),
+ *   x_{n+1} = x_n + (mu(x_n) - c sigma(x_n) sigma'(x_n) / 2) dt + sigma(x_n) dW_n,
+ * where c = 1 when the increments come from a (smooth) KL expansion: such paths
+ * converge to the Stratonovich solution, and the term restores the Ito drift;
+ * c = 0 for per-step normal increments.                                       */
+/* ------------------------------------------------------------------------- */
+typedef struct oracle_ito {
+    int32_t kind;   /* 0: Ornstein-Uhlenbeck from the system's theta/sigma; 1, 2 as above */
+    int32_t pad;
+    double m0, m1, m2;
+    double s0, s1, s2;
+    double v0, v1, v2, v3, a;
+    double x0;
+} oracle_ito;
+
+static double ito_sigma(const oracle_ito* p, double x)
+{
+    if (p->kind == 1) return p->s0 + p->s1 * x + p->s2 * x * x;
+    double v = p->v0 + p->v1 * x + p->v2 * x * x + p->v3 * fabs(x - p->a);
+    return v > 0.0 ? sqrt(v) : 0.0;
+}
+
+/* sigma(x) sigma'(x): kind 1 by the product rule; kind 2 as half the derivative
+ * of sigma^2 (the sign of x - a for the absolute value; 0 where sigma^2 <= 0). */
+static double ito_sigma_dsigma(const oracle_ito* p, double x)
+{
+    if (p->kind == 1) return ito_sigma(p, x) * (p->s1 + 2.0 * p->s2 * x);
+    double v = p->v0 + p->v1 * x + p->v2 * x * x + p->v3 * fabs(x - p->a);
+    if (v <= 0.0) return 0.0;
+    double sg = (x > p->a) ? 1.0 : ((x < p->a) ? -1.0 : 0.0);
+    return 0.5 * (p->v1 + 2.0 * p->v2 * x + p->v3 * sg);
+}
+
+double oracle_ito_step(const oracle_ito* p, double x, double dt, double dW, int32_t strat)
+{
+    double mu = p->m0 + p->m1 * x + p->m2 * x * x;
+    if (strat) mu -= 0.5 * ito_sigma_dsigma(p, x);
+    return x + mu * dt + ito_sigma(p, x) * dW;
+}
+
+/* Paths x [count][Nt+1] of one disturbance from increments dW [count][Nt]. */
+void oracle_ito_paths(const oracle_ito* p, const double* dW, int64_t count, int32_t Nt, double dt, int32_t strat,
+                      double* x)
+{
+    for (int64_t s = 0; s < count; ++s) {
+        double v = p->x0;
+        x[s * (Nt + 1)] = v;
+        for (int32_t n = 0; n < Nt; ++n) {
+            v = oracle_ito_step(p, v, dt, dW[s * Nt + n], strat);
+            x[s * (Nt + 1) + n + 1] = v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* The system (Eqs. state/algebra reduced to the classical model).            */
 /* ------------------------------------------------------------------------- */
 typedef struct oracle_system {
@@ -378,6 +438,16 @@ typedef struct oracle_system {
     int32_t em;          /* 1: per-step normal increments (Eq. distito), not the KL expansion */
     uint64_t em_seed;    /* Philox key of those normals */
     int64_t em_k0;       /* index of the first simulated sample */
+    /* an event in the style of the paper's generator trip (Section V-A): from grid
+     * time t_{event_step} on, machine event_machine's mechanical power changes by
+     * event_dpm (negative: generation lost); event_machine < 0: no event */
+    int32_t event_machine;
+    int32_t event_step;
+    double event_dpm;
+    /* [d] general disturbances, or NULL: all Ornstein-Uhlenbeck (theta, sigma).
+     * The system is at equilibrium with every disturbance at its x0: the power
+     * balance sees inject (x - x0).                                            */
+    const oracle_ito* ito;
 } oracle_system;
 
 /* Electrical power, textbook pairwise form:
@@ -523,63 +593,69 @@ static void ws_alloc(sim_ws* w, int n, int d, int Nt)
 
 /* Right-hand side of the swing equations at disturbance state xs. */
 static void swing_rhs(const oracle_system* s, const double* pm_eq, const double* delta, const double* omega,
-                      const double* xs, sim_ws* w, int32_t pe_form, double* ddelta, double* domega)
+                      const double* xs, sim_ws* w, int32_t pe_form, int32_t event_on, double* ddelta, double* domega)
 {
     int n = s->n, d = s->d;
     oracle_electrical_power(s, delta, w->pe, pe_form);
     for (int i = 0; i < n; ++i) {
         double force = pm_eq[i];
-        for (int q = 0; q < d; ++q) force += s->inject[i * d + q] * xs[q];
+        if (event_on && i == s->event_machine) force += s->event_dpm;
+        for (int q = 0; q < d; ++q) force += s->inject[i * d + q] * (xs[q] - (s->ito ? s->ito[q].x0 : 0.0));
         ddelta[i] = s->omega_s * omega[i];
         domega[i] = (force - w->pe[i] - s->D[i] * omega[i]) / (2.0 * s->H[i]);
     }
 }
 
 /* Integrates one sample whose increments are dW[w][n]; writes the trajectory
- * traj[n][j] (j < n: delta_j, j >= n: domega_j) for n = 0..Nt.                 */
+ * traj[n][j] (j < n: delta_j, j >= n: domega_j) for n = 0..Nt.  An event (see
+ * oracle_system) acts on whole steps from step event_step on.                 */
 static void simulate_one(const oracle_system* s, const double* delta0, const double* pm_eq, sim_ws* w,
                          int32_t pe_form, double* traj)
 {
     int n = s->n, d = s->d, Nt = s->Nt;
     double dt = s->dt;
+    int32_t ev = 0;
     for (int i = 0; i < n; ++i) { w->delta[i] = delta0[i]; w->omega[i] = 0.0; }
-    for (int q = 0; q < d; ++q) w->x[q] = 0.0;
+    for (int q = 0; q < d; ++q) w->x[q] = s->ito ? s->ito[q].x0 : 0.0;
     for (int i = 0; i < n; ++i) { traj[i] = w->delta[i]; traj[n + i] = w->omega[i]; }
     for (int step = 0; step < Nt; ++step) {
+        ev = (s->event_machine >= 0 && step >= s->event_step);
         /* Euler-Maruyama for the OU disturbance (Eq. distito, Table I) */
         for (int q = 0; q < d; ++q)
-            w->xn[q] = w->x[q] + (-s->theta[q] * w->x[q]) * dt + s->sigma[q] * w->dW[(int64_t)q * Nt + step];
+            w->xn[q] = (s->ito && s->ito[q].kind != 0)
+                           ? oracle_ito_step(&s->ito[q], w->x[q], dt, w->dW[(int64_t)q * Nt + step], !s->em)
+                           : w->x[q] + (-s->theta[q] * w->x[q]) * dt + s->sigma[q] * w->dW[(int64_t)q * Nt + step];
         if (s->integrator == 0) {
             /* classical RK4 */
-            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, w->k1d, w->k1w);
+            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, ev, w->k1d, w->k1w);
             for (int q = 0; q < d; ++q) w->xs[q] = 0.5 * (w->x[q] + w->xn[q]);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k1d[i];
                 w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k1w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, w->k2d, w->k2w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, ev, w->k2d, w->k2w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k2d[i];
                 w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k2w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, w->k3d, w->k3w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, ev, w->k3d, w->k3w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + dt * w->k3d[i];
                 w->tmpw[i] = w->omega[i] + dt * w->k3w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, w->k4d, w->k4w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, ev, w->k4d, w->k4w);
             for (int i = 0; i < n; ++i) {
                 w->delta[i] += dt / 6.0 * (w->k1d[i] + 2.0 * w->k2d[i] + 2.0 * w->k3d[i] + w->k4d[i]);
                 w->omega[i] += dt / 6.0 * (w->k1w[i] + 2.0 * w->k2w[i] + 2.0 * w->k3w[i] + w->k4w[i]);
             }
         } else {
             /* Heun (explicit trapezoid) */
-            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, w->k1d, w->k1w);
+            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, ev, w->k1d, w->k1w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + dt * w->k1d[i];
                 w->tmpw[i] = w->omega[i] + dt * w->k1w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, w->k2d, w->k2w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, ev, w->k2d, w->k2w);
             for (int i = 0; i < n; ++i) {
                 w->delta[i] += 0.5 * dt * (w->k1d[i] + w->k2d[i]);
                 w->omega[i] += 0.5 * dt * (w->k1w[i] + w->k2w[i]);
@@ -602,6 +678,26 @@ static void simulate_one(const oracle_system* s, const double* delta0, const dou
  * Work is split over nthreads POSIX threads by contiguous sample blocks and the
  * per-thread sums are added in thread order.                                   */
 /* ------------------------------------------------------------------------- */
+/* The paper's response function (Section V-B): the RMS over the horizon of the
+ * system frequency deviation, here the inertia-weighted (centre-of-inertia)
+ * speed deviation omega_coi = sum_i H_i domega_i / sum_i H_i, on the grid:
+ *   RRF = sqrt( (1/Nt) sum_{n=1..Nt} omega_coi(t_n)^2 )   (p.u. of speed).      */
+static double rrf_of(const oracle_system* s, const double* traj)
+{
+    int n = s->n, Nt = s->Nt;
+    double hs = 0.0;
+    for (int i = 0; i < n; ++i) hs += s->H[i];
+    double acc = 0.0;
+    for (int step = 1; step <= Nt; ++step) {
+        const double* row = traj + (int64_t)step * 2 * n;
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += s->H[i] * row[n + i];
+        c /= hs;
+        acc += c * c;
+    }
+    return sqrt(acc / (double)Nt);
+}
+
 typedef struct sim_job {
     const oracle_system* s;
     const double* zeta;
@@ -615,6 +711,7 @@ typedef struct sim_job {
     double* traj_out;
     double* S1;
     double* S2;
+    double* rrf_out;
 } sim_job;
 
 static void* sim_worker(void* arg)
@@ -641,6 +738,7 @@ static void* sim_worker(void* arg)
         if (job->dW_out) memcpy(job->dW_out + smp * (int64_t)d * Nt, w.dW, sizeof(double) * (size_t)d * Nt);
         double* traj = job->traj_out ? job->traj_out + smp * cols : traj_local;
         simulate_one(s, job->delta0, job->pm_eq, &w, job->pe_form, traj);
+        if (job->rrf_out) job->rrf_out[smp] = rrf_of(s, traj);
         if (job->S1) {
             for (int64_t c = 0; c < cols; ++c) {
                 double v = traj[c] - job->shift[c];
@@ -656,7 +754,7 @@ static void* sim_worker(void* arg)
 
 int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, int32_t pe_form, int32_t nthreads,
                     double* delta0_out, double* pm_eq_out, double* dW_out, double* traj_out, double* mean,
-                    double* var)
+                    double* var, double* rrf)
 {
     int n = s->n, Nt = s->Nt;
     if (n < 1 || s->d < 1 || s->K < 1 || Nt < 1 || count < 1 || s->dt <= 0.0) return -1;
@@ -684,7 +782,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
     if (want_moments) {
         /* shift = trajectory of the first sample, integrated once on its own */
         shift = (double*)malloc(sizeof(double) * cols);
-        sim_job j0 = {s, zeta, phi, delta0, pm_eq, NULL, 0, 1, pe_form, NULL, shift, NULL, NULL};
+        sim_job j0 = {s, zeta, phi, delta0, pm_eq, NULL, 0, 1, pe_form, NULL, shift, NULL, NULL, NULL};
         /* traj_out for sample 0 only points at `shift`; S1 == NULL disables sums */
         sim_worker(&j0);
         S1 = (double*)calloc((size_t)cols * nthreads, sizeof(double));
@@ -702,6 +800,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
         jobs[t].traj_out = traj_out;
         jobs[t].S1 = want_moments ? S1 + (int64_t)t * cols : NULL;
         jobs[t].S2 = want_moments ? S2 + (int64_t)t * cols : NULL;
+        jobs[t].rrf_out = rrf;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, sim_worker, &jobs[t]);
     sim_worker(&jobs[0]);

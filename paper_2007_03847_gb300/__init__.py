@@ -26,7 +26,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("FASTMC_LIB") or os.path.join(HERE, "lib", "libfastmc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_READY, EBUSY, ECANCELLED, EUNSUPPORTED, ENOCONVERGE = range(10)
-LHS, SRS, LHS_MIDPOINT = 0, 1, 2
+LHS, SRS, LHS_MIDPOINT, SRS_EM = 0, 1, 2, 3
 PREC_F32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 RK4, HEUN = 0, 1
 PATH_FUSED, PATH_PLAIN = 0, 1
@@ -43,21 +43,34 @@ class FastMCError(RuntimeError):
         self.code = code
 
 
+class _Ito(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m", ctypes.c_double * 3),
+                ("s", ctypes.c_double * 3), ("v", ctypes.c_double * 4), ("a", ctypes.c_double),
+                ("x0", ctypes.c_double)]
+
+
+ITO_OU, ITO_POLY, ITO_SQRT = 0, 1, 2
+
+
 class _Scenario(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int32), ("d", ctypes.c_int32), ("K", ctypes.c_int32), ("sampling", ctypes.c_int32),
         ("T", ctypes.c_double), ("dt", ctypes.c_double), ("N", ctypes.c_int64), ("seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("integrator", ctypes.c_int32), ("has_inf_bus", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("omega_s", ctypes.c_double), ("Vinf", ctypes.c_double),
+        ("basis", ctypes.c_int32), ("omega_s", ctypes.c_double), ("Vinf", ctypes.c_double),
         ("G", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Ginf", ctypes.c_void_p), ("Binf", ctypes.c_void_p),
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
+        ("event_machine", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("event_time", ctypes.c_double),
+        ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p),
     ]
 
 
 class _Result(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("latency_us", ctypes.c_double),
-                ("queue_us", ctypes.c_double), ("device_bytes", ctypes.c_uint64), ("message", ctypes.c_char * 256)]
+    _fields_ = [("status", ctypes.c_int32), ("replicates", ctypes.c_int32), ("latency_us", ctypes.c_double),
+                ("queue_us", ctypes.c_double), ("device_bytes", ctypes.c_uint64), ("n_used", ctypes.c_int64),
+                ("err_E", ctypes.c_double), ("err_Var", ctypes.c_double), ("target_met", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("message", ctypes.c_char * 256)]
 
 
 _lib = None
@@ -87,7 +100,7 @@ def load_library():
             "fmc_device_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
             "fmc_lhs_sample": ([vp, u64, i64, i64, i64, i32, i32, vp, vp, vp], ctypes.c_int),
             "fmc_lhs_sample_split": ([vp, u64, i64, i64, i64, i32, i32, i32, vp, vp, vp], ctypes.c_int),
-            "fmc_kl_basis": ([vp, i32, dbl, i32, vp, vp], ctypes.c_int),
+            "fmc_kl_basis": ([vp, i32, dbl, i32, i32, vp, vp], ctypes.c_int),
             "fmc_kle_reconstruct": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
             "fmc_equilibrium": ([vp, ctypes.POINTER(_Scenario), vp, vp], ctypes.c_int),
             "fmc_simulate": ([vp, ctypes.POINTER(_Scenario), i32, vp, vp, vp, vp], ctypes.c_int),
@@ -107,6 +120,9 @@ def load_library():
             "fmc_server_create": ([ctypes.c_int, i32, ctypes.c_size_t, ctypes.POINTER(vp)], ctypes.c_int),
             "fmc_server_destroy": ([vp], ctypes.c_int),
             "fmc_submit": ([vp, ctypes.POINTER(_Scenario), i32, vp, vp, ctypes.POINTER(u64)], ctypes.c_int),
+            "fmc_simulate_rrf": ([vp, ctypes.POINTER(_Scenario), i32, vp, vp, vp, vp], ctypes.c_int),
+            "fmc_submit_target": ([vp, ctypes.POINTER(_Scenario), i32, dbl, dbl, i64, vp, vp, ctypes.POINTER(u64)],
+                                  ctypes.c_int),
             "fmc_poll": ([vp, u64, ctypes.POINTER(_Result)], ctypes.c_int),
             "fmc_wait": ([vp, u64, i64, ctypes.POINTER(_Result)], ctypes.c_int),
             "fmc_cancel": ([vp, u64], ctypes.c_int),
@@ -202,6 +218,28 @@ class ScenarioStruct:
         s.precision = _PRECISION.get(prec, prec) if isinstance(prec, str) else int(prec)
         s.integrator = int(getattr(sc, "integrator", RK4) if integrator is None else integrator)
         s.has_inf_bus = 1 if sc.has_inf_bus else 0
+        s.basis = int(getattr(sc, "basis", BASIS_SINE))
+        specs = getattr(sc, "ito", None)
+        if specs is not None:
+            arr = (_Ito * int(sc.d))()
+            for q, sp in enumerate(specs):
+                it = arr[q]
+                if sp is None:
+                    continue
+                it.kind = int(sp["kind"])
+                it.m[:] = [float(c) for c in sp["m"]]
+                if it.kind == ITO_POLY:
+                    it.s[:] = [float(c) for c in sp["s"]]
+                elif it.kind == ITO_SQRT:
+                    it.v[:] = [float(c) for c in sp["v"]]
+                it.a = float(sp.get("a", 0.0))
+                it.x0 = float(sp.get("x0", 0.0))
+            self.ito = arr
+            s.ito = ctypes.cast(arr, ctypes.c_void_p)
+        ev = getattr(sc, "event_machine", None)
+        s.event_machine = -1 if ev is None else int(ev)
+        s.event_time = float(getattr(sc, "event_time", 0.0))
+        s.event_dpm = float(getattr(sc, "event_dpm", 0.0))
         s.omega_s, s.Vinf = float(sc.omega_s), float(sc.Vinf)
         if sc.has_inf_bus:
             self.keep["Ginf"] = f(sc.Ginf)
@@ -241,13 +279,17 @@ def lhs_sample_split(seed: int, N: int, d: int, K: int, mode: int = LHS, k0: int
     return hi, lo
 
 
-def kl_basis(K: int, T: float, Nt: int, phi=None, ctx: Context | None = None, stream=None):
+BASIS_SINE, BASIS_COSINE = 0, 1
+
+
+def kl_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE, phi=None, ctx: Context | None = None,
+             stream=None):
     """Increment basis phi [K, Nt] float32 (FP64 on the GPU, rounded)."""
     import torch
     ctx = ctx or default_context()
     if phi is None:
         phi = torch.empty((K, Nt), dtype=torch.float32, device="cuda")
-    ctx.check(ctx.lib.fmc_kl_basis(ctx.h, K, T, Nt, _ptr(phi), _stream(stream)))
+    ctx.check(ctx.lib.fmc_kl_basis(ctx.h, K, T, Nt, int(basis), _ptr(phi), _stream(stream)))
     return phi
 
 
@@ -316,6 +358,25 @@ def simulate(scenario, path="fused", precision=None, sampling=None, integrator=N
     ctx.check(ctx.lib.fmc_simulate(ctx.h, ctypes.byref(ss.s), p, _ptr(mean), _ptr(var), _ptr(traj),
                                    _stream(stream)))
     return (mean, var, traj) if (want_traj or traj is not None) else (mean, var)
+
+
+def simulate_rrf(scenario, path="fused", precision=None, sampling=None, integrator=None, ctx: Context | None = None,
+                 stream=None):
+    """The paper's response function (RMS of the centre-of-inertia speed deviation over
+    the horizon) of every sample, reduced to (E[RRF], Var[RRF]) as a [2] float64 device
+    tensor, with the moment trajectories mean, var [Nt+1, 2n]."""
+    import torch
+    ctx = ctx or default_context()
+    p = _PATH.get(path, path) if isinstance(path, str) else path
+    if precision is None:
+        precision = "f32" if p == PATH_PLAIN else "bf16x3"
+    ss = ScenarioStruct(scenario, precision=precision, sampling=sampling, integrator=integrator)
+    rrf = torch.empty(2, dtype=torch.float64, device="cuda")
+    mean = torch.empty((ss.Nt + 1, 2 * scenario.n), dtype=torch.float64, device="cuda")
+    var = torch.empty_like(mean)
+    ctx.check(ctx.lib.fmc_simulate_rrf(ctx.h, ctypes.byref(ss.s), p, _ptr(rrf), _ptr(mean), _ptr(var),
+                                       _stream(stream)))
+    return rrf, mean, var
 
 
 def simulate_sums(scenario, k0: int, count: int, path="fused", precision=None, sampling=None, integrator=None,
@@ -408,14 +469,22 @@ class Server:
         self.h = h
         self.pending = {}
 
-    def submit(self, scenario, path="fused", precision="bf16x3"):
+    def submit(self, scenario, path="fused", precision="bf16x3", tol_E: float = 0.0, tol_Var: float = 0.0,
+               max_N: int = 0):
+        """Queues a request.  With tol_E or tol_Var > 0 the server draws four
+        independent designs of scenario.N samples, growing N until the replicate
+        spread meets the targets or 4 N would pass max_N (fmc_submit_target)."""
         import torch
         p = _PATH.get(path, path) if isinstance(path, str) else path
         ss = ScenarioStruct(scenario, precision=precision)
         mean = torch.empty((ss.Nt + 1, 2 * scenario.n), dtype=torch.float64, device="cuda")
         var = torch.empty_like(mean)
         hd = ctypes.c_uint64()
-        rc = self.lib.fmc_submit(self.h, ctypes.byref(ss.s), p, _ptr(mean), _ptr(var), ctypes.byref(hd))
+        if tol_E > 0 or tol_Var > 0:
+            rc = self.lib.fmc_submit_target(self.h, ctypes.byref(ss.s), p, float(tol_E), float(tol_Var), int(max_N),
+                                            _ptr(mean), _ptr(var), ctypes.byref(hd))
+        else:
+            rc = self.lib.fmc_submit(self.h, ctypes.byref(ss.s), p, _ptr(mean), _ptr(var), ctypes.byref(hd))
         if rc != OK:
             raise FastMCError(rc, "fmc_submit failed")
         self.pending[hd.value] = (mean, var)
@@ -424,7 +493,9 @@ class Server:
     def _finish(self, handle, res):
         mean, var = self.pending.pop(handle)
         out = {"status": res.status, "latency_us": res.latency_us, "queue_us": res.queue_us,
-               "device_bytes": res.device_bytes, "message": res.message.decode()}
+               "device_bytes": res.device_bytes, "n_used": res.n_used, "replicates": res.replicates,
+               "err_E": res.err_E, "err_Var": res.err_Var, "target_met": bool(res.target_met),
+               "message": res.message.decode()}
         return out, mean, var
 
     def poll(self, handle):

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -43,6 +44,7 @@ struct ProfRec {
 struct Workspace {
     DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
     DevBuf wconst;  // constant block of the large-system kernel
+    DevBuf rrf;     // [4] FP64: sums of the response function and its square, a zero shift
 };
 
 struct fmc_ctx {
@@ -66,6 +68,7 @@ struct fmc_ctx {
     DevBuf& status = ws.status;
     DevBuf& zeta32 = ws.zeta32;
     DevBuf& wconst = ws.wconst;
+    DevBuf& rrfbuf = ws.rrf;
     // profiling of kernel phases (CUDA events on the launching stream)
     bool prof = false;
     std::vector<ProfRec> recs;
@@ -206,10 +209,30 @@ static int check_scenario(fmc_ctx* ctx, const fmc_scenario* s, int* Nt)
     if (s->K < 1) return fail(ctx, FMC_EINVAL, "K = %d < 1", s->K);
     if ((int64_t)s->d * s->K > (1 << 24)) return fail(ctx, FMC_EINVAL, "d*K too large");
     if (s->N < 1 || s->N > (int64_t(1) << 30)) return fail(ctx, FMC_EINVAL, "N = %lld outside [1, 2^30]", (long long)s->N);
-    if (s->sampling < 0 || s->sampling > 2) return fail(ctx, FMC_EINVAL, "sampling mode %d", s->sampling);
+    if (s->sampling < 0 || s->sampling > 3) return fail(ctx, FMC_EINVAL, "sampling mode %d", s->sampling);
     if (s->precision < 0 || s->precision > 2) return fail(ctx, FMC_EINVAL, "precision %d", s->precision);
     if (s->integrator != FMC_RK4 && s->integrator != FMC_HEUN)
         return fail(ctx, FMC_EINVAL, "integrator %d", s->integrator);
+    if (s->basis != FMC_BASIS_SINE && s->basis != FMC_BASIS_COSINE) return fail(ctx, FMC_EINVAL, "basis %d", s->basis);
+    if (s->event_machine >= s->n) return fail(ctx, FMC_EINVAL, "event machine %d of %d", s->event_machine, s->n);
+    if (s->ito) {
+        for (int q = 0; q < s->d; ++q) {
+            const fmc_ito& m = s->ito[q];
+            if (m.kind != FMC_ITO_OU && m.kind != FMC_ITO_POLY && m.kind != FMC_ITO_SQRT)
+                return fail(ctx, FMC_EINVAL, "disturbance %d: model kind %d", q, m.kind);
+            bool fin = std::isfinite(m.a) && std::isfinite(m.x0);
+            for (double c : m.m) fin = fin && std::isfinite(c);
+            for (double c : m.s) fin = fin && std::isfinite(c);
+            for (double c : m.v) fin = fin && std::isfinite(c);
+            if (!fin) return fail(ctx, FMC_EINVAL, "disturbance %d: coefficients must be finite", q);
+        }
+    }
+    if (s->event_machine >= 0) {
+        if (!(s->event_time >= 0.0) || !std::isfinite(s->event_time) || !std::isfinite(s->event_dpm))
+            return fail(ctx, FMC_EINVAL, "event time and power step must be finite, time >= 0");
+        if (s->d + 1 > FMC_MAX_DISTURBANCES)
+            return fail(ctx, FMC_EUNSUPPORTED, "an event takes a disturbance slot: d <= %d", FMC_MAX_DISTURBANCES - 1);
+    }
     if (!s->G || !s->B || !s->H || !s->D || !s->E || !s->Pm || !s->theta || !s->sigma || !s->inject)
         return fail(ctx, FMC_EINVAL, "a scenario array is NULL");
     if (s->has_inf_bus && (!s->Ginf || !s->Binf)) return fail(ctx, FMC_EINVAL, "infinite bus arrays are NULL");
@@ -218,6 +241,41 @@ static int check_scenario(fmc_ctx* ctx, const fmc_scenario* s, int* Nt)
     if (!(s->omega_s > 0.0)) return fail(ctx, FMC_EINVAL, "omega_s must be > 0");
     return steps_of(ctx, s->T, s->dt, Nt);
 }
+
+// General disturbances in the kernels' form (see ItoParams): the polynomials of
+// fmc_ito re-expanded about x0 in FP64 and rounded; the Stratonovich correction
+// applies to KL-driven paths.
+template <int ND>
+static void build_ito(const fmc_scenario* s, ItoParams<ND>& it)
+{
+    memset(&it, 0, sizeof it);
+    if (!s->ito) return;
+    it.strat = (s->sampling == FMC_SRS_EM) ? 0.f : 1.f;
+    for (int q = 0; q < s->d && q < ND; ++q) {
+        const fmc_ito& m = s->ito[q];
+        it.kind[q] = m.kind;
+        if (m.kind == FMC_ITO_OU) continue;
+        it.on = 1;
+        const double x0 = m.x0;
+        it.c0[q] = (float)(m.m[0] + m.m[1] * x0 + m.m[2] * x0 * x0);
+        it.c1[q] = (float)(m.m[1] + 2.0 * m.m[2] * x0);
+        it.c2[q] = (float)m.m[2];
+        if (m.kind == FMC_ITO_POLY) {
+            it.e0[q] = (float)(m.s[0] + m.s[1] * x0 + m.s[2] * x0 * x0);
+            it.e1[q] = (float)(m.s[1] + 2.0 * m.s[2] * x0);
+            it.e2[q] = (float)m.s[2];
+        } else {
+            it.e0[q] = (float)(m.v[0] + m.v[1] * x0 + m.v[2] * x0 * x0);
+            it.e1[q] = (float)(m.v[1] + 2.0 * m.v[2] * x0);
+            it.e2[q] = (float)m.v[2];
+            it.e3[q] = (float)m.v[3];
+            it.ap[q] = (float)(m.a - x0);
+        }
+    }
+}
+
+// Grid step at which an event takes effect.
+static int event_step_of(const fmc_scenario* s) { return (int)std::llround(s->event_time / s->dt); }
 
 static int nd_bucket_for(int d)
 {
@@ -274,6 +332,20 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
         p.ou_a[q] = (float)(1.0 - s->theta[q] * s->dt);
         p.ou_s[q] = (float)s->sigma[q];
     }
+    double hsum = 0.0;
+    for (int i = 0; i < n; ++i) hsum += s->H[i];
+    for (int i = 0; i < n; ++i) p.hw[i] = (float)(s->H[i] / hsum);
+    build_ito<ND>(s, p.ito);
+    p.ev_slot = -1;
+    p.ev_step = 0;
+    if (s->event_machine >= 0) {
+        // the event rides in the spare slot d: held at 0 before, 1 from the event step
+        p.ev_slot = d;
+        p.ev_step = event_step_of(s);
+        p.inj[s->event_machine][d] = (float)s->event_dpm;
+        p.ou_a[d] = 1.f;
+        p.ou_s[d] = 0.f;
+    }
     p.omega_s = (float)s->omega_s;
     p.dt = (float)s->dt;
     p.d = d;
@@ -313,7 +385,8 @@ static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const dou
 static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, std::vector<float>& out)
 {
     const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
-    out.assign(wide_const_floats(n, nmt, d), 0.f);
+    const int dx = d + (s->event_machine >= 0 ? 1 : 0);
+    out.assign(wide_const_floats(n, nmt, dx), 0.f);
     float* GE = out.data();
     float* BE = GE + n * 4 * nmtp;
     float* pm = BE + n * 4 * nmtp;
@@ -332,7 +405,7 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
             double ge = s->E[i] * s->E[j] * s->G[i * n + j];
             double be = s->E[i] * s->E[j] * s->B[i * n + j];
             GE[(j * 4 + h) * nmtp + k] = (float)ge;
-            BE[(j * 4 + h) * nmtp + k] = (float)be;
+            BE[(j * 4 + h) * nmtp + k] = (float)-be;  // stored negated (see the kernel's network sum)
             u += ge * c[j] - be * sn[j];
             v += ge * sn[j] + be * c[j];
         }
@@ -347,8 +420,12 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
         pm[4 * g4 + i] = (float)delta0[i];
         pm[5 * g4 + i] = (float)(1.0 / (2.0 * s->H[i]));
         pm[6 * g4 + i] = (float)s->D[i];
-        for (int q = 0; q < d; ++q) pm[(7 + q) * g4 + i] = (float)s->inject[i * d + q];
+        for (int q = 0; q < d; ++q) pm[(8 + q) * g4 + i] = (float)s->inject[i * d + q];
     }
+    double hsum = 0.0;
+    for (int i = 0; i < n; ++i) hsum += s->H[i];
+    for (int i = 0; i < n; ++i) pm[7 * g4 + i] = (float)(s->H[i] / hsum);
+    if (s->event_machine >= 0) pm[(8 + d) * g4 + s->event_machine] = (float)s->event_dpm;
 }
 
 // Copies the system arrays to the device and launches the FP64 Newton kernel.
@@ -412,16 +489,18 @@ static int make_map_bf16(fmc_ctx* ctx, CUtensorMap* m, const void* base, uint64_
     return FMC_OK;
 }
 
-// Tensor maps of the split operands: zeta [rows][d*Ks], phi [Nt][Kpad].
+// Tensor maps of the split operands: zeta [rows][d*Ks] in tiles of TM rows,
+// phi [Nt][Kpad] in tiles of TN rows.
 static int make_contract_maps_at(fmc_ctx* ctx, CUtensorMap maps[4], const void* zhi, const void* zlo, const void* phi_hi,
-                                 const void* phi_lo, int64_t rows, int d, int Ks, int Nt, int Kpad, int TN, int split)
+                                 const void* phi_lo, int64_t rows, int d, int Ks, int Nt, int Kpad, int TN, int split,
+                                 int TM = TC_M)
 {
-    int rc = make_map_bf16(ctx, &maps[0], zhi, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+    int rc = make_map_bf16(ctx, &maps[0], zhi, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, (uint32_t)TM);
     if (rc) return rc;
     rc = make_map_bf16(ctx, &maps[2], phi_hi, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
     if (rc) return rc;
     if (split) {
-        rc = make_map_bf16(ctx, &maps[1], zlo, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, TC_M);
+        rc = make_map_bf16(ctx, &maps[1], zlo, (uint64_t)d * Ks, (uint64_t)rows, TC_BK, (uint32_t)TM);
         if (rc) return rc;
         rc = make_map_bf16(ctx, &maps[3], phi_lo, (uint64_t)Kpad, (uint64_t)Nt, TC_BK, (uint32_t)TN);
         if (rc) return rc;
@@ -518,7 +597,7 @@ int fmc_destroy(fmc_ctx* ctx)
     prof_clear(ctx);
     DevBuf* bufs[] = {&ctx->zeta_hi, &ctx->zeta_lo, &ctx->phi_hi, &ctx->phi_lo, &ctx->phi32,  &ctx->dW,
                       &ctx->traj,    &ctx->part,    &ctx->eq,     &ctx->scen,   &ctx->status, &ctx->zeta32,
-                      &ctx->wconst};
+                      &ctx->wconst,  &ctx->rrfbuf};
     for (DevBuf* b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     delete ctx;
@@ -570,12 +649,13 @@ int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int
     return FMC_OK;
 }
 
-int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, float* phi_dev, void* stream)
+int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, int32_t basis, float* phi_dev, void* stream)
 {
     if (!ctx) return FMC_EINVAL;
+    if (basis != FMC_BASIS_SINE && basis != FMC_BASIS_COSINE) return fail(ctx, FMC_EINVAL, "basis %d", basis);
     if (K < 1 || Nt < 1 || !(T > 0.0)) return fail(ctx, FMC_EINVAL, "K = %d, Nt = %d, T = %g", K, Nt, T);
     if (!phi_dev) return fail(ctx, FMC_EINVAL, "phi is NULL");
-    FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, phi_dev, ctx->sms, (cudaStream_t)stream), "basis kernel");
+    FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, basis, phi_dev, ctx->sms, (cudaStream_t)stream), "basis kernel");
     return FMC_OK;
 }
 
@@ -592,7 +672,7 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
     if (precision == FMC_PREC_F32) {
         rc = ensure(ctx, ctx->phi32, (size_t)K * Nt * sizeof(float));
         if (rc) return rc;
-        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, (float*)ctx->phi32.ptr, ctx->sms, st), "basis kernel");
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, FMC_BASIS_SINE, (float*)ctx->phi32.ptr, ctx->sms, st), "basis kernel");
         FMC_CUDA(ctx, launch_sgemm_nn(count * d, Nt, K, zeta_dev, (const float*)ctx->phi32.ptr, dW_dev, st),
                  "sgemm kernel");
         return FMC_OK;
@@ -613,7 +693,7 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
     if ((rc = ensure(ctx, ctx->phi_lo, (size_t)Nt * Kpad * 2))) return rc;
     if ((rc = ensure(ctx, ctx->status, 64))) return rc;
     FMC_CUDA(ctx, launch_split_rows(zeta_dev, count, d, K, Ks, ctx->zeta_hi.ptr, ctx->zeta_lo.ptr, st), "split");
-    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, Kpad, ctx->phi_hi.ptr, ctx->phi_lo.ptr, ctx->sms, st), "basis");
+    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, FMC_BASIS_SINE, Kpad, ctx->phi_hi.ptr, ctx->phi_lo.ptr, ctx->sms, st), "basis");
     CUtensorMap maps[4];
     if ((rc = make_contract_maps(ctx, maps, count, d, Ks, Nt, Kpad, TN, split))) return rc;
     FMC_CUDA(ctx, cudaMemsetAsync(ctx->status.ptr, 0, 64, st), "memset");
@@ -660,7 +740,7 @@ int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t cou
     if ((rc = noalloc_scratch(ctx, &base))) return rc;
     if (precision == FMC_PREC_F32) {
         float* phi32 = reinterpret_cast<float*>(base + o_phi32);
-        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, phi32, ctx->sms, st), "basis kernel");
+        FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, FMC_BASIS_SINE, phi32, ctx->sms, st), "basis kernel");
         FMC_CUDA(ctx, launch_sgemm_nn(count * d, Nt, K, zeta_dev, phi32, dW_dev, st), "sgemm kernel");
         return FMC_OK;
     }
@@ -673,7 +753,7 @@ int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t cou
     void* phi_lo = base + o_phi_lo;
     int* status = reinterpret_cast<int*>(base + o_status);
     FMC_CUDA(ctx, launch_split_rows(zeta_dev, count, d, K, Ks, zhi, zlo, st), "split");
-    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, Kpad, phi_hi, phi_lo, ctx->sms, st), "basis");
+    FMC_CUDA(ctx, launch_basis_split(K, Nt, T, FMC_BASIS_SINE, Kpad, phi_hi, phi_lo, ctx->sms, st), "basis");
     CUtensorMap maps[4];
     if ((rc = make_contract_maps_at(ctx, maps, zhi, zlo, phi_hi, phi_lo, count, d, Ks, Nt, Kpad, TN, split)))
         return rc;
@@ -749,7 +829,7 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         P.nmt = 0;
     else
         P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
-    P.nd = nd_bucket_for(s->d);
+    P.nd = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
     P.path = path;
     P.k0 = k0;
     P.count = count;
@@ -784,18 +864,36 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
 // CTA may take more columns, so the chunk grows (up to 256 steps) and the
 // boundaries become rarer; launches that share the GPU (batches, the server)
 // keep 128 columns per CTA.
-static int fused_tc(int d, int64_t ntiles, int sms, bool wide, bool exclusive)
+//
+// Samples per CTA: 128 (four warps).  The kernel also runs 64-sample CTAs (two
+// warps); they would even out the warps per SM of 2^16 samples (at most 14
+// instead of 16), but their TMEM share forces 16-step chunks and the doubled
+// design-tile reloads cost more than the balance gains (38.9 vs 35.1 ms), so
+// the automatic shape keeps 128.
+struct FusedShape {
+    int rows;       // samples per CTA
+    int max_ctas;   // resident CTAs per SM allowed
+    int TC;         // time chunk
+    int64_t ctas;   // grid
+};
+
+static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
 {
-    int per_sm = 4;
-    if (exclusive) {
-        const int64_t need = (ntiles + sms - 1) / sms;
-        per_sm = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
+    const int d = P.s.d, sms = ctx->sms;
+    const bool wide = P.nmt > 0;
+    const int64_t full = (P.count + TC_M - 1) / TC_M;
+    FusedShape f{TC_M, 4, 32, 0};
+    if (P.exclusive) {
+        const int64_t need = (full + sms - 1) / sms;
+        f.max_ctas = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
     }
-    const int cols = 512 / per_sm;
+    const int cols = 512 / f.max_ctas;
     // the large-system kernel's shared memory leaves room for a ring of 128-step chunks
     int TC = wide ? 128 : 256;
     while (TC > 16 && d * TC > cols) TC >>= 1;
-    return TC;
+    f.TC = TC;
+    f.ctas = (P.count + f.rows - 1) / f.rows;
+    return f;
 }
 
 // All device buffers the enqueue of P needs (grows the workspace; may allocate).
@@ -807,10 +905,11 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
     const int64_t count = P.count, Nt1 = (int64_t)Nt + 1;
     const int S = 2 * n;
     int rc;
+    const bool em = (P.s.sampling == FMC_SRS_EM);
     if (P.path == FMC_PATH_PLAIN) {
         const int M = d * K;
-        if ((rc = ensure(ctx, ws.zeta32, (size_t)count * M * sizeof(float)))) return rc;
-        if ((rc = ensure(ctx, ws.phi32, (size_t)K * Nt * sizeof(float)))) return rc;
+        if (!em && (rc = ensure(ctx, ws.zeta32, (size_t)count * M * sizeof(float)))) return rc;
+        if (!em && (rc = ensure(ctx, ws.phi32, (size_t)K * Nt * sizeof(float)))) return rc;
         if ((rc = ensure(ctx, ws.dW, (size_t)count * d * Nt * sizeof(float)))) return rc;
         if (!want_traj && (rc = ensure(ctx, ws.traj, (size_t)count * Nt1 * S * sizeof(float)))) return rc;
         return FMC_OK;
@@ -818,12 +917,14 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
     const int split = (P.s.precision == FMC_PREC_BF16X3);
     const int Ks = round_up(K, 8);
     const int Kpad = round_up(K, TC_BK);
-    const int64_t ntiles = (count + TC_M - 1) / TC_M;
+    const int64_t ntiles = fused_shape(ctx, P).ctas;
     size_t zbytes = (size_t)count * d * Ks * 2;
-    if ((rc = ensure(ctx, ws.zeta_hi, zbytes))) return rc;
-    if (split && (rc = ensure(ctx, ws.zeta_lo, zbytes))) return rc;
-    if ((rc = ensure(ctx, ws.phi_hi, (size_t)Nt * Kpad * 2))) return rc;
-    if (split && (rc = ensure(ctx, ws.phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+    if (!em) {
+        if ((rc = ensure(ctx, ws.zeta_hi, zbytes))) return rc;
+        if (split && (rc = ensure(ctx, ws.zeta_lo, zbytes))) return rc;
+        if ((rc = ensure(ctx, ws.phi_hi, (size_t)Nt * Kpad * 2))) return rc;
+        if (split && (rc = ensure(ctx, ws.phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+    }
     if (per_tile_partials && (rc = ensure(ctx, ws.part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
     return FMC_OK;
 }
@@ -832,7 +933,7 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
 // under stream capture once reserve() has run).  S1, S2 [Nt+1][2n] receive the
 // shifted sums over the block; the shift is at ws.eq + 2n.
 static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, double* S2, float* traj_dev,
-                   bool per_tile_partials, cudaStream_t st)
+                   bool per_tile_partials, cudaStream_t st, double* rrf = nullptr)
 {
     const fmc_scenario* s = &P.s;
     const int n = s->n, d = s->d, K = s->K, Nt = P.Nt;
@@ -844,26 +945,39 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     int rc;
     ProfRec* pr;
 
+    const bool em = (s->sampling == FMC_SRS_EM);
+    EmSpec ems{em ? 1 : 0, (uint32_t)s->seed, (uint32_t)(s->seed >> 32), k0, (float)std::sqrt(s->dt)};
+
     if (P.path == FMC_PATH_PLAIN) {
         const int M = d * K;
         float* traj = traj_dev ? traj_dev : (float*)ws.traj.ptr;
-        prof_begin(ctx, PH_LHS, st, &pr);
-        FMC_CUDA(ctx,
-                 launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ws.zeta32.ptr, nullptr, ctx->sms, st),
-                 "lhs kernel");
-        prof_end(pr, st);
-        prof_begin(ctx, PH_BASIS, st, &pr);
-        FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, (float*)ws.phi32.ptr, ctx->sms, st), "basis kernel");
-        prof_end(pr, st);
-        prof_begin(ctx, PH_CONTRACT, st, &pr);
-        FMC_CUDA(ctx,
-                 launch_sgemm_nn(count * d, Nt, K, (const float*)ws.zeta32.ptr, (const float*)ws.phi32.ptr,
-                                 (float*)ws.dW.ptr, st),
-                 "sgemm kernel");
-        prof_end(pr, st);
+        if (em) {
+            prof_begin(ctx, PH_LHS, st, &pr);
+            FMC_CUDA(ctx, launch_em_increments(s->seed, k0, count, d, Nt, s->dt, (float*)ws.dW.ptr, ctx->sms, st),
+                     "increments kernel");
+            prof_end(pr, st);
+        } else {
+            prof_begin(ctx, PH_LHS, st, &pr);
+            FMC_CUDA(ctx,
+                     launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ws.zeta32.ptr, nullptr, ctx->sms,
+                                    st),
+                     "lhs kernel");
+            prof_end(pr, st);
+            prof_begin(ctx, PH_BASIS, st, &pr);
+            FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, s->basis, (float*)ws.phi32.ptr, ctx->sms, st),
+                     "basis kernel");
+            prof_end(pr, st);
+            prof_begin(ctx, PH_CONTRACT, st, &pr);
+            FMC_CUDA(ctx,
+                     launch_sgemm_nn(count * d, Nt, K, (const float*)ws.zeta32.ptr, (const float*)ws.phi32.ptr,
+                                     (float*)ws.dW.ptr, st),
+                     "sgemm kernel");
+            prof_end(pr, st);
+        }
         prof_begin(ctx, PH_INTEGRATE, st, &pr);
         FMC_CUDA(ctx,
-                 launch_simulate_plain(P.nm, P.nd, P.params.data(), eq, (const float*)ws.dW.ptr, count, Nt, traj, st),
+                 launch_simulate_plain(P.nm, P.nd, P.params.data(), eq, (const float*)ws.dW.ptr, count, Nt, traj, rrf,
+                                       st),
                  "plain integrator");
         prof_end(pr, st);
         prof_begin(ctx, PH_MOMENTS, st, &pr);
@@ -877,25 +991,32 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     const int Ks = round_up(K, 8);
     const int Kpad = round_up(K, TC_BK);
     const int nkb = (Ks + TC_BK - 1) / TC_BK;
-    const int64_t ntiles = (count + TC_M - 1) / TC_M;
-    const int TC = fused_tc(d, ntiles, ctx->sms, P.nmt > 0, P.exclusive);
+    const FusedShape shape = fused_shape(ctx, P);
+    const int64_t ntiles = shape.ctas;
+    const int TC = shape.TC;
     uint32_t tmem_cols = 32;
     while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
-    prof_begin(ctx, PH_LHS, st, &pr);
-    FMC_CUDA(ctx,
-             launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr,
-                              ctx->sms, st),
-             "lhs kernel");
-    prof_end(pr, st);
-    prof_begin(ctx, PH_BASIS, st, &pr);
-    FMC_CUDA(ctx,
-             launch_basis_split(K, Nt, s->T, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr, ctx->sms, st),
-             "basis kernel");
-    prof_end(pr, st);
     CUtensorMap maps[4];
-    if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
-                                    Ks, Nt, Kpad, TC, split)))
-        return rc;
+    if (em) {
+        // no design and no contraction: the kernels draw the increments
+        memset(maps, 0, sizeof maps);
+    } else {
+        prof_begin(ctx, PH_LHS, st, &pr);
+        FMC_CUDA(ctx,
+                 launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr,
+                                  ctx->sms, st),
+                 "lhs kernel");
+        prof_end(pr, st);
+        prof_begin(ctx, PH_BASIS, st, &pr);
+        FMC_CUDA(ctx,
+                 launch_basis_split(K, Nt, s->T, s->basis, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr, ctx->sms,
+                                    st),
+                 "basis kernel");
+        prof_end(pr, st);
+        if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
+                                        Ks, Nt, Kpad, TC, split, shape.rows)))
+            return rc;
+    }
     FMC_CUDA(ctx, cudaMemsetAsync((char*)ws.status.ptr + 4, 0, 4, st), "memset");
     if (!per_tile_partials) {
         FMC_CUDA(ctx, cudaMemsetAsync(S1, 0, Nt1 * S * sizeof(double), st), "memset");
@@ -929,12 +1050,21 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         wa.S2 = per_tile_partials ? nullptr : S2;
         wa.traj = traj_dev;
         wa.err = (int*)ws.status.ptr + 1;
+        wa.em = ems;
+        wa.dx = d + (s->event_machine >= 0 ? 1 : 0);
+        wa.ev_step = s->event_machine >= 0 ? event_step_of(s) : 0;
+        if (s->event_machine >= 0) {
+            wa.ou_a[d] = 1.f;
+            wa.ou_s[d] = 0.f;
+        }
+        wa.rrf = rrf;
+        build_ito<8>(s, wa.ito);
         e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
     } else {
         e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
-                                  eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
+                                  shape.rows, shape.max_ctas, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
                                   per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
-                                  (int*)ws.status.ptr + 1, st, &occ);
+                                  (int*)ws.status.ptr + 1, ems, rrf, st, &occ);
     }
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)
@@ -944,7 +1074,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     prof_end(pr, st);
     if (per_tile_partials) {
         prof_begin(ctx, PH_REDUCE, st, &pr);
-        FMC_CUDA(ctx, launch_fused_sums((const float*)ws.part.ptr, (int)ntiles, Nt1, S, S1, S2, st), "moment sums");
+        FMC_CUDA(ctx, launch_fused_sums((const float*)ws.part.ptr, (int)ntiles, Nt1, S, count, shape.rows, S1, S2, st), "moment sums");
         prof_end(pr, st);
     }
     return FMC_OK;
@@ -954,14 +1084,14 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
 // increments, integration and per-time shifted sums S1, S2 [Nt+1][2n] (FP64).
 // The shift (FP64 [2n]: delta*, then zeros) is left at ctx->eq + 2n.
 static int simulate_core(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1,
-                         double* S2, float* traj_dev, cudaStream_t st)
+                         double* S2, float* traj_dev, cudaStream_t st, double* rrf = nullptr)
 {
     if (!S1 || !S2) return fail(ctx, FMC_EINVAL, "moment outputs are NULL");
     Prepared P;
     int rc = prepare(ctx, ctx->ws, s, k0, count, path, st, P);
     if (rc) return rc;
     if ((rc = reserve(ctx, ctx->ws, P, traj_dev != nullptr, true))) return rc;
-    return enqueue(ctx, ctx->ws, P, S1, S2, traj_dev, true, st);
+    return enqueue(ctx, ctx->ws, P, S1, S2, traj_dev, true, st, rrf);
 }
 
 }  // extern "C"
@@ -1006,6 +1136,34 @@ int fmc_simulate(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean
     return FMC_OK;
 }
 
+int fmc_simulate_rrf(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* rrf_dev, double* mean_dev,
+                     double* var_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!s || !rrf_dev) return fail(ctx, FMC_EINVAL, "NULL scenario or output");
+    if ((mean_dev == nullptr) != (var_dev == nullptr)) return fail(ctx, FMC_EINVAL, "give both moment outputs or none");
+    int Nt = 0;
+    int rc = check_scenario(ctx, s, &Nt);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cols = (size_t)(Nt + 1) * 2 * s->n;
+    // [0] sum RRF, [1] sum RRF^2, [2] zero shift, [3] pad, then moments if the caller gives none
+    if ((rc = ensure(ctx, ctx->rrfbuf, sizeof(double) * (4 + (mean_dev ? 0 : 2 * cols))))) return rc;
+    double* buf = (double*)ctx->rrfbuf.ptr;
+    if (!mean_dev) {
+        mean_dev = buf + 4;
+        var_dev = buf + 4 + cols;
+    }
+    FMC_CUDA(ctx, cudaMemsetAsync(buf, 0, 4 * sizeof(double), st), "memset");
+    if ((rc = simulate_core(ctx, s, 0, s->N, path, mean_dev, var_dev, nullptr, st, buf))) return rc;
+    FMC_CUDA(ctx,
+             launch_finalize(mean_dev, var_dev, (const double*)ctx->eq.ptr + 2 * s->n, s->N, (int64_t)Nt + 1, 2 * s->n,
+                             mean_dev, var_dev, st),
+             "moment finalize");
+    FMC_CUDA(ctx, launch_finalize(buf, buf + 1, buf + 2, s->N, 1, 1, rrf_dev, rrf_dev + 1, st), "rrf finalize");
+    return FMC_OK;
+}
+
 int fmc_simulate_sums(fmc_ctx* ctx, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path, double* S1_dev,
                       double* S2_dev, double* shift_dev, float* traj_dev, void* stream)
 {
@@ -1037,6 +1195,7 @@ int fmc_moments_from_sums(fmc_ctx* ctx, const double* S1_dev, const double* S2_d
 
 struct fmc_batch {
     fmc_ctx* ctx = nullptr;
+    std::vector<std::unique_ptr<fmc::OwnedScenario>> owned;  // the batch's own copies of the scenarios
     std::vector<Workspace*> ws;
     std::vector<Prepared> prep;
     std::vector<double*> mean, var;
@@ -1059,7 +1218,7 @@ static void batch_free(fmc_batch* b)
     for (Workspace* w : b->ws) {
         DevBuf* bufs[] = {&w->zeta_hi, &w->zeta_lo, &w->phi_hi, &w->phi_lo, &w->phi32,  &w->dW,
                           &w->traj,    &w->part,    &w->eq,     &w->scen,   &w->status, &w->zeta32,
-                          &w->wconst};
+                          &w->wconst,  &w->rrf};
         for (DevBuf* d : bufs)
             if (d->ptr) {
                 cudaFree(d->ptr);
@@ -1117,7 +1276,9 @@ int fmc_batch_create(fmc_ctx* ctx, const fmc_scenario* scen, int32_t n_scen, int
         Workspace* w = new Workspace();
         b->ws.push_back(w);
         b->prep.emplace_back();
-        rc = prepare(ctx, *w, &scen[i], 0, scen[i].N, path, st0, b->prep.back(), false);  // scenarios share the GPU
+        b->owned.push_back(std::make_unique<fmc::OwnedScenario>(scen[i]));
+        const fmc_scenario* si = &b->owned.back()->s;
+        rc = prepare(ctx, *w, si, 0, si->N, path, st0, b->prep.back(), false);  // scenarios share the GPU
         if (rc == FMC_OK) rc = reserve(ctx, *w, b->prep.back(), false, path == FMC_PATH_PLAIN);
         b->mean.push_back(mean_dev[i]);
         b->var.push_back(var_dev[i]);
@@ -1220,7 +1381,25 @@ int fmc_moments(fmc_ctx* ctx, const float* x_dev, int64_t N, int64_t C, double* 
     return FMC_OK;
 }
 
+}  // extern "C"
+
 // ---- diagnostics -------------------------------------------------------------
+
+int fmc::device_status_on(fmc_ctx* ctx, cudaStream_t st)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!ctx->status.ptr) return FMC_OK;
+    int h[2] = {0, 0};
+    FMC_CUDA(ctx, cudaMemcpyAsync(h, ctx->status.ptr, sizeof h, cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+    if (h[0] < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    if (h[1] == DEV_TIMEOUT_MMA || h[1] == DEV_TIMEOUT_TMA)
+        return fail(ctx, FMC_ETIMEOUT, "a bounded device wait gave up (code %d)", h[1]);
+    if (h[1] != 0) return fail(ctx, FMC_ECUDA, "device error %d", h[1]);
+    return FMC_OK;
+}
+
+extern "C" {
 
 int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error)
 {

@@ -3,9 +3,58 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/fastmc.h"
 
 namespace fmc {
+
+// Deep copy of a scenario, so that the caller's arrays may go away (requests of
+// the server, scenarios of a batch).
+struct OwnedScenario {
+    fmc_scenario s{};
+    std::vector<double> G, B, Ginf, Binf, H, D, E, Pm, theta, sigma, inject;
+    std::vector<fmc_ito> ito;
+
+    explicit OwnedScenario(const fmc_scenario& in) : s(in)
+    {
+        const size_t n = (size_t)in.n, d = (size_t)in.d;
+        auto cp = [](std::vector<double>& dst, const double* src, size_t k) {
+            if (src) dst.assign(src, src + k);
+        };
+        cp(G, in.G, n * n);
+        cp(B, in.B, n * n);
+        cp(H, in.H, n);
+        cp(D, in.D, n);
+        cp(E, in.E, n);
+        cp(Pm, in.Pm, n);
+        cp(theta, in.theta, d);
+        cp(sigma, in.sigma, d);
+        cp(inject, in.inject, n * d);
+        if (in.has_inf_bus) {
+            cp(Ginf, in.Ginf, n);
+            cp(Binf, in.Binf, n);
+        }
+        auto ptr = [](const std::vector<double>& v) -> const double* { return v.empty() ? nullptr : v.data(); };
+        s.G = ptr(G);
+        s.B = ptr(B);
+        s.H = ptr(H);
+        s.D = ptr(D);
+        s.E = ptr(E);
+        s.Pm = ptr(Pm);
+        s.theta = ptr(theta);
+        s.sigma = ptr(sigma);
+        s.inject = ptr(inject);
+        s.Ginf = ptr(Ginf);
+        s.Binf = ptr(Binf);
+        if (in.ito) {
+            ito.assign(in.ito, in.ito + d);
+            s.ito = ito.data();
+        }
+    }
+};
+
+
 
 // fmc_simulate with a choice of how the fused kernel combines its per-time sums:
 // per_tile_partials = true writes FP32 partials per 128-sample tile and adds them
@@ -13,5 +62,9 @@ namespace fmc {
 // partial buffer; the order of the FP64 additions is not fixed).
 int simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
                      bool per_tile_partials, cudaStream_t st);
+
+// fmc_device_status for the work enqueued on one stream: waits for that stream
+// only (not the device), so concurrent requests of the server keep running.
+int device_status_on(fmc_ctx* ctx, cudaStream_t st);
 
 }  // namespace fmc

@@ -43,6 +43,111 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
     return c;
 }
 
+// zeta = Phi^-1(p), p = num2 / (N 2^33) given as the exact integer numerator
+// num2 = 2 s 2^32 + 2 r + 1 (LHS), 2 s 2^32 + 2^32 (midpoint), 2 r + 1 (SRS, N=1).
+// The argument of the CUDA inverse error functions is formed from exact integer
+// differences so that it carries FP32 relative accuracy in both tails and at
+// the centre:  Phi^-1(p) = -sqrt2 erfcinv(2p) = sqrt2 erfinv(2p - 1)
+//            = sqrt2 erfcinv(2(1-p)).
+__device__ __forceinline__ float normal_from_fraction(uint64_t num2, uint32_t N)
+{
+    const uint64_t half = (uint64_t)N << 32;   // den/2
+    const float fhalf = (float)N * 4294967296.0f;
+    const float SQRT2 = 1.41421356237309515f;
+    if (num2 <= (half >> 1)) {                  // p <= 1/4
+        float twop = (float)num2 / fhalf;
+        return -SQRT2 * erfcinvf(twop);
+    }
+    uint64_t den = half << 1;
+    if (num2 >= den - (half >> 1)) {            // p >= 3/4
+        float twoq = (float)(den - num2) / fhalf;
+        return SQRT2 * erfcinvf(twoq);
+    }
+    int64_t c = (int64_t)(num2 - half);         // 2p - 1 = c / half
+    return SQRT2 * erfinvf((float)c / fhalf);
+}
+
+// The normal of (sample k, disturbance w, step n) of the per-step-normal Monte
+// Carlo: Phi^-1((r + 1/2) 2^-32), r = Philox(key, counter (k, n, 256, w / 4))
+// word w mod 4 (the tag 256 keeps these counters apart from the design's).
+constexpr uint32_t EM_TAG = 256u;
+
+__device__ __forceinline__ float em_normal(uint32_t k, int w, int n, uint32_t k0, uint32_t k1)
+{
+    const U4 o = philox4x32_10(U4{k, (uint32_t)n, EM_TAG, (uint32_t)(w >> 2)}, k0, k1);
+    const uint32_t r = (w & 3) == 0 ? o.x : ((w & 3) == 1 ? o.y : ((w & 3) == 2 ? o.z : o.w));
+    return normal_from_fraction(2ull * r + 1ull, 1u);
+}
+
+// Sum and squared deviations from their mean of the first na of 32 values
+// column[rr * stride] (the rest hold 0): two passes, the second around the
+// pass-one mean, so that M2 keeps FP32 accuracy relative to the spread however
+// far the values sit from zero.  Four interleaved partials per pass.
+__device__ __forceinline__ void column_sum_m2(const float* column, int stride, int na, float* sum, float* m2)
+{
+    float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 32; rr += 4) {
+        a += column[rr * stride];
+        b += column[(rr + 1) * stride];
+        c += column[(rr + 2) * stride];
+        e += column[(rr + 3) * stride];
+    }
+    const float s = (a + b) + (c + e);
+    const float mu = na > 0 ? s / (float)na : 0.f;
+    a = b = c = e = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 32; rr += 4) {
+        const float d0 = rr < na ? column[rr * stride] - mu : 0.f;
+        const float d1 = rr + 1 < na ? column[(rr + 1) * stride] - mu : 0.f;
+        const float d2 = rr + 2 < na ? column[(rr + 2) * stride] - mu : 0.f;
+        const float d3 = rr + 3 < na ? column[(rr + 3) * stride] - mu : 0.f;
+        a = fmaf(d0, d0, a);
+        b = fmaf(d1, d1, b);
+        c = fmaf(d2, d2, c);
+        e = fmaf(d3, d3, e);
+    }
+    *sum = s;
+    *m2 = (a + b) + (c + e);
+}
+
+// Parallel-variance combine (Chan, Golub and LeVeque) of up to four groups of
+// na[g] values with sums s[g] and squared deviations m2[g] (strided by `stride`):
+// the combined squared deviation from the combined mean, in a fixed order.
+__device__ __forceinline__ float combine_m2(const float* s, const float* m2, int stride, const int* na, int groups)
+{
+    float st = 0.f;
+    int nt = 0;
+    for (int g = 0; g < groups; ++g) {
+        st += s[g * stride];
+        nt += na[g];
+    }
+    const float mu = nt > 0 ? st / (float)nt : 0.f;
+    float acc = 0.f;
+    for (int g = 0; g < groups; ++g) {
+        if (na[g] == 0) continue;
+        const float dg = s[g * stride] / (float)na[g] - mu;
+        acc += m2[g * stride] + (float)na[g] * dg * dg;
+    }
+    return acc;
+}
+
+// Adds a warp's response-function values and their squares into rrf[0], rrf[1]
+// (FP64; called by all 32 lanes, inactive lanes passing 0).
+__device__ __forceinline__ void rrf_accumulate(float v, double* rrf)
+{
+    double s1 = v, s2 = (double)v * (double)v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(rrf, s1);
+        atomicAdd(rrf + 1, s2);
+    }
+}
+
 // Device error word written by bounded waits and internal checks.
 enum DeviceError : int {
     DEV_OK = 0,

@@ -7,12 +7,38 @@
 
 namespace fmc {
 
+// General Ito disturbances (fmc_ito) as the kernels see them: in the deviation
+// y = xi - x0, mu(y) = c0 + c1 y + c2 y^2; sigma(y) = e0 + e1 y + e2 y^2 (kind
+// POLY) or sqrt(max(0, e0 + e1 y + e2 y^2 + e3 |y - ap|)) (kind SQRT); strat = 1:
+// subtract sigma sigma'/2 (KL paths).  kind OU: the ou_a / ou_s pair.
+template <int ND>
+struct ItoParams {
+    int on;      // any disturbance not OU
+    float strat;
+    int kind[ND];
+    float c0[ND], c1[ND], c2[ND];
+    float e0[ND], e1[ND], e2[ND], e3[ND], ap[ND];
+};
+
+// The per-step-normal Monte Carlo (FMC_SRS_EM): increments drawn in the
+// simulation kernels instead of read from the KL contraction.
+struct EmSpec {
+    int on;
+    uint32_t key0, key1;  // Philox key (the scenario's seed)
+    int64_t k0;           // design index of the launch's first sample
+    float sqdt;           // sqrt(dt)
+};
+
+
 cudaError_t launch_lhs_f32(uint64_t seed, int64_t N, int64_t k0, int64_t count, int M, int mode, float* zeta,
                            uint32_t* strata, int sms, cudaStream_t st);
 cudaError_t launch_lhs_split(uint64_t seed, int64_t N, int64_t k0, int64_t count, int d, int K, int mode, void* hi,
                              void* lo, int sms, cudaStream_t st);
-cudaError_t launch_basis_f32(int K, int Nt, double T, float* phi, int sms, cudaStream_t st);
-cudaError_t launch_basis_split(int K, int Nt, double T, int Kpad, void* hi, void* lo, int sms, cudaStream_t st);
+cudaError_t launch_em_increments(uint64_t seed, int64_t k0, int64_t count, int d, int Nt, double dt, float* dW,
+                                 int sms, cudaStream_t st);
+cudaError_t launch_basis_f32(int K, int Nt, double T, int basis, float* phi, int sms, cudaStream_t st);
+cudaError_t launch_basis_split(int K, int Nt, double T, int basis, int Kpad, void* hi, void* lo, int sms,
+                               cudaStream_t st);
 cudaError_t launch_sgemm_nn(int64_t R, int Ncols, int K, const float* A, const float* B, float* C, cudaStream_t st);
 cudaError_t launch_contract_tc(const CUtensorMap* maps, int64_t count, int d, int Ks, int nkb, int Nt, int TN,
                                int split, float* dW, int* err, cudaStream_t st);
@@ -20,18 +46,22 @@ cudaError_t launch_split_rows(const float* z, int64_t count, int d, int K, int K
 cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G, const double* B, const double* Ginf,
                                const double* Binf, const double* E, const double* Pm, double* out, int* status,
                                cudaStream_t st);
+// rrf (nullable): [2] FP64 sums of the response function and its square
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
-                                  int64_t count, int Nt, float* traj, cudaStream_t st);
-int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm);
+                                  int64_t count, int Nt, float* traj, double* rrf, cudaStream_t st);
+int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows);
+// rows: samples per CTA, 128 (four warps) or 64 (two warps); max_ctas: resident
+// CTAs per SM allowed (further limited by the TMEM columns)
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
-                                  const double* eq, float* part, double* S1, double* S2, float* traj, int* err,
-                                  cudaStream_t st, int* max_ctas_per_sm);
+                                  int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
+                                  float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
+                                  int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
 cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
                              int sms, cudaStream_t st);
-cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, double* S1, double* S2,
-                              cudaStream_t st);
+cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, int64_t count, int rows, double* S1,
+                              double* S2, cudaStream_t st);
 cudaError_t launch_finalize(const double* S1, const double* S2, const double* shift, int64_t N, int64_t Nt1, int S,
                             double* mean, double* var, cudaStream_t st);
 
@@ -52,18 +82,24 @@ struct WideArgs {
     double* S2;
     float* traj;          // [count][Nt+1][2n] or nullptr
     int* err;
+    EmSpec em;
+    int dx;               // disturbance slots in use: d, or d + 1 with the event slot (index d)
+    int ev_step;          // grid step of the event (see SwingParams)
+    double* rrf;          // [2]: sums of the response function and its square, or nullptr
+    ItoParams<8> ito;     // general disturbances (ito.on == 0: all OU)
 };
 
 __host__ __device__ constexpr int wide_nmtp(int nmt) { return (nmt + 3) & ~3; }
 
 // Constant block of the wide kernel (floats):
-//   GE [n][4][NMTP], BE [n][4][NMTP]: entry (j, h, k) = E_i E_j G_ij (resp. B_ij)
+//   GE [n][4][NMTP], NBE [n][4][NMTP]: entry (j, h, k) = E_i E_j G_ij (resp. -E_i E_j B_ij)
 //     for machine i = h + 4k, zero on the diagonal and for padded i;
-//   then seven rows of 4 NMT per machine: cos D*, sin D*, u*, v*, delta*, 1/(2H), D;
-//   then the injection map, d rows of 4 NMT.
-__host__ __device__ inline int wide_const_floats(int n, int nmt, int d)
+//   then eight rows of 4 NMT per machine: cos D*, sin D*, u*, v*, delta*, 1/(2H), D,
+//   H / sum H (centre-of-inertia weight);
+//   then the injection map, dx rows of 4 NMT (the event slot's row last).
+__host__ __device__ inline int wide_const_floats(int n, int nmt, int dx)
 {
-    return 2 * n * 4 * wide_nmtp(nmt) + (7 + d) * 4 * nmt;
+    return 2 * n * 4 * wide_nmtp(nmt) + (8 + dx) * 4 * nmt;
 }
 
 int wide_nmt_for(int n);

@@ -41,30 +41,6 @@ __device__ __forceinline__ uint32_t stratum(uint32_t k, uint32_t dim, uint32_t N
     return y;
 }
 
-// zeta = Phi^-1(p), p = num2 / (N 2^33) given as the exact integer numerator
-// num2 = 2 s 2^32 + 2 r + 1 (LHS), 2 s 2^32 + 2^32 (midpoint), 2 r + 1 (SRS, N=1).
-// The argument of the CUDA inverse error functions is formed from exact integer
-// differences so that it carries FP32 relative accuracy in both tails and at
-// the centre:  Phi^-1(p) = -sqrt2 erfcinv(2p) = sqrt2 erfinv(2p - 1)
-//            = sqrt2 erfcinv(2(1-p)).
-__device__ __forceinline__ float normal_from_fraction(uint64_t num2, uint32_t N)
-{
-    const uint64_t half = (uint64_t)N << 32;   // den/2
-    const float fhalf = (float)N * 4294967296.0f;
-    const float SQRT2 = 1.41421356237309515f;
-    if (num2 <= (half >> 1)) {                  // p <= 1/4
-        float twop = (float)num2 / fhalf;
-        return -SQRT2 * erfcinvf(twop);
-    }
-    uint64_t den = half << 1;
-    if (num2 >= den - (half >> 1)) {            // p >= 3/4
-        float twoq = (float)(den - num2) / fhalf;
-        return SQRT2 * erfcinvf(twoq);
-    }
-    int64_t c = (int64_t)(num2 - half);         // 2p - 1 = c / half
-    return SQRT2 * erfinvf((float)c / fhalf);
-}
-
 __device__ __forceinline__ float lhs_value(uint32_t k, uint32_t dim, uint32_t N, int mode, int h, uint32_t mask,
                                            uint32_t k0, uint32_t k1, uint32_t* s_out)
 {
@@ -142,6 +118,22 @@ __global__ void lhs_split_kernel(uint32_t k0s, uint32_t k1s, uint32_t N, int64_t
     }
 }
 
+// The paper's traditional Monte Carlo (Section V-B, Eq. distito): increments
+// dW[s][w][n] = sqrt(dt) em_normal(seed, k0 + s, w, n) of samples k0..k0+count-1.
+__global__ void em_increments_kernel(uint32_t k0s, uint32_t k1s, int64_t k0, int64_t count, int d, int Nt,
+                                     float sqdt, float* __restrict__ dW)
+{
+    int64_t total = count * (int64_t)d * Nt;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t sw = t / Nt;
+        int n = (int)(t - sw * Nt);
+        int64_t s = sw / d;
+        int w = (int)(sw - s * d);
+        dW[t] = sqdt * em_normal((uint32_t)(k0 + s), w, n, k0s, k1s);
+    }
+}
+
 static int grid_for(int64_t total, int block, int sms)
 {
     int64_t g = (total + block - 1) / block;
@@ -172,6 +164,16 @@ cudaError_t launch_lhs_split(uint64_t seed, int64_t N, int64_t k0, int64_t count
     lhs_split_kernel<<<grid_for(total, 256, sms), 256, 0, st>>>(
         (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)N, k0, count, d, K, Ks, mode, f.h, f.mask,
         (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_em_increments(uint64_t seed, int64_t k0, int64_t count, int d, int Nt, double dt, float* dW,
+                                 int sms, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    int64_t total = count * (int64_t)d * Nt;
+    em_increments_kernel<<<grid_for(total, 256, sms), 256, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), k0, count,
+                                                                    d, Nt, (float)sqrt(dt), dW);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,14 @@
 // Algorithm 1 step 4: expectation and unbiased variance over the samples.
 //
 // Values are shifted by a reference c (row 0 of the data, or the undisturbed
-// equilibrium for the fused simulation), summed in FP32 over short runs of rows,
-// and the run sums are combined in FP64:
+// equilibrium for the fused simulation).  Over short runs of rows the FP32 sum
+// and the squared deviations from the run's own mean are formed (two passes),
+// and the runs are combined in FP64:
 //   mean = c + S1/N,  var = (S2 - S1^2/N) / (N - 1),
-//   S1 = sum (x - c),  S2 = sum (x - c)^2.
-// With c near the data the subtraction in var is well conditioned.
+//   S1 = sum (x - c),  S2 = sum_runs (M2_run + S1_run^2 / n_run) = sum (x - c)^2.
+// The FP32 work only ever squares deviations from a run mean, so the variance
+// keeps FP32 accuracy relative to the spread even when the values drift far from
+// c (a common-mode response); the FP64 combine carries the rest.
 #include "fmc_common.cuh"
 #include "kernels.cuh"
 
@@ -30,14 +33,16 @@ __global__ void __launch_bounds__(MOM_THREADS) moments_partial_kernel(const floa
     double s1 = 0.0, s2 = 0.0;
     for (int64_t r = r0; r < r1; r += MOM_RUN) {
         int64_t re = r + MOM_RUN < r1 ? r + MOM_RUN : r1;
-        float a1 = 0.f, a2 = 0.f;
+        float a1 = 0.f;
+        for (int64_t q = r; q < re; ++q) a1 += x[q * C + c] - shift;
+        const float mu = a1 / (float)(re - r);
+        float m2 = 0.f;
         for (int64_t q = r; q < re; ++q) {
-            float v = x[q * C + c] - shift;
-            a1 += v;
-            a2 = fmaf(v, v, a2);
+            const float dv = (x[q * C + c] - shift) - mu;
+            m2 = fmaf(dv, dv, m2);
         }
         s1 += (double)a1;
-        s2 += (double)a2;
+        s2 += (double)m2 + (double)a1 * (double)a1 / (double)(re - r);
     }
     atomicAdd(&S1[c], s1);
     atomicAdd(&S2[c], s2);
@@ -95,16 +100,19 @@ cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double*
 }
 
 // Fused-simulation partials: part [nblk][Nt1][2*S] floats holding, per block of
-// samples and per grid time, the FP32 sums (S1 for states 0..S-1, then S2 for
-// states 0..S-1) of shifted values.  Combined over blocks in FP64 in a fixed
-// order, so the result does not depend on scheduling; out: S1, S2 [Nt1][S].
-// A CTA owns 32 consecutive entries q of a part row; its 8 warps stride over
-// the blocks (warp g takes blocks g, g+8, ...), each with two accumulators,
-// and the 8 partial sums are added in warp order.
+// `rows` samples (the last block count - (nblk-1) rows) and per grid time, the
+// FP32 sum of the shifted values (states 0..S-1) and their squared deviations
+// from the block's own mean (states 0..S-1).  Combined over blocks in FP64 in a
+// fixed order, so the result does not depend on scheduling:
+//   S1 = sum_b s1_b,  S2 = sum_b (m2_b + s1_b^2 / n_b)   (= sum of squares about the shift);
+// out: S1, S2 [Nt1][S].  A CTA owns 32 consecutive entries q of a part row; its
+// 8 warps stride over the blocks (warp g takes blocks g, g+8, ...), each with
+// two accumulators, and the 8 partial sums are added in warp order.
 constexpr int FS_COLS = 32, FS_GROUPS = 8;
 
 __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const float* __restrict__ part, int nblk,
-                                                                         int64_t Nt1, int S, double* __restrict__ S1o,
+                                                                         int64_t Nt1, int S, int64_t count, int rows,
+                                                                         double* __restrict__ S1o,
                                                                          double* __restrict__ S2o)
 {
     __shared__ double red[FS_GROUPS][FS_COLS];
@@ -115,12 +123,23 @@ __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const f
     double a0 = 0.0, a1 = 0.0;
     if (q < total) {
         const float* p = part + q;
+        const bool second = (q % row) >= S;  // squared deviations: add the block's s1^2 / n
+        auto term = [&](int b) {
+            double t = (double)p[(int64_t)b * total];
+            if (second) {
+                const double s1 = (double)p[(int64_t)b * total - S];
+                const int64_t left = count - (int64_t)b * rows;
+                const double nb = (double)(left < rows ? left : rows);
+                t += s1 * s1 / nb;
+            }
+            return t;
+        };
         int b = g;
         for (; b + FS_GROUPS < nblk; b += 2 * FS_GROUPS) {
-            a0 += (double)p[(int64_t)b * total];
-            a1 += (double)p[(int64_t)(b + FS_GROUPS) * total];
+            a0 += term(b);
+            a1 += term(b + FS_GROUPS);
         }
-        if (b < nblk) a0 += (double)p[(int64_t)b * total];
+        if (b < nblk) a0 += term(b);
     }
     red[g][cx] = a0 + a1;
     __syncthreads();
@@ -137,12 +156,12 @@ __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const f
     }
 }
 
-cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, double* S1, double* S2,
-                              cudaStream_t st)
+cudaError_t launch_fused_sums(const float* part, int nblk, int64_t Nt1, int S, int64_t count, int rows, double* S1,
+                              double* S2, cudaStream_t st)
 {
     int64_t total = Nt1 * 2 * S;
-    fused_sums_kernel<<<(unsigned)((total + FS_COLS - 1) / FS_COLS), FS_COLS * FS_GROUPS, 0, st>>>(part, nblk, Nt1, S,
-                                                                                                 S1, S2);
+    fused_sums_kernel<<<(unsigned)((total + FS_COLS - 1) / FS_COLS), FS_COLS * FS_GROUPS, 0, st>>>(
+        part, nblk, Nt1, S, count, rows, S1, S2);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -24,48 +25,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// Deep copy of a scenario (the caller's arrays may go away after submit).
-struct OwnedScenario {
-    fmc_scenario s{};
-    std::vector<double> G, B, Ginf, Binf, H, D, E, Pm, theta, sigma, inject;
-
-    explicit OwnedScenario(const fmc_scenario& in) : s(in)
-    {
-        const size_t n = (size_t)in.n, d = (size_t)in.d;
-        auto cp = [](std::vector<double>& dst, const double* src, size_t k) {
-            if (src) dst.assign(src, src + k);
-        };
-        cp(G, in.G, n * n);
-        cp(B, in.B, n * n);
-        cp(H, in.H, n);
-        cp(D, in.D, n);
-        cp(E, in.E, n);
-        cp(Pm, in.Pm, n);
-        cp(theta, in.theta, d);
-        cp(sigma, in.sigma, d);
-        cp(inject, in.inject, n * d);
-        if (in.has_inf_bus) {
-            cp(Ginf, in.Ginf, n);
-            cp(Binf, in.Binf, n);
-        }
-        auto ptr = [](const std::vector<double>& v) -> const double* { return v.empty() ? nullptr : v.data(); };
-        s.G = ptr(G);
-        s.B = ptr(B);
-        s.H = ptr(H);
-        s.D = ptr(D);
-        s.E = ptr(E);
-        s.Pm = ptr(Pm);
-        s.theta = ptr(theta);
-        s.sigma = ptr(sigma);
-        s.inject = ptr(inject);
-        s.Ginf = ptr(Ginf);
-        s.Binf = ptr(Binf);
-    }
-};
-
 struct Request {
     uint64_t id = 0;
-    std::unique_ptr<OwnedScenario> scen;
+    std::unique_ptr<fmc::OwnedScenario> scen;
     int32_t path = FMC_PATH_FUSED;
     double* mean = nullptr;
     double* var = nullptr;
@@ -74,7 +36,102 @@ struct Request {
     bool started = false;
     std::string error;
     Clock::time_point t_submit, t_start, t_done;
+    // target-error requests (fmc_submit_target)
+    double tol_E = 0.0, tol_Var = 0.0;
+    int64_t max_N = 0;
+    int replicates = 1;
+    int64_t n_used = 0;
+    double err_E = -1.0, err_Var = -1.0;
+    int target_met = 0;
 };
+
+constexpr int kReplicates = 4;
+
+// splitmix64: seeds of the replicate designs
+uint64_t mix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Runs a target-error request on the slot's contexts and streams (see
+// fmc_submit_target): rounds of kReplicates independent designs, each on its
+// own context and stream so that they run concurrently, n growing fourfold
+// until the replicate spread meets the targets or max_N is reached.
+int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
+{
+    fmc_ctx* ctx = rctx[0];
+    cudaStream_t st = rst[0];
+    fmc_scenario s = r->scen->s;
+    const int R = kReplicates;
+    const int64_t Nt = (int64_t)std::llround(s.T / s.dt);
+    const size_t cols = (size_t)(Nt + 1) * 2 * (size_t)s.n;
+    double* dbuf = nullptr;
+    if (cudaMallocAsync((void**)&dbuf, sizeof(double) * cols * 2 * R, st) != cudaSuccess) return FMC_ENOMEM;
+    std::vector<double> hm(cols * R), hv(cols * R), mbar(cols), vbar(cols);
+    const uint64_t seed0 = s.seed;
+    int64_t n = s.N < 2 ? 2 : s.N;
+    int rc = FMC_OK;
+    for (int round = 0;; ++round) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) {  // the scratch is ready for the replicates
+            rc = FMC_ECUDA;
+            break;
+        }
+        for (int k = 0; k < R && rc == FMC_OK; ++k) {
+            s.N = n;
+            s.seed = mix64(seed0 ^ ((uint64_t)(round * R + k + 1) << 32));
+            rc = fmc::simulate_moments(rctx[k], &s, r->path, dbuf + (size_t)k * cols, dbuf + (size_t)(R + k) * cols,
+                                       false, rst[k]);
+            if (rc != FMC_OK) r->error = fmc_last_error(rctx[k]);
+        }
+        for (int k = 0; k < R; ++k)
+            if (cudaStreamSynchronize(rst[k]) != cudaSuccess) rc = FMC_ECUDA;
+        if (rc != FMC_OK) break;
+        if (cudaMemcpyAsync(hm.data(), dbuf, sizeof(double) * cols * R, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hv.data(), dbuf + cols * R, sizeof(double) * cols * R, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = FMC_ECUDA;
+            break;
+        }
+        double sd_m = 0.0, sd_v = 0.0, scale_m = 0.0, scale_v = 0.0;
+        for (size_t c = 0; c < cols; ++c) {
+            double am = 0.0, av = 0.0;
+            for (int k = 0; k < R; ++k) {
+                am += hm[k * cols + c];
+                av += hv[k * cols + c];
+            }
+            am /= R;
+            av /= R;
+            double qm = 0.0, qv = 0.0;
+            for (int k = 0; k < R; ++k) {
+                qm += (hm[k * cols + c] - am) * (hm[k * cols + c] - am);
+                qv += (hv[k * cols + c] - av) * (hv[k * cols + c] - av);
+            }
+            mbar[c] = am;
+            vbar[c] = av;
+            sd_m = std::fmax(sd_m, std::sqrt(qm / (R - 1)));
+            sd_v = std::fmax(sd_v, std::sqrt(qv / (R - 1)));
+            scale_m = std::fmax(scale_m, std::sqrt(std::fmax(av, 0.0)));
+            scale_v = std::fmax(scale_v, av);
+        }
+        r->err_E = scale_m > 0 ? sd_m / std::sqrt((double)R) / scale_m : 0.0;
+        r->err_Var = scale_v > 0 ? sd_v / std::sqrt((double)R) / scale_v : 0.0;
+        r->n_used = (int64_t)R * n;
+        r->replicates = R;
+        r->target_met = (r->tol_E <= 0 || r->err_E <= r->tol_E) && (r->tol_Var <= 0 || r->err_Var <= r->tol_Var);
+        if (r->target_met || 4 * (int64_t)R * n > r->max_N) break;
+        n *= 4;
+    }
+    if (rc == FMC_OK &&
+        (cudaMemcpyAsync(r->mean, mbar.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(r->var, vbar.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st) != cudaSuccess))
+        rc = FMC_ECUDA;
+    cudaFreeAsync(dbuf, st);
+    return rc;
+}
 
 // Device bytes a request's workspace needs (the design, basis, partials,
 // equilibrium and the plain path's buffers), rounded up generously.
@@ -107,16 +164,18 @@ struct fmc_server {
     std::deque<uint64_t> queue;        // FIFO of waiting requests
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     std::vector<std::thread> workers;
-    std::vector<fmc_ctx*> ctxs;
+    std::vector<fmc_ctx*> ctxs;  // kReplicates per slot
     std::string err;
 };
 
 static void worker_loop(fmc_server* srv, int slot)
 {
-    fmc_ctx* ctx = srv->ctxs[slot];
+    fmc_ctx* const* rctx = &srv->ctxs[(size_t)slot * kReplicates];
+    fmc_ctx* ctx = rctx[0];
     cudaSetDevice(srv->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStream_t rst[kReplicates];
+    for (int k = 0; k < kReplicates; ++k) cudaStreamCreateWithFlags(&rst[k], cudaStreamNonBlocking);
+    cudaStream_t st = rst[0];
     for (;;) {
         Request* r = nullptr;
         {
@@ -137,24 +196,31 @@ static void worker_loop(fmc_server* srv, int slot)
             r->t_start = Clock::now();
         }
         // moments summed with FP64 atomics: no per-tile partial buffers to hold
-        int rc = fmc::simulate_moments(ctx, &r->scen->s, r->path, r->mean, r->var, false, st);
+        int rc;
+        if (r->tol_E > 0 || r->tol_Var > 0) {
+            rc = run_target(rctx, rst, r);
+        } else {
+            rc = fmc::simulate_moments(ctx, &r->scen->s, r->path, r->mean, r->var, false, st);
+            r->n_used = r->scen->s.N;
+        }
         if (rc == FMC_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FMC_ECUDA;
-        if (rc == FMC_OK) {
-            int it = 0, kerr = 0;
-            rc = fmc_device_status(ctx, &it, &kerr);
+        // status words of this slot's streams only (no device-wide wait)
+        for (int k = 0; k < kReplicates && rc == FMC_OK; ++k) {
+            rc = fmc::device_status_on(rctx[k], rst[k]);
+            if (rc != FMC_OK) r->error = fmc_last_error(rctx[k]);
         }
         // the workspace stays with the slot; the charge is released with the request
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             r->status = rc;
-            if (rc != FMC_OK) r->error = fmc_last_error(ctx);
+            if (rc != FMC_OK && r->error.empty()) r->error = fmc_last_error(ctx);
             r->t_done = Clock::now();
             srv->in_use -= r->bytes;
         }
         srv->cv_done.notify_all();
         srv->cv_work.notify_all();
     }
-    cudaStreamDestroy(st);
+    for (int k = 0; k < kReplicates; ++k) cudaStreamDestroy(rst[k]);
 }
 
 extern "C" {
@@ -174,7 +240,7 @@ int fmc_server_create(int device, int32_t slots, size_t mem_budget_bytes, fmc_se
         mem_budget_bytes = fr / 10 * 8;
     }
     srv->budget = mem_budget_bytes;
-    for (int i = 0; i < slots; ++i) {
+    for (int i = 0; i < slots * kReplicates; ++i) {
         fmc_ctx* c = nullptr;
         int rc = fmc_create(&c, device, 0);
         if (rc != FMC_OK) {
@@ -210,19 +276,31 @@ int fmc_server_destroy(fmc_server* srv)
     return FMC_OK;
 }
 
-int fmc_submit(fmc_server* srv, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
-               uint64_t* handle)
+static int submit_request(fmc_server* srv, const fmc_scenario* scen, int32_t path, double tol_E, double tol_Var,
+                          int64_t max_N, double* mean_dev, double* var_dev, uint64_t* handle)
 {
     if (!srv || !scen || !mean_dev || !var_dev || !handle) return FMC_EINVAL;
     if (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) return FMC_EINVAL;
     if (scen->n < 1 || scen->d < 1 || scen->K < 1 || scen->N < 1 || !(scen->dt > 0) || !(scen->T > 0))
         return FMC_EINVAL;
+    const bool target = tol_E > 0 || tol_Var > 0;
+    if (target && (max_N < (int64_t)kReplicates * scen->N || !(tol_E >= 0) || !(tol_Var >= 0))) return FMC_EINVAL;
     auto r = std::make_unique<Request>();
-    r->scen = std::make_unique<OwnedScenario>(*scen);
+    r->scen = std::make_unique<fmc::OwnedScenario>(*scen);
     r->path = path;
     r->mean = mean_dev;
     r->var = var_dev;
-    r->bytes = request_bytes(*scen, path);
+    r->tol_E = tol_E;
+    r->tol_Var = tol_Var;
+    r->max_N = max_N;
+    // charged for the largest design it may draw
+    fmc_scenario largest = *scen;
+    if (target) {
+        int64_t n = scen->N;
+        while (4 * (int64_t)kReplicates * n <= max_N) n *= 4;
+        largest.N = n;
+    }
+    r->bytes = request_bytes(largest, path);
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stopping) return FMC_ECANCELLED;
@@ -235,6 +313,19 @@ int fmc_submit(fmc_server* srv, const fmc_scenario* scen, int32_t path, double* 
     return FMC_OK;
 }
 
+int fmc_submit(fmc_server* srv, const fmc_scenario* scen, int32_t path, double* mean_dev, double* var_dev,
+               uint64_t* handle)
+{
+    return submit_request(srv, scen, path, 0.0, 0.0, 0, mean_dev, var_dev, handle);
+}
+
+int fmc_submit_target(fmc_server* srv, const fmc_scenario* scen, int32_t path, double tol_E, double tol_Var,
+                      int64_t max_N, double* mean_dev, double* var_dev, uint64_t* handle)
+{
+    if (!(tol_E > 0) && !(tol_Var > 0)) return FMC_EINVAL;
+    return submit_request(srv, scen, path, tol_E, tol_Var, max_N, mean_dev, var_dev, handle);
+}
+
 static void fill_result(const Request* r, fmc_result* out)
 {
     if (!out) return;
@@ -245,6 +336,12 @@ static void fill_result(const Request* r, fmc_result* out)
     out->latency_us = us(r->t_submit, r->t_done);
     out->queue_us = r->started ? us(r->t_submit, r->t_start) : out->latency_us;
     out->device_bytes = (uint64_t)r->bytes;
+    out->replicates = r->replicates;
+    out->n_used = r->n_used;
+    out->err_E = r->err_E;
+    out->err_Var = r->err_Var;
+    out->target_met = r->target_met;
+    out->reserved = 0;
     snprintf(out->message, sizeof out->message, "%s", r->error.c_str());
 }
 

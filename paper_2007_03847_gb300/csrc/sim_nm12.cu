@@ -5,25 +5,25 @@
 namespace fmc {
 
 cudaError_t launch_fused_nm12(int nd, const void* params, const CUtensorMap* maps, const FusedArgs& a, int smem,
-                              int ntiles, cudaStream_t st, int* occ)
+                              int ntiles, int rows, cudaStream_t st, int* occ)
 {
     switch (nd) {
-        case 1: return launch_fused_t<12, 1>(params, maps, a, smem, ntiles, st, occ);
-        case 2: return launch_fused_t<12, 2>(params, maps, a, smem, ntiles, st, occ);
-        case 4: return launch_fused_t<12, 4>(params, maps, a, smem, ntiles, st, occ);
-        case 8: return launch_fused_t<12, 8>(params, maps, a, smem, ntiles, st, occ);
+        case 1: return launch_fused_t<12, 1>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 2: return launch_fused_t<12, 2>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 4: return launch_fused_t<12, 4>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 8: return launch_fused_t<12, 8>(params, maps, a, smem, ntiles, rows, st, occ);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_plain_nm12(int nd, const void* params, const double* eq, const float* dW, int64_t count, int Nt,
-                              float* traj, cudaStream_t st)
+                              float* traj, double* rrf, cudaStream_t st)
 {
     switch (nd) {
-        case 1: return launch_plain_t<12, 1>(params, eq, dW, count, Nt, traj, st);
-        case 2: return launch_plain_t<12, 2>(params, eq, dW, count, Nt, traj, st);
-        case 4: return launch_plain_t<12, 4>(params, eq, dW, count, Nt, traj, st);
-        case 8: return launch_plain_t<12, 8>(params, eq, dW, count, Nt, traj, st);
+        case 1: return launch_plain_t<12, 1>(params, eq, dW, count, Nt, traj, rrf, st);
+        case 2: return launch_plain_t<12, 2>(params, eq, dW, count, Nt, traj, rrf, st);
+        case 4: return launch_plain_t<12, 4>(params, eq, dW, count, Nt, traj, rrf, st);
+        case 8: return launch_plain_t<12, 8>(params, eq, dW, count, Nt, traj, rrf, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,5 +1,11 @@
 // Algorithm 1 steps 2-4 fused on one SM-resident CTA per 128 samples:
 //
+// (A CTA may also take 64 samples in two warps -- "half tiles" -- so that a
+// grid that would leave SMs with uneven numbers of 4-warp CTAs spreads its
+// warps more evenly; the MMA then still has M = 128, its upper 64 rows being
+// whatever follows the 64-row tile in shared memory, and lanes 64..127 of the
+// accumulator are never read.)
+//
 //   for each time chunk of TC steps:
 //     tensor cores:  dW[128 x TC] per disturbance = Z_tile . Phi_chunk^T into TMEM
 //                    (BF16 or split BF16x3 operands streamed by TMA, FP32 accumulate)
@@ -22,7 +28,7 @@
 
 namespace fmc {
 
-constexpr int FU_THREADS = 128;
+constexpr int FU_THREADS = 128;  // full tile; a half tile has 64 threads
 constexpr int FU_MS = 8;  // steps between flushes of the moment buffer
 
 struct FusedArgs {
@@ -36,6 +42,8 @@ struct FusedArgs {
     int* err;
     double* S1;         // [Nt+1][2n] when part == nullptr
     double* S2;
+    EmSpec em;          // on: per-step normals instead of the contraction (no tensor cores)
+    double* rrf;        // [2]: sums of the response function and its square, or nullptr
 };
 
 template <int NM, int ND>
@@ -54,15 +62,16 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int rows = blockDim.x, warps = rows / 32;  // samples (= threads) and warps of this CTA
     const int n = p.n, d = p.d, S = 2 * n, S4 = 4 * n;
-    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int64_t row0 = (int64_t)blockIdx.x * rows;
     const int64_t srow = row0 + tid;
     const bool active = srow < a.count;
     const int TC = a.TC;
 
     // ring (used only while the tensor cores fill TMEM) aliases the moment buffers
     TcRing r;
-    r.a_bytes = TC_M * 64;
+    r.a_bytes = rows * 64;
     r.b_bytes = TC * 64;
     r.split = a.split;
     r.base = smem;
@@ -72,11 +81,14 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     uint64_t* done = &bars[2 * TC_MAX_STAGES];
     const int WROW = 2 * NM + 1;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;           // [32][WROW] per warp
-    float* msum = reinterpret_cast<float*>(smem) + 4 * 32 * WROW;              // [FU_MS][4][4*NM]
+    float* msum = reinterpret_cast<float*>(smem) + warps * 32 * WROW;          // [FU_MS][warps][4*NM]
 
+    const bool em = a.em.on != 0;
     if (tid == 0) {
-        prefetch_tmap(&mAh);
-        prefetch_tmap(&mBh);
+        if (!em) {
+            prefetch_tmap(&mAh);
+            prefetch_tmap(&mBh);
+        }
         for (int b = 0; b < 2 * TC_MAX_STAGES + 1; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
         abort_flag = 0;
@@ -111,14 +123,16 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     // time 0: every sample sits at the (rounded) shift, so both sums are zero
     float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4 : nullptr;
     if (part_tile)
-        for (int v = tid; v < S4; v += FU_THREADS) part_tile[v] = 0.f;
+        for (int v = tid; v < S4; v += rows) part_tile[v] = 0.f;
 
     const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
     uint32_t g = 0;  // K blocks issued so far (thread 0)
+    float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
     const int J = d * a.nkb;
 
     for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
+        if (!em) {
         tc_fence_before();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -150,6 +164,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         }
         if (!__syncthreads_and(ok)) break;
         tc_fence_after();
+        }
 
         // ---- FP32 pipes: integrate this chunk ----
         const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
@@ -157,12 +172,21 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             float dw[ND], x1[ND];
 #pragma unroll
             for (int q = 0; q < ND; ++q) dw[q] = 0.f;
+            if (em) {
+                em_increments<ND>(a.em, (uint32_t)(a.em.k0 + srow), n0 + s, d, dw);
+            } else {
 #pragma unroll
-            for (int q = 0; q < ND; ++q)
-                if (q < d) dw[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
-            tmem_ld_wait();
+                for (int q = 0; q < ND; ++q)
+                    if (q < d) dw[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
+                tmem_ld_wait();
+            }
+            event_state<NM, ND>(p, n0 + s, x0);
             ou_step<NM, ND>(p, x0, dw, x1);
             swing_step<NM, ND>(p, del, w, theta, x0, x1);
+            if (a.rrf) {
+                const float cs = coi_speed<NM, ND>(p, w);
+                racc = fmaf(cs, cs, racc);
+            }
 #pragma unroll
             for (int q = 0; q < ND; ++q) x0[q] = x1[q];
 
@@ -187,49 +211,51 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             __syncwarp();
             const int ms = s % FU_MS;
             if (lane < S) {
-                // four interleaved partial sums (shorter dependency chains), combined in a fixed order
-                float s1a = 0.f, s1b = 0.f, s1c = 0.f, s1d = 0.f, s2a = 0.f, s2b = 0.f, s2c = 0.f, s2d = 0.f;
-#pragma unroll
-                for (int rr = 0; rr < 32; rr += 4) {
-                    const float v0 = wbuf[rr * WROW + lane], v1 = wbuf[(rr + 1) * WROW + lane];
-                    const float v2 = wbuf[(rr + 2) * WROW + lane], v3 = wbuf[(rr + 3) * WROW + lane];
-                    s1a += v0;
-                    s1b += v1;
-                    s1c += v2;
-                    s1d += v3;
-                    s2a = fmaf(v0, v0, s2a);
-                    s2b = fmaf(v1, v1, s2b);
-                    s2c = fmaf(v2, v2, s2c);
-                    s2d = fmaf(v3, v3, s2d);
-                }
-                const float s1 = (s1a + s1b) + (s1c + s1d);
-                const float s2 = (s2a + s2b) + (s2c + s2d);
-                msum[(ms * 4 + warp) * (4 * NM) + lane] = s1;
-                msum[(ms * 4 + warp) * (4 * NM) + S + lane] = s2;
+                // the warp's sum and squared deviations from its mean, per state
+                const int64_t left = a.count - (srow - lane);
+                const int na_warp = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+                float s1, m2;
+                column_sum_m2(wbuf + lane, WROW, na_warp, &s1, &m2);
+                msum[(ms * warps + warp) * (4 * NM) + lane] = s1;
+                msum[(ms * warps + warp) * (4 * NM) + S + lane] = m2;
             }
             __syncwarp();
             if (ms == FU_MS - 1 || s == steps - 1) {
-                asm volatile("bar.sync 1, %0;" ::"r"(FU_THREADS) : "memory");
+                asm volatile("bar.sync 1, %0;" ::"r"(rows) : "memory");
                 const int nst = ms + 1;
                 const int tn0 = tn - ms;
-                for (int e = tid; e < nst * S4; e += FU_THREADS) {
+                // samples of this tile in each warp (the last tile may be partly empty)
+                int na_tile[4], n_tile = 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int64_t left = a.count - row0 - 32 * g;
+                    na_tile[g] = g < warps ? (left <= 0 ? 0 : (left >= 32 ? 32 : (int)left)) : 0;
+                    n_tile += na_tile[g];
+                }
+                for (int e = tid; e < nst * S4; e += rows) {
                     const int sl = e / S4, v = e - sl * S4;
-                    const float* m = msum + sl * 4 * (4 * NM) + v;
-                    float acc = ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM];
+                    const int j = v < S ? v : v - S;  // state
+                    const float* m = msum + sl * warps * (4 * NM) + j;
+                    // tile sum; for the second half the tile's squared deviations (parallel combine)
+                    const float t1 =
+                        warps == 4 ? ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM] : m[0] + m[4 * NM];
+                    const float acc = v < S ? t1 : combine_m2(m, m + S, 4 * NM, na_tile, warps);
                     if (part_tile) {
                         part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
                     } else {
+                        // the tile's S1 and S2 (= M2 + S1^2 / n) about the shift, in FP64
                         const int64_t row = (int64_t)(tn0 + sl) * S;
                         if (v < S)
                             atomicAdd(a.S1 + row + v, (double)acc);
-                        else
-                            atomicAdd(a.S2 + row + (v - S), (double)acc);
+                        else if (n_tile > 0)
+                            atomicAdd(a.S2 + row + j, (double)acc + (double)t1 * (double)t1 / (double)n_tile);
                     }
                 }
-                asm volatile("bar.sync 1, %0;" ::"r"(FU_THREADS) : "memory");
+                asm volatile("bar.sync 1, %0;" ::"r"(rows) : "memory");
             }
         }
     }
+    if (a.rrf) rrf_accumulate(active ? sqrtf(racc / (float)a.Nt) : 0.f, a.rrf);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
@@ -237,19 +263,21 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 
 template <int NM, int ND>
 cudaError_t launch_fused_t(const void* params, const CUtensorMap* maps, const FusedArgs& a, int smem, int ntiles,
-                           cudaStream_t st, int* max_ctas_per_sm)
+                           int rows, cudaStream_t st, int* max_ctas_per_sm)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
     auto kern = simulate_fused_kernel<NM, ND>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the attribute is process-wide and launches from several host threads may
+    // race on it: always the same (largest) bound, the launch passes its own size
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, FU_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, rows, smem);
     if (e != cudaSuccess) return e;
     *max_ctas_per_sm = occ;
     // every resident CTA holds tmem_cols TMEM columns; 512 per SM
     if (occ < 1 || (uint32_t)occ * a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
-    kern<<<ntiles, FU_THREADS, smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], a);
+    kern<<<ntiles, rows, smem, st>>>(p, maps[0], maps[1], maps[2], maps[3], a);
     return cudaGetLastError();
 }
 

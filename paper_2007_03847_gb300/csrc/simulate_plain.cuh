@@ -13,10 +13,13 @@ namespace fmc {
 template <int NM, int ND>
 __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_constant__ SwingParams<NM, ND> p,
                                                              const double* __restrict__ eq, const float* __restrict__ dW,
-                                                             int64_t count, int Nt, float* __restrict__ traj)
+                                                             int64_t count, int Nt, float* __restrict__ traj,
+                                                             double* __restrict__ rrf)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= count) return;
+    const bool active = s < count;
+    if (!active && rrf == nullptr) return;
+    if (!active) s = count - 1;  // computes a duplicate that is neither stored nor counted
     const int n = p.n;
     const int d = p.d;
     float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
@@ -32,18 +35,23 @@ __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_consta
     float* out = traj + s * (int64_t)(Nt + 1) * row;
 #pragma unroll
     for (int i = 0; i < NM; ++i)
-        if (i < n) {
+        if (i < n && active) {
             out[i] = p.dst[i];
             out[n + i] = 0.f;
         }
     const float* dws = dW + s * (int64_t)d * Nt;
+    float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
     for (int step = 0; step < Nt; ++step) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) dw[q] = (q < d) ? __ldg(dws + (int64_t)q * Nt + step) : 0.f;
+        event_state<NM, ND>(p, step, x0);
         ou_step<NM, ND>(p, x0, dw, x1);
         swing_step<NM, ND>(p, del, w, theta, x0, x1);
 #pragma unroll
         for (int q = 0; q < ND; ++q) x0[q] = x1[q];
+        const float c = coi_speed<NM, ND>(p, w);
+        racc = fmaf(c, c, racc);
+        if (!active) continue;
         float* o = out + (int64_t)(step + 1) * row;
 #pragma unroll
         for (int i = 0; i < NM; ++i)
@@ -52,15 +60,16 @@ __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_consta
                 o[n + i] = w[i];
             }
     }
+    if (rrf) rrf_accumulate(active ? sqrtf(racc / (float)Nt) : 0.f, rrf);
 }
 
 template <int NM, int ND>
 cudaError_t launch_plain_t(const void* params, const double* eq, const float* dW, int64_t count, int Nt, float* traj,
-                           cudaStream_t st)
+                           double* rrf, cudaStream_t st)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
     int64_t g = (count + 127) / 128;
-    simulate_plain_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, eq, dW, count, Nt, traj);
+    simulate_plain_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, eq, dW, count, Nt, traj, rrf);
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ constexpr int WI_MS = 4;  // steps between flushes of the moment buffer
 template <int NMT>
 __host__ __device__ inline int wide_mom_floats()
 {
-    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 4 * NMT;
+    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 4 * NMT + WI_MS * 4 * 128;
 }
 
 // sin and cos - 1 of a deviation, rotated into (gamma, eta) about the equilibrium.
@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     constexpr int NMTP = wide_nmtp(NMT);
     constexpr int KP = NMT > 10 ? 8 : NMT;  // machine slots per pass over the network sum
     constexpr int JU = NMT > 7 ? 1 : 2;      // unrolling of the loop over j (registers permitting)
+    // packed FP32 where it measured faster (7 and 10 slots; the odd pair of 5
+    // and 13 slots and the second pass of 13 cost more than it saves)
+    constexpr bool PACK = FMC_PACKED_FP32 && (NMT == 7 || NMT == 10);
     constexpr int G4 = 4 * NMT;
     constexpr int WROW = 2 * NMT + 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -95,7 +98,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     float2* gh = reinterpret_cast<float2*>(smem + u_bytes);            // [2][n][128]
     float* w0buf = reinterpret_cast<float*>(gh + 2 * n * 128);         // [2][128]
     float* cst_s = w0buf + 256;
-    const int nconst = wide_const_floats(n, NMT, d);
+    const int dx = a.dx;
+    const int nconst = wide_const_floats(n, NMT, dx);
     for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[e];
     const float* GEs = cst_s;
     const float* BEs = cst_s + n * 4 * NMTP;
@@ -107,11 +111,17 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const float* c_dst = pm + 4 * G4;
     const float* c_i2h = pm + 5 * G4;
     const float* c_D = pm + 6 * G4;
-    const float* c_inj = pm + 7 * G4;  // [d][4 NMT]
+    const float* c_hw = pm + 7 * G4;
+    const float* c_inj = pm + 8 * G4;  // [dx][4 NMT]
+    // per step and warp, the partial centre-of-inertia speed of the warp's machines
+    float* coi_part = msum + WI_MS * 16 * 4 * NMT;  // [WI_MS][4 (h)][128]
 
+    const bool em = a.em.on != 0;
     if (tid == 0) {
-        prefetch_tmap(&mAh);
-        prefetch_tmap(&mBh);
+        if (!em) {
+            prefetch_tmap(&mAh);
+            prefetch_tmap(&mBh);
+        }
         for (int b = 0; b < 2 * TC_MAX_STAGES + 1; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
         abort_flag = 0;
@@ -166,9 +176,11 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const int nst = rk4 ? 4 : 2;
     const float ref = a.rel ? 1.f : 0.f;
     const float hh = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
+    float racc = 0.f;  // (warps h = 0) sum over the grid of the squared centre-of-inertia speed
 
     for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
+        if (!em) {
         tc_fence_before();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -200,6 +212,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
         }
         if (!__syncthreads_and(ok)) break;
         tc_fence_after();
+        }
 
         // ---- FP32 pipes: integrate this chunk ----
         const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
@@ -207,12 +220,24 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             float dw[ND], x1[ND];
 #pragma unroll
             for (int e = 0; e < ND; ++e) dw[e] = 0.f;
+            if (em) {
+                em_increments<ND>(a.em, (uint32_t)(a.em.k0 + srow), n0 + s, d, dw);
+            } else {
 #pragma unroll
-            for (int e = 0; e < ND; ++e)
-                if (e < d) dw[e] = tmem_ld1(lane_addr + (uint32_t)(e * TC + s));
-            tmem_ld_wait();
+                for (int e = 0; e < ND; ++e)
+                    if (e < d) dw[e] = tmem_ld1(lane_addr + (uint32_t)(e * TC + s));
+                tmem_ld_wait();
+            }
 #pragma unroll
-            for (int e = 0; e < ND; ++e) x1[e] = fmaf(a.ou_a[e], x0[e], a.ou_s[e] * dw[e]);
+            for (int e = 0; e < ND; ++e)  // the event slot (index d) is 0 before the event, 1 from it
+                if (e == d && dx > d) x0[e] = (n0 + s >= a.ev_step) ? 1.f : 0.f;
+            if (a.ito.on) {
+#pragma unroll
+                for (int e = 0; e < ND; ++e) x1[e] = ito_step1<8>(a.ito, e, a.ou_a[e], a.ou_s[e], x0[e], dw[e], dt);
+            } else {
+#pragma unroll
+                for (int e = 0; e < ND; ++e) x1[e] = fmaf(a.ou_a[e], x0[e], a.ou_s[e] * dw[e]);
+            }
 
             float ad[NMT], aw[NMT], yw[NMT];
             float ath = 0.f;
@@ -247,11 +272,54 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 // passes above, so that fewer network sums are live at once
 #pragma unroll
                 for (int k0 = 0; k0 < NMT; k0 += KP) {
-                    float du[KP], dv[KP];
+                    float du[KP + 1], dv[KP + 1];
+                    if constexpr (PACK) {
+                        // packed FP32 over pairs of machine slots: (du_k, du_k+1) +=
+                        // (GE_k, GE_k+1)(gamma_j, gamma_j) + (NBE_k, NBE_k+1)(eta_j, eta_j) and
+                        // (dv_k, dv_k+1) += (GE_k, GE_k+1)(eta_j, eta_j) + (NBE_k, NBE_k+1)(-gamma_j, -gamma_j):
+                        // the same roundings as the scalar form, half the instructions
+                        constexpr int KP2 = (KP + 1) / 2;
+                        unsigned long long du2[KP2], dv2[KP2];
 #pragma unroll
-                    for (int k = 0; k < KP; ++k) {
-                        du[k] = 0.f;
-                        dv[k] = 0.f;
+                        for (int k = 0; k < KP2; ++k) {
+                            du2[k] = 0ull;
+                            dv2[k] = 0ull;
+                        }
+#pragma unroll JU
+                        for (int j = 0; j < n; ++j) {
+                            const float2 gej = ghc[j * 128];
+                            const unsigned long long gg2 = f2pack(gej.x, gej.x), ee2 = f2pack(gej.y, gej.y);
+                            const unsigned long long ng2 = f2pack(-gej.x, -gej.x);
+                            const ulonglong2* g4 = reinterpret_cast<const ulonglong2*>(GEs + (j * 4 + h) * NMTP + k0);
+                            const ulonglong2* b4 = reinterpret_cast<const ulonglong2*>(BEs + (j * 4 + h) * NMTP + k0);
+#pragma unroll
+                            for (int k4 = 0; k4 < (KP + 3) / 4; ++k4) {
+                                if (k0 + 4 * k4 < NMT) {
+                                    const ulonglong2 gv = g4[k4], bv = b4[k4];
+#pragma unroll
+                                    for (int kk = 0; kk < 2; ++kk) {
+                                        const int k2 = 2 * k4 + kk;  // pair index
+                                        if (k2 < KP2 && k0 + 2 * k2 < NMT) {
+                                            const unsigned long long ge = kk ? gv.y : gv.x, nb = kk ? bv.y : bv.x;
+                                            du2[k2] = ffma2(ge, gg2, du2[k2]);
+                                            du2[k2] = ffma2(nb, ee2, du2[k2]);
+                                            dv2[k2] = ffma2(ge, ee2, dv2[k2]);
+                                            dv2[k2] = ffma2(nb, ng2, dv2[k2]);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int k2 = 0; k2 < KP2; ++k2) {
+                            f2unpack(du2[k2], du[2 * k2], du[2 * k2 + 1]);
+                            f2unpack(dv2[k2], dv[2 * k2], dv[2 * k2 + 1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < KP; ++k) {
+                            du[k] = 0.f;
+                            dv[k] = 0.f;
                     }
 #pragma unroll JU
                     for (int j = 0; j < n; ++j) {
@@ -269,13 +337,14 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                                     const int k = 4 * k4 + kk;
                                     if (k < KP && k0 + k < NMT) {
                                         du[k] = fmaf(gg[kk], gej.x, du[k]);
-                                        du[k] = fmaf(-bb[kk], gej.y, du[k]);
+                                        du[k] = fmaf(bb[kk], gej.y, du[k]);
                                         dv[k] = fmaf(gg[kk], gej.y, dv[k]);
-                                        dv[k] = fmaf(bb[kk], gej.x, dv[k]);
+                                        dv[k] = fmaf(bb[kk], -gej.x, dv[k]);
                                     }
                                 }
                             }
                         }
+                    }
                     }
 #pragma unroll
                     for (int kq = 0; kq < KP; ++kq) {
@@ -290,7 +359,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                             float f = 0.f;
 #pragma unroll
                             for (int e = 0; e < ND; ++e)
-                                if (e < d) f = fmaf(c_inj[e * G4 + i], xs[e], f);
+                                if (e < dx) f = fmaf(c_inj[e * G4 + i], xs[e], f);
                             const float kd = a.omega_s * (yw[k] - w0);
                             const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
                             ad[k] = fmaf(b, kd, ad[k]);
@@ -352,22 +421,41 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             __syncwarp();
             const int ms = s % WI_MS;
             if (lane < 2 * NMT) {
-                float s1 = 0.f, s2 = 0.f;
-#pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) {
-                    float v = wbuf[rr * WROW + lane];
-                    s1 += v;
-                    s2 = fmaf(v, v, s2);
-                }
+                // the sample group's sum and squared deviations from its mean, per state
+                const int64_t left = a.count - (srow - lane);
+                const int na = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+                float s1, m2;
+                column_sum_m2(wbuf + lane, WROW, na, &s1, &m2);
                 float* slot = msum + ((ms * 4 + q) * 4 + h) * G4;
                 slot[lane] = s1;
-                slot[2 * NMT + lane] = s2;
+                slot[2 * NMT + lane] = m2;
+            }
+            if (a.rrf) {
+                float cp = 0.f;
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) cp = fmaf(c_hw[h + 4 * k], w[k], cp);
+                coi_part[(ms * 4 + h) * 128 + r] = cp;
             }
             __syncwarp();
             if (ms == WI_MS - 1 || s == steps - 1) {
                 __syncthreads();
+                if (a.rrf && h == 0) {
+                    for (int sl = 0; sl <= ms; ++sl) {
+                        const float* cq = coi_part + sl * 4 * 128 + r;
+                        const float c = ((cq[0] + cq[128]) + cq[256]) + cq[384];
+                        racc = fmaf(c, c, racc);
+                    }
+                }
                 const int nsl = ms + 1;
                 const int tn0 = tn - ms;
+                // samples of this tile in each sample group (the last tile may be partly empty)
+                int na_g[4], n_tile = 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int64_t left = a.count - row0 - 32 * g;
+                    na_g[g] = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+                    n_tile += na_g[g];
+                }
                 for (int e = tid; e < nsl * S4; e += WI_THREADS) {
                     const int sl = e / S4, v = e - sl * S4;
                     // v = kind * 2n + state; state < n is delta_i, else omega_(state - n)
@@ -375,23 +463,26 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                     const int stt = v - kind * S;
                     const int isw = stt >= n ? 1 : 0;
                     const int i = stt - isw * n;
-                    const int col = kind * 2 * NMT + isw * NMT + (i >> 2);
-                    const float* m = msum + (sl * 16 + (i & 3)) * G4 + col;
-                    const float acc = ((m[0] + m[4 * G4]) + m[8 * G4]) + m[12 * G4];
+                    const float* m = msum + (sl * 16 + (i & 3)) * G4 + isw * NMT + (i >> 2);
+                    // tile sum; for kind 1 the tile's squared deviations (parallel combine)
+                    const float t1 = ((m[0] + m[4 * G4]) + m[8 * G4]) + m[12 * G4];
+                    const float acc = kind == 0 ? t1 : combine_m2(m, m + 2 * NMT, 4 * G4, na_g, 4);
                     if (part_tile) {
                         part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
                     } else {
+                        // the tile's S1 and S2 (= M2 + S1^2 / n) about the shift, in FP64
                         const int64_t rowt = (int64_t)(tn0 + sl) * S;
                         if (kind == 0)
                             atomicAdd(a.S1 + rowt + stt, (double)acc);
-                        else
-                            atomicAdd(a.S2 + rowt + stt, (double)acc);
+                        else if (n_tile > 0)
+                            atomicAdd(a.S2 + rowt + stt, (double)acc + (double)t1 * (double)t1 / (double)n_tile);
                     }
                 }
                 __syncthreads();
             }
         }
     }
+    if (a.rrf && h == 0) rrf_accumulate(active ? sqrtf(racc / (float)a.Nt) : 0.f, a.rrf);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
@@ -399,12 +490,12 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 
 // Dynamic shared memory of the kernel (bytes), alignment slack included.
 template <int NMT>
-inline int wide_smem_bytes(int TC, int split, int n, int d, int ns)
+inline int wide_smem_bytes(int TC, int split, int n, int dx, int ns)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
     const int mom = wide_mom_floats<NMT>() * 4;
     const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
-    return 1024 + u + 2 * n * 128 * 8 + 256 * 4 + wide_const_floats(n, NMT, d) * 4;
+    return 1024 + u + 2 * n * 128 * 8 + 256 * 4 + wide_const_floats(n, NMT, dx) * 4;
 }
 
 template <int NMT, int ND>
@@ -414,11 +505,13 @@ cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStr
     // as many ring stages as the shared memory left by the other buffers holds
     WideArgs a = args;
     a.ns = 2;
-    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d, a.ns + 1) <= TC_SMEM_DYN_MAX)
+    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.dx, a.ns + 1) <= TC_SMEM_DYN_MAX)
         ++a.ns;
-    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.d, a.ns);
+    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.dx, a.ns);
     if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the attribute is process-wide and launches from several host threads may
+    // race on it: always the same (largest) bound, the launch passes its own size
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WI_THREADS, smem);

@@ -21,6 +21,7 @@
 #pragma once
 
 #include "fmc_common.cuh"
+#include "kernels.cuh"
 
 #ifndef FMC_PACKED_FP32
 #define FMC_PACKED_FP32 1
@@ -77,15 +78,41 @@ struct SwingParams {
     float inv2H[NM];
     float D[NM];
     float inj[NM][ND];
-    float ou_a[ND];              // 1 - theta_w dt
-    float ou_s[ND];              // sigma_w
+    float ou_a[ND];              // 1 - theta_w dt (1 in the event slot)
+    float ou_s[ND];              // sigma_w (0 in the event slot)
+    float hw[NM];                // H_i / sum H: centre-of-inertia weights of the response function
     float omega_s;
     float dt;
     int d;                       // real disturbances (<= ND; the rest are zero)
     int n;                       // real machines (<= NM; the rest are inert padding)
     int integrator;              // FMC_RK4 / FMC_HEUN
     int rel;                     // 1: angles relative to machine 0 (no infinite bus)
+    // An event (a step in one machine's mechanical power from grid step ev_step
+    // on) rides in a spare disturbance slot ev_slot >= d: its "disturbance" is 0
+    // before the event and 1 from it, its injection the power step; -1: none.
+    int ev_slot;
+    int ev_step;
+    ItoParams<ND> ito;           // general disturbances (ito.on == 0: all OU)
 };
+
+// The event slot's value for the step that starts at grid index `step`.
+template <int NM, int ND>
+__device__ __forceinline__ void event_state(const SwingParams<NM, ND>& p, int step, float (&x0)[ND])
+{
+#pragma unroll
+    for (int q = 0; q < ND; ++q)
+        if (q == p.ev_slot) x0[q] = (step >= p.ev_step) ? 1.f : 0.f;
+}
+
+// The centre-of-inertia speed deviation of one sample.
+template <int NM, int ND>
+__device__ __forceinline__ float coi_speed(const SwingParams<NM, ND>& p, const float (&w)[NM])
+{
+    float c = 0.f;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) c = fmaf(p.hw[i], w[i], c);
+    return c;
+}
 
 // sin(a) and cos(a) - 1 of a small deviation angle, without cancellation: the
 // Taylor series to degree 9 and 10 (truncation < 3e-9 for |a| <= 0.8).
@@ -264,11 +291,56 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
     theta = fmaf(h, ath, theta);
 }
 
+// Increments of the per-step-normal Monte Carlo for one sample and step:
+// dw[w] = sqrt(dt) em_normal(k, w, n), one Philox call per four disturbances.
+template <int ND>
+__device__ __forceinline__ void em_increments(const EmSpec& em, uint32_t k, int n, int d, float (&dw)[ND])
+{
+#pragma unroll
+    for (int g = 0; g < (ND + 3) / 4; ++g) {
+        if (4 * g < d) {
+            const U4 o = philox4x32_10(U4{k, (uint32_t)n, EM_TAG, (uint32_t)g}, em.key0, em.key1);
+            const uint32_t r[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (4 * g + e < ND && 4 * g + e < d)
+                    dw[4 * g + e] = em.sqdt * normal_from_fraction(2ull * r[e] + 1ull, 1u);
+        }
+    }
+}
+
+// One step of a general disturbance (see ItoParams) in the deviation y.
+template <int ND>
+__device__ __forceinline__ float ito_step1(const ItoParams<ND>& it, int q, float ou_a, float ou_s, float y, float dw,
+                                           float dt)
+{
+    if (it.kind[q] == FMC_ITO_OU) return fmaf(ou_a, y, ou_s * dw);
+    const float mu = fmaf(fmaf(it.c2[q], y, it.c1[q]), y, it.c0[q]);
+    float sg, corr;
+    if (it.kind[q] == FMC_ITO_POLY) {
+        sg = fmaf(fmaf(it.e2[q], y, it.e1[q]), y, it.e0[q]);
+        corr = sg * fmaf(2.f * it.e2[q], y, it.e1[q]);
+    } else {
+        const float dy = y - it.ap[q];
+        const float v = fmaf(it.e3[q], fabsf(dy), fmaf(fmaf(it.e2[q], y, it.e1[q]), y, it.e0[q]));
+        sg = v > 0.f ? sqrtf(v) : 0.f;
+        const float sgn = dy > 0.f ? 1.f : (dy < 0.f ? -1.f : 0.f);
+        corr = v > 0.f ? 0.5f * fmaf(it.e3[q], sgn, fmaf(2.f * it.e2[q], y, it.e1[q])) : 0.f;
+    }
+    const float drift = fmaf(-0.5f * it.strat, corr, mu);
+    return fmaf(sg, dw, fmaf(drift, dt, y));
+}
+
 // One Euler-Maruyama step of the OU disturbances: x1 = (1 - theta dt) x0 + sigma dW.
 template <int NM, int ND>
 __device__ __forceinline__ void ou_step(const SwingParams<NM, ND>& p, const float (&x0)[ND], const float (&dw)[ND],
                                         float (&x1)[ND])
 {
+    if (p.ito.on) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) x1[q] = ito_step1<ND>(p.ito, q, p.ou_a[q], p.ou_s[q], x0[q], dw[q], p.dt);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < ND; ++q) x1[q] = fmaf(p.ou_a[q], x0[q], p.ou_s[q] * dw[q]);
 }

@@ -54,3 +54,42 @@ def test_binding_fails_loudly_without_gpu():
     import paper_2007_03847_gb300 as fmc
     with pytest.raises(fmc.FastMCError):
         fmc.Context(0)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of fmc_scenario and fmc_result have the C layout (gcc
+    compiles a probe of the header's sizeof/offsetof; no GPU needed)."""
+    import shutil
+    import subprocess
+
+    import paper_2007_03847_gb300 as fmc
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    hdr = os.path.join(ROOT, "include")
+    fields_s = [f for f, _ in fmc._Scenario._fields_]
+    fields_r = [f for f, _ in fmc._Result._fields_]
+    fields_i = [f for f, _ in fmc._Ito._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "fastmc.h"', 'int main(void) {',
+           'printf("%zu %zu\\n", sizeof(fmc_scenario), sizeof(fmc_result));']
+    src += [f'printf("s {f} %zu\\n", offsetof(fmc_scenario, {f}));' for f in fields_s]
+    src += [f'printf("r {f} %zu\\n", offsetof(fmc_result, {f}));' for f in fields_r]
+    src += [f'printf("i {f} %zu\\n", offsetof(fmc_ito, {f}));' for f in fields_i]
+    src += ['printf("i_size %zu 0\\n", sizeof(fmc_ito));']
+    src += ["return 0; }"]
+    c = tmp_path / "probe.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", hdr, str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    size_s, size_r = map(int, out[0].split())
+    assert size_s == ctypes.sizeof(fmc._Scenario)
+    assert size_r == ctypes.sizeof(fmc._Result)
+    for line in out[1:]:
+        if not line:
+            continue
+        kind, name, off = line.split()
+        if kind == "i_size":
+            assert int(name) == ctypes.sizeof(fmc._Ito)
+            continue
+        cls = {"s": fmc._Scenario, "r": fmc._Result, "i": fmc._Ito}[kind]
+        assert getattr(cls, name).offset == int(off), (kind, name)

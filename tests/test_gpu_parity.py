@@ -95,9 +95,10 @@ def test_lhs_split_layout(fmc, orc):
 
 
 @pytest.mark.parametrize("K,T,Nt", [(1, 1.0, 7), (100, 10.0, 1000), (200, 20.0, 4000), (37, 3.3, 333)])
-def test_kl_basis(fmc, orc, K, T, Nt):
-    phi = fmc.kl_basis(K, T, Nt).cpu().numpy()
-    ref = orc.kl_increment_basis(K, T, Nt)
+@pytest.mark.parametrize("basis", [0, 1])
+def test_kl_basis(fmc, orc, K, T, Nt, basis):
+    phi = fmc.kl_basis(K, T, Nt, basis).cpu().numpy()
+    ref = orc.kl_increment_basis(K, T, Nt, basis)
     assert np.max(np.abs(phi - ref)) <= 2 * np.spacing(np.float32(np.max(np.abs(ref))))
 
 
@@ -154,18 +155,20 @@ def _check_moments(m, v, rm, rv, n, tol=1e-5):
 def _small_cases():
     return {
         "smib": fs.smib_case(N=300, K=100, T=2.0, dt=0.01),
+        "mm7_cosine": fs.multimachine_case(n=7, d=2, K=30, T=0.5, dt=0.005, N=150, seed=4).replace(
+            basis=fs.BASIS_COSINE),
         "mm10": fs.multimachine_case(n=10, d=3, K=40, T=1.0, dt=0.005, N=200, seed=1),
         "mm5_ragged": fs.multimachine_case(n=5, d=2, K=23, T=0.333, dt=0.003, N=131, seed=2),
         "mm16_d8": fs.multimachine_case(n=16, d=8, K=16, T=0.2, dt=0.005, N=129, seed=3),
     }
 
 
-@pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8"])
+@pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8", "mm7_cosine"])
 def test_simulate_trajectories_and_moments_plain(fmc, orc, case):
     _trajectories_and_moments(fmc, orc, "plain", "f32", case)
 
 
-@pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8"])
+@pytest.mark.parametrize("case", ["smib", "mm10", "mm5_ragged", "mm16_d8", "mm7_cosine"])
 def test_simulate_trajectories_and_moments_fused(fmc, orc, kernel, case):
     _trajectories_and_moments(fmc, orc, "fused", "bf16x3", case)
 
@@ -191,14 +194,15 @@ def test_simulate_bf16_error_is_stated(fmc, orc, kernel):
     assert ed <= 2e-2 and ew <= 2e-2, (ed, ew)
 
 
-@pytest.mark.parametrize("tiles_per_sm", [1, 2, 3])
+@pytest.mark.parametrize("tiles_per_sm", [1, 2, 3, 3.5])
 @pytest.mark.parametrize("d", [1, 3, 6])
 def test_chunk_length_follows_the_tiles(fmc, orc, tiles_per_sm, d):
     # The time chunk grows when few CTAs share an SM (one, two, or four per SM
     # give 512, 256 or 128 TMEM columns per CTA): sample counts just under each
-    # boundary, a horizon that is not a multiple of any chunk length.
+    # boundary, a horizon that is not a multiple of any chunk length; 3.5 tiles
+    # per SM leaves the SMs unevenly loaded (four CTAs on some, three on others).
     sms, _ = fmc.default_context().info()
-    N = 128 * sms * tiles_per_sm - 37
+    N = int(128 * sms * tiles_per_sm) - 37
     sc = fs.multimachine_case(n=4, d=d, K=24, T=0.305, dt=0.005, N=N, seed=40 + d)
     mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
     fmc.device_status()
@@ -339,3 +343,37 @@ def test_batch_moments_match_oracle(fmc, orc):
         ref = orc.simulate(sc, zr, nthreads=8)
         _check_moments(m.cpu().numpy(), v.cpu().numpy(), ref["mean"], ref["var"], sc.n)
     b.close()
+
+
+# ----------------------------------------------------------------------------- the traditional Monte Carlo
+
+
+@pytest.mark.parametrize("case", ["mm10", "mm16_d8", "smib"])
+def test_srs_em_trajectories_and_moments(fmc, orc, kernel, case):
+    # the paper's comparator (Section V-B): per-step normals drawn inside the
+    # kernels from the same Philox counters as the oracle's
+    sc = _small_cases()[case].replace(sampling=fs.SRS_EM)
+    ref = orc.simulate_em(sc, want_traj=True, nthreads=8)
+    for path, precision in (("fused", "bf16x3"), ("plain", "f32")):
+        if path == "plain" and kernel == "split":
+            continue
+        mean, var, traj = fmc.simulate(sc, path=path, precision=precision, want_traj=True)
+        fmc.device_status()
+        ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+        assert ed <= 1e-4 and ew <= 1e-4, (path, ed, ew)
+        _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_srs_em_sample_blocks(fmc, orc):
+    # blocks of the design through the sums entry point draw the increments of
+    # their own design indices
+    sc = _small_cases()["mm10"].replace(sampling=fs.SRS_EM)
+    ref = orc.simulate_em(sc, nthreads=8)
+    a1, a2, shift = fmc.simulate_sums(sc, 0, 77)
+    b1, b2, _ = fmc.simulate_sums(sc, 77, sc.N - 77)
+    S1 = (a1 + b1).cpu().numpy()
+    S2 = (a2 + b2).cpu().numpy()
+    N = sc.N
+    mean = shift.cpu().numpy()[None, :] + S1 / N
+    var = (S2 - S1 * S1 / N) / (N - 1)
+    _check_moments(mean, var, ref["mean"], ref["var"], sc.n)
