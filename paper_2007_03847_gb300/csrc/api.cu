@@ -386,10 +386,9 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
 {
     const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
     const int dx = d + (s->event_machine >= 0 ? 1 : 0);
-    out.assign(wide_const_floats(n, nmt, dx), 0.f);
-    float* GE = out.data();
-    float* BE = GE + n * 4 * nmtp;
-    float* pm = BE + n * 4 * nmtp;
+    out.assign(wide_const_floats(n, nmt, nd_bucket_for(dx)), 0.f);
+    float* GB = out.data();  // [j][h][GE row | BE row], nmtp each
+    float* pm = GB + 2 * n * 4 * nmtp;
     const bool rel = !s->has_inf_bus;
     std::vector<double> c(n), sn(n);
     for (int j = 0; j < n; ++j) {
@@ -404,8 +403,8 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
             if (j == i) continue;
             double ge = s->E[i] * s->E[j] * s->G[i * n + j];
             double be = s->E[i] * s->E[j] * s->B[i * n + j];
-            GE[(j * 4 + h) * nmtp + k] = (float)ge;
-            BE[(j * 4 + h) * nmtp + k] = (float)-be;  // stored negated (see the kernel's network sum)
+            GB[(j * 4 + h) * 2 * nmtp + k] = (float)ge;
+            GB[(j * 4 + h) * 2 * nmtp + nmtp + k] = (float)(wide_packed(nmt) ? -be : be);  // see the kernel's network sum
             u += ge * c[j] - be * sn[j];
             v += ge * sn[j] + be * c[j];
         }

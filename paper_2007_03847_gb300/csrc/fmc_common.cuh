@@ -80,54 +80,92 @@ __device__ __forceinline__ float em_normal(uint32_t k, int w, int n, uint32_t k0
 }
 
 // Sum and squared deviations from their mean of the first na of 32 values
-// column[rr * stride] (the rest hold 0): two passes, the second around the
-// pass-one mean, so that M2 keeps FP32 accuracy relative to the spread however
-// far the values sit from zero.  Four interleaved partials per pass.
+// column[rr * stride] (the rest are ignored), in one pass over shared memory:
+// the sums of x_r - x_0 and of its square, x_0 the column's first value.  x_0 is
+// itself one of the values, so both sums are on the scale of the spread, and
+//   M2 = sum (x_r - x_0)^2 - (sum (x_r - x_0))^2 / na
+// cancels no more than the spread's own scale allows however far the values sit
+// from zero (the textbook shifted-data form of the sample variance).  Four
+// interleaved partials per sum.
 __device__ __forceinline__ void column_sum_m2(const float* column, int stride, int na, float* sum, float* m2)
 {
+    const float x0 = column[0];
     float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
+    float qa = 0.f, qb = 0.f, qc = 0.f, qe = 0.f;
+    if (na == 32) {
 #pragma unroll
-    for (int rr = 0; rr < 32; rr += 4) {
-        a += column[rr * stride];
-        b += column[(rr + 1) * stride];
-        c += column[(rr + 2) * stride];
-        e += column[(rr + 3) * stride];
-    }
-    const float s = (a + b) + (c + e);
-    const float mu = na > 0 ? s / (float)na : 0.f;
-    a = b = c = e = 0.f;
+        for (int rr = 0; rr < 32; rr += 4) {
+            const float d0 = column[rr * stride] - x0;
+            const float d1 = column[(rr + 1) * stride] - x0;
+            const float d2 = column[(rr + 2) * stride] - x0;
+            const float d3 = column[(rr + 3) * stride] - x0;
+            a += d0;
+            b += d1;
+            c += d2;
+            e += d3;
+            qa = fmaf(d0, d0, qa);
+            qb = fmaf(d1, d1, qb);
+            qc = fmaf(d2, d2, qc);
+            qe = fmaf(d3, d3, qe);
+        }
+    } else {
 #pragma unroll
-    for (int rr = 0; rr < 32; rr += 4) {
-        const float d0 = rr < na ? column[rr * stride] - mu : 0.f;
-        const float d1 = rr + 1 < na ? column[(rr + 1) * stride] - mu : 0.f;
-        const float d2 = rr + 2 < na ? column[(rr + 2) * stride] - mu : 0.f;
-        const float d3 = rr + 3 < na ? column[(rr + 3) * stride] - mu : 0.f;
-        a = fmaf(d0, d0, a);
-        b = fmaf(d1, d1, b);
-        c = fmaf(d2, d2, c);
-        e = fmaf(d3, d3, e);
+        for (int rr = 0; rr < 32; rr += 4) {
+            const float d0 = rr < na ? column[rr * stride] - x0 : 0.f;
+            const float d1 = rr + 1 < na ? column[(rr + 1) * stride] - x0 : 0.f;
+            const float d2 = rr + 2 < na ? column[(rr + 2) * stride] - x0 : 0.f;
+            const float d3 = rr + 3 < na ? column[(rr + 3) * stride] - x0 : 0.f;
+            a += d0;
+            b += d1;
+            c += d2;
+            e += d3;
+            qa = fmaf(d0, d0, qa);
+            qb = fmaf(d1, d1, qb);
+            qc = fmaf(d2, d2, qc);
+            qe = fmaf(d3, d3, qe);
+        }
     }
-    *sum = s;
-    *m2 = (a + b) + (c + e);
+    const float sd = (a + b) + (c + e);
+    const float sq = (qa + qb) + (qc + qe);
+    if (na > 0) {
+        *sum = fmaf((float)na, x0, sd);
+        *m2 = fmaxf(sq - sd * (sd / (float)na), 0.f);
+    } else {
+        *sum = 0.f;
+        *m2 = 0.f;
+    }
 }
 
-// Parallel-variance combine (Chan, Golub and LeVeque) of up to four groups of
-// na[g] values with sums s[g] and squared deviations m2[g] (strided by `stride`):
-// the combined squared deviation from the combined mean, in a fixed order.
-__device__ __forceinline__ float combine_m2(const float* s, const float* m2, int stride, const int* na, int groups)
+// Samples in group g of 32 when `left` samples remain from group 0 on.
+__device__ __forceinline__ int group_count(int64_t left, int g)
+{
+    const int64_t r = left - 32 * (int64_t)g;
+    return r <= 0 ? 0 : (r >= 32 ? 32 : (int)r);
+}
+
+// Parallel-variance combine (Chan, Golub and LeVeque) of `groups` (<= 4) groups
+// of 32 samples, `left` samples remaining from group 0 on, with sums s[g] and
+// squared deviations m2[g] (strided by `stride`): the combined squared deviation
+// from the combined mean, in a fixed order.
+__device__ __forceinline__ float combine_m2(const float* s, const float* m2, int stride, int64_t left, int groups)
 {
     float st = 0.f;
     int nt = 0;
-    for (int g = 0; g < groups; ++g) {
-        st += s[g * stride];
-        nt += na[g];
-    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        if (g < groups) {
+            st += s[g * stride];
+            nt += group_count(left, g);
+        }
     const float mu = nt > 0 ? st / (float)nt : 0.f;
     float acc = 0.f;
-    for (int g = 0; g < groups; ++g) {
-        if (na[g] == 0) continue;
-        const float dg = s[g * stride] / (float)na[g] - mu;
-        acc += m2[g * stride] + (float)na[g] * dg * dg;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int ng = group_count(left, g);
+        if (g < groups && ng > 0) {
+            const float dg = s[g * stride] / (float)ng - mu;
+            acc += m2[g * stride] + (float)ng * dg * dg;
+        }
     }
     return acc;
 }

@@ -91,15 +91,26 @@ struct WideArgs {
 
 __host__ __device__ constexpr int wide_nmtp(int nmt) { return (nmt + 3) & ~3; }
 
+#ifndef FMC_PACKED_FP32
+#define FMC_PACKED_FP32 1
+#endif
+
+// Whether the wide kernel of nmt machine slots sums the network in packed FP32
+// (where it measured faster: 7 and 10 slots; the odd pair of 5 and 13 slots and
+// the second pass of 13 cost more than they save).
+__host__ __device__ constexpr bool wide_packed(int nmt) { return FMC_PACKED_FP32 && (nmt == 7 || nmt == 10); }
+
 // Constant block of the wide kernel (floats):
-//   GE [n][4][NMTP], NBE [n][4][NMTP]: entry (j, h, k) = E_i E_j G_ij (resp. -E_i E_j B_ij)
-//     for machine i = h + 4k, zero on the diagonal and for padded i;
+//   [n][4][2][NMTP]: for (j, h) the row GE (k) = E_i E_j G_ij, then the row BE (k) =
+//     E_i E_j B_ij (stored negated when wide_packed), machine i = h + 4k, zero on the
+//     diagonal and for padded i;
 //   then eight rows of 4 NMT per machine: cos D*, sin D*, u*, v*, delta*, 1/(2H), D,
 //   H / sum H (centre-of-inertia weight);
-//   then the injection map, dx rows of 4 NMT (the event slot's row last).
-__host__ __device__ inline int wide_const_floats(int n, int nmt, int dx)
+//   then the injection map, nd rows of 4 NMT (nd: the kernel's disturbance-slot
+//   bucket; the event slot's row at index d, the rows past the slots in use zero).
+__host__ __device__ inline int wide_const_floats(int n, int nmt, int nd)
 {
-    return 2 * n * 4 * wide_nmtp(nmt) + (8 + dx) * 4 * nmt;
+    return 2 * n * 4 * wide_nmtp(nmt) + (8 + nd) * 4 * nmt;
 }
 
 int wide_nmt_for(int n);

@@ -124,13 +124,16 @@ __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const f
     if (q < total) {
         const float* p = part + q;
         const bool second = (q % row) >= S;  // squared deviations: add the block's s1^2 / n
+        // 1 / n_b: every block holds `rows` samples but the last (FP64 division
+        // is slow; one per thread for the full blocks, one for the last)
+        const double inv_rows = 1.0 / (double)rows;
+        const int64_t last_n = count - (int64_t)(nblk - 1) * rows;
+        const double inv_last = 1.0 / (double)(last_n > 0 ? last_n : 1);
         auto term = [&](int b) {
             double t = (double)p[(int64_t)b * total];
             if (second) {
                 const double s1 = (double)p[(int64_t)b * total - S];
-                const int64_t left = count - (int64_t)b * rows;
-                const double nb = (double)(left < rows ? left : rows);
-                t += s1 * s1 / nb;
+                t = fma(s1 * s1, b == nblk - 1 ? inv_last : inv_rows, t);
             }
             return t;
         };

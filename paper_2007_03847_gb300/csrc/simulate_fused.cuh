@@ -9,9 +9,11 @@
 //   for each time chunk of TC steps:
 //     tensor cores:  dW[128 x TC] per disturbance = Z_tile . Phi_chunk^T into TMEM
 //                    (BF16 or split BF16x3 operands streamed by TMA, FP32 accumulate)
-//     FP32 pipes:    thread r (= sample r of the tile, = TMEM lane r) reads its
-//                    increments with tcgen05.ld, advances the OU disturbances by
-//                    Euler-Maruyama and the swing equations by RK4/Heun, step by step
+//     disturbances:  thread r (= sample r of the tile, = TMEM lane r) turns its
+//                    increments into the chunk's disturbance paths by Euler-Maruyama,
+//                    in place in TMEM (tcgen05.ld / tcgen05.st, see disturb_chunk.cuh)
+//     FP32 pipes:    it reads x(t_{n+1}) with tcgen05.ld and advances the swing
+//                    equations by RK4/Heun, step by step
 //     moments:       per step, each warp transposes its 32 samples' shifted states
 //                    through shared memory and sums them (S1, S2) per state; the
 //                    four warps' sums are added in a fixed order and written as
@@ -25,6 +27,7 @@
 #include "kernels.cuh"
 #include "swing.cuh"
 #include "tc_common.cuh"
+#include "disturb_chunk.cuh"
 
 namespace fmc {
 
@@ -166,22 +169,27 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         tc_fence_after();
         }
 
-        // ---- FP32 pipes: integrate this chunk ----
+        // ---- disturbance paths of this chunk into TMEM (each warp its own lanes) ----
         const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
+        disturbance_chunk<ND, ND>(lane_addr, TC, steps, n0, d, -1, x0, p.ou_a, p.ou_s, p.ito, p.dt, a.em,
+                                  (uint32_t)(a.em.k0 + srow));
+
+        // ---- FP32 pipes: integrate this chunk ----
         for (int s = 0; s < steps; ++s) {
-            float dw[ND], x1[ND];
+            float x1[ND];
 #pragma unroll
-            for (int q = 0; q < ND; ++q) dw[q] = 0.f;
-            if (em) {
-                em_increments<ND>(a.em, (uint32_t)(a.em.k0 + srow), n0 + s, d, dw);
-            } else {
+            for (int q = 0; q < ND; ++q) x1[q] = 0.f;
 #pragma unroll
-                for (int q = 0; q < ND; ++q)
-                    if (q < d) dw[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
-                tmem_ld_wait();
-            }
-            event_state<NM, ND>(p, n0 + s, x0);
-            ou_step<NM, ND>(p, x0, dw, x1);
+            for (int q = 0; q < ND; ++q)
+                if (q < d) x1[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
+            tmem_ld_wait();
+            // the event slot: 0 before the event's grid step, 1 from it
+#pragma unroll
+            for (int q = 0; q < ND; ++q)
+                if (q == p.ev_slot) {
+                    x0[q] = (n0 + s >= p.ev_step) ? 1.f : 0.f;
+                    x1[q] = x0[q];
+                }
             swing_step<NM, ND>(p, del, w, theta, x0, x1);
             if (a.rrf) {
                 const float cs = coi_speed<NM, ND>(p, w);
@@ -224,14 +232,9 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                 asm volatile("bar.sync 1, %0;" ::"r"(rows) : "memory");
                 const int nst = ms + 1;
                 const int tn0 = tn - ms;
-                // samples of this tile in each warp (the last tile may be partly empty)
-                int na_tile[4], n_tile = 0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const int64_t left = a.count - row0 - 32 * g;
-                    na_tile[g] = g < warps ? (left <= 0 ? 0 : (left >= 32 ? 32 : (int)left)) : 0;
-                    n_tile += na_tile[g];
-                }
+                // samples of this tile (the last tile may be partly empty)
+                const int64_t left = a.count - row0;
+                const int n_tile = left <= 0 ? 0 : (left >= rows ? rows : (int)left);
                 for (int e = tid; e < nst * S4; e += rows) {
                     const int sl = e / S4, v = e - sl * S4;
                     const int j = v < S ? v : v - S;  // state
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                     // tile sum; for the second half the tile's squared deviations (parallel combine)
                     const float t1 =
                         warps == 4 ? ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM] : m[0] + m[4 * NM];
-                    const float acc = v < S ? t1 : combine_m2(m, m + S, 4 * NM, na_tile, warps);
+                    const float acc = v < S ? t1 : combine_m2(m, m + S, 4 * NM, left, warps);
                     if (part_tile) {
                         part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
                     } else {

@@ -6,8 +6,9 @@
 // TMEM lanes it may read (subpartition q), so four warps share every sample and
 // each thread holds a quarter of its sample's state.  The KL contraction into
 // TMEM is the fused kernel's (one thread issues TMA loads and tcgen05.mma per
-// time chunk); all four warps of a sample group read the same increments and
-// advance the OU disturbances redundantly.
+// time chunk); the four warps of a sample group then turn the increments into
+// the chunk's disturbance paths in place in TMEM (warp h the disturbances
+// w = h mod 4), and all four read every path.
 //
 // Per RK stage every thread publishes, for its machines, the deviations
 //   gamma_i = cos(D*_i + Delta_i) - cos D*_i,  eta_i = sin(D*_i + Delta_i) - sin D*_i
@@ -24,6 +25,7 @@
 #include "kernels.cuh"
 #include "swing.cuh"
 #include "tc_common.cuh"
+#include "disturb_chunk.cuh"
 
 namespace fmc {
 
@@ -55,10 +57,10 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 {
     constexpr int NMTP = wide_nmtp(NMT);
     constexpr int KP = NMT > 10 ? 8 : NMT;  // machine slots per pass over the network sum
-    constexpr int JU = NMT > 7 ? 1 : 2;      // unrolling of the loop over j (registers permitting)
-    // packed FP32 where it measured faster (7 and 10 slots; the odd pair of 5
-    // and 13 slots and the second pass of 13 cost more than it saves)
-    constexpr bool PACK = FMC_PACKED_FP32 && (NMT == 7 || NMT == 10);
+    constexpr int JU = NMT > 5 ? 2 : 4;  // unrolling of the loop over j (measured; registers)
+    // every pass starts its 16-byte loads of the matrix rows at slot k0, a multiple of KP
+    static_assert(KP >= NMT || KP % 4 == 0, "network passes must start on 16-byte boundaries");
+    constexpr bool PACK = wide_packed(NMT);  // the BE rows hold -BE when packed, BE otherwise
     constexpr int G4 = 4 * NMT;
     constexpr int WROW = 2 * NMT + 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -97,12 +99,13 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     float* msum = reinterpret_cast<float*>(smem) + 16 * 32 * WROW;     // [WI_MS][q][h][4 NMT]
     float2* gh = reinterpret_cast<float2*>(smem + u_bytes);            // [2][n][128]
     float* w0buf = reinterpret_cast<float*>(gh + 2 * n * 128);         // [2][128]
-    float* cst_s = w0buf + 256;
+    float* racc_s = w0buf + 256;                                        // [128] (warps h = 0)
+    float* cst_s = w0buf + 384;
     const int dx = a.dx;
-    const int nconst = wide_const_floats(n, NMT, dx);
+    const int nconst = wide_const_floats(n, NMT, ND);
     for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[e];
-    const float* GEs = cst_s;
-    const float* BEs = cst_s + n * 4 * NMTP;
+    // [j][h][GE row of NMTP | BE row of NMTP]: one address serves both rows
+    const float* GB = cst_s;
     const float* pm = cst_s + 2 * n * 4 * NMTP;
     const float* c_cst = pm;
     const float* c_sst = pm + G4;
@@ -176,7 +179,10 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const int nst = rk4 ? 4 : 2;
     const float ref = a.rel ? 1.f : 0.f;
     const float hh = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
-    float racc = 0.f;  // (warps h = 0) sum over the grid of the squared centre-of-inertia speed
+    // (warps h = 0) sum over the grid of the squared centre-of-inertia speed, kept
+    // in shared memory: it is touched only at the flushes, and a register held
+    // across the step loop costs the network sums more than the round trips
+    if (h == 0) racc_s[r] = 0.f;
 
     for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
@@ -214,30 +220,36 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
         tc_fence_after();
         }
 
-        // ---- FP32 pipes: integrate this chunk ----
+        // ---- disturbance paths of this chunk into TMEM ----
+        // the four warps of a sample group share its lanes: warp h forms the
+        // disturbances w = h mod 4, then all of them read all of them
         const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
+        if (em) {  // (with the contraction, the barrier above already separates the chunks)
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+        disturbance_chunk<ND, 8>(lane_addr, TC, steps, n0, d, h, x0, a.ou_a, a.ou_s, a.ito, dt, a.em,
+                                 (uint32_t)(a.em.k0 + srow));
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+
+        // ---- FP32 pipes: integrate this chunk ----
         for (int s = 0; s < steps; ++s) {
-            float dw[ND], x1[ND];
+            float x1[ND];
 #pragma unroll
-            for (int e = 0; e < ND; ++e) dw[e] = 0.f;
-            if (em) {
-                em_increments<ND>(a.em, (uint32_t)(a.em.k0 + srow), n0 + s, d, dw);
-            } else {
+            for (int e = 0; e < ND; ++e) x1[e] = 0.f;
 #pragma unroll
-                for (int e = 0; e < ND; ++e)
-                    if (e < d) dw[e] = tmem_ld1(lane_addr + (uint32_t)(e * TC + s));
-                tmem_ld_wait();
-            }
+            for (int e = 0; e < ND; ++e)
+                if (e < d) x1[e] = tmem_ld1(lane_addr + (uint32_t)(e * TC + s));
+            tmem_ld_wait();
 #pragma unroll
             for (int e = 0; e < ND; ++e)  // the event slot (index d) is 0 before the event, 1 from it
-                if (e == d && dx > d) x0[e] = (n0 + s >= a.ev_step) ? 1.f : 0.f;
-            if (a.ito.on) {
-#pragma unroll
-                for (int e = 0; e < ND; ++e) x1[e] = ito_step1<8>(a.ito, e, a.ou_a[e], a.ou_s[e], x0[e], dw[e], dt);
-            } else {
-#pragma unroll
-                for (int e = 0; e < ND; ++e) x1[e] = fmaf(a.ou_a[e], x0[e], a.ou_s[e] * dw[e]);
-            }
+                if (e == d && dx > d) {
+                    x0[e] = (n0 + s >= a.ev_step) ? 1.f : 0.f;
+                    x1[e] = x0[e];
+                }
 
             float ad[NMT], aw[NMT], yw[NMT];
             float ath = 0.f;
@@ -290,8 +302,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                             const float2 gej = ghc[j * 128];
                             const unsigned long long gg2 = f2pack(gej.x, gej.x), ee2 = f2pack(gej.y, gej.y);
                             const unsigned long long ng2 = f2pack(-gej.x, -gej.x);
-                            const ulonglong2* g4 = reinterpret_cast<const ulonglong2*>(GEs + (j * 4 + h) * NMTP + k0);
-                            const ulonglong2* b4 = reinterpret_cast<const ulonglong2*>(BEs + (j * 4 + h) * NMTP + k0);
+                            const ulonglong2* g4 = reinterpret_cast<const ulonglong2*>(GB + (j * 4 + h) * 2 * NMTP + k0);
+                            const ulonglong2* b4 = g4 + NMTP / 4;
 #pragma unroll
                             for (int k4 = 0; k4 < (KP + 3) / 4; ++k4) {
                                 if (k0 + 4 * k4 < NMT) {
@@ -324,8 +336,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 #pragma unroll JU
                     for (int j = 0; j < n; ++j) {
                         const float2 gej = ghc[j * 128];
-                        const float4* g4 = reinterpret_cast<const float4*>(GEs + (j * 4 + h) * NMTP + k0);
-                        const float4* b4 = reinterpret_cast<const float4*>(BEs + (j * 4 + h) * NMTP + k0);
+                        const float4* g4 = reinterpret_cast<const float4*>(GB + (j * 4 + h) * 2 * NMTP + k0);
+                        const float4* b4 = g4 + NMTP / 4;
 #pragma unroll
                         for (int k4 = 0; k4 < (KP + 3) / 4; ++k4) {
                             if (k0 + 4 * k4 < NMT) {
@@ -337,9 +349,9 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                                     const int k = 4 * k4 + kk;
                                     if (k < KP && k0 + k < NMT) {
                                         du[k] = fmaf(gg[kk], gej.x, du[k]);
-                                        du[k] = fmaf(bb[kk], gej.y, du[k]);
+                                        du[k] = fmaf(-bb[kk], gej.y, du[k]);
                                         dv[k] = fmaf(gg[kk], gej.y, dv[k]);
-                                        dv[k] = fmaf(bb[kk], -gej.x, dv[k]);
+                                        dv[k] = fmaf(bb[kk], gej.x, dv[k]);
                                     }
                                 }
                             }
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                             float f = 0.f;
 #pragma unroll
                             for (int e = 0; e < ND; ++e)
-                                if (e < dx) f = fmaf(c_inj[e * G4 + i], xs[e], f);
+                                f = fmaf(c_inj[e * G4 + i], xs[e], f);  // rows past the slots in use are zero
                             const float kd = a.omega_s * (yw[k] - w0);
                             const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
                             ad[k] = fmaf(b, kd, ad[k]);
@@ -443,19 +455,14 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                     for (int sl = 0; sl <= ms; ++sl) {
                         const float* cq = coi_part + sl * 4 * 128 + r;
                         const float c = ((cq[0] + cq[128]) + cq[256]) + cq[384];
-                        racc = fmaf(c, c, racc);
+                        racc_s[r] = fmaf(c, c, racc_s[r]);
                     }
                 }
                 const int nsl = ms + 1;
                 const int tn0 = tn - ms;
-                // samples of this tile in each sample group (the last tile may be partly empty)
-                int na_g[4], n_tile = 0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const int64_t left = a.count - row0 - 32 * g;
-                    na_g[g] = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
-                    n_tile += na_g[g];
-                }
+                // samples of this tile (the last tile may be partly empty)
+                const int64_t left = a.count - row0;
+                const int n_tile = left <= 0 ? 0 : (left >= 128 ? 128 : (int)left);
                 for (int e = tid; e < nsl * S4; e += WI_THREADS) {
                     const int sl = e / S4, v = e - sl * S4;
                     // v = kind * 2n + state; state < n is delta_i, else omega_(state - n)
@@ -466,7 +473,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                     const float* m = msum + (sl * 16 + (i & 3)) * G4 + isw * NMT + (i >> 2);
                     // tile sum; for kind 1 the tile's squared deviations (parallel combine)
                     const float t1 = ((m[0] + m[4 * G4]) + m[8 * G4]) + m[12 * G4];
-                    const float acc = kind == 0 ? t1 : combine_m2(m, m + 2 * NMT, 4 * G4, na_g, 4);
+                    const float acc = kind == 0 ? t1 : combine_m2(m, m + 2 * NMT, 4 * G4, left, 4);
                     if (part_tile) {
                         part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
                     } else {
@@ -482,20 +489,20 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             }
         }
     }
-    if (a.rrf && h == 0) rrf_accumulate(active ? sqrtf(racc / (float)a.Nt) : 0.f, a.rrf);
+    if (a.rrf && h == 0) rrf_accumulate(active ? sqrtf(racc_s[r] / (float)a.Nt) : 0.f, a.rrf);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
 // Dynamic shared memory of the kernel (bytes), alignment slack included.
-template <int NMT>
-inline int wide_smem_bytes(int TC, int split, int n, int dx, int ns)
+template <int NMT, int ND>
+inline int wide_smem_bytes(int TC, int split, int n, int ns)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
     const int mom = wide_mom_floats<NMT>() * 4;
     const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
-    return 1024 + u + 2 * n * 128 * 8 + 256 * 4 + wide_const_floats(n, NMT, dx) * 4;
+    return 1024 + u + 2 * n * 128 * 8 + 384 * 4 + wide_const_floats(n, NMT, ND) * 4;
 }
 
 template <int NMT, int ND>
@@ -505,9 +512,9 @@ cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStr
     // as many ring stages as the shared memory left by the other buffers holds
     WideArgs a = args;
     a.ns = 2;
-    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.dx, a.ns + 1) <= TC_SMEM_DYN_MAX)
+    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT, ND>(a.TC, a.split, a.n, a.ns + 1) <= TC_SMEM_DYN_MAX)
         ++a.ns;
-    const int smem = wide_smem_bytes<NMT>(a.TC, a.split, a.n, a.dx, a.ns);
+    const int smem = wide_smem_bytes<NMT, ND>(a.TC, a.split, a.n, a.ns);
     if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size

@@ -23,9 +23,6 @@
 #include "fmc_common.cuh"
 #include "kernels.cuh"
 
-#ifndef FMC_PACKED_FP32
-#define FMC_PACKED_FP32 1
-#endif
 
 namespace fmc {
 
@@ -289,24 +286,6 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
         w[i] = fmaf(h, aw[i], w[i]);
     }
     theta = fmaf(h, ath, theta);
-}
-
-// Increments of the per-step-normal Monte Carlo for one sample and step:
-// dw[w] = sqrt(dt) em_normal(k, w, n), one Philox call per four disturbances.
-template <int ND>
-__device__ __forceinline__ void em_increments(const EmSpec& em, uint32_t k, int n, int d, float (&dw)[ND])
-{
-#pragma unroll
-    for (int g = 0; g < (ND + 3) / 4; ++g) {
-        if (4 * g < d) {
-            const U4 o = philox4x32_10(U4{k, (uint32_t)n, EM_TAG, (uint32_t)g}, em.key0, em.key1);
-            const uint32_t r[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (4 * g + e < ND && 4 * g + e < d)
-                    dw[4 * g + e] = em.sqdt * normal_from_fraction(2ull * r[e] + 1ull, 1u);
-        }
-    }
 }
 
 // One step of a general disturbance (see ItoParams) in the deviation y.
