@@ -21,11 +21,9 @@ namespace fmc {
 // multiple of 8, so the rounding stays inside the disturbance's columns).
 // Warp-collective.  em.on: the increments are drawn here (sqrt(dt) times the
 // normal of (sample k, w, step), em_normal); otherwise they are read from TMEM.
-// Not inlined: the integrator's registers stay allocated for the step loop, and
-// the few values live across the call are saved once per chunk.
 template <int NDI>
-__device__ __noinline__ void disturbance_path(uint32_t col, int steps, int n0, int q, float x, float a, float sg,
-                                              const ItoParams<NDI>& it, float dt, const EmSpec& em, uint32_t k)
+__device__ __forceinline__ void disturbance_path_body(uint32_t col, int steps, int n0, int q, float x, float a, float sg,
+                                                   const ItoParams<NDI>& it, float dt, const EmSpec& em, uint32_t k)
 {
 #pragma unroll 1
     for (int s0 = 0; s0 < steps; s0 += 8) {
@@ -54,12 +52,22 @@ __device__ __noinline__ void disturbance_path(uint32_t col, int steps, int n0, i
     }
 }
 
+// The same, not inlined: the caller's registers stay allocated for its step
+// loop and the few values live across the call are saved once per chunk (the
+// large-system kernel, whose step loop needs every register).
+template <int NDI>
+__device__ __noinline__ void disturbance_path_call(uint32_t col, int steps, int n0, int q, float x, float a, float sg,
+                                                   const ItoParams<NDI>& it, float dt, const EmSpec& em, uint32_t k)
+{
+    disturbance_path_body<NDI>(col, steps, n0, q, x, a, sg, it, dt, em, k);
+}
+
 // The chunk (grid steps n0 .. n0 + steps - 1, TC columns per disturbance) for
 // the disturbances w < d with sel < 0 or w mod 4 == sel (warp-uniform), one at
 // a time; x0[w]: every disturbance at grid index n0.  Ends with the stores
 // complete (tcgen05.wait::st); readers in other warps still need a thread
 // barrier between tcgen05 fences.
-template <int ND, int NDI>
+template <int ND, int NDI, bool INLINE>
 __device__ __forceinline__ void disturbance_chunk(uint32_t lane_addr, int TC, int steps, int n0, int d, int sel,
                                                   const float (&x0)[ND], const float* ou_a, const float* ou_s,
                                                   const ItoParams<NDI>& it, float dt, const EmSpec& em, uint32_t k)
@@ -71,7 +79,11 @@ __device__ __forceinline__ void disturbance_chunk(uint32_t lane_addr, int TC, in
 #pragma unroll
         for (int qq = 0; qq < ND; ++qq)
             if (qq == q) x = x0[qq];
-        disturbance_path<NDI>(lane_addr + (uint32_t)(q * TC), steps, n0, q, x, ou_a[q], ou_s[q], it, dt, em, k);
+        const uint32_t col = lane_addr + (uint32_t)(q * TC);
+        if constexpr (INLINE)
+            disturbance_path_body<NDI>(col, steps, n0, q, x, ou_a[q], ou_s[q], it, dt, em, k);
+        else
+            disturbance_path_call<NDI>(col, steps, n0, q, x, ou_a[q], ou_s[q], it, dt, em, k);
     }
     tmem_st_wait();
 }

@@ -79,6 +79,27 @@ __device__ __forceinline__ float em_normal(uint32_t k, int w, int n, uint32_t k0
     return normal_from_fraction(2ull * r + 1ull, 1u);
 }
 
+// Packed FP32 (two lanes per register pair) fused multiply-add of sm_100+:
+// d = a * b + c elementwise on (x, y) pairs.
+__device__ __forceinline__ unsigned long long f2pack(float x, float y)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+
+__device__ __forceinline__ void f2unpack(unsigned long long r, float& x, float& y)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Sum and squared deviations from their mean of the first na of 32 values
 // column[rr * stride] (the rest are ignored), in one pass over shared memory:
 // the sums of x_r - x_0 and of its square, x_0 the column's first value.  x_0 is
@@ -93,23 +114,26 @@ __device__ __forceinline__ void column_sum_m2(const float* column, int stride, i
     float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
     float qa = 0.f, qb = 0.f, qc = 0.f, qe = 0.f;
     if (na == 32) {
+        // packed FP32, rows (r, r + 1) in one register pair: d = x * 1 - x0 (exact
+        // product, so the same rounding as the subtraction), then the two sums
+        const unsigned long long one = f2pack(1.f, 1.f), nx0 = f2pack(-x0, -x0);
+        unsigned long long s01 = 0ull, s23 = 0ull, q01 = 0ull, q23 = 0ull;
 #pragma unroll
         for (int rr = 0; rr < 32; rr += 4) {
-            const float d0 = column[rr * stride] - x0;
-            const float d1 = column[(rr + 1) * stride] - x0;
-            const float d2 = column[(rr + 2) * stride] - x0;
-            const float d3 = column[(rr + 3) * stride] - x0;
-            a += d0;
-            b += d1;
-            c += d2;
-            e += d3;
-            qa = fmaf(d0, d0, qa);
-            qb = fmaf(d1, d1, qb);
-            qc = fmaf(d2, d2, qc);
-            qe = fmaf(d3, d3, qe);
+            const unsigned long long d01 = ffma2(f2pack(column[rr * stride], column[(rr + 1) * stride]), one, nx0);
+            const unsigned long long d23 =
+                ffma2(f2pack(column[(rr + 2) * stride], column[(rr + 3) * stride]), one, nx0);
+            s01 = ffma2(d01, one, s01);
+            s23 = ffma2(d23, one, s23);
+            q01 = ffma2(d01, d01, q01);
+            q23 = ffma2(d23, d23, q23);
         }
-    } else {
-#pragma unroll
+        f2unpack(s01, a, b);
+        f2unpack(s23, c, e);
+        f2unpack(q01, qa, qb);
+        f2unpack(q23, qc, qe);
+    } else {  // the last warp of the last tile only: kept small (not unrolled)
+#pragma unroll 1
         for (int rr = 0; rr < 32; rr += 4) {
             const float d0 = rr < na ? column[rr * stride] - x0 : 0.f;
             const float d1 = rr + 1 < na ? column[(rr + 1) * stride] - x0 : 0.f;

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             __syncthreads();
             tc_fence_after();
         }
-        disturbance_chunk<ND, 8>(lane_addr, TC, steps, n0, d, h, x0, a.ou_a, a.ou_s, a.ito, dt, a.em,
+        disturbance_chunk<ND, 8, false>(lane_addr, TC, steps, n0, d, h, x0, a.ou_a, a.ou_s, a.ito, dt, a.em,
                                  (uint32_t)(a.em.k0 + srow));
         tc_fence_before();
         __syncthreads();

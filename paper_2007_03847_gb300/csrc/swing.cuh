@@ -136,27 +136,6 @@ __device__ __forceinline__ void sin_cosm1_any(float a, float* sn, float* cm1)
     *cm1 = -2.0f * sh * sh;
 }
 
-// Packed FP32 (two lanes per register pair) fused multiply-add of sm_100+:
-// d = a * b + c elementwise on (x, y) pairs.
-__device__ __forceinline__ unsigned long long f2pack(float x, float y)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-    return r;
-}
-
-__device__ __forceinline__ void f2unpack(unsigned long long r, float& x, float& y)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
-}
-
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
-{
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 // One step of the swing equations, integrated in deviation variables
 //   Delta_i = delta_i - delta*_i - theta   (theta: angle of machine 0 when the
 //   system has no infinite bus, so that the common drift of all angles, which
