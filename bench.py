@@ -155,7 +155,7 @@ def profiled_traffic():
     except (OSError, ValueError):
         return None
     h = hashlib.sha256()
-    for f in ("simulate_fused.cuh", "swing.cuh", "tc_common.cuh"):
+    for f in ("simulate_fused.cuh", "swing.cuh", "tc_common.cuh", "disturb_chunk.cuh", "fmc_common.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2007_03847_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest() != kv.get("source_sha256", "").strip():

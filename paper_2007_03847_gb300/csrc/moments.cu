@@ -102,13 +102,19 @@ cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double*
 // Fused-simulation partials: part [nblk][Nt1][2*S] floats holding, per block of
 // `rows` samples (the last block count - (nblk-1) rows) and per grid time, the
 // FP32 sum of the shifted values (states 0..S-1) and their squared deviations
-// from the block's own mean (states 0..S-1).  Combined over blocks in FP64 in a
-// fixed order, so the result does not depend on scheduling:
-//   S1 = sum_b s1_b,  S2 = sum_b (m2_b + s1_b^2 / n_b)   (= sum of squares about the shift);
-// out: S1, S2 [Nt1][S].  A CTA owns 32 consecutive entries q of a part row; its
-// 8 warps stride over the blocks (warp g takes blocks g, g+8, ...), each with
-// two accumulators, and the 8 partial sums are added in warp order.
-constexpr int FS_COLS = 32, FS_GROUPS = 8;
+// from the block's own mean (states 0..S-1).  Combined into the sums about the
+// shift, S1 = sum_b s1_b and S2 = sum_b (m2_b + s1_b^2 / n_b); out: S1, S2 [Nt1][S].
+//
+// FP64 throughput is a small fraction of FP32 here, so the full blocks are first
+// merged in FP32 in groups of FS_G: the sums s1_g = sum s1_b with a compensated
+// (two-sum) addition, the squared deviations by the parallel-variance combine
+// (equal block sizes n), m2_g = sum m2_b + (1/n) sum (s1_b - s1_g/G)^2, which stays
+// on the scale of the spread (FP32-relative accuracy); each group then enters
+// FP64 once, as s1_g and m2_g + s1_g^2 / (G n).  The partial last block enters
+// FP64 on its own.  A CTA owns 32 consecutive entries q of a part row; its 8 warps
+// stride over the groups (warp g takes groups g, g+8, ...), and the 8 partial sums
+// are added in warp order, so the result does not depend on scheduling.
+constexpr int FS_COLS = 32, FS_GROUPS = 8, FS_G = 8;
 
 __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const float* __restrict__ part, int nblk,
                                                                          int64_t Nt1, int S, int64_t count, int rows,
@@ -120,31 +126,69 @@ __global__ void __launch_bounds__(FS_COLS * FS_GROUPS) fused_sums_kernel(const f
     const int64_t row = 2 * (int64_t)S;
     const int64_t total = Nt1 * row;
     const int64_t q = (int64_t)blockIdx.x * FS_COLS + cx;
-    double a0 = 0.0, a1 = 0.0;
+    double acc = 0.0;
     if (q < total) {
         const float* p = part + q;
-        const bool second = (q % row) >= S;  // squared deviations: add the block's s1^2 / n
-        // 1 / n_b: every block holds `rows` samples but the last (FP64 division
-        // is slow; one per thread for the full blocks, one for the last)
-        const double inv_rows = 1.0 / (double)rows;
+        const bool second = (q % row) >= S;  // squared deviations (s1 of the same state S entries before)
         const int64_t last_n = count - (int64_t)(nblk - 1) * rows;
-        const double inv_last = 1.0 / (double)(last_n > 0 ? last_n : 1);
-        auto term = [&](int b) {
-            double t = (double)p[(int64_t)b * total];
-            if (second) {
-                const double s1 = (double)p[(int64_t)b * total - S];
-                t = fma(s1 * s1, b == nblk - 1 ? inv_last : inv_rows, t);
+        const int nfull = last_n == rows ? nblk : nblk - 1;  // blocks of `rows` samples
+        const float inv_n = 1.f / (float)rows;
+        const double inv_gn = 1.0 / ((double)FS_G * (double)rows);
+        for (int g0 = g * FS_G; g0 < nfull; g0 += FS_GROUPS * FS_G) {
+            const int gc = nfull - g0 < FS_G ? nfull - g0 : FS_G;
+            float sv[FS_G], st = 0.f, mt = 0.f;
+#pragma unroll
+            for (int k = 0; k < FS_G; ++k) {
+                sv[k] = 0.f;
+                if (k < gc) {
+                    const float* pb = p + (int64_t)(g0 + k) * total;
+                    if (second) {
+                        sv[k] = pb[-S];
+                        mt += pb[0];
+                    } else {
+                        sv[k] = pb[0];
+                    }
+                    st += sv[k];
+                }
             }
-            return t;
-        };
-        int b = g;
-        for (; b + FS_GROUPS < nblk; b += 2 * FS_GROUPS) {
-            a0 += term(b);
-            a1 += term(b + FS_GROUPS);
+            if (!second) {
+                // the group's sum, compensated (Knuth's two-sum: the rounding error
+                // of every addition is carried), so that it enters FP64 as exactly as
+                // the blocks would one by one
+                float hi = 0.f, lo = 0.f;
+#pragma unroll
+                for (int k = 0; k < FS_G; ++k) {
+                    const float t = hi + sv[k];
+                    const float z = t - hi;
+                    lo += (hi - (t - z)) + (sv[k] - z);
+                    hi = t;
+                }
+                acc += (double)hi + (double)lo;
+            } else {
+                const float sb = gc == FS_G ? st * (1.f / FS_G) : st / (float)gc;
+                float dd = 0.f;
+#pragma unroll
+                for (int k = 0; k < FS_G; ++k)
+                    if (k < gc) {
+                        const float dv = sv[k] - sb;
+                        dd = fmaf(dv, dv, dd);
+                    }
+                const double ig = gc == FS_G ? inv_gn : 1.0 / ((double)gc * (double)rows);
+                acc += (double)fmaf(dd, inv_n, mt) + (double)st * (double)st * ig;
+            }
         }
-        if (b < nblk) a0 += term(b);
+        // the partial last block, by the warp whose turn it would be
+        if (nfull < nblk && g == (nfull / FS_G) % FS_GROUPS) {
+            const float* pb = p + (int64_t)(nblk - 1) * total;
+            double t = (double)pb[0];
+            if (second) {
+                const double s1 = (double)pb[-S];
+                t += s1 * s1 / (double)last_n;
+            }
+            acc += t;
+        }
     }
-    red[g][cx] = a0 + a1;
+    red[g][cx] = acc;
     __syncthreads();
     if (g == 0 && q < total) {
         double t = 0.0;

@@ -328,9 +328,12 @@ def test_batch_equals_single_scenarios(fmc, use_graph):
             _batch_kernel(fmc, sc)
             m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
             fmc.set_kernel_policy("auto")
-            # same samples, kernel and arithmetic; only the order of the FP64 sums differs
+            # same samples, kernel and per-tile arithmetic.  The batch adds the tiles'
+            # sums in FP64; a single call first merges groups of eight tiles in FP32
+            # (the sums compensated, the squared deviations by the parallel-variance
+            # combine, FP32-relative), so the variances agree to FP32 rounding
             assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
-            assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
+            assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=2e-6, atol=1e-18)
     b.close()
 
 

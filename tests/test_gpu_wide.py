@@ -125,5 +125,6 @@ def test_wide_in_a_batch(fmc):
         m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
         fmc.set_kernel_policy("auto")
         assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
-        assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=1e-9, atol=1e-18)
+        # (FP32 merge of tile groups in a single call, FP64 tile sums in the batch)
+        assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=2e-6, atol=1e-18)
     b.close()
