@@ -790,7 +790,8 @@ struct Prepared {
     fmc_scenario s{};
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
-    bool exclusive = true;  // the launch has the GPU to itself (see fused_tc)
+    bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
+    bool own_sm = false;    // with exclusive: the per-sample kernel takes whole SMs
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
 };
@@ -819,12 +820,15 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     P.exclusive = exclusive;
     // four warps per sample for systems above 16 machines (or on request)
     const int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
-    if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_PER_SAMPLE && P.nm < 0)
+    const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE || policy == FMC_KERNEL_PER_SAMPLE_SHARED ||
+                            policy == FMC_KERNEL_PER_SAMPLE_SM;
+    P.own_sm = exclusive && policy == FMC_KERNEL_PER_SAMPLE_SM;
+    if (path == FMC_PATH_FUSED && per_sample && P.nm < 0)
         return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
                     FMC_MAX_MACHINES_PLAIN, n);
     if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_SPLIT)
         P.nmt = wide_nmt_for(n);
-    else if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_PER_SAMPLE)
+    else if (path == FMC_PATH_FUSED && per_sample)
         P.nmt = 0;
     else
         P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
@@ -864,16 +868,26 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
 // boundaries become rarer; launches that share the GPU (batches, the server)
 // keep 128 columns per CTA.
 //
-// Samples per CTA: 128 (four warps).  The kernel also runs 64-sample CTAs (two
-// warps); they would even out the warps per SM of 2^16 samples (at most 14
-// instead of 16), but their TMEM share forces 16-step chunks and the doubled
-// design-tile reloads cost more than the balance gains (38.9 vs 35.1 ms), so
-// the automatic shape keeps 128.
+// Samples per CTA: 128 (four warps) when the GPU is shared.  The kernel also
+// runs 64-sample CTAs (two warps); they would even out the warps per SM of 2^16
+// samples, but their TMEM share forces 16-step chunks and the doubled
+// design-tile reloads cost more than the balance gains (38.9 vs 35.1 ms), so the
+// automatic shape keeps 128.
+//
+// When a single call has the GPU to itself, the per-sample kernel instead runs
+// one CTA per SM of W warps (W <= 14), W chosen so that the warps of the call
+// spread as evenly as whole warps allow over the SMs (2^16 samples: 147 CTAs of
+// 14 warps, against 512 CTAs of 4 warps that left 56 SMs with 16 warps and 96
+// with 12, the launch lasting as long as the 16-warp SMs).  Its CTA spans
+// ceil(W / 4) MMA tiles; the chunk TC is the largest power of two whose
+// tiles x d x TC columns fit the SM's 512.
 struct FusedShape {
     int rows;       // samples per CTA
     int max_ctas;   // resident CTAs per SM allowed
     int TC;         // time chunk
     int64_t ctas;   // grid
+    bool big;       // the SM-owning form
+    int tiles;      // MMA tiles per CTA
 };
 
 static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
@@ -881,7 +895,23 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
     const int d = P.s.d, sms = ctx->sms;
     const bool wide = P.nmt > 0;
     const int64_t full = (P.count + TC_M - 1) / TC_M;
-    FusedShape f{TC_M, 4, 32, 0};
+    FusedShape f{TC_M, 4, 32, 0, false, 1};
+    if (P.exclusive && !wide && P.own_sm) {
+        const int64_t warps = (P.count + 31) / 32;
+        const int64_t per_wave = (int64_t)sms * (FU_BIG_THREADS / 32);
+        const int64_t waves = (warps + per_wave - 1) / per_wave;
+        int64_t W = (warps + (int64_t)sms * waves - 1) / ((int64_t)sms * waves);
+        if (W < 1) W = 1;
+        f.big = true;
+        f.rows = (int)(32 * W);
+        f.tiles = (int)((W + 3) / 4);
+        f.max_ctas = 1;
+        int TC = 256;
+        while (TC > 16 && f.tiles * d * TC > 512) TC >>= 1;
+        f.TC = TC;
+        f.ctas = (P.count + f.rows - 1) / f.rows;
+        return f;
+    }
     if (P.exclusive) {
         const int64_t need = (full + sms - 1) / sms;
         f.max_ctas = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
@@ -924,7 +954,7 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
         if ((rc = ensure(ctx, ws.phi_hi, (size_t)Nt * Kpad * 2))) return rc;
         if (split && (rc = ensure(ctx, ws.phi_lo, (size_t)Nt * Kpad * 2))) return rc;
     }
-    if (per_tile_partials && (rc = ensure(ctx, ws.part, (size_t)ntiles * Nt1 * 2 * S * sizeof(float)))) return rc;
+    if (per_tile_partials && (rc = ensure(ctx, ws.part, (size_t)ntiles * Nt1 * 3 * S * sizeof(float)))) return rc;
     return FMC_OK;
 }
 
@@ -994,7 +1024,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     const int64_t ntiles = shape.ctas;
     const int TC = shape.TC;
     uint32_t tmem_cols = 32;
-    while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
+    while (tmem_cols < (uint32_t)(shape.tiles * d * TC)) tmem_cols <<= 1;
     CUtensorMap maps[4];
     if (em) {
         // no design and no contraction: the kernels draw the increments
@@ -1013,7 +1043,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
                  "basis kernel");
         prof_end(pr, st);
         if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
-                                        Ks, Nt, Kpad, TC, split, shape.rows)))
+                                        Ks, Nt, Kpad, TC, split, shape.big ? TC_M : shape.rows)))
             return rc;
     }
     FMC_CUDA(ctx, cudaMemsetAsync((char*)ws.status.ptr + 4, 0, 4, st), "memset");
@@ -1061,7 +1091,8 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
     } else {
         e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
-                                  shape.rows, shape.max_ctas, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
+                                  shape.rows, shape.max_ctas, shape.big, eq,
+                                  per_tile_partials ? (float*)ws.part.ptr : nullptr,
                                   per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
                                   (int*)ws.status.ptr + 1, ems, rrf, st, &occ);
     }
@@ -1464,7 +1495,7 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy)
 {
     if (!ctx) return FMC_EINVAL;
-    if (policy != FMC_KERNEL_AUTO && policy != FMC_KERNEL_PER_SAMPLE && policy != FMC_KERNEL_SPLIT)
+    if (policy < FMC_KERNEL_AUTO || policy > FMC_KERNEL_PER_SAMPLE_SM)
         return fail(ctx, FMC_EINVAL, "kernel policy %d", policy);
     ctx->kernel_policy = policy;
     return FMC_OK;

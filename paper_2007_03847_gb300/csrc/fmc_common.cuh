@@ -100,15 +100,15 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
-// Sum and squared deviations from their mean of the first na of 32 values
-// column[rr * stride] (the rest are ignored), in one pass over shared memory:
-// the sums of x_r - x_0 and of its square, x_0 the column's first value.  x_0 is
-// itself one of the values, so both sums are on the scale of the spread, and
-//   M2 = sum (x_r - x_0)^2 - (sum (x_r - x_0))^2 / na
-// cancels no more than the spread's own scale allows however far the values sit
-// from zero (the textbook shifted-data form of the sample variance).  Four
-// interleaved partials per sum.
-__device__ __forceinline__ void column_sum_m2(const float* column, int stride, int na, float* sum, float* m2)
+// The first na of 32 values column[rr * stride] (the rest are ignored) as a
+// reference value, their sum about it and their squared deviations from their
+// mean, in one pass over shared memory: ref = x_0 (the column's first value),
+// dev = sum (x_r - x_0), m2 = sum (x_r - x_0)^2 - dev^2 / na.  x_0 is itself one
+// of the values, so dev and the squares stay on the scale of the spread however
+// far the values sit from zero, and the sum of the values, na x_0 + dev, is
+// never formed in FP32 (its rounding would be on the scale of the values; the
+// combines carry x_0 separately).  Four interleaved partials per sum.
+__device__ __forceinline__ void column_sums(const float* column, int stride, int na, float* ref, float* dev, float* m2)
 {
     const float x0 = column[0];
     float a = 0.f, b = 0.f, c = 0.f, e = 0.f;
@@ -152,10 +152,12 @@ __device__ __forceinline__ void column_sum_m2(const float* column, int stride, i
     const float sd = (a + b) + (c + e);
     const float sq = (qa + qb) + (qc + qe);
     if (na > 0) {
-        *sum = fmaf((float)na, x0, sd);
+        *ref = x0;
+        *dev = sd;
         *m2 = fmaxf(sq - sd * (sd / (float)na), 0.f);
     } else {
-        *sum = 0.f;
+        *ref = 0.f;
+        *dev = 0.f;
         *m2 = 0.f;
     }
 }
@@ -167,31 +169,38 @@ __device__ __forceinline__ int group_count(int64_t left, int g)
     return r <= 0 ? 0 : (r >= 32 ? 32 : (int)r);
 }
 
-// Parallel-variance combine (Chan, Golub and LeVeque) of `groups` (<= 4) groups
-// of 32 samples, `left` samples remaining from group 0 on, with sums s[g] and
-// squared deviations m2[g] (strided by `stride`): the combined squared deviation
-// from the combined mean, in a fixed order.
-__device__ __forceinline__ float combine_m2(const float* s, const float* m2, int stride, int64_t left, int groups)
+// Combines `groups` groups of 32 samples (`left` samples remaining from group 0
+// on) given as column_sums triples ref[g], dev[g], m2[g] (strided by `stride`)
+// into one triple about the first group's reference c = ref[0]:
+//   dev = sum_g (n_g (ref_g - c) + dev_g),
+//   m2  = sum_g m2_g + sum_g n_g (mu_g - mu)^2   (Chan, Golub and LeVeque),
+// with mu_g - mu = (ref_g - c) + dev_g / n_g - dev / n: every term is on the
+// scale of the spread.  Fixed order.
+__device__ __forceinline__ void combine_groups(const float* ref, const float* dev, const float* m2, int stride,
+                                               int64_t left, int groups, float* c_out, float* dev_out, float* m2_out)
 {
-    float st = 0.f;
+    const float c = ref[0];
+    float dt = 0.f;
     int nt = 0;
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-        if (g < groups) {
-            st += s[g * stride];
-            nt += group_count(left, g);
-        }
-    const float mu = nt > 0 ? st / (float)nt : 0.f;
-    float acc = 0.f;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
+#pragma unroll 1
+    for (int g = 0; g < groups; ++g) {
         const int ng = group_count(left, g);
-        if (g < groups && ng > 0) {
-            const float dg = s[g * stride] / (float)ng - mu;
-            acc += m2[g * stride] + (float)ng * dg * dg;
+        if (ng > 0) dt += fmaf((float)ng, ref[g * stride] - c, dev[g * stride]);
+        nt += ng;
+    }
+    const float mu = nt > 0 ? dt / (float)nt : 0.f;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int g = 0; g < groups; ++g) {
+        const int ng = group_count(left, g);
+        if (ng > 0) {
+            const float dg = (ref[g * stride] - c) + dev[g * stride] / (float)ng - mu;
+            acc += fmaf((float)ng * dg, dg, m2[g * stride]);
         }
     }
-    return acc;
+    *c_out = c;
+    *dev_out = dt;
+    *m2_out = acc;
 }
 
 // Adds a warp's response-function values and their squares into rrf[0], rrf[1]

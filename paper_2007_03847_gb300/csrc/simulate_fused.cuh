@@ -15,9 +15,11 @@
 //     FP32 pipes:    it reads x(t_{n+1}) with tcgen05.ld and advances the swing
 //                    equations by RK4/Heun, step by step
 //     moments:       per step, each warp transposes its 32 samples' shifted states
-//                    through shared memory and sums them (S1, S2) per state; the
-//                    four warps' sums are added in a fixed order and written as
-//                    FP32 partials [tile][t][S1 | S2]
+//                    through shared memory and forms per state a reference value
+//                    (its first sample), the sum about it and the squared
+//                    deviations (column_sums); every few steps the warps' triples
+//                    are combined in a fixed order into the tile's and written as
+//                    FP32 partials [tile][t][ref | dev | m2]
 //
 // Trajectories never go to HBM (unless a debug buffer is given).  A separate
 // kernel combines the per-tile partials in FP64 in a fixed order.
@@ -32,7 +34,14 @@
 namespace fmc {
 
 constexpr int FU_THREADS = 128;  // full tile; a half tile has 64 threads
-constexpr int FU_MS = 32;  // steps between flushes of the moment buffer (measured: 8 -> 32 saves 0.8%)
+// A CTA that owns its SM (launches that have the GPU to themselves) takes up to
+// FU_BIG_THREADS = 448 threads (14 warps): the samples then spread over the SMs
+// in whole warps (2^16 samples: 13 or 14 warps on every SM instead of 16 on
+// some and 12 on others), and the register budget per thread rises to 144.  Its
+// warps span ceil(warps / 4) MMA tiles of 128 rows, each with its own TMEM columns.
+// steps between flushes of the moment buffer (measured: 8 -> 32 saves 0.8%; 16
+// above 10 machine slots, so that four CTAs' buffers still share an SM)
+__host__ __device__ constexpr int fu_ms(int nm) { return nm > 10 ? 16 : 32; }
 
 struct FusedArgs {
     int64_t count;
@@ -40,7 +49,7 @@ struct FusedArgs {
     int ns;             // ring stages
     uint32_t tmem_cols;
     const double* eq;   // [delta* n][pm n][moment shift 2n] (the shift is used by the reduce)
-    float* part;        // [ntiles][Nt+1][4n], or nullptr: add into S1, S2 with FP64 atomics
+    float* part;        // [ntiles][Nt+1][3][2n] (ref | dev | m2), or nullptr: add into S1, S2 with FP64 atomics
     float* traj;        // [count][Nt+1][2n] or nullptr
     int* err;
     double* S1;         // [Nt+1][2n] when part == nullptr
@@ -49,8 +58,8 @@ struct FusedArgs {
     double* rrf;        // [2]: sums of the response function and its square, or nullptr
 };
 
-template <int NM, int ND>
-__global__ void __launch_bounds__(FU_THREADS, 4)
+template <int NM, int ND, bool BIG>
+__global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4)
     simulate_fused_kernel(const __grid_constant__ SwingParams<NM, ND> p, const __grid_constant__ CUtensorMap mAh,
                           const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBh,
                           const __grid_constant__ CUtensorMap mBl, FusedArgs a)
@@ -66,7 +75,12 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int rows = blockDim.x, warps = rows / 32;  // samples (= threads) and warps of this CTA
-    const int n = p.n, d = p.d, S = 2 * n, S4 = 4 * n;
+    // MMA tiles of 128 rows (a half tile's MMA still has M = 128: see above)
+    const int tiles = BIG ? (warps + 3) / 4 : 1;
+    const int arows = BIG ? TC_M : rows;  // rows of one A box
+    const int n = p.n, d = p.d, S = 2 * n, S3 = 3 * S;
+    constexpr int FU_MS = fu_ms(NM);
+    constexpr int MSLOT = 6 * NM;  // floats per (step, warp) slot: ref | dev | m2 of up to 2 NM states
     const int64_t row0 = (int64_t)blockIdx.x * rows;
     const int64_t srow = row0 + tid;
     const bool active = srow < a.count;
@@ -74,7 +88,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
 
     // ring (used only while the tensor cores fill TMEM) aliases the moment buffers
     TcRing r;
-    r.a_bytes = rows * 64;
+    r.a_bytes = arows * 64;
     r.b_bytes = TC * 64;
     r.split = a.split;
     r.base = smem;
@@ -84,7 +98,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     uint64_t* done = &bars[2 * TC_MAX_STAGES];
     const int WROW = 2 * NM + 1;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;           // [32][WROW] per warp
-    float* msum = reinterpret_cast<float*>(smem) + warps * 32 * WROW;          // [FU_MS][warps][4*NM]
+    float* msum = reinterpret_cast<float*>(smem) + warps * 32 * WROW;          // [FU_MS][warps][MSLOT]
 
     const bool em = a.em.on != 0;
     if (tid == 0) {
@@ -101,7 +115,8 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    // the warp's 32 TMEM lanes (sub-partition warp mod 4) in the columns of its MMA tile
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * d * TC);
 
     float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND];
@@ -124,14 +139,15 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             }
     }
     // time 0: every sample sits at the (rounded) shift, so both sums are zero
-    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4 : nullptr;
+    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S3 : nullptr;
     if (part_tile)
-        for (int v = tid; v < S4; v += rows) part_tile[v] = 0.f;
+        for (int v = tid; v < S3; v += rows) part_tile[v] = 0.f;
 
     const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
     uint32_t g = 0;  // K blocks issued so far (thread 0)
     float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
-    const int J = d * a.nkb;
+    const int JT = d * a.nkb;  // K blocks per MMA tile
+    const int J = tiles * JT;
 
     for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
@@ -141,15 +157,24 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            bool ok = ring_load(r, g, &mAh, &mAl, &mBh, &mBl, 0, (int)row0, 0, n0);
+            // item j: MMA tile t, disturbance wj, K block kb; loads run up to ns - 1
+            // items ahead of the MMAs (a stage is refilled once its MMAs completed)
+            auto load_item = [&](int j) {
+                const int t = j / JT, rem = j - t * JT, wj = rem / a.nkb, kb = rem - wj * a.nkb;
+                return ring_load(r, g + (uint32_t)j, &mAh, &mAl, &mBh, &mBl, wj * a.Ks + kb * TC_BK,
+                                 (int)(row0 + (int64_t)t * TC_M), kb * TC_BK, n0);
+            };
+            bool ok = true;
+            int issued = 0;
+            for (; issued < J && issued + 1 < (int)r.ns && ok; ++issued) ok = load_item(issued);
             for (int j = 0; j < J && ok; ++j) {
-                if (j + 1 < J) {
-                    const int w1 = (j + 1) / a.nkb, kb1 = (j + 1) % a.nkb;
-                    ok = ring_load(r, g + j + 1, &mAh, &mAl, &mBh, &mBl, w1 * a.Ks + kb1 * TC_BK, (int)row0,
-                                   kb1 * TC_BK, n0);
+                if (issued < J) {
+                    ok = load_item(issued);
+                    ++issued;
+                    if (!ok) break;
                 }
-                const int wj = j / a.nkb, kbj = j % a.nkb;
-                if (ok) ok = ring_mma(r, g + j, tmem + (uint32_t)(wj * TC), idesc, kbj == 0);
+                const int t = j / JT, rem = j - t * JT, wj = rem / a.nkb, kb = rem - wj * a.nkb;
+                ok = ring_mma(r, g + (uint32_t)j, tmem + (uint32_t)((t * d + wj) * TC), idesc, kb == 0);
             }
             g += (uint32_t)J;
             if (ok) {
@@ -219,13 +244,15 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             __syncwarp();
             const int ms = s % FU_MS;
             if (lane < S) {
-                // the warp's sum and squared deviations from its mean, per state
+                // the warp's reference value, sum about it and squared deviations, per state
                 const int64_t left = a.count - (srow - lane);
                 const int na_warp = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
-                float s1, m2;
-                column_sum_m2(wbuf + lane, WROW, na_warp, &s1, &m2);
-                msum[(ms * warps + warp) * (4 * NM) + lane] = s1;
-                msum[(ms * warps + warp) * (4 * NM) + S + lane] = m2;
+                float rf, dv, m2;
+                column_sums(wbuf + lane, WROW, na_warp, &rf, &dv, &m2);
+                float* slot = msum + (ms * warps + warp) * MSLOT;
+                slot[lane] = rf;
+                slot[S + lane] = dv;
+                slot[2 * S + lane] = m2;
             }
             __syncwarp();
             if (ms == FU_MS - 1 || s == steps - 1) {
@@ -235,23 +262,23 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                 // samples of this tile (the last tile may be partly empty)
                 const int64_t left = a.count - row0;
                 const int n_tile = left <= 0 ? 0 : (left >= rows ? rows : (int)left);
-                for (int e = tid; e < nst * S4; e += rows) {
-                    const int sl = e / S4, v = e - sl * S4;
-                    const int j = v < S ? v : v - S;  // state
-                    const float* m = msum + sl * warps * (4 * NM) + j;
-                    // tile sum; for the second half the tile's squared deviations (parallel combine)
-                    const float t1 =
-                        warps == 4 ? ((m[0] + m[4 * NM]) + m[2 * 4 * NM]) + m[3 * 4 * NM] : m[0] + m[4 * NM];
-                    const float acc = v < S ? t1 : combine_m2(m, m + S, 4 * NM, left, warps);
+                for (int e = tid; e < nst * S; e += rows) {
+                    const int sl = e / S, j = e - sl * S;  // step slot, state
+                    const float* m = msum + sl * warps * MSLOT + j;
+                    // the tile's triple: reference (warp 0's), sum about it, squared deviations
+                    float c, dv, m2;
+                    combine_groups(m, m + S, m + 2 * S, MSLOT, left, warps, &c, &dv, &m2);
                     if (part_tile) {
-                        part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
-                    } else {
+                        float* o = part_tile + (int64_t)(tn0 + sl) * S3;
+                        o[j] = c;
+                        o[S + j] = dv;
+                        o[2 * S + j] = m2;
+                    } else if (n_tile > 0) {
                         // the tile's S1 and S2 (= M2 + S1^2 / n) about the shift, in FP64
                         const int64_t row = (int64_t)(tn0 + sl) * S;
-                        if (v < S)
-                            atomicAdd(a.S1 + row + v, (double)acc);
-                        else if (n_tile > 0)
-                            atomicAdd(a.S2 + row + j, (double)acc + (double)t1 * (double)t1 / (double)n_tile);
+                        const double s1 = fma((double)n_tile, (double)c, (double)dv);
+                        atomicAdd(a.S1 + row + j, s1);
+                        atomicAdd(a.S2 + row + j, (double)m2 + s1 * s1 / (double)n_tile);
                     }
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(rows) : "memory");
@@ -264,12 +291,13 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
-template <int NM, int ND>
+template <int NM, int ND, bool BIG>
 cudaError_t launch_fused_t(const void* params, const CUtensorMap* maps, const FusedArgs& a, int smem, int ntiles,
                            int rows, cudaStream_t st, int* max_ctas_per_sm)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
-    auto kern = simulate_fused_kernel<NM, ND>;
+    if (rows % 32 != 0 || rows > (BIG ? FU_BIG_THREADS : FU_THREADS)) return cudaErrorInvalidValue;
+    auto kern = simulate_fused_kernel<NM, ND, BIG>;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);

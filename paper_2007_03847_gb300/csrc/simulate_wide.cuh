@@ -35,7 +35,7 @@ constexpr int WI_MS = 4;  // steps between flushes of the moment buffer
 template <int NMT>
 __host__ __device__ inline int wide_mom_floats()
 {
-    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 4 * NMT + WI_MS * 4 * 128;
+    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 6 * NMT + WI_MS * 4 * 128;
 }
 
 // sin and cos - 1 of a deviation, rotated into (gamma, eta) about the equilibrium.
@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int q = warp & 3, h = warp >> 2;
-    const int n = a.n, d = a.d, S = 2 * n, S4 = 4 * n;
+    const int n = a.n, d = a.d, S = 2 * n, S3 = 3 * S;
+    constexpr int GS = 6 * NMT;  // floats per (step, sample group, h) slot: ref | dev | m2 of 2 NMT states
     const int r = 32 * q + lane;  // sample row within the tile = TMEM lane
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
     const int64_t srow = row0 + r;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const float* c_hw = pm + 7 * G4;
     const float* c_inj = pm + 8 * G4;  // [dx][4 NMT]
     // per step and warp, the partial centre-of-inertia speed of the warp's machines
-    float* coi_part = msum + WI_MS * 16 * 4 * NMT;  // [WI_MS][4 (h)][128]
+    float* coi_part = msum + WI_MS * 16 * GS;  // [WI_MS][4 (h)][128]
 
     const bool em = a.em.on != 0;
     if (tid == 0) {
@@ -158,9 +159,9 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             }
         }
     }
-    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S4 : nullptr;
+    float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S3 : nullptr;
     if (part_tile)
-        for (int v = tid; v < S4; v += WI_THREADS) part_tile[v] = 0.f;
+        for (int v = tid; v < S3; v += WI_THREADS) part_tile[v] = 0.f;
 
     // stage-0 input of the first step: every deviation is zero
     int gb = 0;
@@ -433,14 +434,15 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             __syncwarp();
             const int ms = s % WI_MS;
             if (lane < 2 * NMT) {
-                // the sample group's sum and squared deviations from its mean, per state
+                // the sample group's reference value, sum about it and squared deviations
                 const int64_t left = a.count - (srow - lane);
                 const int na = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
-                float s1, m2;
-                column_sum_m2(wbuf + lane, WROW, na, &s1, &m2);
-                float* slot = msum + ((ms * 4 + q) * 4 + h) * G4;
-                slot[lane] = s1;
-                slot[2 * NMT + lane] = m2;
+                float rf, dv, m2;
+                column_sums(wbuf + lane, WROW, na, &rf, &dv, &m2);
+                float* slot = msum + ((ms * 4 + q) * 4 + h) * GS;
+                slot[lane] = rf;
+                slot[2 * NMT + lane] = dv;
+                slot[4 * NMT + lane] = m2;
             }
             if (a.rrf) {
                 float cp = 0.f;
@@ -463,26 +465,26 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 // samples of this tile (the last tile may be partly empty)
                 const int64_t left = a.count - row0;
                 const int n_tile = left <= 0 ? 0 : (left >= 128 ? 128 : (int)left);
-                for (int e = tid; e < nsl * S4; e += WI_THREADS) {
-                    const int sl = e / S4, v = e - sl * S4;
-                    // v = kind * 2n + state; state < n is delta_i, else omega_(state - n)
-                    const int kind = v >= S ? 1 : 0;
-                    const int stt = v - kind * S;
+                for (int e = tid; e < nsl * S; e += WI_THREADS) {
+                    const int sl = e / S, stt = e - sl * S;
+                    // state stt < n is delta_i, else omega_(stt - n)
                     const int isw = stt >= n ? 1 : 0;
                     const int i = stt - isw * n;
-                    const float* m = msum + (sl * 16 + (i & 3)) * G4 + isw * NMT + (i >> 2);
-                    // tile sum; for kind 1 the tile's squared deviations (parallel combine)
-                    const float t1 = ((m[0] + m[4 * G4]) + m[8 * G4]) + m[12 * G4];
-                    const float acc = kind == 0 ? t1 : combine_m2(m, m + 2 * NMT, 4 * G4, left, 4);
+                    const float* m = msum + (sl * 16 + (i & 3)) * GS + isw * NMT + (i >> 2);
+                    // the tile's triple over its four sample groups
+                    float c, dv, m2;
+                    combine_groups(m, m + 2 * NMT, m + 4 * NMT, 4 * GS, left, 4, &c, &dv, &m2);
                     if (part_tile) {
-                        part_tile[(int64_t)(tn0 + sl) * S4 + v] = acc;
-                    } else {
+                        float* o = part_tile + (int64_t)(tn0 + sl) * S3;
+                        o[stt] = c;
+                        o[S + stt] = dv;
+                        o[2 * S + stt] = m2;
+                    } else if (n_tile > 0) {
                         // the tile's S1 and S2 (= M2 + S1^2 / n) about the shift, in FP64
                         const int64_t rowt = (int64_t)(tn0 + sl) * S;
-                        if (kind == 0)
-                            atomicAdd(a.S1 + rowt + stt, (double)acc);
-                        else if (n_tile > 0)
-                            atomicAdd(a.S2 + rowt + stt, (double)acc + (double)t1 * (double)t1 / (double)n_tile);
+                        const double s1 = fma((double)n_tile, (double)c, (double)dv);
+                        atomicAdd(a.S1 + rowt + stt, s1);
+                        atomicAdd(a.S2 + rowt + stt, (double)m2 + s1 * s1 / (double)n_tile);
                     }
                 }
                 __syncthreads();

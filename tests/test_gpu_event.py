@@ -45,11 +45,11 @@ def _rrf_check(rrf, ref_rrf):
     assert abs(v - ref_rrf.var(ddof=1)) <= 1e-4 * ref_rrf.var(ddof=1)
 
 
-@pytest.mark.parametrize("kernel", ["per_sample", "split"])
+@pytest.mark.parametrize("kernel", ["per_sample", "split", "per_sample_sm"])
 @pytest.mark.parametrize("case", ["mm10_trip", "mm7_d4_gain", "mm22_trip", "smib_step"])
 def test_event_fused(fmc, orc, kernel, case):
     sc = _cases()[case]
-    if kernel == "per_sample" and sc.n > 16:
+    if kernel.startswith("per_sample") and sc.n > 16:
         pytest.skip("the per-sample kernel takes up to 16 machines")
     fmc.set_kernel_policy(kernel)
     try:

@@ -121,10 +121,14 @@ def test_wide_in_a_batch(fmc):
     fmc.device_status()
     for sc, m, v in zip(scs, means, vars_):
         # the kernel the batch takes for this scenario on a shared GPU
-        fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
+        fmc.set_kernel_policy("per_sample_shared" if sc.n <= 16 else "split")
         m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
         fmc.set_kernel_policy("auto")
-        assert np.allclose(m.cpu().numpy(), m1.cpu().numpy(), rtol=1e-12, atol=1e-15)
-        # (FP32 merge of tile groups in a single call, FP64 tile sums in the batch)
-        assert np.allclose(v.cpu().numpy(), v1.cpu().numpy(), rtol=2e-6, atol=1e-18)
+        # FP32 merge of tile groups in a single call, FP64 tile sums in the batch:
+        # equal to FP32 rounding on the scale of the spread
+        mm, vv, mm1, vv1 = m.cpu().numpy(), v.cpu().numpy(), m1.cpu().numpy(), v1.cpu().numpy()
+        for sl in (slice(0, sc.n), slice(sc.n, 2 * sc.n)):
+            sd = float(np.sqrt(np.max(vv1[:, sl])))
+            assert np.max(np.abs(mm[:, sl] - mm1[:, sl])) <= 1e-6 * sd + 1e-15
+            assert np.allclose(vv[:, sl], vv1[:, sl], rtol=2e-6, atol=1e-18)
     b.close()
