@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
     ap.add_argument("--machines", type=int, default=10, help="machines of the system (17..52: large-system kernel)")
     ap.add_argument("--disturbances", type=int, default=3)
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "per_sample", "split"],
+                    help="fused-path kernel policy of the timed calls (see fmc_set_kernel_policy)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "tol", "batch", "serve", "dn"],
@@ -491,6 +494,7 @@ def main():
     fmc.build()
     ctx = fmc.Context(local)
     sms, gpu_name = ctx.info()
+    fmc.set_kernel_policy(args.kernel, ctx=ctx)
     path = args.path
     precision = args.precision or ("f32" if path == "plain" else "bf16x3")
     # weak scaling: every rank simulates `samples` samples, its own block of one
@@ -598,7 +602,8 @@ def main():
             "data": "synthetic (seeded system and LHS design)",
             "config": {"workload": workload_name(args), "path": path, "precision": precision, "samples_per_gpu": count,
                        "steps_per_sample": Nt, "machines": n, "disturbances": sc.d, "K": sc.K,
-                       "l2": "flushed between timed steps (512 MB write)", "gpu": gpu_name, "sms": sms},
+                       "l2": "flushed between timed steps (512 MB write)", "gpu": gpu_name, "sms": sms,
+                       "kernel_policy": args.kernel},
             "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline, "cpu_baseline": base,
             "clocks": clk,
         }

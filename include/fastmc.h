@@ -468,20 +468,13 @@ int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);
 #define FMC_KERNEL_AUTO 0        /* per sample for n <= 16, split above */
 #define FMC_KERNEL_PER_SAMPLE 1  /* one thread integrates a whole sample (n <= FMC_MAX_MACHINES_PLAIN) */
 #define FMC_KERNEL_SPLIT 2       /* four warps share each sample's machines (any n up to FMC_MAX_MACHINES) */
-#define FMC_KERNEL_PER_SAMPLE_SHARED 3  /* per sample, in the CTA shape of batches and the server */
-#define FMC_KERNEL_PER_SAMPLE_SM 4      /* per sample, one CTA of up to 14 warps per SM */
 
 /*
  * Chooses the fused kernel for this context's later single-scenario calls
  * (fmc_simulate, fmc_simulate_sums).  AUTO takes the per-sample kernel up to 16
  * machines (the faster one there, at any sample count) and the split kernel
- * above; PER_SAMPLE and AUTO run it in the CTA shape measured fastest for a
- * single call.  Batches and the server share the GPU between scenarios and use
- * 128-sample CTAs, up to four per SM; PER_SAMPLE_SHARED selects that shape for a
- * single call (the same tiles, hence the same FP32 partial sums, as a batch).
- * PER_SAMPLE_SM selects the SM-owning shape: one CTA of up to 14 warps per SM,
- * the warps of the call spread evenly over the SMs.  FMC_EINVAL for an unknown
- * policy; a per-sample request above 16 machines fails at the call with
+ * above.  Batches and the server always use AUTO's choice.  FMC_EINVAL for an
+ * unknown policy; a per-sample request above 16 machines fails at the call with
  * FMC_EUNSUPPORTED.
  */
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy);

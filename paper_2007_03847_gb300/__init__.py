@@ -580,15 +580,12 @@ def test_sincos(x, ctx: Context | None = None, stream=None):
     return outs
 
 
-KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT, KERNEL_PER_SAMPLE_SHARED, KERNEL_PER_SAMPLE_SM = 0, 1, 2, 3, 4
-_KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT,
-           "per_sample_shared": KERNEL_PER_SAMPLE_SHARED, "per_sample_sm": KERNEL_PER_SAMPLE_SM}
+KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT = 0, 1, 2
+_KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT}
 
 
 def set_kernel_policy(policy, ctx: Context | None = None) -> None:
-    """Fused-path kernel for later single-scenario calls: "auto", "per_sample", "split",
-    "per_sample_shared" (the per-sample kernel in the CTA shape batches and the server use)
-    or "per_sample_sm" (the per-sample kernel with one CTA of up to 14 warps per SM)."""
+    """Fused-path kernel for later single-scenario calls: "auto", "per_sample" or "split"."""
     ctx = ctx or default_context()
     ctx.check(ctx.lib.fmc_set_kernel_policy(ctx.h, _KERNEL.get(policy, policy)))
 

@@ -791,7 +791,6 @@ struct Prepared {
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
     bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
-    bool own_sm = false;    // with exclusive: the per-sample kernel takes whole SMs
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
 };
@@ -820,9 +819,7 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     P.exclusive = exclusive;
     // four warps per sample for systems above 16 machines (or on request)
     const int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
-    const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE || policy == FMC_KERNEL_PER_SAMPLE_SHARED ||
-                            policy == FMC_KERNEL_PER_SAMPLE_SM;
-    P.own_sm = exclusive && policy == FMC_KERNEL_PER_SAMPLE_SM;
+    const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE;
     if (path == FMC_PATH_FUSED && per_sample && P.nm < 0)
         return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
                     FMC_MAX_MACHINES_PLAIN, n);
@@ -874,20 +871,18 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
 // design-tile reloads cost more than the balance gains (38.9 vs 35.1 ms), so the
 // automatic shape keeps 128.
 //
-// When a single call has the GPU to itself, the per-sample kernel instead runs
-// one CTA per SM of W warps (W <= 14), W chosen so that the warps of the call
-// spread as evenly as whole warps allow over the SMs (2^16 samples: 147 CTAs of
-// 14 warps, against 512 CTAs of 4 warps that left 56 SMs with 16 warps and 96
-// with 12, the launch lasting as long as the 16-warp SMs).  Its CTA spans
-// ceil(W / 4) MMA tiles; the chunk TC is the largest power of two whose
-// tiles x d x TC columns fit the SM's 512.
+// With N = 2^16 the 2048 warps of 4-warp CTAs leave 3.37 warps per SM
+// sub-partition on average against at most 4 (56 SMs with four CTAs, 96 with
+// three), and the launch lasts as long as the 4-warp sub-partitions: a
+// quantisation of whole warps that no CTA shape removes.  (A form with one CTA
+// of 14 integrating warps and a producer warp per SM, the contraction
+// double-buffered in TMEM, measured no faster: two of its four sub-partitions
+// still hold four warps.)
 struct FusedShape {
     int rows;       // samples per CTA
     int max_ctas;   // resident CTAs per SM allowed
     int TC;         // time chunk
     int64_t ctas;   // grid
-    bool big;       // the SM-owning form
-    int tiles;      // MMA tiles per CTA
 };
 
 static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
@@ -895,23 +890,7 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
     const int d = P.s.d, sms = ctx->sms;
     const bool wide = P.nmt > 0;
     const int64_t full = (P.count + TC_M - 1) / TC_M;
-    FusedShape f{TC_M, 4, 32, 0, false, 1};
-    if (P.exclusive && !wide && P.own_sm) {
-        const int64_t warps = (P.count + 31) / 32;
-        const int64_t per_wave = (int64_t)sms * (FU_BIG_THREADS / 32);
-        const int64_t waves = (warps + per_wave - 1) / per_wave;
-        int64_t W = (warps + (int64_t)sms * waves - 1) / ((int64_t)sms * waves);
-        if (W < 1) W = 1;
-        f.big = true;
-        f.rows = (int)(32 * W);
-        f.tiles = (int)((W + 3) / 4);
-        f.max_ctas = 1;
-        int TC = 256;
-        while (TC > 16 && f.tiles * d * TC > 512) TC >>= 1;
-        f.TC = TC;
-        f.ctas = (P.count + f.rows - 1) / f.rows;
-        return f;
-    }
+    FusedShape f{TC_M, 4, 32, 0};
     if (P.exclusive) {
         const int64_t need = (full + sms - 1) / sms;
         f.max_ctas = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
@@ -1024,7 +1003,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     const int64_t ntiles = shape.ctas;
     const int TC = shape.TC;
     uint32_t tmem_cols = 32;
-    while (tmem_cols < (uint32_t)(shape.tiles * d * TC)) tmem_cols <<= 1;
+    while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
     CUtensorMap maps[4];
     if (em) {
         // no design and no contraction: the kernels draw the increments
@@ -1043,7 +1022,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
                  "basis kernel");
         prof_end(pr, st);
         if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
-                                        Ks, Nt, Kpad, TC, split, shape.big ? TC_M : shape.rows)))
+                                        Ks, Nt, Kpad, TC, split, shape.rows)))
             return rc;
     }
     FMC_CUDA(ctx, cudaMemsetAsync((char*)ws.status.ptr + 4, 0, 4, st), "memset");
@@ -1091,8 +1070,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
     } else {
         e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
-                                  shape.rows, shape.max_ctas, shape.big, eq,
-                                  per_tile_partials ? (float*)ws.part.ptr : nullptr,
+                                  shape.rows, shape.max_ctas, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
                                   per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
                                   (int*)ws.status.ptr + 1, ems, rrf, st, &occ);
     }
@@ -1495,7 +1473,7 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy)
 {
     if (!ctx) return FMC_EINVAL;
-    if (policy < FMC_KERNEL_AUTO || policy > FMC_KERNEL_PER_SAMPLE_SM)
+    if (policy < FMC_KERNEL_AUTO || policy > FMC_KERNEL_SPLIT)
         return fail(ctx, FMC_EINVAL, "kernel policy %d", policy);
     ctx->kernel_policy = policy;
     return FMC_OK;

@@ -180,6 +180,23 @@ __device__ __forceinline__ void combine_groups(const float* ref, const float* de
                                                int64_t left, int groups, float* c_out, float* dev_out, float* m2_out)
 {
     const float c = ref[0];
+    if (left >= 32 * (int64_t)groups) {
+        // every group full: n_g = 32, and the divisions by 32 are exact products
+        float dt = 0.f;
+#pragma unroll 1
+        for (int g = 0; g < groups; ++g) dt += fmaf(32.f, ref[g * stride] - c, dev[g * stride]);
+        const float mu = dt / (float)(32 * groups);
+        float acc = 0.f;
+#pragma unroll 1
+        for (int g = 0; g < groups; ++g) {
+            const float dg = (ref[g * stride] - c) + dev[g * stride] * 0.03125f - mu;
+            acc += fmaf(32.f * dg, dg, m2[g * stride]);
+        }
+        *c_out = c;
+        *dev_out = dt;
+        *m2_out = acc;
+        return;
+    }
     float dt = 0.f;
     int nt = 0;
 #pragma unroll 1

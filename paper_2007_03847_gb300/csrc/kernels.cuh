@@ -49,17 +49,13 @@ cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G,
 // rrf (nullable): [2] FP64 sums of the response function and its square
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
                                   int64_t count, int Nt, float* traj, double* rrf, cudaStream_t st);
-// threads of the fused kernel's SM-owning form (one CTA per SM, 14 warps)
-constexpr int FU_BIG_THREADS = 448;
-int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows, bool big);
+int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows);
 // rows: samples per CTA, 128 (four warps) or 64 (two warps); max_ctas: resident
-// CTAs per SM allowed (further limited by the TMEM columns).  big: the SM-owning
-// form, one CTA per SM with rows a multiple of 32 up to 448 spanning
-// ceil(rows / 128) MMA tiles (tmem_cols >= tiles x d x TC).
+// CTAs per SM allowed (further limited by the TMEM columns)
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
-                                  int rows, int max_ctas, bool big, const double* eq, float* part, double* S1,
-                                  double* S2, float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
+                                  int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
+                                  float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
                                   int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
 cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,

@@ -8,10 +8,10 @@ cudaError_t launch_fused_nm16(int nd, const void* params, const CUtensorMap* map
                               int ntiles, int rows, cudaStream_t st, int* occ)
 {
     switch (nd) {
-        case 1: return launch_fused_t<16, 1, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 2: return launch_fused_t<16, 2, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 4: return launch_fused_t<16, 4, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 8: return launch_fused_t<16, 8, false>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 1: return launch_fused_t<16, 1>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 2: return launch_fused_t<16, 2>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 4: return launch_fused_t<16, 4>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 8: return launch_fused_t<16, 8>(params, maps, a, smem, ntiles, rows, st, occ);
         default: return cudaErrorInvalidValue;
     }
 }

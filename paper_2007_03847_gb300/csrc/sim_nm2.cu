@@ -8,10 +8,10 @@ cudaError_t launch_fused_nm2(int nd, const void* params, const CUtensorMap* maps
                               int ntiles, int rows, cudaStream_t st, int* occ)
 {
     switch (nd) {
-        case 1: return launch_fused_t<2, 1, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 2: return launch_fused_t<2, 2, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 4: return launch_fused_t<2, 4, false>(params, maps, a, smem, ntiles, rows, st, occ);
-        case 8: return launch_fused_t<2, 8, false>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 1: return launch_fused_t<2, 1>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 2: return launch_fused_t<2, 2>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 4: return launch_fused_t<2, 4>(params, maps, a, smem, ntiles, rows, st, occ);
+        case 8: return launch_fused_t<2, 8>(params, maps, a, smem, ntiles, rows, st, occ);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -20,13 +20,6 @@ cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int
 cudaError_t launch_fused_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
 cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
 
-cudaError_t launch_fused_big_nm1(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm2(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm4(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm8(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm10(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm12(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_fused_big_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
 
 cudaError_t launch_wide_nmt1(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
 cudaError_t launch_wide_nmt2(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
@@ -65,22 +58,20 @@ cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const
 // Ring stages of the fused kernel: as many as a CTA's share of the SM's shared
 // memory holds (2..TC_MAX_STAGES), so that more of a chunk's loads are in flight.
 // A half tile (64 rows) keeps 4 KB after the ring: its M = 128 MMA reads 64 rows
-// past the last loaded tile.  The SM-owning form (big) loads 128-row A boxes.
-int fused_ring_stages(int TC, int split, int max_ctas_per_sm, int rows, bool big)
+// past the last loaded tile.
+int fused_ring_stages(int TC, int split, int max_ctas_per_sm, int rows)
 {
-    const int arows = big ? TC_M : rows;
-    const int stage = (arows * 64 + TC * 64) * (split ? 2 : 1);
+    const int stage = (rows * 64 + TC * 64) * (split ? 2 : 1);
     int share = 233472 / max_ctas_per_sm - 2048;  // per CTA: 1 KB reserved, 1 KB static
     if (share > TC_SMEM_DYN_MAX) share = TC_SMEM_DYN_MAX;
-    int ns = (share - 1024 - (TC_M - arows) * 64) / stage;
+    int ns = (share - 1024 - (TC_M - rows) * 64) / stage;
     return ns < 2 ? 2 : (ns > TC_MAX_STAGES ? TC_MAX_STAGES : ns);
 }
 
-int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows, bool big)
+int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows)
 {
-    const int arows = big ? TC_M : rows;
-    const int stage = (arows * 64 + TC * 64) * (split ? 2 : 1);
-    const int ring = fused_ring_stages(TC, split, max_ctas_per_sm, rows, big) * stage + (TC_M - arows) * 64;
+    const int stage = (rows * 64 + TC * 64) * (split ? 2 : 1);
+    const int ring = fused_ring_stages(TC, split, max_ctas_per_sm, rows) * stage + (TC_M - rows) * 64;
     const int warps = rows / 32;
     const int mom = (warps * 32 * (2 * nm_bucket + 1) + fu_ms(nm_bucket) * warps * 6 * nm_bucket) * 4;
     int need = (ring > mom ? ring : mom) + 1024;
@@ -92,32 +83,17 @@ int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int 
 
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
-                                  int rows, int max_ctas, bool big, const double* eq, float* part, double* S1,
-                                  double* S2, float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
+                                  int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
+                                  float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
                                   int* max_ctas_per_sm)
 {
-    if (big ? (rows % 32 != 0 || rows < 32 || rows > FU_BIG_THREADS) : (rows != TC_M && rows != TC_M / 2))
-        return cudaErrorInvalidValue;
+    if (rows != TC_M && rows != TC_M / 2) return cudaErrorInvalidValue;
     int cap = (int)(512u / tmem_cols) < max_ctas ? (int)(512u / tmem_cols) : max_ctas;
-    if (big) cap = 1;
-    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, fused_ring_stages(TC, split, cap, rows, big), tmem_cols, eq, part,
+    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, fused_ring_stages(TC, split, cap, rows), tmem_cols, eq, part,
                 traj, err, S1, S2, em, rrf};
-    const int smem = fused_smem_bytes(nm_bucket, TC, split, cap, rows, big);
-    if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
+    const int smem = fused_smem_bytes(nm_bucket, TC, split, cap, rows);
     const int64_t ntiles = (count + rows - 1) / rows;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
-    if (big) {
-        switch (nm_bucket) {
-            case 1: return launch_fused_big_nm1(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 2: return launch_fused_big_nm2(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 4: return launch_fused_big_nm4(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 8: return launch_fused_big_nm8(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 10: return launch_fused_big_nm10(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 12: return launch_fused_big_nm12(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            case 16: return launch_fused_big_nm16(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
-            default: return cudaErrorInvalidValue;
-        }
-    }
     switch (nm_bucket) {
         case 1: return launch_fused_nm1(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);
         case 2: return launch_fused_nm2(nd_bucket, params, maps, a, smem, (int)ntiles, rows, st, max_ctas_per_sm);

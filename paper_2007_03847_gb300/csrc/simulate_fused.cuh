@@ -34,12 +34,7 @@
 namespace fmc {
 
 constexpr int FU_THREADS = 128;  // full tile; a half tile has 64 threads
-// A CTA that owns its SM (launches that have the GPU to themselves) takes up to
-// FU_BIG_THREADS = 448 threads (14 warps): the samples then spread over the SMs
-// in whole warps (2^16 samples: 13 or 14 warps on every SM instead of 16 on
-// some and 12 on others), and the register budget per thread rises to 144.  Its
-// warps span ceil(warps / 4) MMA tiles of 128 rows, each with its own TMEM columns.
-// steps between flushes of the moment buffer (measured: 8 -> 32 saves 0.8%; 16
+// Steps between flushes of the moment buffer (measured: 8 -> 32 saves 0.8%; 16
 // above 10 machine slots, so that four CTAs' buffers still share an SM)
 __host__ __device__ constexpr int fu_ms(int nm) { return nm > 10 ? 16 : 32; }
 
@@ -58,8 +53,8 @@ struct FusedArgs {
     double* rrf;        // [2]: sums of the response function and its square, or nullptr
 };
 
-template <int NM, int ND, bool BIG>
-__global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4)
+template <int NM, int ND>
+__global__ void __launch_bounds__(FU_THREADS, 4)
     simulate_fused_kernel(const __grid_constant__ SwingParams<NM, ND> p, const __grid_constant__ CUtensorMap mAh,
                           const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBh,
                           const __grid_constant__ CUtensorMap mBl, FusedArgs a)
@@ -75,9 +70,6 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int rows = blockDim.x, warps = rows / 32;  // samples (= threads) and warps of this CTA
-    // MMA tiles of 128 rows (a half tile's MMA still has M = 128: see above)
-    const int tiles = BIG ? (warps + 3) / 4 : 1;
-    const int arows = BIG ? TC_M : rows;  // rows of one A box
     const int n = p.n, d = p.d, S = 2 * n, S3 = 3 * S;
     constexpr int FU_MS = fu_ms(NM);
     constexpr int MSLOT = 6 * NM;  // floats per (step, warp) slot: ref | dev | m2 of up to 2 NM states
@@ -88,7 +80,7 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
 
     // ring (used only while the tensor cores fill TMEM) aliases the moment buffers
     TcRing r;
-    r.a_bytes = arows * 64;
+    r.a_bytes = rows * 64;
     r.b_bytes = TC * 64;
     r.split = a.split;
     r.base = smem;
@@ -115,8 +107,9 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    // the warp's 32 TMEM lanes (sub-partition warp mod 4) in the columns of its MMA tile
-    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * d * TC);
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const int J = d * a.nkb;  // K blocks of a chunk
+    const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
 
     float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND];
@@ -143,11 +136,8 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
     if (part_tile)
         for (int v = tid; v < S3; v += rows) part_tile[v] = 0.f;
 
-    const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
     uint32_t g = 0;  // K blocks issued so far (thread 0)
     float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
-    const int JT = d * a.nkb;  // K blocks per MMA tile
-    const int J = tiles * JT;
 
     for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
@@ -157,12 +147,12 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            // item j: MMA tile t, disturbance wj, K block kb; loads run up to ns - 1
-            // items ahead of the MMAs (a stage is refilled once its MMAs completed)
+            // item j: disturbance wj, K block kb; loads run up to ns - 1 items ahead
+            // of the MMAs (a stage is refilled once its MMAs completed)
             auto load_item = [&](int j) {
-                const int t = j / JT, rem = j - t * JT, wj = rem / a.nkb, kb = rem - wj * a.nkb;
-                return ring_load(r, g + (uint32_t)j, &mAh, &mAl, &mBh, &mBl, wj * a.Ks + kb * TC_BK,
-                                 (int)(row0 + (int64_t)t * TC_M), kb * TC_BK, n0);
+                const int wj = j / a.nkb, kb = j - wj * a.nkb;
+                return ring_load(r, g + (uint32_t)j, &mAh, &mAl, &mBh, &mBl, wj * a.Ks + kb * TC_BK, (int)row0,
+                                 kb * TC_BK, n0);
             };
             bool ok = true;
             int issued = 0;
@@ -173,8 +163,8 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
                     ++issued;
                     if (!ok) break;
                 }
-                const int t = j / JT, rem = j - t * JT, wj = rem / a.nkb, kb = rem - wj * a.nkb;
-                ok = ring_mma(r, g + (uint32_t)j, tmem + (uint32_t)((t * d + wj) * TC), idesc, kb == 0);
+                const int wj = j / a.nkb, kb = j - wj * a.nkb;
+                ok = ring_mma(r, g + (uint32_t)j, tmem + (uint32_t)(wj * TC), idesc, kb == 0);
             }
             g += (uint32_t)J;
             if (ok) {
@@ -291,13 +281,12 @@ __global__ void __launch_bounds__(BIG ? FU_BIG_THREADS : FU_THREADS, BIG ? 1 : 4
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);
 }
 
-template <int NM, int ND, bool BIG>
+template <int NM, int ND>
 cudaError_t launch_fused_t(const void* params, const CUtensorMap* maps, const FusedArgs& a, int smem, int ntiles,
                            int rows, cudaStream_t st, int* max_ctas_per_sm)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
-    if (rows % 32 != 0 || rows > (BIG ? FU_BIG_THREADS : FU_THREADS)) return cudaErrorInvalidValue;
-    auto kern = simulate_fused_kernel<NM, ND, BIG>;
+    auto kern = simulate_fused_kernel<NM, ND>;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);

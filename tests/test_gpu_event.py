@@ -45,7 +45,7 @@ def _rrf_check(rrf, ref_rrf):
     assert abs(v - ref_rrf.var(ddof=1)) <= 1e-4 * ref_rrf.var(ddof=1)
 
 
-@pytest.mark.parametrize("kernel", ["per_sample", "split", "per_sample_sm"])
+@pytest.mark.parametrize("kernel", ["per_sample", "split"])
 @pytest.mark.parametrize("case", ["mm10_trip", "mm7_d4_gain", "mm22_trip", "smib_step"])
 def test_event_fused(fmc, orc, kernel, case):
     sc = _cases()[case]

@@ -33,7 +33,7 @@ def _case(n, seed, N=160, T=0.6):
     return sc.replace(inject=inj, ito=[fs.ito_wind(), fs.ito_gamma(2.0, 4.0), fs.ito_laplace(0.1, 0.05)])
 
 
-@pytest.mark.parametrize("kernel", ["per_sample", "split", "per_sample_sm"])
+@pytest.mark.parametrize("kernel", ["per_sample", "split"])
 @pytest.mark.parametrize("sampling", [fs.LHS, fs.SRS_EM])
 def test_general_disturbances(fmc, orc, kernel, sampling):
     sc = _case(8, 61).replace(sampling=sampling)

@@ -31,10 +31,9 @@ def fmc():
     return need_gpu()
 
 
-@pytest.fixture(params=["per_sample", "split", "per_sample_sm"])
+@pytest.fixture(params=["per_sample", "split"])
 def kernel(fmc, request):
-    """Runs a test with each fused kernel forced (the per-sample one in both its
-    SM-owning and its shared CTA shape), then restores the automatic choice."""
+    """Runs a test with each fused kernel forced, then restores the automatic choice."""
     fmc.set_kernel_policy(request.param)
     yield request.param
     fmc.set_kernel_policy("auto")
@@ -52,8 +51,8 @@ def _same_to_fp32(m, v, m1, v1):
 
 
 def _batch_kernel(fmc, sc):
-    # the kernel and CTA shape a batch (shared GPU) takes for this scenario
-    fmc.set_kernel_policy("per_sample_shared" if sc.n <= 16 else "split")
+    # the kernel a batch (shared GPU) takes for this scenario
+    fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
 
 
 def _zeta_tol(zref):
@@ -208,22 +207,15 @@ def test_simulate_bf16_error_is_stated(fmc, orc, kernel):
 
 @pytest.mark.parametrize("tiles_per_sm", [1, 2, 3, 3.5])
 @pytest.mark.parametrize("d", [1, 3, 6])
-@pytest.mark.parametrize("policy", ["auto", "per_sample_sm"])
-def test_chunk_length_follows_the_tiles(fmc, orc, tiles_per_sm, d, policy):
-    # Shared shape: the time chunk grows when few CTAs share an SM (one, two, or
-    # four per SM give 512, 256 or 128 TMEM columns per CTA); SM-owning shape
-    # (auto on a single call): 1..14 warps per CTA over 1..4 MMA tiles, the chunk
-    # from tiles x d.  Sample counts just under each boundary, a horizon that is
-    # not a multiple of any chunk length; 3.5 tiles per SM leaves the shared
-    # shape unevenly loaded (four CTAs on some SMs, three on others).
+def test_chunk_length_follows_the_tiles(fmc, orc, tiles_per_sm, d):
+    # The time chunk grows when few CTAs share an SM (one, two, or four per SM
+    # give 512, 256 or 128 TMEM columns per CTA): sample counts just under each
+    # boundary, a horizon that is not a multiple of any chunk length; 3.5 tiles
+    # per SM leaves the SMs unevenly loaded (four CTAs on some, three on others).
     sms, _ = fmc.default_context().info()
     N = int(128 * sms * tiles_per_sm) - 37
     sc = fs.multimachine_case(n=4, d=d, K=24, T=0.305, dt=0.005, N=N, seed=40 + d)
-    fmc.set_kernel_policy(policy)
-    try:
-        mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
-    finally:
-        fmc.set_kernel_policy("auto")
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
     fmc.device_status()
     zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
     ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)

@@ -42,8 +42,8 @@ def _same_within_rounding(m, v, m0, v0, n):
 def test_results_same_alone_and_in_the_mix(fmc):
     scs = _mix()
     # alone: the same kernel as the server's (a shared GPU takes the per-sample
-    # kernel in its shared CTA shape for these sizes)
-    fmc.set_kernel_policy("per_sample_shared")
+    # kernel for these sizes)
+    fmc.set_kernel_policy("per_sample")
     try:
         alone = [fmc.simulate(sc, path="fused", precision="bf16x3") for sc in scs]
     finally:

@@ -121,7 +121,7 @@ def test_wide_in_a_batch(fmc):
     fmc.device_status()
     for sc, m, v in zip(scs, means, vars_):
         # the kernel the batch takes for this scenario on a shared GPU
-        fmc.set_kernel_policy("per_sample_shared" if sc.n <= 16 else "split")
+        fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
         m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
         fmc.set_kernel_policy("auto")
         # FP32 merge of tile groups in a single call, FP64 tile sums in the batch:
