@@ -47,7 +47,7 @@ extern "C" {
 #define FMC_NOT_READY 5     /* asynchronous result not available yet */
 #define FMC_EBUSY 6         /* resource in use */
 #define FMC_ECANCELLED 7    /* request cancelled */
-#define FMC_EUNSUPPORTED 8  /* valid request outside what this build handles */
+#define FMC_EUNSUPPORTED 8  /* valid request outside what the library handles */
 #define FMC_ENOCONVERGE 9   /* equilibrium Newton iteration did not converge */
 
 /* ---- sampling modes (Section IV-B) ---------------------------------------- */
@@ -76,7 +76,7 @@ extern "C" {
 #define FMC_PATH_FUSED 0    /* one kernel: contraction in TMEM -> integrator -> moment partials */
 #define FMC_PATH_PLAIN 1    /* unfused FP32: increments and trajectories through HBM */
 
-/* ---- limits of this build -------------------------------------------------- */
+/* ---- limits of the library ------------------------------------------------ */
 #define FMC_MAX_MACHINES 52        /* fused path (17..52 machines: four warps per sample) */
 #define FMC_MAX_MACHINES_PLAIN 16  /* plain FP32 path */
 #define FMC_MAX_DISTURBANCES 8
@@ -294,7 +294,7 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
  * The FP64 equilibrium is solved on the GPU first; the call then waits for the
  * stream once (to read the equilibrium angles, from which the integrator's
  * constants are formed) and enqueues the rest without waiting.
- * Errors: FMC_EINVAL, FMC_EUNSUPPORTED (n or d above this build's limits),
+ * Errors: FMC_EINVAL, FMC_EUNSUPPORTED (n or d above the library's limits),
  * FMC_ENOMEM, FMC_ENOCONVERGE, FMC_ETIMEOUT (a bounded device wait gave up),
  * FMC_ECUDA.
  */
