@@ -75,6 +75,11 @@ struct fmc_ctx {
     size_t prof_cap = 0;
     int last_fused_ctas_per_sm = 0;
     int kernel_policy = FMC_KERNEL_AUTO;
+    // Contexts used on one stream only (the server's) grow their workspace in
+    // stream order on that stream (cudaFreeAsync / cudaMallocAsync) instead of
+    // synchronising the whole device, which would stall every other request.
+    bool stream_ordered = false;
+    cudaStream_t ws_stream = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -127,14 +132,19 @@ static int ensure(fmc_ctx* ctx, DevBuf& b, size_t bytes)
         if (ctx->used - b.bytes + want > ctx->budget)
             return fail(ctx, FMC_ENOMEM, "workspace of %zu bytes exceeds the budget of %zu", bytes, ctx->budget);
     }
+    const bool ordered = ctx->stream_ordered && ctx->ws_stream != nullptr;
     if (b.ptr) {
-        cudaDeviceSynchronize();
-        cudaFree(b.ptr);
+        if (ordered) {
+            cudaFreeAsync(b.ptr, ctx->ws_stream);
+        } else {
+            cudaDeviceSynchronize();
+            cudaFree(b.ptr);
+        }
         ctx->used -= b.bytes;
         b.ptr = nullptr;
         b.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&b.ptr, want);
+    cudaError_t e = ordered ? cudaMallocAsync(&b.ptr, want, ctx->ws_stream) : cudaMalloc(&b.ptr, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, FMC_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
@@ -1109,6 +1119,7 @@ int fmc::simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, dou
 {
     if (!ctx) return FMC_EINVAL;
     if (!s || !mean_dev || !var_dev) return fail(ctx, FMC_EINVAL, "NULL scenario or output");
+    if (ctx->stream_ordered) ctx->ws_stream = st;
     Prepared P;
     int rc = prepare(ctx, ctx->ws, s, 0, s->N, path, st, P, false);  // requests of the server share the GPU
     if (rc) return rc;
@@ -1120,6 +1131,32 @@ int fmc::simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, dou
                              2 * s->n, mean_dev, var_dev, st),
              "moment finalize");
     return FMC_OK;
+}
+
+void fmc::set_stream_ordered(fmc_ctx* ctx, bool on)
+{
+    if (ctx) ctx->stream_ordered = on;
+}
+
+int fmc::reserve_workspace(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int64_t count, cudaStream_t st)
+{
+    if (!ctx || !s) return FMC_EINVAL;
+    int Nt = 0;
+    int rc = check_scenario(ctx, s, &Nt);
+    if (rc) return rc;
+    if (ctx->stream_ordered) ctx->ws_stream = st;
+    // the sizes simulate_moments will need (a shared GPU: AUTO's kernel, atomics)
+    Prepared P;
+    P.s = *s;
+    P.Nt = Nt;
+    P.nm = nm_bucket_for(s->n);
+    P.nmt = P.nm < 0 ? wide_nmt_for(s->n) : 0;
+    P.nd = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+    P.path = path;
+    P.exclusive = false;
+    P.k0 = 0;
+    P.count = count;
+    return reserve(ctx, ctx->ws, P, false, path == FMC_PATH_PLAIN);
 }
 
 extern "C" {

@@ -56,6 +56,14 @@ struct OwnedScenario {
 
 
 
+// Contexts used on one stream only grow their workspace in stream order on it
+// (no device-wide synchronisation); the server's contexts.
+void set_stream_ordered(fmc_ctx* ctx, bool on);
+
+// Grows ctx's workspace to what simulate_moments needs for `count` samples of s
+// (without solving anything), on stream st when the context is stream-ordered.
+int reserve_workspace(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int64_t count, cudaStream_t st);
+
 // fmc_simulate with a choice of how the fused kernel combines its per-time sums:
 // per_tile_partials = true writes FP32 partials per 128-sample tile and adds them
 // in a fixed order (deterministic); false adds them with FP64 atomics (no

@@ -70,6 +70,22 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
     const size_t cols = (size_t)(Nt + 1) * 2 * (size_t)s.n;
     double* dbuf = nullptr;
     if (cudaMallocAsync((void**)&dbuf, sizeof(double) * cols * 2 * R, st) != cudaSuccess) return FMC_ENOMEM;
+    // every replicate's workspace sized once for the largest round this request
+    // may reach, so that no round grows (and reallocates) it
+    {
+        fmc_scenario big = s;
+        int64_t nb = s.N < 2 ? 2 : s.N;
+        while (4 * (int64_t)R * nb <= r->max_N) nb *= 4;
+        big.N = nb;
+        for (int k = 0; k < R; ++k) {
+            const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, nb, rst[k]);
+            if (rc0 != FMC_OK) {
+                r->error = fmc_last_error(rctx[k]);
+                cudaFreeAsync(dbuf, st);
+                return rc0;
+            }
+        }
+    }
     std::vector<double> hm(cols * R), hv(cols * R), mbar(cols), vbar(cols);
     const uint64_t seed0 = s.seed;
     int64_t n = s.N < 2 ? 2 : s.N;
@@ -248,6 +264,7 @@ int fmc_server_create(int device, int32_t slots, size_t mem_budget_bytes, fmc_se
             delete srv;
             return rc;
         }
+        fmc::set_stream_ordered(c, true);  // each is used on its worker's replicate stream only
         srv->ctxs.push_back(c);
     }
     for (int i = 0; i < slots; ++i) srv->workers.emplace_back(worker_loop, srv, i);
@@ -293,14 +310,14 @@ static int submit_request(fmc_server* srv, const fmc_scenario* scen, int32_t pat
     r->tol_E = tol_E;
     r->tol_Var = tol_Var;
     r->max_N = max_N;
-    // charged for the largest design it may draw
+    // charged for the largest design it may draw, in each of its replicates
     fmc_scenario largest = *scen;
     if (target) {
         int64_t n = scen->N;
         while (4 * (int64_t)kReplicates * n <= max_N) n *= 4;
         largest.N = n;
     }
-    r->bytes = request_bytes(largest, path);
+    r->bytes = request_bytes(largest, path) * (target ? (size_t)kReplicates : 1u);
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stopping) return FMC_ECANCELLED;
