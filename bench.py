@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--max-machines", type=int, default=50,
                     help="upper end of the machine count drawn for the batch and serve studies")
     ap.add_argument("--seeds", type=int, default=32)
+    ap.add_argument("--slots", type=int, default=16, help="concurrent requests of the serve study's server")
     return ap.parse_args()
 
 
@@ -374,7 +375,7 @@ def run_serve_study(args):
 
     import paper_2007_03847_gb300 as fmc
     fmc.build()
-    srv = fmc.Server(slots=16, mem_budget_bytes=120 << 30)
+    srv = fmc.Server(slots=args.slots, mem_budget_bytes=120 << 30)
     pool = fs.batched_cases(count=256, seed=1, n_range=(3, args.max_machines))
     rng = np.random.default_rng(0)
     rows = []
@@ -405,7 +406,7 @@ def run_serve_study(args):
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "samples_per_s": samples / t_all, "machine_steps_per_s": msteps / t_all, "wall_s": t_all})
     srv.close()
-    print(json.dumps({"study": "serve", "slots": 16, "budget_bytes": 120 << 30, "replicates": 4,
+    print(json.dumps({"study": "serve", "slots": args.slots, "budget_bytes": 120 << 30, "replicates": 4,
                       "initial_samples_per_design": 256, "max_samples": 1 << 20, "rows": rows}))
     return 0
 

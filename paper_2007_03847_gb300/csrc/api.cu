@@ -1138,6 +1138,25 @@ void fmc::set_stream_ordered(fmc_ctx* ctx, bool on)
     if (ctx) ctx->stream_ordered = on;
 }
 
+int fmc::release_workspace(fmc_ctx* ctx, cudaStream_t st)
+{
+    if (!ctx) return FMC_EINVAL;
+    // the buffers that scale with the samples or the horizon; the small ones stay
+    DevBuf* big[] = {&ctx->ws.zeta_hi, &ctx->ws.zeta_lo, &ctx->ws.phi_hi, &ctx->ws.phi_lo, &ctx->ws.phi32,
+                     &ctx->ws.dW,      &ctx->ws.traj,    &ctx->ws.part,   &ctx->ws.zeta32};
+    for (DevBuf* b : big) {
+        if (!b->ptr) continue;
+        if (ctx->stream_ordered)
+            cudaFreeAsync(b->ptr, st);
+        else
+            cudaFree(b->ptr);
+        ctx->used -= b->bytes;
+        b->ptr = nullptr;
+        b->bytes = 0;
+    }
+    return FMC_OK;
+}
+
 int fmc::reserve_workspace(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int64_t count, cudaStream_t st)
 {
     if (!ctx || !s) return FMC_EINVAL;

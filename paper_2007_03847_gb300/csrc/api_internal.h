@@ -60,6 +60,10 @@ struct OwnedScenario {
 // (no device-wide synchronisation); the server's contexts.
 void set_stream_ordered(fmc_ctx* ctx, bool on);
 
+// Frees the workspace buffers that scale with the samples or the horizon (in
+// stream order on st for a stream-ordered context).
+int release_workspace(fmc_ctx* ctx, cudaStream_t st);
+
 // Grows ctx's workspace to what simulate_moments needs for `count` samples of s
 // (without solving anything), on stream st when the context is stream-ordered.
 int reserve_workspace(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int64_t count, cudaStream_t st);

@@ -225,7 +225,10 @@ static void worker_loop(fmc_server* srv, int slot)
             rc = fmc::device_status_on(rctx[k], rst[k]);
             if (rc != FMC_OK) r->error = fmc_last_error(rctx[k]);
         }
-        // the workspace stays with the slot; the charge is released with the request
+        // the charge is released with the request, and so is the memory it paid
+        // for: the slot's workspaces go back to the device's memory pool (in stream
+        // order), where any slot's next allocation can reuse them
+        for (int k = 0; k < kReplicates; ++k) fmc::release_workspace(rctx[k], rst[k]);
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             r->status = rc;
@@ -256,6 +259,15 @@ int fmc_server_create(int device, int32_t slots, size_t mem_budget_bytes, fmc_se
         mem_budget_bytes = fr / 10 * 8;
     }
     srv->budget = mem_budget_bytes;
+    // keep freed workspace memory in the device's default pool for reuse by the
+    // next requests instead of returning it to the driver at every synchronisation
+    {
+        cudaMemPool_t pool = nullptr;
+        if (cudaSetDevice(device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = (uint64_t)mem_budget_bytes;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     for (int i = 0; i < slots * kReplicates; ++i) {
         fmc_ctx* c = nullptr;
         int rc = fmc_create(&c, device, 0);
