@@ -41,6 +41,9 @@ HEUN = 1
 BASIS_SINE = 0    # Brownian eigenbasis
 BASIS_COSINE = 1  # the paper's cosine white-noise basis
 
+FORCING_INCREMENTS = 0  # Euler-Maruyama on the KL increments of each step
+FORCING_SMOOTH = 1      # the random ODE of Eq. (eqkl): the smooth KL forcing at the RK stage times
+
 
 @dataclasses.dataclass
 class Scenario:
@@ -79,6 +82,9 @@ class Scenario:
     # general Ito disturbances (one dict per disturbance, see ito_* below), or
     # None: every disturbance is Ornstein-Uhlenbeck with theta, sigma
     ito: list | None = None
+    # how the KL path drives the disturbances: FORCING_INCREMENTS (the GPU library
+    # and the oracle) or FORCING_SMOOTH (the oracle only, so far)
+    forcing: int = FORCING_INCREMENTS
 
     @property
     def Nt(self) -> int:

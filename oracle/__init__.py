@@ -96,6 +96,7 @@ class _System(ctypes.Structure):
         ("init_delta", ctypes.c_void_p), ("basis", ctypes.c_int32), ("em", ctypes.c_int32),
         ("em_seed", ctypes.c_uint64), ("em_k0", ctypes.c_int64), ("event_machine", ctypes.c_int32),
         ("event_step", ctypes.c_int32), ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p),
+        ("smooth", ctypes.c_int32),
     ]
 
 
@@ -141,6 +142,11 @@ def _load():
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
             lib.oracle_moments_twopass.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_kl_forcing_basis_ex.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                       ctypes.c_int32, ctypes.c_void_p]
+            lib.oracle_smooth_paths.argtypes = [ctypes.POINTER(_System), ctypes.c_void_p, ctypes.c_int64,
+                                                ctypes.c_int32, ctypes.c_void_p]
+            lib.oracle_smooth_paths.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -199,6 +205,14 @@ def kl_path_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndar
     return psi
 
 
+def kl_forcing_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndarray:
+    """m_k(j dt / 2), j = 0..2 Nt: the time derivatives of the KL basis functions (the
+    smooth forcing of Eq. eqkl is sum_k zeta_k m_k(t)); [K, 2 Nt + 1]."""
+    mdot = np.zeros((K, 2 * Nt + 1), dtype=np.float64)
+    _load().oracle_kl_forcing_basis_ex(basis, K, T, Nt, _ptr(mdot))
+    return mdot
+
+
 def kle_reconstruct(zeta: np.ndarray, d: int, K: int, T: float, Nt: int, basis: int = BASIS_SINE) -> np.ndarray:
     zeta = np.ascontiguousarray(zeta, dtype=np.float64)
     count = zeta.shape[0]
@@ -230,6 +244,7 @@ class _Holder:
         s.event_machine = int(ev if ev is not None else -1)
         s.event_step = int(round(float(getattr(sc, "event_time", 0.0)) / float(sc.dt)))
         s.event_dpm = float(getattr(sc, "event_dpm", 0.0))
+        s.smooth = 1 if int(getattr(sc, "forcing", 0)) == 1 else 0
         specs = getattr(sc, "ito", None)
         if specs is not None:
             self.ito = (_Ito * sc.d)(*[_ito_struct(sp) for sp in specs])
@@ -239,6 +254,20 @@ class _Holder:
         for name, arr in self.arrays.items():
             setattr(s, name, arr.ctypes.data)
         self.s = s
+
+
+def smooth_paths(sc, zeta, q: int = 0, integrator=None) -> np.ndarray:
+    """Disturbance q alone under the smooth forcing (the random ODE of Eq. eqkl), by the
+    scenario's integrator (or the one given) and the simulation's own step:
+    x [count, Nt + 1] for the coefficient rows zeta [count, d K]."""
+    h = _Holder(sc, integrator=integrator)
+    zeta = np.ascontiguousarray(zeta, dtype=np.float64)
+    count = zeta.shape[0]
+    x = np.zeros((count, sc.Nt + 1), dtype=np.float64)
+    rc = _load().oracle_smooth_paths(ctypes.byref(h.s), _ptr(zeta), count, q, _ptr(x))
+    if rc != 0:
+        raise ValueError("oracle_smooth_paths: invalid arguments")
+    return x
 
 
 def electrical_power(sc, delta, form: int = PE_PAIRWISE) -> np.ndarray:

@@ -317,6 +317,31 @@ void oracle_kl_path_basis_ex(int32_t basis, int32_t K, double T, int32_t Nt, dou
             psi[(int64_t)(j - 1) * (Nt + 1) + n] = cos_basis_integral(j, T, (double)n * dt);
 }
 
+/* The forcing of the random ODE of Eq. (eqkl): the time derivatives m_k(t) of
+ * the KL basis functions, dW/dt = sum_k zeta_k m_k(t).  Brownian eigenbasis:
+ * m_k(t) = sqrt(2/T) cos((k - 1/2) pi t / T); Eq. (klb2): m_1 = 1/sqrt(T),
+ * m_j = sqrt(2/T) cos((j - 1) pi t / T).  Sampled at the half-step times
+ * t = j dt / 2, j = 0 .. 2 Nt (the stage times of RK4 and Heun): mdot [K][2Nt+1]. */
+void oracle_kl_forcing_basis_ex(int32_t basis, int32_t K, double T, int32_t Nt, double* mdot)
+{
+    const double hdt = 0.5 * T / (double)Nt;
+    const int32_t J = 2 * Nt + 1;
+    for (int32_t k = 1; k <= K; ++k) {
+        double a, c;
+        if (basis == 0) {
+            a = ((double)k - 0.5) * ORACLE_PI / T;
+            c = sqrt(2.0 / T);
+        } else if (k == 1) {
+            a = 0.0;
+            c = 1.0 / sqrt(T);
+        } else {
+            a = (double)(k - 1) * ORACLE_PI / T;
+            c = sqrt(2.0 / T);
+        }
+        for (int32_t j = 0; j < J; ++j) mdot[(int64_t)(k - 1) * J + j] = c * cos(a * (double)j * hdt);
+    }
+}
+
 /* Eq. (eqkl) as increments: dW[s][w][n] = sum_k zeta[s][w*K + k] phi[k][n]. */
 void oracle_kle_reconstruct(const double* zeta, int64_t count, int32_t d, int32_t K, const double* phi,
                             int32_t Nt, double* dW)
@@ -448,6 +473,13 @@ typedef struct oracle_system {
      * The system is at equilibrium with every disturbance at its x0: the power
      * balance sees inject (x - x0).                                            */
     const oracle_ito* ito;
+    /* 1: the disturbances follow the random ODE of Eq. (eqkl), driven by the
+     * smooth forcing f(t) = sum_k zeta_k m_k(t) and integrated jointly with the
+     * swing equations by the same RK4 or Heun stages (the swing stage j sees the
+     * disturbance's own stage value); 0: Euler-Maruyama on the KL increments.
+     * The smooth paths converge to the Stratonovich solution, so a general Ito
+     * disturbance carries the drift mu - sigma sigma' / 2 (as the KL increments do). */
+    int32_t smooth;
 } oracle_system;
 
 /* Electrical power, textbook pairwise form:
@@ -572,23 +604,100 @@ int oracle_equilibrium(const oracle_system* s, double* delta0, double* pm_eq)
 }
 
 /* ------------------------------------------------------------------------- */
+/* The random ODE of Eq. (eqkl) for disturbance q: dx/dt = mu~(x) + sigma(x) f,   */
+/* f the smooth forcing at the stage time; mu~ = -theta x for the OU disturbance, */
+/* mu - sigma sigma' / 2 for a general one (see oracle_system.smooth).           */
+/* ------------------------------------------------------------------------- */
+static double smooth_rate(const oracle_system* s, int q, double x, double f)
+{
+    if (s->ito && s->ito[q].kind != 0) {
+        const oracle_ito* p = &s->ito[q];
+        double mu = p->m0 + p->m1 * x + p->m2 * x * x - 0.5 * ito_sigma_dsigma(p, x);
+        return mu + ito_sigma(p, x) * f;
+    }
+    return -s->theta[q] * x + s->sigma[q] * f;
+}
+
+/* One step of the disturbance's random ODE from x at grid time t_n, with the
+ * forcing f0 = f(t_n), fh = f(t_n + dt/2), f1 = f(t_{n+1}): the stage values
+ * X[0..3] (RK4; Heun fills X[0..1]) and the new value.                        */
+static double smooth_step(const oracle_system* s, int q, double x, double f0, double fh, double f1, double X[4])
+{
+    const double dt = s->dt;
+    if (s->integrator == 0) {
+        X[0] = x;
+        double k1 = smooth_rate(s, q, X[0], f0);
+        X[1] = x + 0.5 * dt * k1;
+        double k2 = smooth_rate(s, q, X[1], fh);
+        X[2] = x + 0.5 * dt * k2;
+        double k3 = smooth_rate(s, q, X[2], fh);
+        X[3] = x + dt * k3;
+        double k4 = smooth_rate(s, q, X[3], f1);
+        return x + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    }
+    X[0] = x;
+    double k1 = smooth_rate(s, q, X[0], f0);
+    X[1] = x + dt * k1;
+    double k2 = smooth_rate(s, q, X[1], f1);
+    X[2] = X[3] = X[1];
+    return x + 0.5 * dt * (k1 + k2);
+}
+
+/* The disturbance q alone under the smooth forcing (the random ODE of
+ * Eq. (eqkl)), by the system's integrator and the same step as the simulation:
+ * x [count][Nt+1] for the coefficient rows zeta [count][d*K].                 */
+int oracle_smooth_paths(const oracle_system* s, const double* zeta, int64_t count, int32_t q, double* x)
+{
+    const int Nt = s->Nt, K = s->K, d = s->d;
+    if (q < 0 || q >= d || Nt < 1 || K < 1 || count < 1) return -1;
+    const int64_t J = 2 * (int64_t)Nt + 1;
+    double* mdot = (double*)malloc(sizeof(double) * (size_t)K * (size_t)J);
+    double* f = (double*)malloc(sizeof(double) * (size_t)J);
+    oracle_kl_forcing_basis_ex(s->basis, K, s->T, Nt, mdot);
+    for (int64_t smp = 0; smp < count; ++smp) {
+        const double* z = zeta + smp * (int64_t)d * K + (int64_t)q * K;
+        for (int64_t j = 0; j < J; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += z[k] * mdot[(int64_t)k * J + j];
+            f[j] = acc;
+        }
+        double v = (s->ito && s->ito[q].kind != 0) ? s->ito[q].x0 : 0.0;
+        double* row = x + smp * (int64_t)(Nt + 1);
+        row[0] = v;
+        for (int step = 0; step < Nt; ++step) {
+            double X[4];
+            v = smooth_step(s, q, v, f[2 * step], f[2 * step + 1], f[2 * step + 2], X);
+            row[step + 1] = v;
+        }
+    }
+    free(mdot);
+    free(f);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Algorithm 1 step 3: the dynamic simulation of one sample.                   */
 /* ------------------------------------------------------------------------- */
 typedef struct sim_ws {
     double *delta, *omega, *pe, *force, *x, *xn, *xs;
     double *k1d, *k1w, *k2d, *k2w, *k3d, *k3w, *k4d, *k4w, *tmpd, *tmpw;
     double *dW;
+    double *xst;  /* [4][d] stage values of the smooth form */
+    double *f;    /* [d][2 Nt + 1] the smooth forcing of this sample */
 } sim_ws;
 
 static void ws_alloc(sim_ws* w, int n, int d, int Nt)
 {
-    double* buf = (double*)calloc((size_t)(16 * n + 3 * d) + (size_t)d * Nt, sizeof(double));
+    double* buf = (double*)calloc((size_t)(16 * n + 7 * d) + (size_t)d * Nt + (size_t)d * (2 * Nt + 1),
+                                  sizeof(double));
     w->delta = buf; w->omega = buf + n; w->pe = buf + 2 * n; w->force = buf + 3 * n;
     w->k1d = buf + 4 * n; w->k1w = buf + 5 * n; w->k2d = buf + 6 * n; w->k2w = buf + 7 * n;
     w->k3d = buf + 8 * n; w->k3w = buf + 9 * n; w->k4d = buf + 10 * n; w->k4w = buf + 11 * n;
     w->tmpd = buf + 12 * n; w->tmpw = buf + 13 * n;
     w->x = buf + 16 * n; w->xn = w->x + d; w->xs = w->xn + d;
-    w->dW = w->xs + d;
+    w->xst = w->xs + d;
+    w->dW = w->xst + 4 * d;
+    w->f = w->dW + (size_t)d * Nt;
 }
 
 /* Right-hand side of the swing equations at disturbance state xs. */
@@ -620,42 +729,66 @@ static void simulate_one(const oracle_system* s, const double* delta0, const dou
     for (int i = 0; i < n; ++i) { traj[i] = w->delta[i]; traj[n + i] = w->omega[i]; }
     for (int step = 0; step < Nt; ++step) {
         ev = (s->event_machine >= 0 && step >= s->event_step);
-        /* Euler-Maruyama for the OU disturbance (Eq. distito, Table I) */
-        for (int q = 0; q < d; ++q)
-            w->xn[q] = (s->ito && s->ito[q].kind != 0)
-                           ? oracle_ito_step(&s->ito[q], w->x[q], dt, w->dW[(int64_t)q * Nt + step], !s->em)
-                           : w->x[q] + (-s->theta[q] * w->x[q]) * dt + s->sigma[q] * w->dW[(int64_t)q * Nt + step];
+        /* the disturbance values the swing stages see: xa, xb, xc, xd (RK4) or
+         * xa, xb (Heun) */
+        const double *xa, *xb, *xc, *xd;
+        if (s->smooth) {
+            /* the random ODE of Eq. (eqkl), stage by stage with the swing equations */
+            const int64_t J = 2 * (int64_t)Nt + 1;
+            for (int q = 0; q < d; ++q) {
+                const double* f = w->f + (int64_t)q * J + 2 * (int64_t)step;
+                double X[4];
+                w->xn[q] = smooth_step(s, q, w->x[q], f[0], f[1], f[2], X);
+                for (int st = 0; st < 4; ++st) w->xst[st * d + q] = X[st];
+            }
+            xa = w->xst;
+            xb = w->xst + d;
+            xc = w->xst + 2 * d;
+            xd = w->xst + 3 * d;
+        } else {
+            /* Euler-Maruyama for the OU disturbance (Eq. distito, Table I) */
+            for (int q = 0; q < d; ++q)
+                w->xn[q] = (s->ito && s->ito[q].kind != 0)
+                               ? oracle_ito_step(&s->ito[q], w->x[q], dt, w->dW[(int64_t)q * Nt + step], !s->em)
+                               : w->x[q] + (-s->theta[q] * w->x[q]) * dt + s->sigma[q] * w->dW[(int64_t)q * Nt + step];
+            /* RK4 sees x at t_n, at the midpoint as the mean of the grid values, and
+             * at t_{n+1}; Heun sees the grid values */
+            for (int q = 0; q < d; ++q) w->xs[q] = 0.5 * (w->x[q] + w->xn[q]);
+            xa = w->x;
+            xb = (s->integrator == 0) ? w->xs : w->xn;
+            xc = w->xs;
+            xd = w->xn;
+        }
         if (s->integrator == 0) {
             /* classical RK4 */
-            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, ev, w->k1d, w->k1w);
-            for (int q = 0; q < d; ++q) w->xs[q] = 0.5 * (w->x[q] + w->xn[q]);
+            swing_rhs(s, pm_eq, w->delta, w->omega, xa, w, pe_form, ev, w->k1d, w->k1w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k1d[i];
                 w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k1w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, ev, w->k2d, w->k2w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, xb, w, pe_form, ev, w->k2d, w->k2w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + 0.5 * dt * w->k2d[i];
                 w->tmpw[i] = w->omega[i] + 0.5 * dt * w->k2w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xs, w, pe_form, ev, w->k3d, w->k3w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, xc, w, pe_form, ev, w->k3d, w->k3w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + dt * w->k3d[i];
                 w->tmpw[i] = w->omega[i] + dt * w->k3w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, ev, w->k4d, w->k4w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, xd, w, pe_form, ev, w->k4d, w->k4w);
             for (int i = 0; i < n; ++i) {
                 w->delta[i] += dt / 6.0 * (w->k1d[i] + 2.0 * w->k2d[i] + 2.0 * w->k3d[i] + w->k4d[i]);
                 w->omega[i] += dt / 6.0 * (w->k1w[i] + 2.0 * w->k2w[i] + 2.0 * w->k3w[i] + w->k4w[i]);
             }
         } else {
             /* Heun (explicit trapezoid) */
-            swing_rhs(s, pm_eq, w->delta, w->omega, w->x, w, pe_form, ev, w->k1d, w->k1w);
+            swing_rhs(s, pm_eq, w->delta, w->omega, xa, w, pe_form, ev, w->k1d, w->k1w);
             for (int i = 0; i < n; ++i) {
                 w->tmpd[i] = w->delta[i] + dt * w->k1d[i];
                 w->tmpw[i] = w->omega[i] + dt * w->k1w[i];
             }
-            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, w->xn, w, pe_form, ev, w->k2d, w->k2w);
+            swing_rhs(s, pm_eq, w->tmpd, w->tmpw, xb, w, pe_form, ev, w->k2d, w->k2w);
             for (int i = 0; i < n; ++i) {
                 w->delta[i] += 0.5 * dt * (w->k1d[i] + w->k2d[i]);
                 w->omega[i] += 0.5 * dt * (w->k1w[i] + w->k2w[i]);
@@ -702,6 +835,7 @@ typedef struct sim_job {
     const oracle_system* s;
     const double* zeta;
     const double* phi;
+    const double* mdot;  /* [K][2Nt+1] the forcing basis (smooth form) */
     const double* delta0;
     const double* pm_eq;
     const double* shift;
@@ -735,6 +869,17 @@ static void* sim_worker(void* arg)
                     w.dW[(int64_t)q * Nt + step] = acc;
                 }
         }
+        if (s->smooth) {
+            /* f[w][j] = sum_k zeta[w*K + k] m_k(j dt / 2) */
+            const double* z = job->zeta + smp * (int64_t)d * K;
+            const int64_t J = 2 * (int64_t)Nt + 1;
+            for (int q = 0; q < d; ++q)
+                for (int64_t j = 0; j < J; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < K; ++k) acc += z[q * K + k] * job->mdot[(int64_t)k * J + j];
+                    w.f[(int64_t)q * J + j] = acc;
+                }
+        }
         if (job->dW_out) memcpy(job->dW_out + smp * (int64_t)d * Nt, w.dW, sizeof(double) * (size_t)d * Nt);
         double* traj = job->traj_out ? job->traj_out + smp * cols : traj_local;
         simulate_one(s, job->delta0, job->pm_eq, &w, job->pe_form, traj);
@@ -761,12 +906,18 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
     if (nthreads < 1) nthreads = 1;
     if (nthreads > count) nthreads = (int32_t)count;
     int64_t cols = (int64_t)(Nt + 1) * 2 * n;
+    if (s->smooth && s->em) return -1;  /* per-step normals have no smooth form */
     double* phi = (double*)malloc(sizeof(double) * (size_t)s->K * Nt);
     oracle_kl_increment_basis_ex(s->basis, s->K, s->T, Nt, phi);
+    double* mdot = NULL;
+    if (s->smooth) {
+        mdot = (double*)malloc(sizeof(double) * (size_t)s->K * (2 * (size_t)Nt + 1));
+        oracle_kl_forcing_basis_ex(s->basis, s->K, s->T, Nt, mdot);
+    }
     double* delta0 = (double*)malloc(sizeof(double) * n);
     double* pm_eq = (double*)malloc(sizeof(double) * n);
     if (oracle_equilibrium(s, delta0, pm_eq) < 0) {
-        free(phi); free(delta0); free(pm_eq);
+        free(phi); free(mdot); free(delta0); free(pm_eq);
         return -2;
     }
     /* a prescribed initial state (used to test the integrator off equilibrium) */
@@ -782,7 +933,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
     if (want_moments) {
         /* shift = trajectory of the first sample, integrated once on its own */
         shift = (double*)malloc(sizeof(double) * cols);
-        sim_job j0 = {s, zeta, phi, delta0, pm_eq, NULL, 0, 1, pe_form, NULL, shift, NULL, NULL, NULL};
+        sim_job j0 = {s, zeta, phi, mdot, delta0, pm_eq, NULL, 0, 1, pe_form, NULL, shift, NULL, NULL, NULL};
         /* traj_out for sample 0 only points at `shift`; S1 == NULL disables sums */
         sim_worker(&j0);
         S1 = (double*)calloc((size_t)cols * nthreads, sizeof(double));
@@ -791,7 +942,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
     sim_job* jobs = (sim_job*)malloc(sizeof(sim_job) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        jobs[t].s = s; jobs[t].zeta = zeta; jobs[t].phi = phi; jobs[t].delta0 = delta0;
+        jobs[t].s = s; jobs[t].zeta = zeta; jobs[t].phi = phi; jobs[t].mdot = mdot; jobs[t].delta0 = delta0;
         jobs[t].pm_eq = pm_eq; jobs[t].shift = shift;
         jobs[t].s0 = count * t / nthreads;
         jobs[t].s1 = count * (t + 1) / nthreads;
@@ -815,7 +966,7 @@ int oracle_simulate(const oracle_system* s, const double* zeta, int64_t count, i
         }
         free(shift); free(S1); free(S2);
     }
-    free(th); free(jobs); free(phi); free(delta0); free(pm_eq);
+    free(th); free(jobs); free(phi); free(mdot); free(delta0); free(pm_eq);
     return 0;
 }
 

@@ -208,6 +208,9 @@ class ScenarioStruct:
     """fmc_scenario built from an object with the fields of fmc_synth.Scenario."""
 
     def __init__(self, sc, precision=None, sampling=None, integrator=None):
+        if int(getattr(sc, "forcing", 0)) != 0:
+            # the library consumes the KL path as per-step increments only
+            raise FastMCError(EUNSUPPORTED, "the smooth random-ODE forcing is not in the GPU library")
         f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64))
         self.keep = {k: f(getattr(sc, k)) for k in ("G", "B", "H", "D", "E", "Pm", "theta", "sigma", "inject")}
         s = _Scenario()
