@@ -129,6 +129,9 @@ typedef struct fmc_ito {
     double x0;
 } fmc_ito;
 
+#define FMC_FORCING_INCREMENTS 0
+#define FMC_FORCING_SMOOTH 1
+
 typedef struct fmc_scenario {
     int32_t n;              /* machines, 1..FMC_MAX_MACHINES (FMC_MAX_MACHINES_PLAIN on the plain path) */
     int32_t d;              /* disturbances = Wiener processes, 1..FMC_MAX_DISTURBANCES */
@@ -160,7 +163,15 @@ typedef struct fmc_scenario {
      * changes by event_dpm p.u. (negative: generation lost), for whole steps.
      * event_machine < 0: none.  It takes a disturbance slot: d <= 7 with an event. */
     int32_t event_machine;
-    int32_t reserved1;
+    /* How the KL path drives the disturbances: FMC_FORCING_INCREMENTS (default):
+     * Euler-Maruyama (Eq. distito) on the path's increments over each step;
+     * FMC_FORCING_SMOOTH: the random ODE of Eq. (eqkl), dx/dt = mu(x) +
+     * sigma(x) sum_k zeta_k m_k(t) (m_k the time derivative of the KL basis
+     * function; a general disturbance with the Stratonovich drift), stepped by
+     * the same RK4/Heun stages as the swing equations.  The smooth form runs on
+     * the plain path only (FMC_EUNSUPPORTED on the fused path) and not with
+     * FMC_SRS_EM (FMC_EINVAL). */
+    int32_t forcing;
     double event_time;      /* s */
     double event_dpm;       /* p.u. */
     const fmc_ito* ito;     /* [d] disturbance models, or NULL: all Ornstein-Uhlenbeck (theta, sigma) */

@@ -61,7 +61,7 @@ class _Scenario(ctypes.Structure):
         ("G", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Ginf", ctypes.c_void_p), ("Binf", ctypes.c_void_p),
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
-        ("event_machine", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("event_time", ctypes.c_double),
+        ("event_machine", ctypes.c_int32), ("forcing", ctypes.c_int32), ("event_time", ctypes.c_double),
         ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p),
     ]
 
@@ -208,9 +208,6 @@ class ScenarioStruct:
     """fmc_scenario built from an object with the fields of fmc_synth.Scenario."""
 
     def __init__(self, sc, precision=None, sampling=None, integrator=None):
-        if int(getattr(sc, "forcing", 0)) != 0:
-            # the library consumes the KL path as per-step increments only
-            raise FastMCError(EUNSUPPORTED, "the smooth random-ODE forcing is not in the GPU library")
         f = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64))
         self.keep = {k: f(getattr(sc, k)) for k in ("G", "B", "H", "D", "E", "Pm", "theta", "sigma", "inject")}
         s = _Scenario()
@@ -222,6 +219,7 @@ class ScenarioStruct:
         s.integrator = int(getattr(sc, "integrator", RK4) if integrator is None else integrator)
         s.has_inf_bus = 1 if sc.has_inf_bus else 0
         s.basis = int(getattr(sc, "basis", BASIS_SINE))
+        s.forcing = int(getattr(sc, "forcing", FORCING_INCREMENTS))
         specs = getattr(sc, "ito", None)
         if specs is not None:
             arr = (_Ito * int(sc.d))()
@@ -283,6 +281,7 @@ def lhs_sample_split(seed: int, N: int, d: int, K: int, mode: int = LHS, k0: int
 
 
 BASIS_SINE, BASIS_COSINE = 0, 1
+FORCING_INCREMENTS, FORCING_SMOOTH = 0, 1
 
 
 def kl_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE, phi=None, ctx: Context | None = None,

@@ -225,6 +225,10 @@ static int check_scenario(fmc_ctx* ctx, const fmc_scenario* s, int* Nt)
         return fail(ctx, FMC_EINVAL, "integrator %d", s->integrator);
     if (s->basis != FMC_BASIS_SINE && s->basis != FMC_BASIS_COSINE) return fail(ctx, FMC_EINVAL, "basis %d", s->basis);
     if (s->event_machine >= s->n) return fail(ctx, FMC_EINVAL, "event machine %d of %d", s->event_machine, s->n);
+    if (s->forcing != FMC_FORCING_INCREMENTS && s->forcing != FMC_FORCING_SMOOTH)
+        return fail(ctx, FMC_EINVAL, "forcing %d", s->forcing);
+    if (s->forcing == FMC_FORCING_SMOOTH && s->sampling == FMC_SRS_EM)
+        return fail(ctx, FMC_EINVAL, "per-step normals have no smooth forcing");
     if (s->ito) {
         for (int q = 0; q < s->d; ++q) {
             const fmc_ito& m = s->ito[q];
@@ -341,6 +345,7 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
     for (int q = 0; q < d; ++q) {
         p.ou_a[q] = (float)(1.0 - s->theta[q] * s->dt);
         p.ou_s[q] = (float)s->sigma[q];
+        p.th[q] = (float)s->theta[q];
     }
     double hsum = 0.0;
     for (int i = 0; i < n; ++i) hsum += s->H[i];
@@ -817,6 +822,8 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) return fail(ctx, FMC_EINVAL, "path %d", path);
     if (path == FMC_PATH_PLAIN && s->precision != FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the plain path computes in FP32 (precision FMC_PREC_F32)");
+    if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH)
+        return fail(ctx, FMC_EUNSUPPORTED, "the smooth forcing runs on the plain path");
     if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
     const int n = s->n;
@@ -926,9 +933,11 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
     const bool em = (P.s.sampling == FMC_SRS_EM);
     if (P.path == FMC_PATH_PLAIN) {
         const int M = d * K;
+        // the smooth form takes the forcing at the 2 Nt + 1 half-step times
+        const int64_t cols = P.s.forcing == FMC_FORCING_SMOOTH ? 2 * (int64_t)Nt + 1 : (int64_t)Nt;
         if (!em && (rc = ensure(ctx, ws.zeta32, (size_t)count * M * sizeof(float)))) return rc;
-        if (!em && (rc = ensure(ctx, ws.phi32, (size_t)K * Nt * sizeof(float)))) return rc;
-        if ((rc = ensure(ctx, ws.dW, (size_t)count * d * Nt * sizeof(float)))) return rc;
+        if (!em && (rc = ensure(ctx, ws.phi32, (size_t)K * cols * sizeof(float)))) return rc;
+        if ((rc = ensure(ctx, ws.dW, (size_t)count * d * cols * sizeof(float)))) return rc;
         if (!want_traj && (rc = ensure(ctx, ws.traj, (size_t)count * Nt1 * S * sizeof(float)))) return rc;
         return FMC_OK;
     }
@@ -981,13 +990,20 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
                                     st),
                      "lhs kernel");
             prof_end(pr, st);
+            // the increment basis [K][Nt], or the smooth form's forcing basis [K][2 Nt + 1]
+            const bool smooth = (s->forcing == FMC_FORCING_SMOOTH);
+            const int cols = smooth ? 2 * Nt + 1 : Nt;
             prof_begin(ctx, PH_BASIS, st, &pr);
-            FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, s->basis, (float*)ws.phi32.ptr, ctx->sms, st),
-                     "basis kernel");
+            if (smooth)
+                FMC_CUDA(ctx, launch_forcing_f32(K, Nt, s->T, s->basis, (float*)ws.phi32.ptr, ctx->sms, st),
+                         "forcing basis kernel");
+            else
+                FMC_CUDA(ctx, launch_basis_f32(K, Nt, s->T, s->basis, (float*)ws.phi32.ptr, ctx->sms, st),
+                         "basis kernel");
             prof_end(pr, st);
             prof_begin(ctx, PH_CONTRACT, st, &pr);
             FMC_CUDA(ctx,
-                     launch_sgemm_nn(count * d, Nt, K, (const float*)ws.zeta32.ptr, (const float*)ws.phi32.ptr,
+                     launch_sgemm_nn(count * d, cols, K, (const float*)ws.zeta32.ptr, (const float*)ws.phi32.ptr,
                                      (float*)ws.dW.ptr, st),
                      "sgemm kernel");
             prof_end(pr, st);
@@ -995,7 +1011,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         prof_begin(ctx, PH_INTEGRATE, st, &pr);
         FMC_CUDA(ctx,
                  launch_simulate_plain(P.nm, P.nd, P.params.data(), eq, (const float*)ws.dW.ptr, count, Nt, traj, rrf,
-                                       st),
+                                       s->forcing == FMC_FORCING_SMOOTH ? 1 : 0, st),
                  "plain integrator");
         prof_end(pr, st);
         prof_begin(ctx, PH_MOMENTS, st, &pr);

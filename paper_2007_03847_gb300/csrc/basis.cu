@@ -65,6 +65,44 @@ __global__ void basis_split_kernel(int K, int Nt, double T, int basis, int Kpad,
     }
 }
 
+// The forcing of the smooth form (Eq. eqkl as a random ODE): the time
+// derivative of the basis function at the half-step times t = j T / (2 Nt),
+// j = 0..2 Nt.  Brownian eigenbasis: sqrt(2/T) cos((k+1/2) pi t / T) =
+// sqrt(2/T) cospi((2k+1) j / (4 Nt)), the argument reduced modulo 8 Nt; the
+// paper's basis: 1/sqrt(T) (k = 0), sqrt(2/T) cospi(k j / (2 Nt)) (mod 4 Nt).
+__device__ __forceinline__ double forcing_value(int k, int j, int Nt, double T, int basis)
+{
+    if (basis == FMC_BASIS_COSINE) {
+        if (k == 0) return 1.0 / sqrt(T);
+        int64_t m = ((int64_t)k * (int64_t)j) % (4LL * Nt);
+        return sqrt(2.0 / T) * cospi((double)m / (2.0 * Nt));
+    }
+    int64_t m = ((int64_t)(2 * k + 1) * (int64_t)j) % (8LL * Nt);
+    return sqrt(2.0 / T) * cospi((double)m / (4.0 * Nt));
+}
+
+// mdot [K][2 Nt + 1] FP32
+__global__ void forcing_f32_kernel(int K, int Nt, double T, int basis, float* __restrict__ mdot)
+{
+    const int J = 2 * Nt + 1;
+    int64_t total = (int64_t)K * J;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k = (int)(t / J);
+        int j = (int)(t - (int64_t)k * J);
+        mdot[t] = (float)forcing_value(k, j, Nt, T, basis);
+    }
+}
+
+cudaError_t launch_forcing_f32(int K, int Nt, double T, int basis, float* mdot, int sms, cudaStream_t st)
+{
+    int64_t total = (int64_t)K * (2 * (int64_t)Nt + 1);
+    int64_t g = (total + 255) / 256;
+    if (g > sms * 16) g = sms * 16;
+    forcing_f32_kernel<<<(int)g, 256, 0, st>>>(K, Nt, T, basis, mdot);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_basis_f32(int K, int Nt, double T, int basis, float* phi, int sms, cudaStream_t st)
 {
     int64_t total = (int64_t)K * Nt;

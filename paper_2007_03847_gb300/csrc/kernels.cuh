@@ -37,6 +37,8 @@ cudaError_t launch_lhs_split(uint64_t seed, int64_t N, int64_t k0, int64_t count
 cudaError_t launch_em_increments(uint64_t seed, int64_t k0, int64_t count, int d, int Nt, double dt, float* dW,
                                  int sms, cudaStream_t st);
 cudaError_t launch_basis_f32(int K, int Nt, double T, int basis, float* phi, int sms, cudaStream_t st);
+// the smooth form's forcing basis mdot [K][2 Nt + 1] (half-step times), FP32
+cudaError_t launch_forcing_f32(int K, int Nt, double T, int basis, float* mdot, int sms, cudaStream_t st);
 cudaError_t launch_basis_split(int K, int Nt, double T, int basis, int Kpad, void* hi, void* lo, int sms,
                                cudaStream_t st);
 cudaError_t launch_sgemm_nn(int64_t R, int Ncols, int K, const float* A, const float* B, float* C, cudaStream_t st);
@@ -47,8 +49,9 @@ cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G,
                                const double* Binf, const double* E, const double* Pm, double* out, int* status,
                                cudaStream_t st);
 // rrf (nullable): [2] FP64 sums of the response function and its square
+// dW: increments [count][d][Nt]; smooth: the forcing [count][d][2 Nt + 1] instead
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
-                                  int64_t count, int Nt, float* traj, double* rrf, cudaStream_t st);
+                                  int64_t count, int Nt, float* traj, double* rrf, int smooth, cudaStream_t st);
 int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows);
 // rows: samples per CTA, 128 (four warps) or 64 (two warps); max_ctas: resident
 // CTAs per SM allowed (further limited by the TMEM columns)

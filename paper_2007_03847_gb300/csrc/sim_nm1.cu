@@ -17,13 +17,13 @@ cudaError_t launch_fused_nm1(int nd, const void* params, const CUtensorMap* maps
 }
 
 cudaError_t launch_plain_nm1(int nd, const void* params, const double* eq, const float* dW, int64_t count, int Nt,
-                              float* traj, double* rrf, cudaStream_t st)
+                              float* traj, double* rrf, int smooth, cudaStream_t st)
 {
     switch (nd) {
-        case 1: return launch_plain_t<1, 1>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 2: return launch_plain_t<1, 2>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 4: return launch_plain_t<1, 4>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 8: return launch_plain_t<1, 8>(params, eq, dW, count, Nt, traj, rrf, st);
+        case 1: return launch_plain_t<1, 1>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 2: return launch_plain_t<1, 2>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 4: return launch_plain_t<1, 4>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 8: return launch_plain_t<1, 8>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
         default: return cudaErrorInvalidValue;
     }
 }

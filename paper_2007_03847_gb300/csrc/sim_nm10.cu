@@ -17,13 +17,13 @@ cudaError_t launch_fused_nm10(int nd, const void* params, const CUtensorMap* map
 }
 
 cudaError_t launch_plain_nm10(int nd, const void* params, const double* eq, const float* dW, int64_t count, int Nt,
-                              float* traj, double* rrf, cudaStream_t st)
+                              float* traj, double* rrf, int smooth, cudaStream_t st)
 {
     switch (nd) {
-        case 1: return launch_plain_t<10, 1>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 2: return launch_plain_t<10, 2>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 4: return launch_plain_t<10, 4>(params, eq, dW, count, Nt, traj, rrf, st);
-        case 8: return launch_plain_t<10, 8>(params, eq, dW, count, Nt, traj, rrf, st);
+        case 1: return launch_plain_t<10, 1>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 2: return launch_plain_t<10, 2>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 4: return launch_plain_t<10, 4>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 8: return launch_plain_t<10, 8>(params, eq, dW, count, Nt, traj, rrf, smooth, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -6,19 +6,19 @@
 namespace fmc {
 
 cudaError_t launch_fused_nm1(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm1(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm1(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm2(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm2(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm2(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm4(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm4(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm4(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm8(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm8(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm8(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm10(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm10(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm10(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm12(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm12(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 cudaError_t launch_fused_nm16(int, const void*, const CUtensorMap*, const FusedArgs&, int, int, int, cudaStream_t, int*);
-cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, double*, cudaStream_t);
+cudaError_t launch_plain_nm16(int, const void*, const double*, const float*, int64_t, int, float*, double*, int, cudaStream_t);
 
 
 cudaError_t launch_wide_nmt1(int, const CUtensorMap*, const WideArgs&, cudaStream_t, int*);
@@ -107,16 +107,16 @@ cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* para
 }
 
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
-                                  int64_t count, int Nt, float* traj, double* rrf, cudaStream_t st)
+                                  int64_t count, int Nt, float* traj, double* rrf, int smooth, cudaStream_t st)
 {
     switch (nm_bucket) {
-        case 1: return launch_plain_nm1(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 2: return launch_plain_nm2(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 4: return launch_plain_nm4(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 8: return launch_plain_nm8(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 10: return launch_plain_nm10(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 12: return launch_plain_nm12(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
-        case 16: return launch_plain_nm16(nd_bucket, params, eq, dW, count, Nt, traj, rrf, st);
+        case 1: return launch_plain_nm1(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 2: return launch_plain_nm2(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 4: return launch_plain_nm4(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 8: return launch_plain_nm8(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 10: return launch_plain_nm10(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 12: return launch_plain_nm12(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
+        case 16: return launch_plain_nm16(nd_bucket, params, eq, dW, count, Nt, traj, rrf, smooth, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -63,13 +63,114 @@ __global__ void __launch_bounds__(128) simulate_plain_kernel(const __grid_consta
     if (rrf) rrf_accumulate(active ? sqrtf(racc / (float)Nt) : 0.f, rrf);
 }
 
+// The smooth form (FMC_FORCING_SMOOTH): the disturbances follow the random ODE
+// of Eq. (eqkl), dy/dt = rate(y, f(t)) with the forcing F [count][d][2 Nt + 1]
+// at the half-step times (the KL coefficients times the basis functions'
+// derivatives), stepped by the same RK4 / Heun stages as the swing equations;
+// each swing stage sees the disturbance's own stage value.
+template <int NM, int ND>
+__global__ void __launch_bounds__(128) simulate_plain_smooth_kernel(const __grid_constant__ SwingParams<NM, ND> p,
+                                                                    const float* __restrict__ F, int64_t count,
+                                                                    int Nt, float* __restrict__ traj,
+                                                                    double* __restrict__ rrf)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = s < count;
+    if (!active && rrf == nullptr) return;
+    if (!active) s = count - 1;  // computes a duplicate that is neither stored nor counted
+    const int n = p.n;
+    const int d = p.d;
+    const float dt = p.dt;
+    const bool rk4 = (p.integrator == FMC_RK4);
+    float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
+    float x0[ND], f0[ND];
+    const int64_t J = 2 * (int64_t)Nt + 1;
+    const float* fs = F + s * (int64_t)d * J;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        del[i] = 0.f;
+        w[i] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+        x0[q] = 0.f;
+        f0[q] = (q < d) ? __ldg(fs + (int64_t)q * J) : 0.f;
+    }
+    const int64_t row = 2 * (int64_t)n;
+    float* out = traj + s * (int64_t)(Nt + 1) * row;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+        if (i < n && active) {
+            out[i] = p.dst[i];
+            out[n + i] = 0.f;
+        }
+    float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
+    for (int step = 0; step < Nt; ++step) {
+        float xst[4][ND];
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+            float xn = 0.f;
+            if (q < d) {
+                const float fh = __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 1);
+                const float f1 = __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 2);
+                const float x = x0[q];
+                const float k1 = smooth_rate<NM, ND>(p, q, x, f0[q]);
+                if (rk4) {
+                    const float X2 = fmaf(0.5f * dt, k1, x);
+                    const float k2 = smooth_rate<NM, ND>(p, q, X2, fh);
+                    const float X3 = fmaf(0.5f * dt, k2, x);
+                    const float k3 = smooth_rate<NM, ND>(p, q, X3, fh);
+                    const float X4 = fmaf(dt, k3, x);
+                    const float k4 = smooth_rate<NM, ND>(p, q, X4, f1);
+                    xst[0][q] = x;
+                    xst[1][q] = X2;
+                    xst[2][q] = X3;
+                    xst[3][q] = X4;
+                    xn = fmaf(dt * (1.0f / 6.0f), (k1 + 2.f * k2) + (2.f * k3 + k4), x);
+                } else {
+                    const float X2 = fmaf(dt, k1, x);
+                    const float k2 = smooth_rate<NM, ND>(p, q, X2, f1);
+                    xst[0][q] = x;
+                    xst[1][q] = X2;
+                    xst[2][q] = X2;
+                    xst[3][q] = X2;
+                    xn = fmaf(0.5f * dt, k1 + k2, x);
+                }
+                f0[q] = f1;
+            } else {
+                // padding: 0; the event slot: 0 before the event's grid step, 1 from it
+                const float ev = (q == p.ev_slot && step >= p.ev_step) ? 1.f : 0.f;
+                xst[0][q] = xst[1][q] = xst[2][q] = xst[3][q] = ev;
+                xn = ev;
+            }
+            x0[q] = xn;
+        }
+        swing_step_staged<NM, ND>(p, del, w, theta, xst);
+        const float c = coi_speed<NM, ND>(p, w);
+        racc = fmaf(c, c, racc);
+        if (!active) continue;
+        float* o = out + (int64_t)(step + 1) * row;
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+            if (i < n) {
+                o[i] = (theta + del[i]) + p.dst[i];
+                o[n + i] = w[i];
+            }
+    }
+    if (rrf) rrf_accumulate(active ? sqrtf(racc / (float)Nt) : 0.f, rrf);
+}
+
+// dW: the increments [count][d][Nt], or with smooth the forcing [count][d][2 Nt + 1].
 template <int NM, int ND>
 cudaError_t launch_plain_t(const void* params, const double* eq, const float* dW, int64_t count, int Nt, float* traj,
-                           double* rrf, cudaStream_t st)
+                           double* rrf, int smooth, cudaStream_t st)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
     int64_t g = (count + 127) / 128;
-    simulate_plain_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, eq, dW, count, Nt, traj, rrf);
+    if (smooth)
+        simulate_plain_smooth_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, dW, count, Nt, traj, rrf);
+    else
+        simulate_plain_kernel<NM, ND><<<(unsigned)g, 128, 0, st>>>(p, eq, dW, count, Nt, traj, rrf);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,7 @@ struct SwingParams {
     int ev_slot;
     int ev_step;
     ItoParams<ND> ito;           // general disturbances (ito.on == 0: all OU)
+    float th[ND];                // theta_w, the OU rate (the smooth form's drift; 0 in padding and the event slot)
 };
 
 // The event slot's value for the step that starts at grid index `step`.
@@ -157,9 +158,10 @@ __device__ __forceinline__ void sin_cosm1_any(float a, float* sn, float* cm1)
 // stages.  The disturbance enters stage st at x0 + xw (x1 - x0): RK4 xw = 0,
 // 1/2, 1/2, 1 (the midpoint value is the average of the two grid values), Heun
 // xw = 0, 1.
-template <int NM, int ND>
-__device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
-                                           float& theta, const float (&x0)[ND], const float (&x1)[ND])
+template <int NM, int ND, bool STAGED>
+__device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
+                                                float& theta, const float (&x0)[ND], const float (&x1)[ND],
+                                                const float (&xst)[4][ND])
 {
     const float dt = p.dt;
     const bool rk4 = (p.integrator == FMC_RK4);
@@ -187,8 +189,16 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
             xw = (st == 0) ? 0.f : 1.f;
         }
         float xs[ND];
+        if constexpr (STAGED) {
+            // the smooth form: the disturbances' own stage values (a select, the
+            // stage loop is not unrolled)
 #pragma unroll
-        for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
+            for (int q = 0; q < ND; ++q)
+                xs[q] = st == 0 ? xst[0][q] : (st == 1 ? xst[1][q] : (st == 2 ? xst[2][q] : xst[3][q]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
+        }
         float ga[NM], et[NM];
         bool big = false;
 #pragma unroll
@@ -267,6 +277,23 @@ __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (
     theta = fmaf(h, ath, theta);
 }
 
+// The disturbance entering stage st at x0 + xw (x1 - x0) (see swing_step_impl).
+template <int NM, int ND>
+__device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
+                                           float& theta, const float (&x0)[ND], const float (&x1)[ND])
+{
+    const float unused[4][ND] = {};
+    swing_step_impl<NM, ND, false>(p, del, w, theta, x0, x1, unused);
+}
+
+// The smooth form: the disturbance's value at RK stage st is xst[st] (Heun: st < 2).
+template <int NM, int ND>
+__device__ __forceinline__ void swing_step_staged(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
+                                                  float& theta, const float (&xst)[4][ND])
+{
+    swing_step_impl<NM, ND, true>(p, del, w, theta, xst[0], xst[3], xst);
+}
+
 // One step of a general disturbance (see ItoParams) in the deviation y.
 template <int ND>
 __device__ __forceinline__ float ito_step1(const ItoParams<ND>& it, int q, float ou_a, float ou_s, float y, float dw,
@@ -287,6 +314,29 @@ __device__ __forceinline__ float ito_step1(const ItoParams<ND>& it, int q, float
     }
     const float drift = fmaf(-0.5f * it.strat, corr, mu);
     return fmaf(sg, dw, fmaf(drift, dt, y));
+}
+
+// The smooth form's rate of disturbance q at deviation y under forcing f:
+// dy/dt = -theta y + sigma f (OU), or the general model's drift with the
+// Stratonovich correction (its limit on a smooth path) plus sigma(y) f.
+template <int NM, int ND>
+__device__ __forceinline__ float smooth_rate(const SwingParams<NM, ND>& p, int q, float y, float f)
+{
+    const ItoParams<ND>& it = p.ito;
+    if (!it.on || it.kind[q] == FMC_ITO_OU) return fmaf(-p.th[q], y, p.ou_s[q] * f);
+    const float mu = fmaf(fmaf(it.c2[q], y, it.c1[q]), y, it.c0[q]);
+    float sg, corr;
+    if (it.kind[q] == FMC_ITO_POLY) {
+        sg = fmaf(fmaf(it.e2[q], y, it.e1[q]), y, it.e0[q]);
+        corr = sg * fmaf(2.f * it.e2[q], y, it.e1[q]);
+    } else {
+        const float dy = y - it.ap[q];
+        const float v = fmaf(it.e3[q], fabsf(dy), fmaf(fmaf(it.e2[q], y, it.e1[q]), y, it.e0[q]));
+        sg = v > 0.f ? sqrtf(v) : 0.f;
+        const float sgn = dy > 0.f ? 1.f : (dy < 0.f ? -1.f : 0.f);
+        corr = v > 0.f ? 0.5f * fmaf(it.e3[q], sgn, fmaf(2.f * it.e2[q], y, it.e1[q])) : 0.f;
+    }
+    return fmaf(sg, f, fmaf(-0.5f, corr, mu));
 }
 
 // One Euler-Maruyama step of the OU disturbances: x1 = (1 - theta dt) x0 + sigma dW.
