@@ -93,3 +93,21 @@ def test_binding_structs_match_the_header(tmp_path):
             continue
         cls = {"s": fmc._Scenario, "r": fmc._Result, "i": fmc._Ito}[kind]
         assert getattr(cls, name).offset == int(off), (kind, name)
+
+
+def test_scenario_marshalling_carries_the_options():
+    """The binding's fmc_scenario carries every option of a synthetic scenario
+    (pure marshalling, no library call)."""
+    import fmc_synth as fs
+    import paper_2007_03847_gb300 as fmc
+    sc = fs.multimachine_case(n=4, d=2, K=7, T=0.5, dt=0.005, N=33, seed=9).replace(
+        forcing=fs.FORCING_SMOOTH, basis=fs.BASIS_COSINE, integrator=fs.HEUN, sampling=fs.LHS_MIDPOINT,
+        event_machine=2, event_time=0.1, event_dpm=-0.3, ito=[fs.ito_gamma(2.0, 4.0), None])
+    st = fmc.ScenarioStruct(sc, precision="f32")
+    s = st.s
+    assert (s.n, s.d, s.K, s.N, s.seed) == (4, 2, 7, 33, 9)
+    assert s.forcing == fmc.FORCING_SMOOTH and s.basis == fmc.BASIS_COSINE
+    assert s.integrator == fmc.HEUN and s.sampling == fs.LHS_MIDPOINT
+    assert s.event_machine == 2 and s.event_time == 0.1 and s.event_dpm == -0.3
+    assert s.ito and st.ito[0].kind == fmc.ITO_SQRT and st.ito[1].kind == 0
+    assert fmc.ScenarioStruct(sc.replace(forcing=fs.FORCING_INCREMENTS)).s.forcing == fmc.FORCING_INCREMENTS
