@@ -62,7 +62,6 @@ uint64_t mix64(uint64_t x)
 // until the replicate spread meets the targets or max_N is reached.
 int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
 {
-    fmc_ctx* ctx = rctx[0];
     cudaStream_t st = rst[0];
     fmc_scenario s = r->scen->s;
     const int R = kReplicates;
