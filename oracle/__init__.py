@@ -147,6 +147,7 @@ def _load():
             lib.oracle_smooth_paths.argtypes = [ctypes.POINTER(_System), ctypes.c_void_p, ctypes.c_int64,
                                                 ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_smooth_paths.restype = ctypes.c_int
+            lib.oracle_plant_stage_forcing.argtypes = [ctypes.c_int32]
             _lib = lib
     return _lib
 
@@ -268,6 +269,13 @@ def smooth_paths(sc, zeta, q: int = 0, integrator=None) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle_smooth_paths: invalid arguments")
     return x
+
+
+def plant_stage_forcing(mode: int) -> None:
+    """Test hook: plants a known mistake in the disturbance values the RK stages see
+    (1: x_n at every stage; 2: x_{n+1} at the midpoint stages; 0: none), so that a
+    pin can show it catches it.  Process-wide; reset to 0 after use."""
+    _load().oracle_plant_stage_forcing(int(mode))
 
 
 def electrical_power(sc, delta, form: int = PE_PAIRWISE) -> np.ndarray:

@@ -715,6 +715,15 @@ static void swing_rhs(const oracle_system* s, const double* pm_eq, const double*
     }
 }
 
+/* Test hook, off unless a pin test turns it on: plants a known mistake in the
+ * disturbance values the swing stages see (increment form only), so that the
+ * stage-forcing pin can show that it catches one.  1: x_n at every stage (the
+ * forcing lags by half a step); 2: x_{n+1} at the two midpoint stages.  Not
+ * thread-safe; tests set it around single-threaded calls.                    */
+static int32_t g_stage_plant = 0;
+
+void oracle_plant_stage_forcing(int32_t mode) { g_stage_plant = mode; }
+
 /* Integrates one sample whose increments are dW[w][n]; writes the trajectory
  * traj[n][j] (j < n: delta_j, j >= n: domega_j) for n = 0..Nt.  An event (see
  * oracle_system) acts on whole steps from step event_step on.                 */
@@ -758,6 +767,8 @@ static void simulate_one(const oracle_system* s, const double* delta0, const dou
             xb = (s->integrator == 0) ? w->xs : w->xn;
             xc = w->xs;
             xd = w->xn;
+            if (g_stage_plant == 1) { xb = w->x; xc = w->x; xd = w->x; }
+            if (g_stage_plant == 2 && s->integrator == 0) { xb = w->xn; xc = w->xn; }
         }
         if (s->integrator == 0) {
             /* classical RK4 */
