@@ -79,17 +79,35 @@ def workload_name(args) -> str:
             f"K=200, T={args.horizon:g}s, dt=5ms, N={args.samples}, LHS")
 
 
-def algorithmic_flops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
-    """FP32 work of one sample over one time step in the deviation form of the
-    swing equations, counted as FMA-pipe operations (each FMA, multiply or add
-    = one operation = 2 flop at the FMA rate).  Per RK stage and machine:
-    sin/cos series of the angle deviation 11, cos/sin expansion (gamma, eta) 4,
-    network products 4(n-1), electrical-power deviation 6, forcing d,
-    derivatives 5, RK accumulate and next-stage input 4; per step the state
-    update 2n and Euler-Maruyama plus stage forcing 6d."""
-    per_stage = n * (4 * (n - 1) + 30 + d)
-    ops = integrator_stages * per_stage + 2 * n + 6 * d
-    return 2.0 * ops
+def algorithmic_flops_per_machine_step(n: int, integrator_stages: int = 4) -> float:
+    """The method's FP32 work per machine and time step: per RK stage and machine
+    4n + 8 FMA (the network sums u = G a - B b, v = G b + B a of the product form,
+    4n; the angle's cosine and sine scaled by E, the electrical power a u + b v,
+    the two derivatives and the RK accumulation, 8), i.e. 16n + 32 FMA per RK4
+    step, 2 flop each.  The sine and cosine themselves belong to the MUFU pipe in
+    this count (4 sincos per machine-step) and are reported apart."""
+    return 2.0 * integrator_stages * (4 * n + 8)
+
+
+def implementation_ops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
+    """What the fused kernel actually executes on the FP32 pipe per sample and step,
+    counted from its source (every FMA, multiply or add = one operation; a packed
+    FMA = two): per RK stage and machine the short sin / cos - 1 series of the
+    angle deviation (5), the rotated network sums 4(n-1), the electrical-power
+    deviation (3), the forcing d + 1, the derivatives (1) and the RK accumulate
+    and next-stage input (4); per step the state update 2n and the stage forcing
+    of the disturbances 3d.  Only for the issue-level fraction reported beside
+    the algorithmic one."""
+    per_stage = n * (4 * (n - 1) + 14 + d)
+    return float(integrator_stages * per_stage + 2 * n + 3 * d)
+
+
+def algorithmic_bytes_per_launch(N: int, n: int, d: int, K: int, Nt: int, split: bool = True) -> float:
+    """HBM bytes the method must move per launch: the design zeta [N][d K] in BF16
+    (hi and lo for the split form), the increment basis [Nt][K] likewise, and the
+    FP64 mean and variance [Nt+1][2n] written out."""
+    parts = 2 if split else 1
+    return float(parts * 2 * N * d * K + parts * 2 * Nt * K + 2 * 8 * (Nt + 1) * 2 * n)
 
 
 class ClockSampler:
@@ -555,22 +573,35 @@ def main():
     ms_per_step = total_ms / args.steps
     value = sc.N * Nt * n / (ms_per_step / 1e3)
 
-    # roofline of the dominant kernel: FP32 FMA pipe
+    # roofline of the dominant kernel: FP32 FMA pipe, on the method's own count
     kernel_ms = k_ms / max(1, k_launches)
-    flops_per_launch = algorithmic_flops_per_sample_step(n, sc.d) * count * Nt
+    stages = 4
+    units_per_launch = count * Nt * n
+    flops_per_launch = algorithmic_flops_per_machine_step(n, stages) * units_per_launch
     achieved_tflops = flops_per_launch / (kernel_ms / 1e3) / 1e12
     mhz = clk.get("sm_mhz") or (measured_peaks() or {}).get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
     peak_tflops = sms * 128 * 2 * mhz * 1e6 / 1e12
+    # MUFU: 16 lanes per SM and clock; the method's 4 sincos per machine-step as 8 MUFU operations
+    mufu_ops = 8.0 * units_per_launch
+    mufu_peak = sms * 16 * mhz * 1e6
+    impl_ops = implementation_ops_per_sample_step(n, sc.d, stages) * count * Nt
     traffic = profiled_traffic() if (path == "fused" and precision == "bf16x3" and sc.N == (1 << 16)
                                      and Nt == 4000 and n == 10 and world == 1) else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                "algorithmic_bytes": algorithmic_bytes_per_launch(count, n, sc.d, sc.K, Nt, precision == "bf16x3"),
                 "kernel": ("simulate_wide_kernel" if n > 16 else "simulate_fused_kernel") if path == "fused"
                           else "simulate_plain_kernel",
                 "kernel_ms": kernel_ms,
-                "peak_note": f"FP32 FMA pipe: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (median SM clock "
-                             f"sampled during the timed region); achieved counts the method's FP32 operations "
-                             f"({algorithmic_flops_per_sample_step(n, sc.d) / 2:.0f} per sample-step) at 2 flop each"}
+                "peak_note": f"FP32 FMA pipe, of measured clock: {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz "
+                             f"(median SM clock sampled during the timed region); achieved counts the method's "
+                             f"16n+32 FMA per machine-step ({algorithmic_flops_per_machine_step(n, stages):.0f} flop "
+                             f"at n={n}) x {units_per_launch} machine-steps per launch / kernel time",
+                "mufu_frac": mufu_ops / (kernel_ms / 1e3) / mufu_peak,
+                "implementation_frac": 2.0 * impl_ops / (kernel_ms / 1e3) / 1e12 / peak_tflops,
+                "implementation_note": f"the kernel's own FP32-pipe operations "
+                                       f"({implementation_ops_per_sample_step(n, sc.d, stages):.0f} per sample-step, "
+                                       f"sin/cos series and bookkeeping included) against the same peak"}
 
     # end to end through the public API: scenario from host memory, moments read back
     e2e = None

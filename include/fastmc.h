@@ -267,11 +267,17 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
  * and results as fmc_kle_reconstruct.
  *
  * Limits and behaviour:
- *   - A call needs 2*align256(count*d*round_up(K,8)*2) + 2*align256(Nt*round_up(K,32)*2)
- *     + 256 bytes (BF16/BF16X3) or align256(K*Nt*4) bytes (F32); a larger call
+ *   - A call needs 256 + 2*align256(count*d*round_up(K,8)*2) + 2*align256(Nt*round_up(K,32)*2)
+ *     bytes (BF16/BF16X3) or 256 + align256(K*Nt*4) bytes (F32); a larger call
  *     returns FMC_EINVAL and says so in fmc_last_error.
+ *   - The caller's current device must be the context's device (FMC_EINVAL
+ *     otherwise): the kernels run on the current device and address its array.
  *   - The first call on a device looks up the array's device address with that
  *     device current; make that first call before any stream capture.
+ *   - The array's first 256 bytes hold the call's device error word, cleared at
+ *     the start of every call.  fmc_device_status reads it (after synchronising
+ *     the device): FMC_ETIMEOUT if a bounded wait of the contraction gave up, in
+ *     which case dW is not valid.  It reports the last call on the device.
  *   - All calls share the one array and it keeps the last call's contents: calls
  *     whose work overlaps on the GPU (different streams, or different host
  *     threads) race.  Serialise them on one stream.
@@ -279,6 +285,23 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
 #define FMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
                                 double dt, int32_t precision, float* dW_dev, void* stream);
+
+/*
+ * Self-check of the failure-detection path (no counterpart in the paper).  Every
+ * spin of the library's kernels on an mbarrier is bounded; when it runs out the
+ * kernel records a timeout code in a device status word and returns, and
+ * fmc_device_status reports FMC_ETIMEOUT.  This call exercises that path without
+ * a fault: it clears the status word and launches one CTA whose thread waits, at
+ * most poll_limit polls (1 .. 2^24), on an mbarrier that nothing arrives at,
+ * with no bulk copy or MMA in flight, so the wait runs out and the timeout is
+ * recorded.
+ *   target 0: the context's status word (as fmc_simulate's kernels use it);
+ *   target 1: the allocation-free reconstruction's word in its scratch array
+ *             (same device rule as fmc_kle_reconstruct_noalloc).
+ * Asynchronous on `stream`; a following fmc_device_status returns FMC_ETIMEOUT.
+ * Errors: FMC_EINVAL (target, poll_limit, device), FMC_ENOMEM, FMC_ECUDA.
+ */
+int fmc_check_wait_path(fmc_ctx* ctx, int32_t target, int64_t poll_limit, void* stream);
 
 /* ---- equilibrium (Section V-A: "at equilibrium at t = 0") --------------------- */
 

@@ -129,6 +129,7 @@ def load_library():
             "fmc_server_stats": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)],
                                  ctypes.c_int),
             "fmc_kle_reconstruct_noalloc": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
+            "fmc_check_wait_path": ([vp, i32, i64, vp], ctypes.c_int),
             "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_moments_from_sums": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         }
@@ -558,6 +559,14 @@ def device_status(ctx: Context | None = None):
     it, err = ctypes.c_int(), ctypes.c_int()
     ctx.check(ctx.lib.fmc_device_status(ctx.h, ctypes.byref(it), ctypes.byref(err)))
     return it.value, err.value
+
+
+def check_wait_path(target: int = 0, poll_limit: int = 1000, ctx: Context | None = None, stream=None):
+    """fmc_check_wait_path: a bounded device wait that runs out on purpose (no fault);
+    the next device_status raises FastMCError with code ETIMEOUT.  target 0: the
+    context's status word; 1: the allocation-free reconstruction's."""
+    ctx = ctx or default_context()
+    ctx.check(ctx.lib.fmc_check_wait_path(ctx.h, target, poll_limit, _stream(stream)))
 
 
 def profile(enable: bool, max_records: int = 100000, ctx: Context | None = None):

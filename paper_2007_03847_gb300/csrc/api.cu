@@ -563,6 +563,19 @@ static int noalloc_scratch(fmc_ctx* ctx, unsigned char** out)
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The first bytes of the scratch array: word 1 is the last allocation-free
+// call's device error code (0: none), read by fmc_device_status.
+static constexpr size_t NOALLOC_STATUS_BYTES = 256;
+
+// The device address of the scratch array on the context's device if an
+// allocation-free call (or the self-check) has looked it up, else nullptr.
+static void* noalloc_scratch_if_known(const fmc_ctx* ctx)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    const int dev = ctx->device;
+    return (dev >= 0 && dev < 64) ? g_noalloc_addr[dev] : nullptr;
+}
+
 extern "C" {
 
 int fmc_create(fmc_ctx** out, int device, size_t mem_budget_bytes)
@@ -728,21 +741,30 @@ int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t cou
     if (precision != FMC_PREC_F32 && precision != FMC_PREC_BF16 && precision != FMC_PREC_BF16X3)
         return fail(ctx, FMC_EINVAL, "precision %d", precision);
     cudaStream_t st = (cudaStream_t)stream;
+    // the kernels run on the caller's current device, which must be the one whose
+    // scratch array is addressed
+    int cur = -1;
+    FMC_CUDA(ctx, cudaGetDevice(&cur), "cudaGetDevice");
+    if (cur != ctx->device)
+        return fail(ctx, FMC_EINVAL, "the current device (%d) is not the context's device (%d)", cur, ctx->device);
     const int Ks = round_up(K, 8);
     const int Kpad = round_up(K, TC_BK);
-    // layout of the scratch array for this call
+    // layout of the scratch array for this call: the status words first, at a
+    // fixed place that fmc_device_status reads, then the working buffers
     size_t need;
-    size_t o_zhi = 0, o_zlo = 0, o_phi_hi = 0, o_phi_lo = 0, o_status = 0, o_phi32 = 0;
+    const size_t o_status = 0;
+    size_t o_zhi = 0, o_zlo = 0, o_phi_hi = 0, o_phi_lo = 0, o_phi32 = 0;
     if (precision == FMC_PREC_F32) {
-        need = align256((size_t)K * Nt * sizeof(float));
+        o_phi32 = NOALLOC_STATUS_BYTES;
+        need = o_phi32 + align256((size_t)K * Nt * sizeof(float));
     } else {
         const size_t zb = align256((size_t)count * d * Ks * 2);
         const size_t pb = align256((size_t)Nt * Kpad * 2);
-        o_zlo = zb;
-        o_phi_hi = 2 * zb;
-        o_phi_lo = 2 * zb + pb;
-        o_status = 2 * zb + 2 * pb;
-        need = o_status + 256;
+        o_zhi = NOALLOC_STATUS_BYTES;
+        o_zlo = o_zhi + zb;
+        o_phi_hi = o_zlo + zb;
+        o_phi_lo = o_phi_hi + pb;
+        need = o_phi_lo + pb;
     }
     if (need > (size_t)FMC_NOALLOC_SCRATCH_BYTES)
         return fail(ctx, FMC_EINVAL,
@@ -752,6 +774,9 @@ int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t cou
     if (count > (int64_t(1) << 31) - 256) return fail(ctx, FMC_EINVAL, "count too large for the tensor-core path");
     unsigned char* base = nullptr;
     if ((rc = noalloc_scratch(ctx, &base))) return rc;
+    int* status = reinterpret_cast<int*>(base + o_status);
+    // the array keeps the previous call's contents: the error word must start at zero
+    FMC_CUDA(ctx, cudaMemsetAsync(status, 0, NOALLOC_STATUS_BYTES, st), "memset");
     if (precision == FMC_PREC_F32) {
         float* phi32 = reinterpret_cast<float*>(base + o_phi32);
         FMC_CUDA(ctx, launch_basis_f32(K, Nt, T, FMC_BASIS_SINE, phi32, ctx->sms, st), "basis kernel");
@@ -765,14 +790,11 @@ int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t cou
     void* zlo = base + o_zlo;
     void* phi_hi = base + o_phi_hi;
     void* phi_lo = base + o_phi_lo;
-    int* status = reinterpret_cast<int*>(base + o_status);
     FMC_CUDA(ctx, launch_split_rows(zeta_dev, count, d, K, Ks, zhi, zlo, st), "split");
     FMC_CUDA(ctx, launch_basis_split(K, Nt, T, FMC_BASIS_SINE, Kpad, phi_hi, phi_lo, ctx->sms, st), "basis");
     CUtensorMap maps[4];
     if ((rc = make_contract_maps_at(ctx, maps, zhi, zlo, phi_hi, phi_lo, count, d, Ks, Nt, Kpad, TN, split)))
         return rc;
-    // the array keeps the previous call's contents: the error word must start at zero
-    FMC_CUDA(ctx, cudaMemsetAsync(status, 0, 256, st), "memset");
     FMC_CUDA(ctx, launch_contract_tc(maps, count, d, Ks, nkb, Nt, TN, split, dW_dev, status + 1, st),
              "tensor-core contraction");
     return FMC_OK;
@@ -1485,19 +1507,49 @@ int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error)
 {
     if (!ctx) return FMC_EINVAL;
     int h[2] = {0, 0};
-    if (!ctx->status.ptr) {
-        if (eq_iterations) *eq_iterations = 0;
-        if (kernel_error) *kernel_error = 0;
-        return FMC_OK;
-    }
-    FMC_CUDA(ctx, cudaDeviceSynchronize(), "sync");
-    FMC_CUDA(ctx, cudaMemcpy(h, ctx->status.ptr, sizeof h, cudaMemcpyDeviceToHost), "copy");
+    int hn[2] = {0, 0};
+    void* scratch = noalloc_scratch_if_known(ctx);
+    if (ctx->status.ptr || scratch) FMC_CUDA(ctx, cudaDeviceSynchronize(), "sync");
+    if (ctx->status.ptr) FMC_CUDA(ctx, cudaMemcpy(h, ctx->status.ptr, sizeof h, cudaMemcpyDeviceToHost), "copy");
+    // the allocation-free reconstruction keeps its error word in the scratch array
+    if (scratch) FMC_CUDA(ctx, cudaMemcpy(hn, scratch, sizeof hn, cudaMemcpyDeviceToHost), "copy");
     if (eq_iterations) *eq_iterations = h[0];
-    if (kernel_error) *kernel_error = h[1];
+    if (kernel_error) *kernel_error = h[1] != 0 ? h[1] : hn[1];
     if (h[0] < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
     if (h[1] == DEV_TIMEOUT_MMA || h[1] == DEV_TIMEOUT_TMA)
         return fail(ctx, FMC_ETIMEOUT, "a bounded device wait gave up (code %d)", h[1]);
     if (h[1] != 0) return fail(ctx, FMC_ECUDA, "device error %d", h[1]);
+    if (hn[1] == DEV_TIMEOUT_MMA || hn[1] == DEV_TIMEOUT_TMA)
+        return fail(ctx, FMC_ETIMEOUT, "a bounded device wait of the allocation-free reconstruction gave up (code %d)",
+                    hn[1]);
+    if (hn[1] != 0) return fail(ctx, FMC_ECUDA, "allocation-free reconstruction: device error %d", hn[1]);
+    return FMC_OK;
+}
+
+int fmc_check_wait_path(fmc_ctx* ctx, int32_t target, int64_t poll_limit, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (target != 0 && target != 1) return fail(ctx, FMC_EINVAL, "target %d", target);
+    if (poll_limit < 1 || poll_limit > (int64_t)TC_WAIT_LIMIT)
+        return fail(ctx, FMC_EINVAL, "poll limit %lld outside 1..%u", (long long)poll_limit, TC_WAIT_LIMIT);
+    cudaStream_t st = (cudaStream_t)stream;
+    int* word = nullptr;
+    int rc;
+    if (target == 0) {
+        if ((rc = ensure(ctx, ctx->status, 64))) return rc;
+        FMC_CUDA(ctx, cudaMemsetAsync(ctx->status.ptr, 0, 64, st), "memset");
+        word = (int*)ctx->status.ptr + 1;
+    } else {
+        int cur = -1;
+        FMC_CUDA(ctx, cudaGetDevice(&cur), "cudaGetDevice");
+        if (cur != ctx->device)
+            return fail(ctx, FMC_EINVAL, "the current device (%d) is not the context's device (%d)", cur, ctx->device);
+        unsigned char* base = nullptr;
+        if ((rc = noalloc_scratch(ctx, &base))) return rc;
+        FMC_CUDA(ctx, cudaMemsetAsync(base, 0, NOALLOC_STATUS_BYTES, st), "memset");
+        word = reinterpret_cast<int*>(base) + 1;
+    }
+    FMC_CUDA(ctx, launch_wait_check(word, (uint32_t)poll_limit, st), "wait check kernel");
     return FMC_OK;
 }
 

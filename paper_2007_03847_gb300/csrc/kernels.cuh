@@ -120,6 +120,9 @@ int wide_nmt_for(int n);
 cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
                                  int* max_ctas_per_sm);
 
+// one CTA whose bounded mbarrier wait runs out; records DEV_TIMEOUT_MMA in *err
+cudaError_t launch_wait_check(int* err, uint32_t limit, cudaStream_t st);
+
 cudaError_t launch_sincos_probe(const float* x, int64_t n, float* s_cw, float* c_cw, float* s_ref, float* c_ref,
                                 cudaStream_t st);
 

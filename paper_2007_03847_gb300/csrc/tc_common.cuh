@@ -57,14 +57,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // Bounded wait for the phase with the given parity to complete.  Returns false
-// after TC_WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         __nanosleep(64);
     }
     return false;
+}
+
+// The same with the production limit, TC_WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    return mbar_wait_n(bar, parity, TC_WAIT_LIMIT);
 }
 
 // 2-D tiled TMA load of box {x: inner elements, y: rows} into shared memory,
