@@ -299,10 +299,13 @@ static int nd_bucket_for(int d)
     return -1;
 }
 
-// Integrator constants in deviation form (see swing_step): the network matrices
-// without their diagonal, and cos, sin of the equilibrium angles in the frame of
-// the integration (relative to machine 0 without an infinite bus) with the
-// off-diagonal sums u*, v* of the product form, all from the FP64 equilibrium.
+// Integrator constants in the rotated deviation form (see swing_step_impl), all
+// from the FP64 equilibrium and rounded once: the network coupling at the
+// equilibrium angles A_ij = E_iE_j(G_ij cos d*_ij + B_ij sin d*_ij), Bm_ij =
+// E_iE_j(B_ij cos d*_ij - G_ij sin d*_ij) without the diagonal, the machine's
+// off-diagonal equilibrium power P*_i = c*_i u*_i + s*_i v*_i and its quadrature
+// Q*_i = c*_i v*_i - s*_i u*_i (u*, v* the product-form sums, the infinite bus
+// included), every row divided by 2 H_i.
 template <int NM, int ND>
 static void build_params(const fmc_scenario* s, const double* delta0, std::vector<unsigned char>& out)
 {
@@ -317,15 +320,20 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
         sn[j] = std::sin(a);
     }
     for (int i = 0; i < n; ++i) {
+        const double h = 1.0 / (2.0 * s->H[i]);
         double u = 0.0, v = 0.0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
-            double ge = s->E[i] * s->E[j] * s->G[i * n + j];
-            double be = s->E[i] * s->E[j] * s->B[i * n + j];
-            p.GE[i][j] = (float)ge;
-            p.BE[i][j] = (float)be;
-            p.P1[i][j] = make_float2((float)ge, (float)ge);
-            p.P2[i][j] = make_float2((float)-be, (float)be);
+            const double ge = s->E[i] * s->E[j] * s->G[i * n + j];
+            const double be = s->E[i] * s->E[j] * s->B[i * n + j];
+            const double cij = c[i] * c[j] + sn[i] * sn[j];   // cos(d*_i - d*_j)
+            const double sij = sn[i] * c[j] - c[i] * sn[j];   // sin(d*_i - d*_j)
+            const double A = (ge * cij + be * sij) * h;
+            const double Bm = (be * cij - ge * sij) * h;
+            p.Ah[i][j] = (float)A;
+            p.Bh[i][j] = (float)Bm;
+            p.P1[i][j] = make_float2((float)A, (float)A);
+            p.P2[i][j] = make_float2((float)-Bm, (float)Bm);
             u += ge * c[j] - be * sn[j];
             v += ge * sn[j] + be * c[j];
         }
@@ -333,14 +341,11 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
             u += s->E[i] * s->Vinf * s->Ginf[i];
             v += s->E[i] * s->Vinf * s->Binf[i];
         }
-        p.cst[i] = (float)c[i];
-        p.sst[i] = (float)sn[i];
-        p.ust[i] = (float)u;
-        p.vst[i] = (float)v;
+        p.pst[i] = (float)((c[i] * u + sn[i] * v) * h);
+        p.qst[i] = (float)((c[i] * v - sn[i] * u) * h);
         p.dst[i] = (float)delta0[i];
-        p.inv2H[i] = (float)(1.0 / (2.0 * s->H[i]));
-        p.D[i] = (float)s->D[i];
-        for (int q = 0; q < d; ++q) p.inj[i][q] = (float)s->inject[i * d + q];
+        p.Dh[i] = (float)(s->D[i] * h);
+        for (int q = 0; q < d; ++q) p.injh[i][q] = (float)(s->inject[i * d + q] * h);
     }
     for (int q = 0; q < d; ++q) {
         p.ou_a[q] = (float)(1.0 - s->theta[q] * s->dt);
@@ -357,7 +362,7 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
         // the event rides in the spare slot d: held at 0 before, 1 from the event step
         p.ev_slot = d;
         p.ev_step = event_step_of(s);
-        p.inj[s->event_machine][d] = (float)s->event_dpm;
+        p.injh[s->event_machine][d] = (float)(s->event_dpm / (2.0 * s->H[s->event_machine]));
         p.ou_a[d] = 1.f;
         p.ou_s[d] = 0.f;
     }

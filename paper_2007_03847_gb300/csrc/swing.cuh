@@ -65,16 +65,19 @@ __device__ __forceinline__ void sincos_cw(float x, float* s_out, float* c_out)
 
 template <int NM, int ND>
 struct SwingParams {
-    float GE[NM][NM];            // E_i E_j G_ij, zero diagonal
-    float BE[NM][NM];            // E_i E_j B_ij, zero diagonal
-    float2 P1[NM][NM];           // (GE_ij, GE_ij): packed multiplier of (gamma_j, eta_j)
-    float2 P2[NM][NM];           // (-BE_ij, BE_ij): packed multiplier of (eta_j, gamma_j)
-    float cst[NM], sst[NM];      // cos, sin of the equilibrium angle (reference frame)
-    float ust[NM], vst[NM];      // u*, v*: off-diagonal network sums at the equilibrium (+ infinite bus)
+    // The network in the rotated deviation form (see swing_step_impl), each row i
+    // divided by 2 H_i; zero diagonal.  With delta*_ij = delta*_i - delta*_j,
+    //   A_ij  = E_i E_j (G_ij cos delta*_ij + B_ij sin delta*_ij),
+    //   Bm_ij = E_i E_j (B_ij cos delta*_ij - G_ij sin delta*_ij).
+    float2 P1[NM][NM];           // (A_ij, -Bm_ij) / 2H_i: packed multiplier of (cos D_j - 1, sin D_j) -> U
+    float2 P2[NM][NM];           // (Bm_ij, A_ij) / 2H_i: packed multiplier of (cos D_j - 1, sin D_j) -> V
+    float Ah[NM][NM];            // A_ij / 2H_i (scalar network sum)
+    float Bh[NM][NM];            // Bm_ij / 2H_i
+    float pst[NM];               // P*_i / 2H_i = (c*_i u*_i + s*_i v*_i) / 2H_i
+    float qst[NM];               // Q*_i / 2H_i = (c*_i v*_i - s*_i u*_i) / 2H_i
     float dst[NM];               // equilibrium angles delta*_i (absolute)
-    float inv2H[NM];
-    float D[NM];
-    float inj[NM][ND];
+    float Dh[NM];                // D_i / 2H_i
+    float injh[NM][ND];          // inj[i][w] / 2H_i
     float ou_a[ND];              // 1 - theta_w dt (1 in the event slot)
     float ou_s[ND];              // sigma_w (0 in the event slot)
     float hw[NM];                // H_i / sum H: centre-of-inertia weights of the response function
@@ -112,6 +115,28 @@ __device__ __forceinline__ float coi_speed(const SwingParams<NM, ND>& p, const f
     return c;
 }
 
+// sin(a) and cos(a) - 1 of a deviation angle below 0.05 in magnitude: a - a^3/6
+// and -a^2/2 + a^4/24, whose truncation, a^4/120 and a^4/360 relative, stays
+// below 2^-24 for |a| <= 0.052 (half an FP32 ulp of the result).
+__device__ __forceinline__ void sin_cosm1_tiny(float a, float* sn, float* cm1)
+{
+    const float a2 = a * a;
+    *sn = fmaf(a2 * a, -1.6666666666666667e-1f, a);
+    *cm1 = fmaf(a2, 4.1666666666666667e-2f, -0.5f) * a2;
+}
+
+// The same to degree 5 and 6 for |a| <= 0.25: truncation a^6/5040 and a^6/20160
+// relative, below 5e-8.
+__device__ __forceinline__ void sin_cosm1_mid(float a, float* sn, float* cm1)
+{
+    const float a2 = a * a;
+    float ps = fmaf(a2, 8.3333333333333333e-3f, -1.6666666666666667e-1f);
+    *sn = fmaf(ps * a2, a, a);
+    float pc = fmaf(a2, -1.3888888888888889e-3f, 4.1666666666666667e-2f);
+    pc = fmaf(pc, a2, -0.5f);
+    *cm1 = pc * a2;
+}
+
 // sin(a) and cos(a) - 1 of a small deviation angle, without cancellation: the
 // Taylor series to degree 9 and 10 (truncation < 3e-9 for |a| <= 0.8).
 __device__ __forceinline__ void sin_cosm1_small(float a, float* sn, float* cm1)
@@ -137,22 +162,121 @@ __device__ __forceinline__ void sin_cosm1_any(float a, float* sn, float* cm1)
     *cm1 = -2.0f * sh * sh;
 }
 
+// The angle tier of a stage: 0 when every machine of every lane of the warp
+// deviates by at most 0.05 rad, 1 up to 0.25, 2 up to 0.8, 3 beyond
+// (warp-uniform, so the series below never diverge inside a warp).
+template <int NM>
+__device__ __forceinline__ int angle_tier(const float (&yd)[NM])
+{
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) m = fmaxf(m, fabsf(yd[j]));
+    const unsigned mask = __activemask();
+    if (__all_sync(mask, m <= 0.05f)) return 0;
+    if (__all_sync(mask, m <= 0.25f)) return 1;
+    if (__all_sync(mask, m <= 0.8f)) return 2;
+    return 3;
+}
+
+// sin and cos - 1 of one deviation angle by the series of the warp's tier.
+template <int TIER>
+__device__ __forceinline__ void deviation_trig1(float a, float* sn, float* cm1)
+{
+    if constexpr (TIER == 0)
+        sin_cosm1_tiny(a, sn, cm1);
+    else if constexpr (TIER == 1)
+        sin_cosm1_mid(a, sn, cm1);
+    else if constexpr (TIER == 2)
+        sin_cosm1_small(a, sn, cm1);
+    else
+        sin_cosm1_any(a, sn, cm1);
+}
+
+// The network sums of one RK stage in outer-product order: machine j's pair
+// (cos Delta_j - 1, sin Delta_j) is formed once (cs2[j]) and added into every
+// other row's packed accumulator acc[i] = (U_i, V_i) (see swing_step_impl).
+template <int TIER, int NM, int ND>
+__device__ __forceinline__ void stage_network(const SwingParams<NM, ND>& p, const float (&yd)[NM],
+                                              unsigned long long (&acc)[NM], unsigned long long (&cs2)[NM])
+{
+#pragma unroll
+    for (int i = 0; i < NM; ++i) acc[i] = 0ull;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        float c, sj;
+        deviation_trig1<TIER>(yd[j], &sj, &c);
+        cs2[j] = f2pack(c, sj);
+#if FMC_PACKED_FP32
+        const unsigned long long sc = f2pack(sj, c);
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+            if (i == j) continue;
+            acc[i] = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P1[i][j]), cs2[j], acc[i]);
+            acc[i] = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P2[i][j]), sc, acc[i]);
+        }
+#else
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+            if (i == j) continue;
+            float u, v;
+            f2unpack(acc[i], u, v);
+            u = fmaf(p.Ah[i][j], c, u);
+            u = fmaf(-p.Bh[i][j], sj, u);
+            v = fmaf(p.Bh[i][j], c, v);
+            v = fmaf(p.Ah[i][j], sj, v);
+            acc[i] = f2pack(u, v);
+        }
+#endif
+    }
+}
+
+// One RK stage's right-hand side for every machine, folded into the RK
+// accumulators (ad, aw) and the next stage's input (yd, yw); see swing_step_impl.
+template <int TIER, int NM, int ND>
+__device__ __forceinline__ void stage_rhs(const SwingParams<NM, ND>& p, const float (&xs)[ND], float w0, float b,
+                                          float cn, const float (&del)[NM], const float (&w)[NM], float (&ad)[NM],
+                                          float (&aw)[NM], float (&yd)[NM], float (&yw)[NM])
+{
+    unsigned long long acc[NM], cs2[NM];
+    stage_network<TIER, NM, ND>(p, yd, acc, cs2);
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        float U, V, cmi, sni;
+        f2unpack(acc[i], U, V);
+        f2unpack(cs2[i], cmi, sni);
+        V += p.qst[i];
+        // (forcing - D domega - dPe) / 2H, the rows already scaled
+        float dpe = fmaf(cmi, U + p.pst[i], U);
+        dpe = fmaf(sni, V, dpe);
+        float f = 0.f;
+#pragma unroll
+        for (int q = 0; q < ND; ++q) f = fmaf(p.injh[i][q], xs[q], f);
+        const float kw = fmaf(-p.Dh[i], yw[i], f - dpe);
+        const float kd = p.omega_s * (yw[i] - w0);
+        ad[i] = fmaf(b, kd, ad[i]);
+        aw[i] = fmaf(b, kw, aw[i]);
+        yd[i] = fmaf(cn, kd, del[i]);
+        yw[i] = fmaf(cn, kw, w[i]);
+    }
+}
+
 // One step of the swing equations, integrated in deviation variables
 //   Delta_i = delta_i - delta*_i - theta   (theta: angle of machine 0 when the
 //   system has no infinite bus, so that the common drift of all angles, which
 //   the network does not see, never enters the FP32 network terms; 0 otherwise)
-// With c_i = cos(delta_i) = c*_i + gamma_i, s_i = s*_i + eta_i,
-//   gamma_i = c*_i (cos Delta_i - 1) - s*_i sin Delta_i,
-//   eta_i   = s*_i (cos Delta_i - 1) + c*_i sin Delta_i,
-// the electrical power's deviation from equilibrium is
-//   dPe_i = c*_i du_i + s*_i dv_i + gamma_i (u*_i + du_i) + eta_i (v*_i + dv_i),
-//   du_i = sum_{j!=i} GE_ij gamma_j - BE_ij eta_j,  dv_i = sum_{j!=i} GE_ij eta_j + BE_ij gamma_j
-// (the diagonal contributes the constant E_i^2 G_ii), and since Pm = Pe(delta*)
-// at the equilibrium,
-//   2H_i d(domega_i)/dt = sum_w inj[i][w] x_w - dPe_i - D_i domega_i.
-// Every quantity in the network terms is small, so FP32 keeps its relative
-// precision; the state is the same RK4 trajectory as in absolute angles
-// (RK4 commutes with the linear change of variables).
+// With cm_j = cos Delta_j - 1 and sn_j = sin Delta_j, the angle-difference
+// identities give the electrical power's deviation from equilibrium exactly as
+//   dPe_i = U_i + cm_i (U_i + P*_i) + sn_i (V_i + Q*_i),
+//   U_i = sum_{j!=i} A_ij cm_j - Bm_ij sn_j,   V_i = sum_{j!=i} Bm_ij cm_j + A_ij sn_j,
+// with A, Bm the network coupling at the equilibrium angles and P*_i, Q*_i the
+// machine's off-diagonal equilibrium power and its quadrature (the infinite bus
+// included); the diagonal E_i^2 G_ii is constant.  Every quantity is on the
+// scale of the deviations, so FP32 keeps its relative precision, and since
+// Pm = Pe(delta*) at the equilibrium,
+//   d(domega_i)/dt = (sum_w inj[i][w] x_w - dPe_i - D_i domega_i) / 2H_i,
+// with every row already divided by 2H_i on the host.  The state follows the
+// same RK4 trajectory as in absolute angles (RK4 commutes with the linear change
+// of variables).
 // The stages run as a loop that is not unrolled, so the right-hand side exists
 // once in the code and its constant operands are not held in registers across
 // stages.  The disturbance enters stage st at x0 + xw (x1 - x0): RK4 xw = 0,
@@ -199,73 +323,15 @@ __device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, fl
 #pragma unroll
             for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
         }
-        float ga[NM], et[NM];
-        bool big = false;
-#pragma unroll
-        for (int j = 0; j < NM; ++j) big = big || (fabsf(yd[j]) > 0.8f);
-        // warp-uniform choice: the series for the usual small deviations, the
-        // reduced-argument form for all machines when any lane swings far
-        if (__any_sync(__activemask(), big)) {
-#pragma unroll
-            for (int j = 0; j < NM; ++j) {
-                float sn, cm1;
-                sin_cosm1_any(yd[j], &sn, &cm1);
-                ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
-                et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < NM; ++j) {
-                float sn, cm1;
-                sin_cosm1_small(yd[j], &sn, &cm1);
-                ga[j] = fmaf(p.cst[j], cm1, -p.sst[j] * sn);
-                et[j] = fmaf(p.sst[j], cm1, p.cst[j] * sn);
-            }
-        }
         const float w0 = yw[0] * ref;
         ath = fmaf(b, p.omega_s * w0, ath);
-#if FMC_PACKED_FP32
-        unsigned long long ge2[NM], eg2[NM];
-#pragma unroll
-        for (int j = 0; j < NM; ++j) {
-            ge2[j] = f2pack(ga[j], et[j]);
-            eg2[j] = f2pack(et[j], ga[j]);
-        }
-#endif
-#pragma unroll
-        for (int i = 0; i < NM; ++i) {
-            float du = 0.f, dv = 0.f;
-#if FMC_PACKED_FP32
-            unsigned long long acc = 0ull;
-#pragma unroll
-            for (int j = 0; j < NM; ++j) {
-                if (j == i) continue;
-                acc = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P1[i][j]), ge2[j], acc);
-                acc = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P2[i][j]), eg2[j], acc);
-            }
-            f2unpack(acc, du, dv);
-#else
-#pragma unroll
-            for (int j = 0; j < NM; ++j) {
-                if (j == i) continue;
-                du = fmaf(p.GE[i][j], ga[j], du);
-                du = fmaf(-p.BE[i][j], et[j], du);
-                dv = fmaf(p.GE[i][j], et[j], dv);
-                dv = fmaf(p.BE[i][j], ga[j], dv);
-            }
-#endif
-            float dpe = fmaf(p.cst[i], du, p.sst[i] * dv);
-            dpe = fmaf(ga[i], p.ust[i] + du, dpe);
-            dpe = fmaf(et[i], p.vst[i] + dv, dpe);
-            float f = 0.f;
-#pragma unroll
-            for (int q = 0; q < ND; ++q) f = fmaf(p.inj[i][q], xs[q], f);
-            const float kd = p.omega_s * (yw[i] - w0);
-            const float kw = (f - dpe - p.D[i] * yw[i]) * p.inv2H[i];
-            ad[i] = fmaf(b, kd, ad[i]);
-            aw[i] = fmaf(b, kw, aw[i]);
-            yd[i] = fmaf(cn, kd, del[i]);
-            yw[i] = fmaf(cn, kw, w[i]);
+        // the whole stage per angle tier, so that only the state arrays meet
+        // where the branches join
+        switch (angle_tier<NM>(yd)) {
+            case 0: stage_rhs<0, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
+            case 1: stage_rhs<1, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
+            case 2: stage_rhs<2, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
+            default: stage_rhs<3, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
         }
     }
     const float h = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
