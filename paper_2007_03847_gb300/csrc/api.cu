@@ -50,6 +50,7 @@ struct Workspace {
 struct fmc_ctx {
     int device = 0;
     int sms = 0;
+    int64_t l2_bytes = 0;   // the device's L2 cache
     char name[256] = {0};
     size_t budget = 0;
     size_t used = 0;
@@ -332,8 +333,8 @@ static void build_params(const fmc_scenario* s, const double* delta0, std::vecto
             const double Bm = (be * cij - ge * sij) * h;
             p.Ah[i][j] = (float)A;
             p.Bh[i][j] = (float)Bm;
-            p.P1[i][j] = make_float2((float)A, (float)A);
-            p.P2[i][j] = make_float2((float)-Bm, (float)Bm);
+            p.P1[i][j] = make_float2((float)A, (float)-Bm);
+            p.P2[i][j] = make_float2((float)Bm, (float)A);
             u += ge * c[j] - be * sn[j];
             v += ge * sn[j] + be * c[j];
         }
@@ -615,6 +616,7 @@ int fmc_create(fmc_ctx** out, int device, size_t mem_budget_bytes)
     fmc_ctx* c = new fmc_ctx();
     c->device = device;
     c->sms = prop.multiProcessorCount;
+    c->l2_bytes = prop.l2CacheSize;
     snprintf(c->name, sizeof c->name, "%s", prop.name);
     c->budget = mem_budget_bytes;
     *out = c;
@@ -1122,10 +1124,19 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         build_ito<8>(s, wa.ito);
         e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
     } else {
+        // a launch that has the GPU to itself keeps as many design tiles in L2 as
+        // 60 % of it holds: every chunk re-reads each tile, and the whole design
+        // may not fit
+        L2Keep keep{ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr, (int64_t)d * Ks * 2, 0};
+        if (!em && P.exclusive && ctx->l2_bytes > 0) {
+            const double tile_bytes = (double)shape.rows * keep.row_bytes * (split ? 2 : 1);
+            const double t = 0.6 * (double)ctx->l2_bytes / tile_bytes;
+            keep.tiles = t >= (double)ntiles ? (int)ntiles : (int)t;
+        }
         e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
                                   shape.rows, shape.max_ctas, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
                                   per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
-                                  (int*)ws.status.ptr + 1, ems, rrf, st, &occ);
+                                  (int*)ws.status.ptr + 1, ems, rrf, keep, st, &occ);
     }
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)

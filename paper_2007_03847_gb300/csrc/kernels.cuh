@@ -53,13 +53,22 @@ cudaError_t launch_equilibrium(int n, int has_inf, double Vinf, const double* G,
 cudaError_t launch_simulate_plain(int nm_bucket, int nd_bucket, const void* params, const double* eq, const float* dW,
                                   int64_t count, int Nt, float* traj, double* rrf, int smooth, cudaStream_t st);
 int fused_smem_bytes(int nm_bucket, int TC, int split, int max_ctas_per_sm, int rows);
+// L2 residency of the design rows [count][row_bytes] (BF16 hi and lo): the first
+// `tiles` tiles of a fused launch load theirs with evict_last, the rest with
+// evict_first; tiles 0: no hint
+struct L2Keep {
+    const void* hi;
+    const void* lo;
+    int64_t row_bytes;
+    int tiles;
+};
 // rows: samples per CTA, 128 (four warps) or 64 (two warps); max_ctas: resident
 // CTAs per SM allowed (further limited by the TMEM columns)
 cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* params, const CUtensorMap* maps,
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
                                   int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
-                                  float* traj, int* err, const EmSpec& em, double* rrf, cudaStream_t st,
-                                  int* max_ctas_per_sm);
+                                  float* traj, int* err, const EmSpec& em, double* rrf, const L2Keep& keep,
+                                  cudaStream_t st, int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
 cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
                              int sms, cudaStream_t st);

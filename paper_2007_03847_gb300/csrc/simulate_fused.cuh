@@ -51,6 +51,13 @@ struct FusedArgs {
     double* S2;
     EmSpec em;          // on: per-step normals instead of the contraction (no tensor cores)
     double* rrf;        // [2]: sums of the response function and its square, or nullptr
+    // L2 residency of the design: tiles below keep_tiles load their rows with an
+    // evict_last policy (every chunk re-reads them), the others evict_first; at
+    // exit the kept lines return to normal priority.  keep_tiles 0: no hint.
+    const uint8_t* zeta_hi;
+    const uint8_t* zeta_lo;
+    int64_t zeta_row_bytes;
+    int keep_tiles;
 };
 
 template <int NM, int ND>
@@ -87,6 +94,8 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     r.ns = (uint32_t)a.ns;
     r.full = &bars[0];
     r.freed = &bars[TC_MAX_STAGES];
+    r.a_policy = 0;
+    if (a.keep_tiles > 0) r.a_policy = (int)blockIdx.x < a.keep_tiles ? l2_policy_evict_last() : l2_policy_evict_first();
     uint64_t* done = &bars[2 * TC_MAX_STAGES];
     const int WROW = 2 * NM + 1;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;           // [32][WROW] per warp
@@ -224,21 +233,25 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                     }
             }
             // ---- moments: transpose the warp's states and sum per state ----
+            // (row r holds lane r's sample: angles in columns 0..NM-1, speeds in
+            // NM..2NM-1; rows past the tile's last sample hold whatever those
+            // lanes integrated, and column_sums reads only the first na_warp rows)
             float* myrow = wbuf + lane * WROW;
 #pragma unroll
-            for (int i = 0; i < NM; ++i)
-                if (i < n) {
-                    myrow[i] = active ? theta + del[i] : 0.f;
-                    myrow[n + i] = active ? w[i] : 0.f;
-                }
+            for (int i = 0; i < NM; ++i) {
+                myrow[i] = theta + del[i];
+                myrow[NM + i] = w[i];
+            }
             __syncwarp();
             const int ms = s % FU_MS;
             if (lane < S) {
-                // the warp's reference value, sum about it and squared deviations, per state
+                // the warp's reference value, sum about it and squared deviations, per
+                // state (lane j: state j, its column of the transpose buffer)
+                const int mcol = lane < n ? lane : NM + lane - n;
                 const int64_t left = a.count - (srow - lane);
                 const int na_warp = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
                 float rf, dv, m2;
-                column_sums(wbuf + lane, WROW, na_warp, &rf, &dv, &m2);
+                column_sums(wbuf + mcol, WROW, na_warp, &rf, &dv, &m2);
                 float* slot = msum + (ms * warps + warp) * MSLOT;
                 slot[lane] = rf;
                 slot[S + lane] = dv;
@@ -276,6 +289,15 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         }
     }
     if (a.rrf) rrf_accumulate(active ? sqrtf(racc / (float)a.Nt) : 0.f, a.rrf);
+    if (!em && (int)blockIdx.x < a.keep_tiles) {
+        // the tile's design rows back to normal L2 priority
+        const int64_t left = a.count - row0;
+        const int64_t bytes = (left < rows ? left : rows) * a.zeta_row_bytes;
+        for (int64_t o = (int64_t)tid * 128; o < bytes; o += (int64_t)rows * 128) {
+            l2_priority_normal(a.zeta_hi + row0 * a.zeta_row_bytes + o);
+            if (a.split) l2_priority_normal(a.zeta_lo + row0 * a.zeta_row_bytes + o);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, a.tmem_cols);

@@ -192,57 +192,68 @@ __device__ __forceinline__ void deviation_trig1(float a, float* sn, float* cm1)
         sin_cosm1_any(a, sn, cm1);
 }
 
-// The network sums of one RK stage in outer-product order: machine j's pair
-// (cos Delta_j - 1, sin Delta_j) is formed once (cs2[j]) and added into every
-// other row's packed accumulator acc[i] = (U_i, V_i) (see swing_step_impl).
-template <int TIER, int NM, int ND>
-__device__ __forceinline__ void stage_network(const SwingParams<NM, ND>& p, const float (&yd)[NM],
-                                              unsigned long long (&acc)[NM], unsigned long long (&cs2)[NM])
+// The pair (cos Delta_j - 1, sin Delta_j) of every machine for one RK stage.
+template <int TIER, int NM>
+__device__ __forceinline__ void stage_trig(const float (&yd)[NM], unsigned long long (&cs2)[NM])
 {
-#pragma unroll
-    for (int i = 0; i < NM; ++i) acc[i] = 0ull;
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
         float c, sj;
         deviation_trig1<TIER>(yd[j], &sj, &c);
         cs2[j] = f2pack(c, sj);
-#if FMC_PACKED_FP32
-        const unsigned long long sc = f2pack(sj, c);
-#pragma unroll
-        for (int i = 0; i < NM; ++i) {
-            if (i == j) continue;
-            acc[i] = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P1[i][j]), cs2[j], acc[i]);
-            acc[i] = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P2[i][j]), sc, acc[i]);
-        }
-#else
-#pragma unroll
-        for (int i = 0; i < NM; ++i) {
-            if (i == j) continue;
-            float u, v;
-            f2unpack(acc[i], u, v);
-            u = fmaf(p.Ah[i][j], c, u);
-            u = fmaf(-p.Bh[i][j], sj, u);
-            v = fmaf(p.Bh[i][j], c, v);
-            v = fmaf(p.Ah[i][j], sj, v);
-            acc[i] = f2pack(u, v);
-        }
-#endif
     }
 }
 
-// One RK stage's right-hand side for every machine, folded into the RK
-// accumulators (ad, aw) and the next stage's input (yd, yw); see swing_step_impl.
+// Row i's network sums (U_i, V_i) (see swing_step_impl) over the pairs cs2:
+// packed, as two partial sums (A cm, -Bm sn) and (Bm cm, A sn) whose halves
+// add to U and V.
+template <int NM, int ND>
+__device__ __forceinline__ void row_network(const SwingParams<NM, ND>& p, int i, const unsigned long long (&cs2)[NM],
+                                            float& U, float& V)
+{
+#if FMC_PACKED_FP32
+    unsigned long long au = 0ull, av = 0ull;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j == i) continue;
+        au = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P1[i][j]), cs2[j], au);
+        av = ffma2(*reinterpret_cast<const unsigned long long*>(&p.P2[i][j]), cs2[j], av);
+    }
+    float u0, u1, v0, v1;
+    f2unpack(au, u0, u1);
+    f2unpack(av, v0, v1);
+    U = u0 + u1;
+    V = v0 + v1;
+#else
+    U = 0.f;
+    V = 0.f;
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j == i) continue;
+        float c, sj;
+        f2unpack(cs2[j], c, sj);
+        U = fmaf(p.Ah[i][j], c, U);
+        U = fmaf(-p.Bh[i][j], sj, U);
+        V = fmaf(p.Bh[i][j], c, V);
+        V = fmaf(p.Ah[i][j], sj, V);
+    }
+#endif
+}
+
+// The angle derivative omega_s (domega_i - domega_0) enters through cnw = cn
+// omega_s, and ad accumulates the speed differences themselves (the caller
+// multiplies by omega_s once per step).
 template <int TIER, int NM, int ND>
 __device__ __forceinline__ void stage_rhs(const SwingParams<NM, ND>& p, const float (&xs)[ND], float w0, float b,
-                                          float cn, const float (&del)[NM], const float (&w)[NM], float (&ad)[NM],
-                                          float (&aw)[NM], float (&yd)[NM], float (&yw)[NM])
+                                          float cn, float cnw, const float (&del)[NM], const float (&w)[NM],
+                                          float (&ad)[NM], float (&aw)[NM], float (&yd)[NM], float (&yw)[NM])
 {
-    unsigned long long acc[NM], cs2[NM];
-    stage_network<TIER, NM, ND>(p, yd, acc, cs2);
+    unsigned long long cs2[NM];
+    stage_trig<TIER, NM>(yd, cs2);
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
         float U, V, cmi, sni;
-        f2unpack(acc[i], U, V);
+        row_network<NM, ND>(p, i, cs2, U, V);
         f2unpack(cs2[i], cmi, sni);
         V += p.qst[i];
         // (forcing - D domega - dPe) / 2H, the rows already scaled
@@ -252,10 +263,10 @@ __device__ __forceinline__ void stage_rhs(const SwingParams<NM, ND>& p, const fl
 #pragma unroll
         for (int q = 0; q < ND; ++q) f = fmaf(p.injh[i][q], xs[q], f);
         const float kw = fmaf(-p.Dh[i], yw[i], f - dpe);
-        const float kd = p.omega_s * (yw[i] - w0);
-        ad[i] = fmaf(b, kd, ad[i]);
+        const float kv = yw[i] - w0;   // the angle's rate over omega_s
+        ad[i] = fmaf(b, kv, ad[i]);
         aw[i] = fmaf(b, kw, aw[i]);
-        yd[i] = fmaf(cn, kd, del[i]);
+        yd[i] = fmaf(cnw, kv, del[i]);
         yw[i] = fmaf(cn, kw, w[i]);
     }
 }
@@ -324,23 +335,25 @@ __device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, fl
             for (int q = 0; q < ND; ++q) xs[q] = fmaf(xw, x1[q] - x0[q], x0[q]);
         }
         const float w0 = yw[0] * ref;
-        ath = fmaf(b, p.omega_s * w0, ath);
+        ath = fmaf(b, w0, ath);
+        const float cnw = cn * p.omega_s;
         // the whole stage per angle tier, so that only the state arrays meet
         // where the branches join
         switch (angle_tier<NM>(yd)) {
-            case 0: stage_rhs<0, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
-            case 1: stage_rhs<1, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
-            case 2: stage_rhs<2, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
-            default: stage_rhs<3, NM, ND>(p, xs, w0, b, cn, del, w, ad, aw, yd, yw); break;
+            case 0: stage_rhs<0, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
+            case 1: stage_rhs<1, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
+            case 2: stage_rhs<2, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
+            default: stage_rhs<3, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
         }
     }
     const float h = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
+    const float hw = h * p.omega_s;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-        del[i] = fmaf(h, ad[i], del[i]);
+        del[i] = fmaf(hw, ad[i], del[i]);
         w[i] = fmaf(h, aw[i], w[i]);
     }
-    theta = fmaf(h, ath, theta);
+    theta = fmaf(hw, ath, theta);
 }
 
 // The disturbance entering stage st at x0 + xw (x1 - x0) (see swing_step_impl).

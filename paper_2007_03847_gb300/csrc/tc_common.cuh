@@ -84,6 +84,39 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
+// The same with an L2 cache policy (createpolicy) on the loaded lines.
+__device__ __forceinline__ void tma_load_2d_hint(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                                 uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// L2 policies: lines kept in preference to others (evict_last), or given up
+// first (evict_first).
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Returns the 128-byte L2 line holding global address a to normal priority.
+__device__ __forceinline__ void l2_priority_normal(const void* a)
+{
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(__cvta_generic_to_global(a)) : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -225,6 +258,7 @@ struct TcRing {
     uint32_t b_bytes;       // TN rows x 64 B
     uint32_t ns;            // stages, 2..TC_MAX_STAGES
     int split;              // 1 for BF16x3 (hi/lo operands present)
+    uint64_t a_policy = 0;  // L2 policy of the A (design) loads, or 0: none
 };
 
 __device__ __forceinline__ uint32_t ring_stage_bytes(const TcRing& r)
@@ -243,10 +277,16 @@ __device__ __forceinline__ bool ring_load(const TcRing& r, uint32_t g, const CUt
     }
     uint8_t* base = r.base + st * ring_stage_bytes(r);
     mbar_arrive_expect_tx(&r.full[st], ring_stage_bytes(r));
-    tma_load_2d(base, mAh, ax, ay, &r.full[st]);
+    if (r.a_policy)
+        tma_load_2d_hint(base, mAh, ax, ay, &r.full[st], r.a_policy);
+    else
+        tma_load_2d(base, mAh, ax, ay, &r.full[st]);
     tma_load_2d(base + r.a_bytes * (r.split ? 2 : 1), mBh, bx, by, &r.full[st]);
     if (r.split) {
-        tma_load_2d(base + r.a_bytes, mAl, ax, ay, &r.full[st]);
+        if (r.a_policy)
+            tma_load_2d_hint(base + r.a_bytes, mAl, ax, ay, &r.full[st], r.a_policy);
+        else
+            tma_load_2d(base + r.a_bytes, mAl, ax, ay, &r.full[st]);
         tma_load_2d(base + r.a_bytes * 2 + r.b_bytes, mBl, bx, by, &r.full[st]);
     }
     return true;
