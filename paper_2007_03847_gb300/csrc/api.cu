@@ -300,6 +300,7 @@ static int nd_bucket_for(int d)
     return -1;
 }
 
+
 // Integrator constants in the rotated deviation form (see swing_step_impl), all
 // from the FP64 equilibrium and rounded once: the network coupling at the
 // equilibrium angles A_ij = E_iE_j(G_ij cos d*_ij + B_ij sin d*_ij), Bm_ij =

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                     x0[q] = (n0 + s >= p.ev_step) ? 1.f : 0.f;
                     x1[q] = x0[q];
                 }
-            swing_step<NM, ND>(p, del, w, theta, x0, x1);
+            swing_step<NM, ND, (NM <= 10)>(p, del, w, theta, x0, x1);
             if (a.rrf) {
                 const float cs = coi_speed<NM, ND>(p, w);
                 racc = fmaf(cs, cs, racc);

@@ -165,15 +165,17 @@ __device__ __forceinline__ void sin_cosm1_any(float a, float* sn, float* cm1)
 // The angle tier of a stage: 0 when every machine of every lane of the warp
 // deviates by at most 0.05 rad, 1 up to 0.25, 2 up to 0.8, 3 beyond
 // (warp-uniform, so the series below never diverge inside a warp).
-template <int NM>
+// SHORT false: only tiers 2 and 3 (kernels where code size and compile time
+// matter more than the shorter series).
+template <int NM, bool SHORT>
 __device__ __forceinline__ int angle_tier(const float (&yd)[NM])
 {
     float m = 0.f;
 #pragma unroll
     for (int j = 0; j < NM; ++j) m = fmaxf(m, fabsf(yd[j]));
     const unsigned mask = __activemask();
-    if (__all_sync(mask, m <= 0.05f)) return 0;
-    if (__all_sync(mask, m <= 0.25f)) return 1;
+    if (SHORT && __all_sync(mask, m <= 0.05f)) return 0;
+    if (SHORT && __all_sync(mask, m <= 0.25f)) return 1;
     if (__all_sync(mask, m <= 0.8f)) return 2;
     return 3;
 }
@@ -243,13 +245,23 @@ __device__ __forceinline__ void row_network(const SwingParams<NM, ND>& p, int i,
 // The angle derivative omega_s (domega_i - domega_0) enters through cnw = cn
 // omega_s, and ad accumulates the speed differences themselves (the caller
 // multiplies by omega_s once per step).
+// TIER < 0: the tier is the run-time rtier (2 or 3), branching only around the
+// sines and cosines.
 template <int TIER, int NM, int ND>
 __device__ __forceinline__ void stage_rhs(const SwingParams<NM, ND>& p, const float (&xs)[ND], float w0, float b,
                                           float cn, float cnw, const float (&del)[NM], const float (&w)[NM],
-                                          float (&ad)[NM], float (&aw)[NM], float (&yd)[NM], float (&yw)[NM])
+                                          float (&ad)[NM], float (&aw)[NM], float (&yd)[NM], float (&yw)[NM],
+                                          int rtier = 0)
 {
     unsigned long long cs2[NM];
-    stage_trig<TIER, NM>(yd, cs2);
+    if constexpr (TIER >= 0) {
+        stage_trig<TIER, NM>(yd, cs2);
+    } else {
+        if (rtier == 2)
+            stage_trig<2, NM>(yd, cs2);
+        else
+            stage_trig<3, NM>(yd, cs2);
+    }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
         float U, V, cmi, sni;
@@ -293,7 +305,7 @@ __device__ __forceinline__ void stage_rhs(const SwingParams<NM, ND>& p, const fl
 // stages.  The disturbance enters stage st at x0 + xw (x1 - x0): RK4 xw = 0,
 // 1/2, 1/2, 1 (the midpoint value is the average of the two grid values), Heun
 // xw = 0, 1.
-template <int NM, int ND, bool STAGED>
+template <int NM, int ND, bool STAGED, bool SHORT>
 __device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
                                                 float& theta, const float (&x0)[ND], const float (&x1)[ND],
                                                 const float (&xst)[4][ND])
@@ -339,11 +351,19 @@ __device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, fl
         const float cnw = cn * p.omega_s;
         // the whole stage per angle tier, so that only the state arrays meet
         // where the branches join
-        switch (angle_tier<NM>(yd)) {
-            case 0: stage_rhs<0, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
-            case 1: stage_rhs<1, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
-            case 2: stage_rhs<2, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
-            default: stage_rhs<3, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw); break;
+        const int tier = angle_tier<NM, SHORT>(yd);
+        if constexpr (SHORT) {
+            if (tier == 0)
+                stage_rhs<0, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw);
+            else if (tier == 1)
+                stage_rhs<1, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw);
+            else if (tier == 2)
+                stage_rhs<2, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw);
+            else
+                stage_rhs<3, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw);
+        } else {
+            // one copy of the stage: only the sines and cosines branch
+            stage_rhs<-1, NM, ND>(p, xs, w0, b, cn, cnw, del, w, ad, aw, yd, yw, tier);
         }
     }
     const float h = rk4 ? dt * (1.0f / 6.0f) : 0.5f * dt;
@@ -357,12 +377,13 @@ __device__ __forceinline__ void swing_step_impl(const SwingParams<NM, ND>& p, fl
 }
 
 // The disturbance entering stage st at x0 + xw (x1 - x0) (see swing_step_impl).
-template <int NM, int ND>
+// SHORT: the short series for small angle deviations are compiled in.
+template <int NM, int ND, bool SHORT = false>
 __device__ __forceinline__ void swing_step(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
                                            float& theta, const float (&x0)[ND], const float (&x1)[ND])
 {
     const float unused[4][ND] = {};
-    swing_step_impl<NM, ND, false>(p, del, w, theta, x0, x1, unused);
+    swing_step_impl<NM, ND, false, SHORT>(p, del, w, theta, x0, x1, unused);
 }
 
 // The smooth form: the disturbance's value at RK stage st is xst[st] (Heun: st < 2).
@@ -370,7 +391,7 @@ template <int NM, int ND>
 __device__ __forceinline__ void swing_step_staged(const SwingParams<NM, ND>& p, float (&del)[NM], float (&w)[NM],
                                                   float& theta, const float (&xst)[4][ND])
 {
-    swing_step_impl<NM, ND, true>(p, del, w, theta, xst[0], xst[3], xst);
+    swing_step_impl<NM, ND, true, false>(p, del, w, theta, xst[0], xst[3], xst);
 }
 
 // One step of a general disturbance (see ItoParams) in the deviation y.
