@@ -20,6 +20,10 @@ Functions and the passages they follow:
   normal per step.
 * ``electrical_power``, ``equilibrium`` -- Eqs. (state)/(algebra) for the
   classical model; equilibrium at t = 0 as in Section V-A.
+* ``lhs_decorrelate``         -- Section IV-B step 2, the correlation-reducing
+  permutation, by the rank method of Iman and Conover (1982).
+* ``ito_objective``, ``ito_identify`` -- the Appendix's identification of an Ito
+  model from a record (Eqs. likelihood, like, reprob, ident).
 * ``simulate``                -- Algorithm 1 steps 2-4.
 * ``moments_twopass``         -- Algorithm 1 step 4.
 
@@ -148,6 +152,15 @@ def _load():
                                                 ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_smooth_paths.restype = ctypes.c_int
             lib.oracle_plant_stage_forcing.argtypes = [ctypes.c_int32]
+            lib.oracle_lhs_decorrelate.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_lhs_decorrelate.restype = ctypes.c_int
+            lib.oracle_ito_objective.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_ito_objective.restype = ctypes.c_double
+            lib.oracle_ito_identify.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                                ctypes.c_void_p]
+            lib.oracle_ito_identify.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -188,6 +201,47 @@ def lhs_sample(seed: int, N: int, M: int, mode: int = LHS, k0: int = 0, count: i
     if rc != 0:
         raise ValueError("oracle_lhs_sample: invalid arguments")
     return (zeta, strata) if with_strata else zeta
+
+
+def lhs_decorrelate(seed: int, N: int, M: int, mode: int = LHS, want_rstar: bool = False):
+    """Section IV-B step 2 by the rank method of Iman and Conover: the N-sample
+    design with each column rearranged so that the columns' correlation is
+    minimised.  Returns (zeta [N, M], strata [M, N]) or, with want_rstar, also
+    the decorrelated scores R* [N, M] whose ranks give the strata."""
+    zeta = np.zeros((N, M), dtype=np.float64)
+    strata = np.zeros((M, N), dtype=np.uint32)
+    rstar = np.zeros((N, M), dtype=np.float64) if want_rstar else None
+    rc = _load().oracle_lhs_decorrelate(seed, N, M, mode, _ptr(zeta), _ptr(strata), _ptr(rstar))
+    if rc == -2:
+        raise ValueError("oracle_lhs_decorrelate: the score correlation is not positive definite")
+    if rc != 0:
+        raise ValueError("oracle_lhs_decorrelate: invalid arguments (needs N > M and an LHS mode)")
+    return (zeta, strata, rstar) if want_rstar else (zeta, strata)
+
+
+ITO_SIGMA_POLY, ITO_SIGMA_SQUARED_POLY = 1, 2
+
+
+def ito_objective(kind: int, q, xi, h: float, derivatives: bool = False):
+    """The Appendix's objective L' (Eq. ident) of the record xi for the model
+    mu = q0 + q1 x + q2 x^2 and sigma = q3 + q4 x + q5 x^2 (kind 1) or
+    sigma^2 = q3 + q4 x + q5 x^2 (kind 2); with derivatives, (L', grad, Hessian)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    g = np.zeros(6) if derivatives else None
+    H = np.zeros((6, 6)) if derivatives else None
+    L = _load().oracle_ito_objective(kind, _ptr(q), _ptr(xi), xi.size, h, _ptr(g), _ptr(H))
+    return (L, g, H) if derivatives else L
+
+
+def ito_identify(kind: int, xi, h: float, q0):
+    """Newton's method on L' from q0 -> (q, iterations); raises if it does not converge."""
+    q = np.array(q0, dtype=np.float64)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    it = _load().oracle_ito_identify(kind, _ptr(xi), xi.size, h, _ptr(q))
+    if it < 0:
+        raise RuntimeError("oracle_ito_identify did not converge")
+    return q, it
 
 
 BASIS_SINE = 0    # Brownian eigenbasis (the Karhunen-Loeve basis of min(s, t))

@@ -217,6 +217,240 @@ int oracle_lhs_sample(uint64_t seed, int64_t N, int64_t k0, int64_t count, int32
 }
 
 /* ------------------------------------------------------------------------- */
+/* Section IV-B step 2: a permutation of the primary sampling matrix that
+ * minimises the correlation between its columns.  The paper points to a
+ * Cholesky-based method without giving it; this is the rank method of Iman and
+ * Conover ("A distribution-free approach to inducing rank correlation among
+ * input variables", Commun. Statist. B 11 (1982)) with the identity as the
+ * target correlation:
+ *   1. score matrix R[k][i] = Phi^-1((pi_i(k) + 1) / (N + 1)) (van der Waerden
+ *      scores, randomly paired by the design's own permutations pi_i);
+ *   2. its sample correlation T = corr(R) and the Cholesky factor T = Q Q^T;
+ *   3. R* = R Q^-T, whose sample correlation is the identity;
+ *   4. each column of the design is rearranged to the ranks of the same column
+ *      of R*: sample k of dimension i takes stratum pi'_i(k) = rank of R*[k][i]
+ *      among R*[.][i] (ascending, ties by sample index), keeping its uniform
+ *      u_ik, so zeta'[k][i] = Phi^-1((pi'_i(k) + u_ik) / N).
+ * Every stratum is still hit once per dimension.  Needs N > M (T has full
+ * rank) and an LHS mode.  Outputs (each may be NULL): zeta [N][M], strata
+ * [M][N] (pi'), rstar [N][M].  Returns 0, or -1 on invalid arguments, -2 if T
+ * is not positive definite.                                                   */
+/* ------------------------------------------------------------------------- */
+static const double* g_rank_col;   /* the column being ranked (qsort has no context) */
+static int64_t g_rank_stride;
+
+static int rank_cmp(const void* pa, const void* pb)
+{
+    int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+    double va = g_rank_col[a * g_rank_stride], vb = g_rank_col[b * g_rank_stride];
+    if (va < vb) return -1;
+    if (va > vb) return 1;
+    return (a < b) ? -1 : (a > b);
+}
+
+int oracle_lhs_decorrelate(uint64_t seed, int64_t N, int32_t M, int32_t mode, double* zeta, uint32_t* strata,
+                           double* rstar)
+{
+    if (N < 2 || M < 1 || N <= M || N > 2147483648LL || (mode != 0 && mode != 2)) return -1;
+    double* R = (double*)malloc(sizeof(double) * (size_t)N * M);
+    double* T = (double*)malloc(sizeof(double) * (size_t)M * M);
+    double* mean = (double*)malloc(sizeof(double) * M);
+    double* row = (double*)malloc(sizeof(double) * M);
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    uint32_t* sp = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+    int rc = 0;
+    /* 1. scores */
+    for (int64_t k = 0; k < N; ++k)
+        for (int32_t i = 0; i < M; ++i)
+            R[k * M + i] = oracle_ppnd16(((double)oracle_lhs_stratum(seed, N, i, k) + 1.0) / ((double)N + 1.0));
+    /* 2. sample correlation and its Cholesky factor (lower triangle of T) */
+    for (int32_t i = 0; i < M; ++i) {
+        double m = 0.0;
+        for (int64_t k = 0; k < N; ++k) m += R[k * M + i];
+        mean[i] = m / (double)N;
+    }
+    for (int32_t i = 0; i < M; ++i)
+        for (int32_t j = 0; j <= i; ++j) {
+            double c = 0.0;
+            for (int64_t k = 0; k < N; ++k) c += (R[k * M + i] - mean[i]) * (R[k * M + j] - mean[j]);
+            T[i * M + j] = c;
+        }
+    for (int32_t i = 0; i < M; ++i)
+        for (int32_t j = 0; j < i; ++j) T[i * M + j] /= sqrt(T[i * M + i] * T[j * M + j]);
+    for (int32_t i = 0; i < M; ++i) T[i * M + i] = 1.0;
+    for (int32_t j = 0; j < M && rc == 0; ++j) {
+        double d = T[j * M + j];
+        for (int32_t q = 0; q < j; ++q) d -= T[j * M + q] * T[j * M + q];
+        if (!(d > 0.0)) {
+            rc = -2;
+            break;
+        }
+        d = sqrt(d);
+        T[j * M + j] = d;
+        for (int32_t i = j + 1; i < M; ++i) {
+            double v = T[i * M + j];
+            for (int32_t q = 0; q < j; ++q) v -= T[i * M + q] * T[j * M + q];
+            T[i * M + j] = v / d;
+        }
+    }
+    if (rc == 0) {
+        /* 3. R* = R Q^-T, row by row: Q r*^T = r^T by forward substitution */
+        for (int64_t k = 0; k < N; ++k) {
+            for (int32_t i = 0; i < M; ++i) {
+                double v = R[k * M + i];
+                for (int32_t q = 0; q < i; ++q) v -= T[i * M + q] * row[q];
+                row[i] = v / T[i * M + i];
+            }
+            for (int32_t i = 0; i < M; ++i) R[k * M + i] = row[i];
+        }
+        if (rstar) memcpy(rstar, R, sizeof(double) * (size_t)N * M);
+        /* 4. ranks of R* per column; the design takes them as strata */
+        for (int32_t i = 0; i < M; ++i) {
+            for (int64_t k = 0; k < N; ++k) idx[k] = k;
+            g_rank_col = R + i;
+            g_rank_stride = M;
+            qsort(idx, (size_t)N, sizeof(int64_t), rank_cmp);
+            for (int64_t r = 0; r < N; ++r) sp[idx[r]] = (uint32_t)r;
+            for (int64_t k = 0; k < N; ++k) {
+                if (strata) strata[(int64_t)i * N + k] = sp[k];
+                if (zeta) {
+                    double u = (mode == 2) ? 0.5 : oracle_lhs_uniform(seed, i, k);
+                    zeta[k * M + i] = oracle_ppnd16(((double)sp[k] + u) / (double)N);
+                }
+            }
+        }
+    }
+    free(R); free(T); free(mean); free(row); free(idx); free(sp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Appendix (Eqs. likelihood, like, reprob, ident): identification of a scalar
+ * Ito model from a record xi_0, xi_h, ..., by minimising
+ *   L'(q) = 1/4 sum_j (dxi_j - h mu_j)^2 / D_j + 1/2 sum_j log D_j,
+ *   D_j = h sigma(xi_j)^2 / 2,  dxi_j = xi_{(j+1)h} - xi_{jh},
+ * (the log-likelihood of the Euler-Maruyama transition densities, Eq. reprob,
+ * without its constants; the sign of Eq. like read as the minimisation the
+ * paper then performs).  Model: mu(x) = q0 + q1 x + q2 x^2 and either
+ * sigma(x) = q3 + q4 x + q5 x^2 (kind 1, the form of Eq. windito) or
+ * sigma(x)^2 = q3 + q4 x + q5 x^2 (kind 2, the Table I forms).
+ * oracle_ito_objective returns L' and, if g / H are not NULL, its gradient [6]
+ * and Hessian [6][6]; +inf where some D_j <= 0.                              */
+/* ------------------------------------------------------------------------- */
+double oracle_ito_objective(int32_t kind, const double* q, const double* xi, int64_t n, double h, double* g,
+                            double* H)
+{
+    if (g) for (int a = 0; a < 6; ++a) g[a] = 0.0;
+    if (H) for (int a = 0; a < 36; ++a) H[a] = 0.0;
+    double L = 0.0;
+    for (int64_t j = 0; j + 1 < n; ++j) {
+        const double x = xi[j];
+        const double phi[3] = {1.0, x, x * x};
+        const double mu = q[0] + q[1] * x + q[2] * x * x;
+        const double sp = q[3] + q[4] * x + q[5] * x * x;
+        const double D = (kind == 1) ? 0.5 * h * sp * sp : 0.5 * h * sp;
+        if (!(D > 0.0)) return INFINITY;
+        const double r = (xi[j + 1] - x) - h * mu;
+        L += 0.25 * r * r / D + 0.5 * log(D);
+        if (!g && !H) continue;
+        /* derivatives of l_j with respect to mu's coefficients and to D */
+        const double lD = -0.25 * r * r / (D * D) + 0.5 / D;
+        const double lDD = 0.5 * r * r / (D * D * D) - 0.5 / (D * D);
+        double Dq[3], Dqq[3][3];
+        for (int a = 0; a < 3; ++a) {
+            Dq[a] = (kind == 1) ? h * sp * phi[a] : 0.5 * h * phi[a];
+            for (int b = 0; b < 3; ++b) Dqq[a][b] = (kind == 1) ? h * phi[a] * phi[b] : 0.0;
+        }
+        if (g) {
+            for (int a = 0; a < 3; ++a) {
+                g[a] += -h * r * phi[a] / (2.0 * D);
+                g[3 + a] += lD * Dq[a];
+            }
+        }
+        if (H) {
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    H[a * 6 + b] += h * h * phi[a] * phi[b] / (2.0 * D);
+                    const double mD = h * r * phi[a] / (2.0 * D * D) * Dq[b];
+                    H[a * 6 + 3 + b] += mD;
+                    H[(3 + b) * 6 + a] += mD;
+                    H[(3 + a) * 6 + 3 + b] += lDD * Dq[a] * Dq[b] + lD * Dqq[a][b];
+                }
+        }
+    }
+    return L;
+}
+
+/* Cholesky solve of (A + lambda I) x = b on a 6 x 6 system; returns -1 if the
+ * shifted matrix is not positive definite.                                    */
+static int chol6(const double* A, double lambda, double* b)
+{
+    double Lm[36];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = A[i * 6 + j] + (i == j ? lambda : 0.0);
+            for (int k = 0; k < j; ++k) v -= Lm[i * 6 + k] * Lm[j * 6 + k];
+            if (i == j) {
+                if (!(v > 0.0)) return -1;
+                Lm[i * 6 + i] = sqrt(v);
+            } else {
+                Lm[i * 6 + j] = v / Lm[j * 6 + j];
+            }
+        }
+    for (int i = 0; i < 6; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= Lm[i * 6 + k] * b[k];
+        b[i] = v / Lm[i * 6 + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double v = b[i];
+        for (int k = i + 1; k < 6; ++k) v -= Lm[k * 6 + i] * b[k];
+        b[i] = v / Lm[i * 6 + i];
+    }
+    return 0;
+}
+
+/* Newton's method on L' from the start q (overwritten by the estimate): the
+ * Hessian is shifted by lambda I (Levenberg-Marquardt) until it is positive
+ * definite, so every step descends, and a backtracking line search keeps L'
+ * decreasing.  Stops when the step is below 1e-12 relative with an unshifted
+ * (positive definite) Hessian.  Returns the iterations, or -1 if it did not
+ * converge within 200.                                                        */
+int oracle_ito_identify(int32_t kind, const double* xi, int64_t n, double h, double* q)
+{
+    if (n < 8 || !(h > 0.0) || (kind != 1 && kind != 2)) return -1;
+    double g[6], H[36];
+    double L = oracle_ito_objective(kind, q, xi, n, h, g, H);
+    if (!isfinite(L)) return -1;
+    for (int it = 1; it <= 200; ++it) {
+        double step[6], lambda = 0.0, dmax = 0.0;
+        for (int a = 0; a < 6; ++a) dmax = fmax(dmax, fabs(H[a * 6 + a]));
+        for (;;) {
+            for (int a = 0; a < 6; ++a) step[a] = -g[a];
+            if (chol6(H, lambda, step) == 0) break;
+            lambda = (lambda == 0.0) ? 1e-10 * dmax : 10.0 * lambda;
+            if (lambda > 1e30) return -1;
+        }
+        double t = 1.0, qn[6], Ln = INFINITY;
+        for (int ls = 0; ls < 60; ++ls, t *= 0.5) {
+            for (int a = 0; a < 6; ++a) qn[a] = q[a] + t * step[a];
+            Ln = oracle_ito_objective(kind, qn, xi, n, h, NULL, NULL);
+            if (Ln <= L) break;
+        }
+        if (!(Ln <= L)) return -1;
+        double dq = 0.0, qs = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            dq += (qn[a] - q[a]) * (qn[a] - q[a]);
+            qs += qn[a] * qn[a];
+            q[a] = qn[a];
+        }
+        L = oracle_ito_objective(kind, q, xi, n, h, g, H);
+        if (lambda == 0.0 && dq <= 1e-24 * (qs + 1e-300)) return it;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------- */
 /* The paper's "traditional MCs" (Section V-B): the disturbance advanced by the
  * scheme of Eq. (distito) with a fresh standard normal per step, i.e. Wiener
  * increments dW = sqrt(dt) zeta_{k,w,n} instead of a KL expansion.  The normal
