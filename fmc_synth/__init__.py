@@ -44,6 +44,9 @@ BASIS_COSINE = 1  # the paper's cosine white-noise basis
 FORCING_INCREMENTS = 0  # Euler-Maruyama on the KL increments of each step
 FORCING_SMOOTH = 1      # the random ODE of Eq. (eqkl): the smooth KL forcing at the RK stage times
 
+CORR_NONE = 0   # the design's random permutations (Section IV-B step 2) as they are
+CORR_RANK = 1   # the correlation-reducing permutation (rank method of Iman and Conover)
+
 
 @dataclasses.dataclass
 class Scenario:
@@ -85,6 +88,9 @@ class Scenario:
     # how the KL path drives the disturbances: FORCING_INCREMENTS (the GPU library
     # and the oracle) or FORCING_SMOOTH (the oracle only, so far)
     forcing: int = FORCING_INCREMENTS
+    # Section IV-B step 2: CORR_NONE (the design's random permutations as they
+    # are) or CORR_RANK (the correlation-reducing permutation)
+    correlation: int = 0
 
     @property
     def Nt(self) -> int:

@@ -175,7 +175,17 @@ typedef struct fmc_scenario {
     double event_time;      /* s */
     double event_dpm;       /* p.u. */
     const fmc_ito* ito;     /* [d] disturbance models, or NULL: all Ornstein-Uhlenbeck (theta, sigma) */
+    /* Section IV-B step 2: FMC_CORR_NONE (default): the random permutations of the
+     * design as they are; FMC_CORR_RANK: the permutation that minimises the
+     * correlation between the design's columns (see fmc_lhs_decorrelate).  Needs
+     * an LHS sampling mode and N > d K; the whole N-sample design is formed on
+     * every call, also when a call simulates a block of it. */
+    int32_t correlation;
+    int32_t reserved;
 } fmc_scenario;
+
+#define FMC_CORR_NONE 0
+#define FMC_CORR_RANK 1
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -238,6 +248,53 @@ int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int
  * Errors: FMC_EINVAL if K < 1, Nt < 1, T <= 0 or an unknown basis.
  */
 int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, int32_t basis, float* phi_dev, void* stream);
+
+/*
+ * Section IV-B step 2: the permutation of the N x M Latin hypercube design of
+ * fmc_lhs_sample that minimises the correlation between its columns.  The
+ * paper points to a Cholesky-based method without giving it; this is the rank
+ * method of Iman and Conover (1982) with the identity as target correlation:
+ * van der Waerden scores a(s) = Phi^-1((s + 1)/(N + 1)) paired by the design's
+ * own permutations form R[k][i] = a(pi_i(k)); with corr(R) = Q Q^T (Cholesky),
+ * R* = R Q^-T has uncorrelated columns, and sample k of dimension i takes as
+ * its new stratum the rank of R*[k][i] in column i (ascending, ties by sample
+ * index), keeping its own uniform inside the stratum.  Every stratum is still
+ * hit once per dimension; the first dimension keeps its permutation.
+ *   mode       FMC_LHS or FMC_LHS_MIDPOINT
+ *   zeta_dev   [N][M] float (device), or NULL
+ *   strata_dev [M][N] uint32 (device), or NULL: the new strata
+ * Limits: 2 <= N, M < N, M <= 4096, N*M < 2^31.  Synchronises `stream` (the
+ * call reads back whether the score correlation factorised).  Uses library
+ * workspace (about 4 N M * 4 bytes).  Errors: FMC_EINVAL (sizes, mode, or a
+ * score correlation that is not positive definite), FMC_ENOMEM, FMC_ECUDA.
+ */
+int fmc_lhs_decorrelate(fmc_ctx* ctx, uint64_t seed, int64_t N, int32_t M, int32_t mode, float* zeta_dev,
+                        uint32_t* strata_dev, void* stream);
+
+/*
+ * Appendix (Eqs. likelihood, like, reprob, ident): identification of a scalar
+ * Ito model dxi = mu(xi) dt + sigma(xi) dW from a record xi_dev [n] (device,
+ * double) sampled every h seconds, by minimising
+ *   L'(q) = 1/4 sum_j (dxi_j - h mu_j)^2 / D_j + 1/2 sum_j log D_j,
+ *   D_j = h sigma(xi_j)^2 / 2,  dxi_j = xi_{j+1} - xi_j,
+ * the negative log-likelihood of the Euler-Maruyama transition densities less
+ * its constant.  Model (q[6], host): mu(x) = q0 + q1 x + q2 x^2 and
+ *   kind FMC_IDENT_SIGMA:   sigma(x)   = q3 + q4 x + q5 x^2 (the form of Eq. windito),
+ *   kind FMC_IDENT_SIGMA2:  sigma(x)^2 = q3 + q4 x + q5 x^2 (the forms of Table I).
+ * fmc_ito_objective: L' (host *L; +infinity where some D_j <= 0) and, if grad /
+ * hess are not NULL, its gradient [6] and Hessian [6][6] (host), summed on the
+ * GPU in FP64.  fmc_ito_identify: Newton's method from q (overwritten by the
+ * estimate) with the Hessian shifted by lambda I until positive definite and a
+ * backtracking line search; *iterations (nullable) receives the count.  Both
+ * synchronise `stream`.  Errors: FMC_EINVAL (kind, n < 8, h <= 0, a start with
+ * some D_j <= 0), FMC_ENOCONVERGE (200 iterations or a failed line search).
+ */
+#define FMC_IDENT_SIGMA 1
+#define FMC_IDENT_SIGMA2 2
+int fmc_ito_objective(fmc_ctx* ctx, int32_t kind, const double* q, const double* xi_dev, int64_t n, double h,
+                      double* L, double* grad, double* hess, void* stream);
+int fmc_ito_identify(fmc_ctx* ctx, int32_t kind, const double* xi_dev, int64_t n, double h, double* q,
+                     int32_t* iterations, void* stream);
 
 /*
  * Increments of the reconstructed Wiener paths of `count` samples:

@@ -62,7 +62,8 @@ class _Scenario(ctypes.Structure):
         ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("Pm", ctypes.c_void_p),
         ("theta", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("inject", ctypes.c_void_p),
         ("event_machine", ctypes.c_int32), ("forcing", ctypes.c_int32), ("event_time", ctypes.c_double),
-        ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p),
+        ("event_dpm", ctypes.c_double), ("ito", ctypes.c_void_p), ("correlation", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -130,6 +131,9 @@ def load_library():
                                  ctypes.c_int),
             "fmc_kle_reconstruct_noalloc": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
             "fmc_check_wait_path": ([vp, i32, i64, vp], ctypes.c_int),
+            "fmc_lhs_decorrelate": ([vp, u64, i64, i32, i32, vp, vp, vp], ctypes.c_int),
+            "fmc_ito_objective": ([vp, i32, vp, vp, i64, dbl, ctypes.POINTER(dbl), vp, vp, vp], ctypes.c_int),
+            "fmc_ito_identify": ([vp, i32, vp, i64, dbl, vp, ctypes.POINTER(i32), vp], ctypes.c_int),
             "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_moments_from_sums": ([vp, vp, vp, vp, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         }
@@ -221,6 +225,7 @@ class ScenarioStruct:
         s.has_inf_bus = 1 if sc.has_inf_bus else 0
         s.basis = int(getattr(sc, "basis", BASIS_SINE))
         s.forcing = int(getattr(sc, "forcing", FORCING_INCREMENTS))
+        s.correlation = int(getattr(sc, "correlation", CORR_NONE))
         specs = getattr(sc, "ito", None)
         if specs is not None:
             arr = (_Ito * int(sc.d))()
@@ -267,6 +272,47 @@ def lhs_sample(seed: int, N: int, M: int, mode: int = LHS, k0: int = 0, count: i
     return zeta, strata
 
 
+def lhs_decorrelate(seed: int, N: int, M: int, mode: int = LHS, zeta=None, strata=None,
+                    ctx: "Context | None" = None, stream=None):
+    """fmc_lhs_decorrelate: the N x M design with the correlation-reducing
+    permutation (Section IV-B step 2) -> (zeta [N, M] float32, strata [M, N] int32
+    holding uint32 values) device tensors."""
+    import torch
+    ctx = ctx or default_context()
+    zeta = torch.empty((N, M), dtype=torch.float32, device="cuda") if zeta is None else zeta
+    strata = torch.empty((M, N), dtype=torch.int32, device="cuda") if strata is None else strata
+    ctx.check(ctx.lib.fmc_lhs_decorrelate(ctx.h, seed, N, M, mode, _ptr(zeta), _ptr(strata), _stream(stream)))
+    return zeta, strata
+
+
+IDENT_SIGMA, IDENT_SIGMA2 = 1, 2
+
+
+def ito_objective(kind: int, q, xi, h: float, derivatives: bool = False, ctx: "Context | None" = None, stream=None):
+    """fmc_ito_objective: the Appendix's L' of the device record xi (float64) at q;
+    with derivatives (L', grad [6], Hessian [6, 6]) as numpy arrays."""
+    ctx = ctx or default_context()
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    L = ctypes.c_double()
+    g = np.zeros(6) if derivatives else None
+    H = np.zeros((6, 6)) if derivatives else None
+    ctx.check(ctx.lib.fmc_ito_objective(ctx.h, kind, qa.ctypes.data_as(ctypes.c_void_p), _ptr(xi), xi.numel(), h,
+                                        ctypes.byref(L), None if g is None else g.ctypes.data_as(ctypes.c_void_p),
+                                        None if H is None else H.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return (L.value, g, H) if derivatives else L.value
+
+
+def ito_identify(kind: int, xi, h: float, q0, ctx: "Context | None" = None, stream=None):
+    """fmc_ito_identify: Newton's method on L' from q0 over the device record xi
+    (float64) -> (q numpy [6], iterations)."""
+    ctx = ctx or default_context()
+    q = np.array(q0, dtype=np.float64)
+    it = ctypes.c_int32()
+    ctx.check(ctx.lib.fmc_ito_identify(ctx.h, kind, _ptr(xi), xi.numel(), h, q.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(it), _stream(stream)))
+    return q, it.value
+
+
 def lhs_sample_split(seed: int, N: int, d: int, K: int, mode: int = LHS, k0: int = 0, count: int | None = None,
                      ctx: Context | None = None, stream=None):
     """Split-BF16 design [count, d, round_up(K, 8)] as (hi, lo) bfloat16 tensors."""
@@ -283,6 +329,7 @@ def lhs_sample_split(seed: int, N: int, d: int, K: int, mode: int = LHS, k0: int
 
 BASIS_SINE, BASIS_COSINE = 0, 1
 FORCING_INCREMENTS, FORCING_SMOOTH = 0, 1
+CORR_NONE, CORR_RANK = 0, 1
 
 
 def kl_basis(K: int, T: float, Nt: int, basis: int = BASIS_SINE, phi=None, ctx: Context | None = None,

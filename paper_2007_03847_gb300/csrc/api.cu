@@ -45,6 +45,8 @@ struct Workspace {
     DevBuf zeta_hi, zeta_lo, phi_hi, phi_lo, phi32, dW, traj, part, eq, scen, status, zeta32;
     DevBuf wconst;  // constant block of the large-system kernel
     DevBuf rrf;     // [4] FP64: sums of the response function and its square, a zero shift
+    DevBuf ic, ic_strata;  // the correlation-reducing permutation: working memory, new strata [M][N]
+    DevBuf ident;          // identification sums [43], flag, Newton step [6], flag
 };
 
 struct fmc_ctx {
@@ -221,6 +223,15 @@ static int check_scenario(fmc_ctx* ctx, const fmc_scenario* s, int* Nt)
     if ((int64_t)s->d * s->K > (1 << 24)) return fail(ctx, FMC_EINVAL, "d*K too large");
     if (s->N < 1 || s->N > (int64_t(1) << 30)) return fail(ctx, FMC_EINVAL, "N = %lld outside [1, 2^30]", (long long)s->N);
     if (s->sampling < 0 || s->sampling > 3) return fail(ctx, FMC_EINVAL, "sampling mode %d", s->sampling);
+    if (s->correlation != FMC_CORR_NONE && s->correlation != FMC_CORR_RANK)
+        return fail(ctx, FMC_EINVAL, "correlation option %d", s->correlation);
+    if (s->correlation == FMC_CORR_RANK) {
+        const int64_t M = (int64_t)s->d * s->K;
+        if (s->sampling != FMC_LHS && s->sampling != FMC_LHS_MIDPOINT)
+            return fail(ctx, FMC_EINVAL, "the correlation-reducing permutation needs an LHS design");
+        if (s->N <= M || M > 4096 || s->N * M >= (int64_t(1) << 31))
+            return fail(ctx, FMC_EINVAL, "the correlation-reducing permutation needs d K < N, d K <= 4096, N d K < 2^31");
+    }
     if (s->precision < 0 || s->precision > 2) return fail(ctx, FMC_EINVAL, "precision %d", s->precision);
     if (s->integrator != FMC_RK4 && s->integrator != FMC_HEUN)
         return fail(ctx, FMC_EINVAL, "integrator %d", s->integrator);
@@ -632,7 +643,8 @@ int fmc_destroy(fmc_ctx* ctx)
     prof_clear(ctx);
     DevBuf* bufs[] = {&ctx->zeta_hi, &ctx->zeta_lo, &ctx->phi_hi, &ctx->phi_lo, &ctx->phi32,  &ctx->dW,
                       &ctx->traj,    &ctx->part,    &ctx->eq,     &ctx->scen,   &ctx->status, &ctx->zeta32,
-                      &ctx->wconst,  &ctx->rrfbuf};
+                      &ctx->wconst,  &ctx->rrfbuf, &ctx->ws.ic, &ctx->ws.ic_strata,
+                      &ctx->ws.ident};
     for (DevBuf* b : bufs)
         if (b->ptr) cudaFree(b->ptr);
     delete ctx;
@@ -682,6 +694,174 @@ int fmc_lhs_sample_split(fmc_ctx* ctx, uint64_t seed, int64_t N, int64_t k0, int
     cudaStream_t st = (cudaStream_t)stream;
     FMC_CUDA(ctx, launch_lhs_split(seed, N, k0, count, d, K, mode, hi_dev, lo_dev, ctx->sms, st), "lhs kernel");
     return FMC_OK;
+}
+
+}  // extern "C"
+
+// The correlation-reducing permutation of the whole N-sample design (see
+// fmc_lhs_decorrelate) into ws.ic_strata [M][N]; synchronises st to read back
+// whether the score correlation factorised.
+static int run_decorrelate(fmc_ctx* ctx, Workspace& ws, uint64_t seed, int64_t N, int M, cudaStream_t st)
+{
+    int rc;
+    const size_t NM = (size_t)N * M, MM = (size_t)M * M;
+    const size_t sort = ic_sort_bytes(N, M);
+    // carve the working memory: a, mom, G | R, Rs, A, B | vals, vals_out | off, ok | sort
+    size_t off[16], o = 0;
+    auto take = [&](int k, size_t bytes) { off[k] = o; o += (bytes + 255) & ~(size_t)255; };
+    take(0, N * sizeof(double));
+    take(1, 2 * sizeof(double));
+    take(2, MM * sizeof(double));
+    take(3, NM * sizeof(float));
+    take(4, NM * sizeof(float));
+    take(5, MM * sizeof(float));
+    take(6, MM * sizeof(float));
+    take(7, NM * sizeof(uint32_t));
+    take(8, NM * sizeof(uint32_t));
+    take(9, (M + 1) * sizeof(int));
+    take(10, sizeof(int));
+    take(11, sort);
+    if ((rc = ensure(ctx, ws.ic, o))) return rc;
+    if ((rc = ensure(ctx, ws.ic_strata, NM * sizeof(uint32_t)))) return rc;
+    char* b = static_cast<char*>(ws.ic.ptr);
+    IcWork w{reinterpret_cast<double*>(b + off[0]), reinterpret_cast<double*>(b + off[1]),
+             reinterpret_cast<float*>(b + off[3]),  reinterpret_cast<float*>(b + off[4]),
+             reinterpret_cast<double*>(b + off[2]), reinterpret_cast<float*>(b + off[5]),
+             reinterpret_cast<float*>(b + off[6]),  reinterpret_cast<uint32_t*>(b + off[7]),
+             reinterpret_cast<uint32_t*>(b + off[8]), reinterpret_cast<int*>(b + off[9]),
+             reinterpret_cast<int*>(b + off[10]),   b + off[11], sort};
+    FMC_CUDA(ctx, launch_ic_strata(seed, N, M, w, (uint32_t*)ws.ic_strata.ptr, ctx->sms, st),
+             "correlation-reducing permutation");
+    int ok = 0;
+    FMC_CUDA(ctx, cudaMemcpyAsync(&ok, w.ok, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+    if (!ok) return fail(ctx, FMC_EINVAL, "the design's score correlation is not positive definite");
+    return FMC_OK;
+}
+
+extern "C" {
+
+int fmc_lhs_decorrelate(fmc_ctx* ctx, uint64_t seed, int64_t N, int32_t M, int32_t mode, float* zeta_dev,
+                        uint32_t* strata_dev, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (mode != FMC_LHS && mode != FMC_LHS_MIDPOINT) return fail(ctx, FMC_EINVAL, "mode %d is not an LHS mode", mode);
+    if (N < 2 || M < 1 || M >= N || M > 4096 || N * (int64_t)M >= (int64_t(1) << 31))
+        return fail(ctx, FMC_EINVAL, "N = %lld, M = %d: needs 2 <= N, M < N, M <= 4096, N M < 2^31", (long long)N, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = run_decorrelate(ctx, ctx->ws, seed, N, M, st);
+    if (rc) return rc;
+    const uint32_t* strata = (const uint32_t*)ctx->ws.ic_strata.ptr;
+    if (zeta_dev) FMC_CUDA(ctx, launch_ic_values(seed, N, 0, N, M, mode, strata, zeta_dev, ctx->sms, st), "values");
+    if (strata_dev)
+        FMC_CUDA(ctx, cudaMemcpyAsync(strata_dev, strata, (size_t)N * M * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st),
+                 "copy");
+    return FMC_OK;
+}
+
+}  // extern "C"
+
+// L' (and with derivs its gradient and Hessian) of the record at q, read back:
+// h_out [43]; returns FMC_OK, with *finite = 0 where some D_j <= 0.
+static int ident_eval(fmc_ctx* ctx, int kind, const double* q, const double* xi, int64_t n, double h, int derivs,
+                      double* h_out, int* finite, cudaStream_t st)
+{
+    int rc;
+    if ((rc = ensure(ctx, ctx->ws.ident, 512))) return rc;
+    double* out = static_cast<double*>(ctx->ws.ident.ptr);
+    int* bad = reinterpret_cast<int*>(out + 43);
+    FMC_CUDA(ctx, launch_ito_objective(kind, q, xi, n, h, derivs, out, bad, ctx->sms, st), "objective kernel");
+    int hb = 0;
+    FMC_CUDA(ctx, cudaMemcpyAsync(h_out, out, sizeof(double) * (derivs ? 43 : 1), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+    *finite = hb == 0 && std::isfinite(h_out[0]);
+    return FMC_OK;
+}
+
+static int ident_check(fmc_ctx* ctx, int32_t kind, const double* xi, int64_t n, double h)
+{
+    if (kind != FMC_IDENT_SIGMA && kind != FMC_IDENT_SIGMA2) return fail(ctx, FMC_EINVAL, "identification kind %d", kind);
+    if (!xi || n < 8) return fail(ctx, FMC_EINVAL, "the record needs at least 8 values");
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(ctx, FMC_EINVAL, "sampling interval h = %g", h);
+    return FMC_OK;
+}
+
+extern "C" {
+
+int fmc_ito_objective(fmc_ctx* ctx, int32_t kind, const double* q, const double* xi_dev, int64_t n, double h,
+                      double* L, double* grad, double* hess, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    int rc = ident_check(ctx, kind, xi_dev, n, h);
+    if (rc) return rc;
+    if (!q || !L) return fail(ctx, FMC_EINVAL, "NULL q or L");
+    double o[43];
+    int finite = 0;
+    const int derivs = (grad || hess) ? 1 : 0;
+    if ((rc = ident_eval(ctx, kind, q, xi_dev, n, h, derivs, o, &finite, (cudaStream_t)stream))) return rc;
+    *L = finite ? o[0] : HUGE_VAL;
+    if (grad) memcpy(grad, o + 1, 6 * sizeof(double));
+    if (hess) memcpy(hess, o + 7, 36 * sizeof(double));
+    return FMC_OK;
+}
+
+int fmc_ito_identify(fmc_ctx* ctx, int32_t kind, const double* xi_dev, int64_t n, double h, double* q,
+                     int32_t* iterations, void* stream)
+{
+    if (!ctx) return FMC_EINVAL;
+    int rc = ident_check(ctx, kind, xi_dev, n, h);
+    if (rc) return rc;
+    if (!q) return fail(ctx, FMC_EINVAL, "NULL q");
+    cudaStream_t st = (cudaStream_t)stream;
+    double o[43];
+    int finite = 0;
+    if ((rc = ident_eval(ctx, kind, q, xi_dev, n, h, 1, o, &finite, st))) return rc;
+    if (!finite) return fail(ctx, FMC_EINVAL, "the start gives a non-positive diffusion on the record");
+    double* dev = static_cast<double*>(ctx->ws.ident.ptr);
+    double* step_dev = dev + 44;
+    int* ok_dev = reinterpret_cast<int*>(dev + 50);
+    double L = o[0];
+    for (int it = 1; it <= 200; ++it) {
+        double dmax = 0.0;
+        for (int a = 0; a < 6; ++a) dmax = std::max(dmax, std::fabs(o[7 + a * 7]));
+        // the sums of the current point are on the device (out); shift until the
+        // Cholesky factorisation succeeds
+        double lambda = 0.0, step[6];
+        for (;;) {
+            int ok = 0;
+            FMC_CUDA(ctx, launch_ito_newton_step(dev, lambda, step_dev, ok_dev, st), "newton step kernel");
+            FMC_CUDA(ctx, cudaMemcpyAsync(&ok, ok_dev, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+            FMC_CUDA(ctx, cudaMemcpyAsync(step, step_dev, sizeof step, cudaMemcpyDeviceToHost, st), "copy");
+            FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
+            if (ok) break;
+            lambda = lambda == 0.0 ? 1e-10 * dmax : 10.0 * lambda;
+            if (lambda > 1e30) return fail(ctx, FMC_ENOCONVERGE, "the Hessian could not be made positive definite");
+        }
+        double t = 1.0, qn[6], Ln = HUGE_VAL;
+        int f2 = 0;
+        for (int ls = 0; ls < 60; ++ls, t *= 0.5) {
+            for (int a = 0; a < 6; ++a) qn[a] = q[a] + t * step[a];
+            double l1;
+            if ((rc = ident_eval(ctx, kind, qn, xi_dev, n, h, 0, &l1, &f2, st))) return rc;
+            Ln = f2 ? l1 : HUGE_VAL;
+            if (Ln <= L) break;
+        }
+        if (!(Ln <= L)) return fail(ctx, FMC_ENOCONVERGE, "the line search found no decrease");
+        double dq = 0.0, qs = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            dq += (qn[a] - q[a]) * (qn[a] - q[a]);
+            qs += qn[a] * qn[a];
+            q[a] = qn[a];
+        }
+        if ((rc = ident_eval(ctx, kind, q, xi_dev, n, h, 1, o, &finite, st))) return rc;
+        L = o[0];
+        if (lambda == 0.0 && dq <= 1e-24 * (qs + 1e-300)) {
+            if (iterations) *iterations = it;
+            return FMC_OK;
+        }
+    }
+    return fail(ctx, FMC_ENOCONVERGE, "no convergence in 200 Newton iterations");
 }
 
 int fmc_kl_basis(fmc_ctx* ctx, int32_t K, double T, int32_t Nt, int32_t basis, float* phi_dev, void* stream)
@@ -889,6 +1069,10 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     FMC_CUDA(ctx, cudaMemcpyAsync(&eq_status, ws.status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
     FMC_CUDA(ctx, cudaStreamSynchronize(st), "sync");
     if (eq_status < 0) return fail(ctx, FMC_ENOCONVERGE, "equilibrium Newton iteration did not converge");
+    // the correlation-reducing permutation of the whole design, here (it reads
+    // back a status, outside any stream capture)
+    if (s->correlation == FMC_CORR_RANK && (rc = run_decorrelate(ctx, ws, s->seed, s->N, s->d * s->K, st)))
+        return rc;
     if (P.nmt > 0) {
         // constants of the large-system kernel go to the device once, here
         // (outside any stream capture)
@@ -1016,8 +1200,11 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         } else {
             prof_begin(ctx, PH_LHS, st, &pr);
             FMC_CUDA(ctx,
-                     launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ws.zeta32.ptr, nullptr, ctx->sms,
-                                    st),
+                     s->correlation == FMC_CORR_RANK
+                         ? launch_ic_values(s->seed, N, k0, count, M, s->sampling, (const uint32_t*)ws.ic_strata.ptr,
+                                            (float*)ws.zeta32.ptr, ctx->sms, st)
+                         : launch_lhs_f32(s->seed, N, k0, count, M, s->sampling, (float*)ws.zeta32.ptr, nullptr,
+                                          ctx->sms, st),
                      "lhs kernel");
             prof_end(pr, st);
             // the increment basis [K][Nt], or the smooth form's forcing basis [K][2 Nt + 1]
@@ -1067,8 +1254,11 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     } else {
         prof_begin(ctx, PH_LHS, st, &pr);
         FMC_CUDA(ctx,
-                 launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr,
-                                  ctx->sms, st),
+                 s->correlation == FMC_CORR_RANK
+                     ? launch_ic_split(s->seed, N, k0, count, d, K, s->sampling, (const uint32_t*)ws.ic_strata.ptr,
+                                       ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st)
+                     : launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr,
+                                        split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st),
                  "lhs kernel");
         prof_end(pr, st);
         prof_begin(ctx, PH_BASIS, st, &pr);
@@ -1198,7 +1388,8 @@ int fmc::release_workspace(fmc_ctx* ctx, cudaStream_t st)
     if (!ctx) return FMC_EINVAL;
     // the buffers that scale with the samples or the horizon; the small ones stay
     DevBuf* big[] = {&ctx->ws.zeta_hi, &ctx->ws.zeta_lo, &ctx->ws.phi_hi, &ctx->ws.phi_lo, &ctx->ws.phi32,
-                     &ctx->ws.dW,      &ctx->ws.traj,    &ctx->ws.part,   &ctx->ws.zeta32};
+                     &ctx->ws.dW,      &ctx->ws.traj,    &ctx->ws.part,   &ctx->ws.zeta32,
+                     &ctx->ws.ic,      &ctx->ws.ic_strata};
     for (DevBuf* b : big) {
         if (!b->ptr) continue;
         if (ctx->stream_ordered)
@@ -1337,7 +1528,7 @@ static void batch_free(fmc_batch* b)
     for (Workspace* w : b->ws) {
         DevBuf* bufs[] = {&w->zeta_hi, &w->zeta_lo, &w->phi_hi, &w->phi_lo, &w->phi32,  &w->dW,
                           &w->traj,    &w->part,    &w->eq,     &w->scen,   &w->status, &w->zeta32,
-                          &w->wconst,  &w->rrf};
+                          &w->wconst,  &w->rrf,    &w->ic,     &w->ic_strata};
         for (DevBuf* d : bufs)
             if (d->ptr) {
                 cudaFree(d->ptr);

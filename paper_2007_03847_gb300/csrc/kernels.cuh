@@ -129,6 +129,50 @@ int wide_nmt_for(int n);
 cudaError_t launch_simulate_wide(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
                                  int* max_ctas_per_sm);
 
+// Section IV-B step 2, the correlation-reducing permutation (rank method of
+// Iman and Conover): working buffers of launch_ic_strata for N samples and M
+// dimensions (a: N doubles; mom: 2 doubles; R, Rs: N*M floats; G: M*M doubles;
+// A, B: M*M floats; vals, vals_out: N*M uint32; off: M+1 ints; ok: 1 int, 1 if
+// the score correlation was positive definite; sort_tmp: sort_bytes bytes)
+struct IcWork {
+    double* a;
+    double* mom;
+    float* R;
+    float* Rs;
+    double* G;
+    float* A;
+    float* B;
+    uint32_t* vals;
+    uint32_t* vals_out;
+    int* off;
+    int* ok;
+    void* sort_tmp;
+    size_t sort_bytes;
+};
+size_t ic_sort_bytes(int64_t N, int M);
+// strata [M][N] of the decorrelated design (M <= 4096, N*M < 2^31)
+cudaError_t launch_ic_strata(uint64_t seed, int64_t N, int M, const IcWork& w, uint32_t* strata, int sms,
+                             cudaStream_t st);
+// design values of rows k0..k0+count-1 from strata [M][N]: zeta [count][M] FP32,
+// or the split-BF16 layout [count][d][round_up(K, 8)]
+cudaError_t launch_ic_values(uint64_t seed, int64_t N, int64_t k0, int64_t count, int M, int mode,
+                             const uint32_t* strata, float* zeta, int sms, cudaStream_t st);
+cudaError_t launch_ic_split(uint64_t seed, int64_t N, int64_t k0, int64_t count, int d, int K, int mode,
+                            const uint32_t* strata, void* hi, void* lo, int sms, cudaStream_t st);
+
+// The Appendix's identification: the objective L' of a record xi [n] (FP64)
+// for the coefficients q (kind 1: sigma polynomial; kind 2: sigma^2
+// polynomial) into out [43] = (L', gradient [6], Hessian [6][6]); *bad = 1 if
+// some D_j <= 0.  derivs 0: L' only.
+struct ItoQ {
+    double c[6];
+};
+cudaError_t launch_ito_objective(int kind, const double* q, const double* xi, int64_t n, double h, int derivs,
+                                 double* out, int* bad, int sms, cudaStream_t st);
+// step [6] = -(H + lambda I)^-1 g from out's gradient and Hessian; *ok = 0 if
+// the shifted Hessian is not positive definite
+cudaError_t launch_ito_newton_step(const double* gH, double lambda, double* step, int* ok, cudaStream_t st);
+
 // one CTA whose bounded mbarrier wait runs out; records DEV_TIMEOUT_MMA in *err
 cudaError_t launch_wait_check(int* err, uint32_t limit, cudaStream_t st);
 
