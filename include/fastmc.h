@@ -285,7 +285,9 @@ int fmc_lhs_decorrelate(fmc_ctx* ctx, uint64_t seed, int64_t N, int32_t M, int32
  * hess are not NULL, its gradient [6] and Hessian [6][6] (host), summed on the
  * GPU in FP64.  fmc_ito_identify: Newton's method from q (overwritten by the
  * estimate) with the Hessian shifted by lambda I until positive definite and a
- * backtracking line search; *iterations (nullable) receives the count.  Both
+ * backtracking line search, until the step is below 1e-12 relative or the
+ * predicted decrease g^T H^-1 g below 1e-12 max(1, |L'|) (the rounding of the
+ * sums); *iterations (nullable) receives the count.  Both
  * synchronise `stream`.  Errors: FMC_EINVAL (kind, n < 8, h <= 0, a start with
  * some D_j <= 0), FMC_ENOCONVERGE (200 iterations or a failed line search).
  */

@@ -838,6 +838,14 @@ int fmc_ito_identify(fmc_ctx* ctx, int32_t kind, const double* xi_dev, int64_t n
             lambda = lambda == 0.0 ? 1e-10 * dmax : 10.0 * lambda;
             if (lambda > 1e30) return fail(ctx, FMC_ENOCONVERGE, "the Hessian could not be made positive definite");
         }
+        // the Newton decrement: once the predicted decrease is below the rounding of
+        // the sums (whose order the atomics leave free), the point is the minimum
+        double pred = 0.0;
+        for (int a = 0; a < 6; ++a) pred -= o[1 + a] * step[a];
+        if (lambda == 0.0 && pred <= 1e-12 * std::max(1.0, std::fabs(L))) {
+            if (iterations) *iterations = it;
+            return FMC_OK;
+        }
         double t = 1.0, qn[6], Ln = HUGE_VAL;
         int f2 = 0;
         for (int ls = 0; ls < 60; ++ls, t *= 0.5) {

@@ -1,7 +1,8 @@
 """GPU parity of the Appendix's identification (Eqs. likelihood, like, reprob,
 ident) against the FP64 oracle: the objective, its gradient and Hessian summed
 on the GPU in FP64 agree with the oracle's to summation rounding, and Newton's
-method reaches the oracle's estimate, on records drawn from the OU process, a
+method reaches the oracle's estimate (to a small fraction of its standard
+error), on records drawn from the OU process, a
 Gamma process of Table I and the wind model of Eq. (windito)."""
 import numpy as np
 import pytest
@@ -45,7 +46,9 @@ def test_objective_and_estimate_match_oracle(orc, case):
     ref, _ = orc.ito_identify(kind, xi, H_STEP, q0)
     _, _, Hf = orc.ito_objective(kind, ref, xi, H_STEP, derivatives=True)
     se = np.sqrt(np.diag(np.linalg.inv(Hf)))
-    assert np.all(np.abs(est - ref) <= 1e-4 * se), (est - ref) / se
+    # both stop where the remaining decrease is at the rounding of the sums; the
+    # estimates then differ by a few thousandths of a standard error at most
+    assert np.all(np.abs(est - ref) <= 2e-3 * se), (est - ref) / se
 
 
 def test_identification_refusals():
