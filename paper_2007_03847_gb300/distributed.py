@@ -20,9 +20,16 @@ def shard_range(N: int, world: int, rank: int) -> tuple[int, int]:
 
 
 def allreduce_sums(S1, S2, group=None):
-    """Sum the shifted sums over all ranks in place (gloo for CPU tensors, NCCL for
-    CUDA tensors)."""
+    """Sum the shifted sums over all ranks in place (NCCL on CUDA tensors; with a
+    gloo group CUDA tensors pass through host copies)."""
     import torch.distributed as dist
+    if S1.is_cuda and dist.get_backend(group) == "gloo":
+        h1, h2 = S1.cpu(), S2.cpu()
+        dist.all_reduce(h1, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(h2, op=dist.ReduceOp.SUM, group=group)
+        S1.copy_(h1)
+        S2.copy_(h2)
+        return S1, S2
     dist.all_reduce(S1, op=dist.ReduceOp.SUM, group=group)
     dist.all_reduce(S2, op=dist.ReduceOp.SUM, group=group)
     return S1, S2
