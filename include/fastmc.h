@@ -169,8 +169,10 @@ typedef struct fmc_scenario {
      * sigma(x) sum_k zeta_k m_k(t) (m_k the time derivative of the KL basis
      * function; a general disturbance with the Stratonovich drift), stepped by
      * the same RK4/Heun stages as the swing equations.  The smooth form runs on
-     * the plain path only (FMC_EUNSUPPORTED on the fused path) and not with
-     * FMC_SRS_EM (FMC_EINVAL). */
+     * the plain path and on the per-sample fused kernel (up to 16 machines; the
+     * forcing at the half steps is contracted on the tensor cores, and a chunk
+     * takes two TMEM columns per step and disturbance); FMC_EUNSUPPORTED on the
+     * large-system kernel, FMC_EINVAL with FMC_SRS_EM. */
     int32_t forcing;
     double event_time;      /* s */
     double event_dpm;       /* p.u. */

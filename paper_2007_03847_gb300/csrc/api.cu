@@ -1040,8 +1040,6 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) return fail(ctx, FMC_EINVAL, "path %d", path);
     if (path == FMC_PATH_PLAIN && s->precision != FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the plain path computes in FP32 (precision FMC_PREC_F32)");
-    if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH)
-        return fail(ctx, FMC_EUNSUPPORTED, "the smooth forcing runs on the plain path");
     if (path == FMC_PATH_FUSED && s->precision == FMC_PREC_F32)
         return fail(ctx, FMC_EINVAL, "the fused path contracts on tensor cores (BF16 or BF16X3)");
     const int n = s->n;
@@ -1064,6 +1062,10 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         P.nmt = 0;
     else
         P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
+    if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && P.nmt > 0)
+        return fail(ctx, FMC_EUNSUPPORTED,
+                    "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
+                    FMC_MAX_MACHINES_PLAIN);
     P.nd = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
     P.path = path;
     P.k0 = k0;
@@ -1134,10 +1136,20 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
         const int64_t need = (full + sms - 1) / sms;
         f.max_ctas = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
     }
-    const int cols = 512 / f.max_ctas;
+    // a CTA's TMEM columns: the largest power of two within its share of the SM's
+    // 512 (allocations are powers of two)
+    int cols = 512;
+    while (cols * f.max_ctas > 512) cols >>= 1;
+    // columns a step takes per disturbance: the path value, or the smooth form's
+    // forcing at two half steps
+    const int per = P.s.forcing == FMC_FORCING_SMOOTH ? 2 : 1;
+    while (per * d * 16 > cols && f.max_ctas > 1) {
+        f.max_ctas = f.max_ctas > 2 ? 2 : 1;
+        cols = 512 / f.max_ctas;
+    }
     // the large-system kernel's shared memory leaves room for a ring of 128-step chunks
     int TC = wide ? 128 : 256;
-    while (TC > 16 && d * TC > cols) TC >>= 1;
+    while (TC > 16 && per * d * TC > cols) TC >>= 1;
     f.TC = TC;
     f.ctas = (P.count + f.rows - 1) / f.rows;
     return f;
@@ -1171,8 +1183,10 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
     if (!em) {
         if ((rc = ensure(ctx, ws.zeta_hi, zbytes))) return rc;
         if (split && (rc = ensure(ctx, ws.zeta_lo, zbytes))) return rc;
-        if ((rc = ensure(ctx, ws.phi_hi, (size_t)Nt * Kpad * 2))) return rc;
-        if (split && (rc = ensure(ctx, ws.phi_lo, (size_t)Nt * Kpad * 2))) return rc;
+        // the increment basis [Nt][Kpad], or the smooth form's forcing at the half steps
+        const size_t brows = P.s.forcing == FMC_FORCING_SMOOTH ? 2 * (size_t)Nt + 1 : (size_t)Nt;
+        if ((rc = ensure(ctx, ws.phi_hi, brows * Kpad * 2))) return rc;
+        if (split && (rc = ensure(ctx, ws.phi_lo, brows * Kpad * 2))) return rc;
     }
     if (per_tile_partials && (rc = ensure(ctx, ws.part, (size_t)ntiles * Nt1 * 3 * S * sizeof(float)))) return rc;
     return FMC_OK;
@@ -1254,7 +1268,9 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     const int64_t ntiles = shape.ctas;
     const int TC = shape.TC;
     uint32_t tmem_cols = 32;
-    while (tmem_cols < (uint32_t)(d * TC)) tmem_cols <<= 1;
+    const bool smooth = (s->forcing == FMC_FORCING_SMOOTH);
+    const int cw = smooth ? 2 * TC : TC;  // TMEM columns (basis rows) per disturbance and chunk
+    while (tmem_cols < (uint32_t)(d * cw)) tmem_cols <<= 1;
     CUtensorMap maps[4];
     if (em) {
         // no design and no contraction: the kernels draw the increments
@@ -1271,12 +1287,14 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         prof_end(pr, st);
         prof_begin(ctx, PH_BASIS, st, &pr);
         FMC_CUDA(ctx,
-                 launch_basis_split(K, Nt, s->T, s->basis, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr, ctx->sms,
-                                    st),
+                 smooth ? launch_forcing_split(K, Nt, s->T, s->basis, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr,
+                                               ctx->sms, st)
+                        : launch_basis_split(K, Nt, s->T, s->basis, Kpad, ws.phi_hi.ptr, split ? ws.phi_lo.ptr : nullptr,
+                                             ctx->sms, st),
                  "basis kernel");
         prof_end(pr, st);
         if ((rc = make_contract_maps_at(ctx, maps, ws.zeta_hi.ptr, ws.zeta_lo.ptr, ws.phi_hi.ptr, ws.phi_lo.ptr, count, d,
-                                        Ks, Nt, Kpad, TC, split, shape.rows)))
+                                        Ks, smooth ? 2 * Nt + 1 : Nt, Kpad, cw, split, shape.rows)))
             return rc;
     }
     FMC_CUDA(ctx, cudaMemsetAsync((char*)ws.status.ptr + 4, 0, 4, st), "memset");
@@ -1335,7 +1353,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         e = launch_simulate_fused(P.nm, P.nd, P.params.data(), maps, count, Nt, TC, d, Ks, nkb, split, tmem_cols,
                                   shape.rows, shape.max_ctas, eq, per_tile_partials ? (float*)ws.part.ptr : nullptr,
                                   per_tile_partials ? nullptr : S1, per_tile_partials ? nullptr : S2, traj_dev,
-                                  (int*)ws.status.ptr + 1, ems, rrf, keep, st, &occ);
+                                  (int*)ws.status.ptr + 1, ems, rrf, keep, smooth ? 1 : 0, st, &occ);
     }
     ctx->last_fused_ctas_per_sm = occ;
     if (e == cudaErrorInvalidConfiguration)

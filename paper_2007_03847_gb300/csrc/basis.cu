@@ -94,6 +94,33 @@ __global__ void forcing_f32_kernel(int K, int Nt, double T, int basis, float* __
     }
 }
 
+// The forcing basis in the split-BF16 layout of the fused path: time-major
+// [2 Nt + 1][Kpad], the K contiguous (the tensor cores' K-major B operand).
+__global__ void forcing_split_kernel(int K, int Nt, double T, int basis, int Kpad, __nv_bfloat16* __restrict__ hi,
+                                     __nv_bfloat16* __restrict__ lo)
+{
+    const int64_t total = (2 * (int64_t)Nt + 1) * Kpad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(t / Kpad);
+        const int k = (int)(t - (int64_t)j * Kpad);
+        const float v = k < K ? (float)forcing_value(k, j, Nt, T, basis) : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[t] = h;
+        if (lo) lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+cudaError_t launch_forcing_split(int K, int Nt, double T, int basis, int Kpad, void* hi, void* lo, int sms,
+                                 cudaStream_t st)
+{
+    int64_t total = (2 * (int64_t)Nt + 1) * Kpad;
+    int64_t g = (total + 255) / 256;
+    if (g > sms * 16) g = sms * 16;
+    forcing_split_kernel<<<(int)g, 256, 0, st>>>(K, Nt, T, basis, Kpad, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forcing_f32(int K, int Nt, double T, int basis, float* mdot, int sms, cudaStream_t st)
 {
     int64_t total = (int64_t)K * (2 * (int64_t)Nt + 1);

@@ -41,6 +41,9 @@ cudaError_t launch_basis_f32(int K, int Nt, double T, int basis, float* phi, int
 cudaError_t launch_forcing_f32(int K, int Nt, double T, int basis, float* mdot, int sms, cudaStream_t st);
 cudaError_t launch_basis_split(int K, int Nt, double T, int basis, int Kpad, void* hi, void* lo, int sms,
                                cudaStream_t st);
+// the smooth form's forcing basis in split BF16, time-major [2 Nt + 1][Kpad]
+cudaError_t launch_forcing_split(int K, int Nt, double T, int basis, int Kpad, void* hi, void* lo, int sms,
+                                 cudaStream_t st);
 cudaError_t launch_sgemm_nn(int64_t R, int Ncols, int K, const float* A, const float* B, float* C, cudaStream_t st);
 cudaError_t launch_contract_tc(const CUtensorMap* maps, int64_t count, int d, int Ks, int nkb, int Nt, int TN,
                                int split, float* dW, int* err, cudaStream_t st);
@@ -68,7 +71,7 @@ cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* para
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
                                   int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
                                   float* traj, int* err, const EmSpec& em, double* rrf, const L2Keep& keep,
-                                  cudaStream_t st, int* max_ctas_per_sm);
+                                  int smooth, cudaStream_t st, int* max_ctas_per_sm);
 cudaError_t launch_moments(const float* x, int64_t N, int64_t C, double* mean, double* var, int sms, cudaStream_t st);
 cudaError_t launch_traj_sums(const float* x, int64_t N, int64_t C, const double* shift, int S, double* S1, double* S2,
                              int sms, cudaStream_t st);

@@ -85,14 +85,15 @@ cudaError_t launch_simulate_fused(int nm_bucket, int nd_bucket, const void* para
                                   int64_t count, int Nt, int TC, int d, int Ks, int nkb, int split, uint32_t tmem_cols,
                                   int rows, int max_ctas, const double* eq, float* part, double* S1, double* S2,
                                   float* traj, int* err, const EmSpec& em, double* rrf, const L2Keep& keep,
-                                  cudaStream_t st, int* max_ctas_per_sm)
+                                  int smooth, cudaStream_t st, int* max_ctas_per_sm)
 {
     if (rows != TC_M && rows != TC_M / 2) return cudaErrorInvalidValue;
     int cap = (int)(512u / tmem_cols) < max_ctas ? (int)(512u / tmem_cols) : max_ctas;
-    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, fused_ring_stages(TC, split, cap, rows), tmem_cols, eq, part,
+    const int cw = smooth ? 2 * TC : TC;  // basis rows of a chunk (the smooth form's half steps)
+    FusedArgs a{count, Nt, TC, d, Ks, nkb, split, fused_ring_stages(cw, split, cap, rows), tmem_cols, eq, part,
                 traj, err, S1, S2, em, rrf, static_cast<const uint8_t*>(keep.hi), static_cast<const uint8_t*>(keep.lo),
-                keep.row_bytes, keep.tiles};
-    const int smem = fused_smem_bytes(nm_bucket, TC, split, cap, rows);
+                keep.row_bytes, keep.tiles, smooth};
+    const int smem = fused_smem_bytes(nm_bucket, cw, split, cap, rows);
     const int64_t ntiles = (count + rows - 1) / rows;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
     switch (nm_bucket) {

@@ -58,9 +58,15 @@ struct FusedArgs {
     const uint8_t* zeta_lo;
     int64_t zeta_row_bytes;
     int keep_tiles;
+    // the smooth form (Eq. eqkl as a random ODE): the contraction gives the
+    // forcing at the 2 TC half-step times t_n0 + dt/2 .. t_n0+TC of each chunk
+    // (2 TC TMEM columns per disturbance; the chunk's first value, at t_n0, is
+    // carried from the chunk before, and a first contraction over rows up to 0
+    // gives f(0)), and the step loop forms the disturbances' RK stage values
+    int smooth;
 };
 
-template <int NM, int ND>
+template <int NM, int ND, bool SMOOTH>
 __global__ void __launch_bounds__(FU_THREADS, 4)
     simulate_fused_kernel(const __grid_constant__ SwingParams<NM, ND> p, const __grid_constant__ CUtensorMap mAh,
                           const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBh,
@@ -84,11 +90,12 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     const int64_t srow = row0 + tid;
     const bool active = srow < a.count;
     const int TC = a.TC;
+    const int CW = SMOOTH ? 2 * TC : TC;  // TMEM columns per disturbance and chunk
 
     // ring (used only while the tensor cores fill TMEM) aliases the moment buffers
     TcRing r;
     r.a_bytes = rows * 64;
-    r.b_bytes = TC * 64;
+    r.b_bytes = CW * 64;
     r.split = a.split;
     r.base = smem;
     r.ns = (uint32_t)a.ns;
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     const uint32_t tmem = tmem_base;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     const int J = d * a.nkb;  // K blocks of a chunk
-    const uint32_t idesc = umma_idesc_bf16(TC_M, TC);
+    const uint32_t idesc = umma_idesc_bf16(TC_M, CW);
 
     float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND];
@@ -148,7 +155,10 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
     uint32_t g = 0;  // K blocks issued so far (thread 0)
     float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
 
-    for (int c = 0, n0 = 0; n0 < a.Nt; ++c, n0 += TC) {
+    float f0[ND];  // the smooth form's forcing at the chunk's first grid time
+#pragma unroll
+    for (int q = 0; q < ND; ++q) f0[q] = 0.f;
+    for (int c = 0, n0 = SMOOTH ? -TC : 0; n0 < a.Nt; ++c, n0 += TC) {
         // ---- tensor cores: dW of this chunk into TMEM ----
         if (!em) {
         tc_fence_before();
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
             auto load_item = [&](int j) {
                 const int wj = j / a.nkb, kb = j - wj * a.nkb;
                 return ring_load(r, g + (uint32_t)j, &mAh, &mAl, &mBh, &mBl, wj * a.Ks + kb * TC_BK, (int)row0,
-                                 kb * TC_BK, n0);
+                                 kb * TC_BK, SMOOTH ? 2 * n0 + 1 : n0);
             };
             bool ok = true;
             int issued = 0;
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
                     if (!ok) break;
                 }
                 const int wj = j / a.nkb, kb = j - wj * a.nkb;
-                ok = ring_mma(r, g + (uint32_t)j, tmem + (uint32_t)(wj * TC), idesc, kb == 0);
+                ok = ring_mma(r, g + (uint32_t)j, tmem + (uint32_t)(wj * CW), idesc, kb == 0);
             }
             g += (uint32_t)J;
             if (ok) {
@@ -193,34 +203,67 @@ __global__ void __launch_bounds__(FU_THREADS, 4)
         tc_fence_after();
         }
 
-        // ---- disturbance paths of this chunk into TMEM (each warp its own lanes) ----
+        if constexpr (SMOOTH) {
+            if (n0 < 0) {
+                // f(0): the last column of the contraction over the rows up to 0
+#pragma unroll
+                for (int q = 0; q < ND; ++q)
+                    if (q < d) f0[q] = tmem_ld1(lane_addr + (uint32_t)(q * CW + CW - 1));
+                tmem_ld_wait();
+                continue;
+            }
+        }
         const int steps = (a.Nt - n0) < TC ? (a.Nt - n0) : TC;
-        disturbance_chunk<ND, ND, true>(lane_addr, TC, steps, n0, d, -1, x0, p.ou_a, p.ou_s, p.ito, p.dt, a.em,
-                                  (uint32_t)(a.em.k0 + srow));
+        // ---- disturbance paths of this chunk into TMEM (each warp its own lanes) ----
+        if constexpr (!SMOOTH)
+            disturbance_chunk<ND, ND, true>(lane_addr, TC, steps, n0, d, -1, x0, p.ou_a, p.ou_s, p.ito, p.dt, a.em,
+                                            (uint32_t)(a.em.k0 + srow));
 
         // ---- FP32 pipes: integrate this chunk ----
         for (int s = 0; s < steps; ++s) {
-            float x1[ND];
+            if constexpr (SMOOTH) {
+                // the forcing at t_n + dt/2 and t_{n+1}; the stage values of the
+                // disturbances' random ODE feed the swing stages
+                float fh[ND], f1[ND], xst[4][ND];
 #pragma unroll
-            for (int q = 0; q < ND; ++q) x1[q] = 0.f;
-#pragma unroll
-            for (int q = 0; q < ND; ++q)
-                if (q < d) x1[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
-            tmem_ld_wait();
-            // the event slot: 0 before the event's grid step, 1 from it
-#pragma unroll
-            for (int q = 0; q < ND; ++q)
-                if (q == p.ev_slot) {
-                    x0[q] = (n0 + s >= p.ev_step) ? 1.f : 0.f;
-                    x1[q] = x0[q];
+                for (int q = 0; q < ND; ++q) {
+                    fh[q] = 0.f;
+                    f1[q] = 0.f;
                 }
-            swing_step<NM, ND, (NM <= 10)>(p, del, w, theta, x0, x1);
+#pragma unroll
+                for (int q = 0; q < ND; ++q)
+                    if (q < d) {
+                        fh[q] = tmem_ld1(lane_addr + (uint32_t)(q * CW + 2 * s));
+                        f1[q] = tmem_ld1(lane_addr + (uint32_t)(q * CW + 2 * s + 1));
+                    }
+                tmem_ld_wait();
+                smooth_stages<NM, ND>(p, n0 + s, x0, f0, fh, f1, xst);
+#pragma unroll
+                for (int q = 0; q < ND; ++q) f0[q] = f1[q];
+                swing_step_staged<NM, ND>(p, del, w, theta, xst);
+            } else {
+                float x1[ND];
+#pragma unroll
+                for (int q = 0; q < ND; ++q) x1[q] = 0.f;
+#pragma unroll
+                for (int q = 0; q < ND; ++q)
+                    if (q < d) x1[q] = tmem_ld1(lane_addr + (uint32_t)(q * TC + s));
+                tmem_ld_wait();
+                // the event slot: 0 before the event's grid step, 1 from it
+#pragma unroll
+                for (int q = 0; q < ND; ++q)
+                    if (q == p.ev_slot) {
+                        x0[q] = (n0 + s >= p.ev_step) ? 1.f : 0.f;
+                        x1[q] = x0[q];
+                    }
+                swing_step<NM, ND, (NM <= 10)>(p, del, w, theta, x0, x1);
+#pragma unroll
+                for (int q = 0; q < ND; ++q) x0[q] = x1[q];
+            }
             if (a.rrf) {
                 const float cs = coi_speed<NM, ND>(p, w);
                 racc = fmaf(cs, cs, racc);
             }
-#pragma unroll
-            for (int q = 0; q < ND; ++q) x0[q] = x1[q];
 
             const int tn = n0 + s + 1;  // grid index of the new state
             if (traj) {
@@ -308,7 +351,7 @@ cudaError_t launch_fused_t(const void* params, const CUtensorMap* maps, const Fu
                            int rows, cudaStream_t st, int* max_ctas_per_sm)
 {
     const SwingParams<NM, ND>& p = *static_cast<const SwingParams<NM, ND>*>(params);
-    auto kern = simulate_fused_kernel<NM, ND>;
+    auto kern = a.smooth ? simulate_fused_kernel<NM, ND, true> : simulate_fused_kernel<NM, ND, false>;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);

@@ -80,8 +80,6 @@ __global__ void __launch_bounds__(128) simulate_plain_smooth_kernel(const __grid
     if (!active) s = count - 1;  // computes a duplicate that is neither stored nor counted
     const int n = p.n;
     const int d = p.d;
-    const float dt = p.dt;
-    const bool rk4 = (p.integrator == FMC_RK4);
     float del[NM], w[NM], theta = 0.f;   // deviations from the equilibrium (see swing_step)
     float x0[ND], f0[ND];
     const int64_t J = 2 * (int64_t)Nt + 1;
@@ -106,45 +104,15 @@ __global__ void __launch_bounds__(128) simulate_plain_smooth_kernel(const __grid
         }
     float racc = 0.f;  // sum over the grid of the squared centre-of-inertia speed
     for (int step = 0; step < Nt; ++step) {
-        float xst[4][ND];
+        float xst[4][ND], fh[ND], f1[ND];
 #pragma unroll
         for (int q = 0; q < ND; ++q) {
-            float xn = 0.f;
-            if (q < d) {
-                const float fh = __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 1);
-                const float f1 = __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 2);
-                const float x = x0[q];
-                const float k1 = smooth_rate<NM, ND>(p, q, x, f0[q]);
-                if (rk4) {
-                    const float X2 = fmaf(0.5f * dt, k1, x);
-                    const float k2 = smooth_rate<NM, ND>(p, q, X2, fh);
-                    const float X3 = fmaf(0.5f * dt, k2, x);
-                    const float k3 = smooth_rate<NM, ND>(p, q, X3, fh);
-                    const float X4 = fmaf(dt, k3, x);
-                    const float k4 = smooth_rate<NM, ND>(p, q, X4, f1);
-                    xst[0][q] = x;
-                    xst[1][q] = X2;
-                    xst[2][q] = X3;
-                    xst[3][q] = X4;
-                    xn = fmaf(dt * (1.0f / 6.0f), (k1 + 2.f * k2) + (2.f * k3 + k4), x);
-                } else {
-                    const float X2 = fmaf(dt, k1, x);
-                    const float k2 = smooth_rate<NM, ND>(p, q, X2, f1);
-                    xst[0][q] = x;
-                    xst[1][q] = X2;
-                    xst[2][q] = X2;
-                    xst[3][q] = X2;
-                    xn = fmaf(0.5f * dt, k1 + k2, x);
-                }
-                f0[q] = f1;
-            } else {
-                // padding: 0; the event slot: 0 before the event's grid step, 1 from it
-                const float ev = (q == p.ev_slot && step >= p.ev_step) ? 1.f : 0.f;
-                xst[0][q] = xst[1][q] = xst[2][q] = xst[3][q] = ev;
-                xn = ev;
-            }
-            x0[q] = xn;
+            fh[q] = (q < d) ? __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 1) : 0.f;
+            f1[q] = (q < d) ? __ldg(fs + (int64_t)q * J + 2 * (int64_t)step + 2) : 0.f;
         }
+        smooth_stages<NM, ND>(p, step, x0, f0, fh, f1, xst);
+#pragma unroll
+        for (int q = 0; q < ND; ++q) f0[q] = f1[q];
         swing_step_staged<NM, ND>(p, del, w, theta, xst);
         const float c = coi_speed<NM, ND>(p, w);
         racc = fmaf(c, c, racc);

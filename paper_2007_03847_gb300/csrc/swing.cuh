@@ -439,6 +439,54 @@ __device__ __forceinline__ float smooth_rate(const SwingParams<NM, ND>& p, int q
     return fmaf(sg, f, fmaf(-0.5f, corr, mu));
 }
 
+// The smooth form's step of every disturbance from grid step `step`: the random
+// ODE dy/dt = smooth_rate(y, f(t)) by the RK4 (or Heun) stages with the forcing
+// f0 at t_n, fh at t_n + dt/2 and f1 at t_{n+1}; xst[st] receives the stage
+// values the swing stages see, x0 the value at t_{n+1}.  Slots q >= d: padding
+// (0), or the event slot (0 before its grid step, 1 from it).
+template <int NM, int ND>
+__device__ __forceinline__ void smooth_stages(const SwingParams<NM, ND>& p, int step, float (&x0)[ND],
+                                              const float (&f0)[ND], const float (&fh)[ND], const float (&f1)[ND],
+                                              float (&xst)[4][ND])
+{
+    const float dt = p.dt;
+    const bool rk4 = (p.integrator == FMC_RK4);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+        float xn;
+        if (q < p.d) {
+            const float x = x0[q];
+            const float k1 = smooth_rate<NM, ND>(p, q, x, f0[q]);
+            if (rk4) {
+                const float X2 = fmaf(0.5f * dt, k1, x);
+                const float k2 = smooth_rate<NM, ND>(p, q, X2, fh[q]);
+                const float X3 = fmaf(0.5f * dt, k2, x);
+                const float k3 = smooth_rate<NM, ND>(p, q, X3, fh[q]);
+                const float X4 = fmaf(dt, k3, x);
+                const float k4 = smooth_rate<NM, ND>(p, q, X4, f1[q]);
+                xst[0][q] = x;
+                xst[1][q] = X2;
+                xst[2][q] = X3;
+                xst[3][q] = X4;
+                xn = fmaf(dt * (1.0f / 6.0f), (k1 + 2.f * k2) + (2.f * k3 + k4), x);
+            } else {
+                const float X2 = fmaf(dt, k1, x);
+                const float k2 = smooth_rate<NM, ND>(p, q, X2, f1[q]);
+                xst[0][q] = x;
+                xst[1][q] = X2;
+                xst[2][q] = X2;
+                xst[3][q] = X2;
+                xn = fmaf(0.5f * dt, k1 + k2, x);
+            }
+        } else {
+            const float ev = (q == p.ev_slot && step >= p.ev_step) ? 1.f : 0.f;
+            xst[0][q] = xst[1][q] = xst[2][q] = xst[3][q] = ev;
+            xn = ev;
+        }
+        x0[q] = xn;
+    }
+}
+
 // One Euler-Maruyama step of the OU disturbances: x1 = (1 - theta dt) x0 + sigma dW.
 template <int NM, int ND>
 __device__ __forceinline__ void ou_step(const SwingParams<NM, ND>& p, const float (&x0)[ND], const float (&dw)[ND],

@@ -1,5 +1,8 @@
 """GPU parity of the smooth forcing (the random ODE of Eq. eqkl; FMC_FORCING_SMOOTH)
-on the plain path against the FP64 oracle.
+against the FP64 oracle, on the plain path and on the fused path (the forcing
+contracted on the tensor cores at the half steps of each chunk, the stage values
+formed in the step loop), with both fused kernels' chunk shapes (alone on the
+GPU and in a batch).
 
 Same tolerances as the other simulation parity tests: trajectories within 1e-4
 normwise relative error on delta and on omega separately, moments within 1e-5.
@@ -58,8 +61,38 @@ def test_smooth_differs_from_the_increment_form(fmc, orc):
     assert not np.array_equal(m0.cpu().numpy(), m1.cpu().numpy())
 
 
-def test_smooth_forcing_on_the_fused_path_is_refused(fmc):
-    sc = _cases()["mm10"].replace(forcing=fs.FORCING_SMOOTH)
+@pytest.mark.parametrize("case", list(_cases()))
+def test_smooth_fused_matches_the_oracle(fmc, orc, case):
+    sc = _cases()[case].replace(forcing=fs.FORCING_SMOOTH)
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    fmc.device_status()
+    zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
+    ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_smooth_fused_in_a_batch_and_at_scale(fmc, orc):
+    # a batch gives the kernel the shared-GPU chunk shape; the larger design runs
+    # several waves with the horizon not a multiple of the chunk
+    scs = [_cases()["mm10"].replace(forcing=fs.FORCING_SMOOTH),
+           fs.multimachine_case(n=8, d=6, K=20, T=0.3, dt=0.005, N=300, seed=75).replace(forcing=fs.FORCING_SMOOTH)]
+    b = fmc.Batch(scs, use_graph=True)
+    means, vars_ = b.launch()
+    fmc.device_status()
+    for sc, m, v in zip(scs, means, vars_):
+        ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), nthreads=8)
+        _check_moments(m.cpu().numpy(), v.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+    b.close()
+    sc = fs.multimachine_case(n=10, d=3, K=40, T=0.305, dt=0.005, N=60000, seed=76).replace(forcing=fs.FORCING_SMOOTH)
+    mean, var = fmc.simulate(sc, path="fused", precision="bf16x3")
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), nthreads=16)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_smooth_forcing_on_the_split_kernel_is_refused(fmc):
+    sc = fs.multimachine_case(n=20, d=2, K=20, T=0.1, dt=0.005, N=64, seed=77).replace(forcing=fs.FORCING_SMOOTH)
     with pytest.raises(fmc.FastMCError) as e:
         fmc.simulate(sc, path="fused")
     assert e.value.code == 8
