@@ -1147,8 +1147,10 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
         f.max_ctas = f.max_ctas > 2 ? 2 : 1;
         cols = 512 / f.max_ctas;
     }
-    // the large-system kernel's shared memory leaves room for a ring of 128-step chunks
-    int TC = wide ? 128 : 256;
+    // the large-system kernel's shared memory leaves room for a ring of 128-step
+    // chunks; a chunk's basis rows (TC, or 2 TC for the smooth form) are one MMA's
+    // N and one tensor-map box, at most 256
+    int TC = (wide || per == 2) ? 128 : 256;
     while (TC > 16 && per * d * TC > cols) TC >>= 1;
     f.TC = TC;
     f.ctas = (P.count + f.rows - 1) / f.rows;
