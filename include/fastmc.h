@@ -574,6 +574,29 @@ int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);
  */
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy);
 
+/*
+ * Launch-shape rules of the fused path (no counterpart in the paper), as an
+ * autotuner that measured the shapes writes them: the first rule whose ranges
+ * hold a launch's machines n, disturbances d and samples N sets its kernel
+ * (AUTO's choice only), the resident CTAs per SM and the time chunk; zero
+ * fields keep the library's own choice.  Applies to the context's single-
+ * scenario calls under FMC_KERNEL_AUTO and to its batches.  A chunk is cut to
+ * what the TMEM share of max_ctas CTAs holds (and to 16 at least); the
+ * large-system kernel keeps one CTA per SM.  The rules are copied; count 0
+ * clears them.  FMC_EINVAL on a malformed rule (empty range, kernel, max_ctas
+ * outside 0..4, TC not 0 or a power of two in 16..256).
+ */
+typedef struct fmc_launch_rule {
+    int32_t n_min, n_max;   /* machines */
+    int32_t d_min, d_max;   /* disturbances */
+    int64_t N_min, N_max;   /* samples of the launch */
+    int32_t kernel;         /* FMC_KERNEL_* (AUTO: the library's choice) */
+    int32_t max_ctas;       /* resident CTAs per SM, 1..4, or 0 */
+    int32_t TC;             /* time chunk, 16..256 and a power of two, or 0 */
+    int32_t reserved;
+} fmc_launch_rule;
+int fmc_set_launch_rules(fmc_ctx* ctx, const fmc_launch_rule* rules, int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,14 @@ class _Scenario(ctypes.Structure):
     ]
 
 
+class LaunchRule(ctypes.Structure):
+    """fmc_launch_rule: a measured launch shape for a range of (n, d, N)."""
+    _fields_ = [("n_min", ctypes.c_int32), ("n_max", ctypes.c_int32), ("d_min", ctypes.c_int32),
+                ("d_max", ctypes.c_int32), ("N_min", ctypes.c_int64), ("N_max", ctypes.c_int64),
+                ("kernel", ctypes.c_int32), ("max_ctas", ctypes.c_int32), ("TC", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class _Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("replicates", ctypes.c_int32), ("latency_us", ctypes.c_double),
                 ("queue_us", ctypes.c_double), ("device_bytes", ctypes.c_uint64), ("n_used", ctypes.c_int64),
@@ -132,6 +140,7 @@ def load_library():
             "fmc_kle_reconstruct_noalloc": ([vp, vp, i64, i32, i32, dbl, dbl, i32, vp, vp], ctypes.c_int),
             "fmc_check_wait_path": ([vp, i32, i64, vp], ctypes.c_int),
             "fmc_lhs_decorrelate": ([vp, u64, i64, i32, i32, vp, vp, vp], ctypes.c_int),
+            "fmc_set_launch_rules": ([vp, ctypes.POINTER(LaunchRule), i32], ctypes.c_int),
             "fmc_ito_objective": ([vp, i32, vp, vp, i64, dbl, ctypes.POINTER(dbl), vp, vp, vp], ctypes.c_int),
             "fmc_ito_identify": ([vp, i32, vp, i64, dbl, vp, ctypes.POINTER(i32), vp], ctypes.c_int),
             "fmc_simulate_sums": ([vp, ctypes.POINTER(_Scenario), i64, i64, i32, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -160,6 +169,9 @@ class Context:
         if rc != OK:
             raise FastMCError(rc, self.lib.fmc_last_error(None).decode())
         self.h = h
+        # the launch shapes the autotuner measured on this GPU model, if cached
+        from . import autotune
+        autotune.apply_cached(self)
 
     def close(self):
         if getattr(self, "h", None):
@@ -640,6 +652,18 @@ def test_sincos(x, ctx: Context | None = None, stream=None):
 
 KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT = 0, 1, 2
 _KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT}
+
+
+def set_launch_rules(rules, ctx: "Context | None" = None) -> None:
+    """fmc_set_launch_rules from dicts with the fields of LaunchRule (missing
+    fields: the whole range / 0); an empty list clears the rules."""
+    ctx = ctx or default_context()
+    arr = (LaunchRule * max(1, len(rules)))()
+    for k, r in enumerate(rules):
+        arr[k] = LaunchRule(int(r.get("n_min", 1)), int(r.get("n_max", 1 << 30)), int(r.get("d_min", 1)),
+                            int(r.get("d_max", 1 << 30)), int(r.get("N_min", 1)), int(r.get("N_max", 1 << 62)),
+                            int(r.get("kernel", 0)), int(r.get("max_ctas", 0)), int(r.get("TC", 0)), 0)
+    ctx.check(ctx.lib.fmc_set_launch_rules(ctx.h, arr, len(rules)))
 
 
 def set_kernel_policy(policy, ctx: Context | None = None) -> None:

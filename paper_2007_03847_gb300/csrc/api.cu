@@ -78,6 +78,7 @@ struct fmc_ctx {
     size_t prof_cap = 0;
     int last_fused_ctas_per_sm = 0;
     int kernel_policy = FMC_KERNEL_AUTO;
+    std::vector<fmc_launch_rule> rules;  // measured launch shapes (fmc_set_launch_rules)
     // Contexts used on one stream only (the server's) grow their workspace in
     // stream order on that stream (cudaFreeAsync / cudaMallocAsync) instead of
     // synchronising the whole device, which would stall every other request.
@@ -1021,12 +1022,23 @@ int fmc_equilibrium(fmc_ctx* ctx, const fmc_scenario* scen, double* delta0, doub
 // GPU, read back once), integrator constants formed for the parameter block.
 struct Prepared {
     fmc_scenario s{};
+
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
     bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
 };
+
+// The first launch rule that holds the scenario and sample count, or nullptr.
+static const fmc_launch_rule* find_rule(const fmc_ctx* ctx, const fmc_scenario* s, int64_t count)
+{
+    for (const fmc_launch_rule& r : ctx->rules)
+        if (s->n >= r.n_min && s->n <= r.n_max && s->d >= r.d_min && s->d <= r.d_max && count >= r.N_min &&
+            count <= r.N_max)
+            return &r;
+    return nullptr;
+}
 
 static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path,
                    cudaStream_t st, Prepared& P, bool exclusive = true)
@@ -1051,7 +1063,12 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     P.nm = nm_bucket_for(n);
     P.exclusive = exclusive;
     // four warps per sample for systems above 16 machines (or on request)
-    const int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
+    int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
+    if (policy == FMC_KERNEL_AUTO && path == FMC_PATH_FUSED) {
+        const fmc_launch_rule* rule = find_rule(ctx, s, count);
+        if (rule && rule->kernel != FMC_KERNEL_AUTO && !(rule->kernel == FMC_KERNEL_PER_SAMPLE && P.nm < 0))
+            policy = rule->kernel;
+    }
     const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE;
     if (path == FMC_PATH_FUSED && per_sample && P.nm < 0)
         return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
@@ -1136,6 +1153,8 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
         const int64_t need = (full + sms - 1) / sms;
         f.max_ctas = wide ? 1 : (need >= 3 ? 4 : (int)(need < 1 ? 1 : need));
     }
+    const fmc_launch_rule* rule = find_rule(ctx, &P.s, P.count);
+    if (rule && rule->max_ctas > 0 && !wide) f.max_ctas = rule->max_ctas;
     // a CTA's TMEM columns: the largest power of two within its share of the SM's
     // 512 (allocations are powers of two)
     int cols = 512;
@@ -1151,6 +1170,7 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
     // chunks; a chunk's basis rows (TC, or 2 TC for the smooth form) are one MMA's
     // N and one tensor-map box, at most 256
     int TC = (wide || per == 2) ? 128 : 256;
+    if (rule && rule->TC > 0 && rule->TC < TC) TC = rule->TC;
     while (TC > 16 && per * d * TC > cols) TC >>= 1;
     f.TC = TC;
     f.ctas = (P.count + f.rows - 1) / f.rows;
@@ -1827,6 +1847,21 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
         return fail(ctx, FMC_EINVAL, "bad arguments");
     FMC_CUDA(ctx, launch_sincos_probe(x_dev, n, s_dev, c_dev, s_ref_dev, c_ref_dev, (cudaStream_t)stream),
              "sincos probe");
+    return FMC_OK;
+}
+
+int fmc_set_launch_rules(fmc_ctx* ctx, const fmc_launch_rule* rules, int32_t count)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (count < 0 || (count > 0 && !rules)) return fail(ctx, FMC_EINVAL, "rules");
+    for (int32_t k = 0; k < count; ++k) {
+        const fmc_launch_rule& r = rules[k];
+        const bool tc_ok = r.TC == 0 || (r.TC >= 16 && r.TC <= 256 && (r.TC & (r.TC - 1)) == 0);
+        if (r.n_min > r.n_max || r.d_min > r.d_max || r.N_min > r.N_max || r.kernel < FMC_KERNEL_AUTO ||
+            r.kernel > FMC_KERNEL_SPLIT || r.max_ctas < 0 || r.max_ctas > 4 || !tc_ok)
+            return fail(ctx, FMC_EINVAL, "launch rule %d is malformed", k);
+    }
+    ctx->rules.assign(rules, rules + count);
     return FMC_OK;
 }
 

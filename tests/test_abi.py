@@ -69,12 +69,15 @@ def test_binding_structs_match_the_header(tmp_path):
     fields_s = [f for f, _ in fmc._Scenario._fields_]
     fields_r = [f for f, _ in fmc._Result._fields_]
     fields_i = [f for f, _ in fmc._Ito._fields_]
+    fields_l = [f for f, _ in fmc.LaunchRule._fields_]
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "fastmc.h"', 'int main(void) {',
            'printf("%zu %zu\\n", sizeof(fmc_scenario), sizeof(fmc_result));']
     src += [f'printf("s {f} %zu\\n", offsetof(fmc_scenario, {f}));' for f in fields_s]
     src += [f'printf("r {f} %zu\\n", offsetof(fmc_result, {f}));' for f in fields_r]
     src += [f'printf("i {f} %zu\\n", offsetof(fmc_ito, {f}));' for f in fields_i]
+    src += [f'printf("l {f} %zu\\n", offsetof(fmc_launch_rule, {f}));' for f in fields_l]
     src += ['printf("i_size %zu 0\\n", sizeof(fmc_ito));']
+    src += ['printf("l_size %zu 0\\n", sizeof(fmc_launch_rule));']
     src += ["return 0; }"]
     c = tmp_path / "probe.c"
     c.write_text("\n".join(src))
@@ -91,7 +94,10 @@ def test_binding_structs_match_the_header(tmp_path):
         if kind == "i_size":
             assert int(name) == ctypes.sizeof(fmc._Ito)
             continue
-        cls = {"s": fmc._Scenario, "r": fmc._Result, "i": fmc._Ito}[kind]
+        if kind == "l_size":
+            assert int(name) == ctypes.sizeof(fmc.LaunchRule)
+            continue
+        cls = {"s": fmc._Scenario, "r": fmc._Result, "i": fmc._Ito, "l": fmc.LaunchRule}[kind]
         assert getattr(cls, name).offset == int(off), (kind, name)
 
 
