@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="T in seconds (profiling of shorter runs)")
     ap.add_argument("--machines", type=int, default=10, help="machines of the system (17..52: large-system kernel)")
     ap.add_argument("--disturbances", type=int, default=3)
+    ap.add_argument("--forcing", default="increments", choices=["increments", "smooth"],
+                    help="smooth: the random ODE of Eq. (eqkl) (the forcing at the RK stage times)")
+    ap.add_argument("--correlation", default="none", choices=["none", "rank"],
+                    help="rank: the correlation-reducing permutation of the design (Section IV-B step 2)")
     ap.add_argument("--kernel", default="auto",
                     choices=["auto", "per_sample", "split"],
                     help="fused-path kernel policy of the timed calls (see fmc_set_kernel_policy)")
@@ -73,10 +77,12 @@ def workload(samples: int, horizon: float = 20.0, machines: int = 10, disturbanc
 
 
 def workload_name(args) -> str:
+    extra = ("" if getattr(args, "forcing", "increments") == "increments" else ", smooth forcing") + \
+            ("" if getattr(args, "correlation", "none") == "none" else ", correlation-reducing permutation")
     if args.machines == 10 and args.disturbances == 3 and args.samples == (1 << 16) and args.horizon == 20.0:
-        return WORKLOAD
+        return WORKLOAD + extra
     return (f"classical {args.machines}-machine system (39-bus-shaped draws), {args.disturbances} OU disturbances, "
-            f"K=200, T={args.horizon:g}s, dt=5ms, N={args.samples}, LHS")
+            f"K=200, T={args.horizon:g}s, dt=5ms, N={args.samples}, LHS" + extra)
 
 
 def algorithmic_flops_per_machine_step(n: int, integrator_stages: int = 4) -> float:
@@ -90,16 +96,19 @@ def algorithmic_flops_per_machine_step(n: int, integrator_stages: int = 4) -> fl
 
 
 def implementation_ops_per_sample_step(n: int, d: int, integrator_stages: int = 4) -> float:
-    """What the fused kernel actually executes on the FP32 pipe per sample and step,
-    counted from its source (every FMA, multiply or add = one operation; a packed
-    FMA = two): per RK stage and machine the short sin / cos - 1 series of the
-    angle deviation (5), the rotated network sums 4(n-1), the electrical-power
-    deviation (3), the forcing d + 1, the derivatives (1) and the RK accumulate
-    and next-stage input (4); per step the state update 2n and the stage forcing
-    of the disturbances 3d.  Only for the issue-level fraction reported beside
-    the algorithmic one."""
-    per_stage = n * (4 * (n - 1) + 14 + d)
-    return float(integrator_stages * per_stage + 2 * n + 3 * d)
+    """What the per-sample fused kernel executes on the FP32 pipe per sample and
+    step, counted from its source for the smallest angle tier (every FMA, multiply
+    or add = one operation; a packed FMA = two): per RK stage and machine the sin /
+    cos - 1 series (5), the row's network sums 4(n-1) and their two halves (2),
+    the equilibrium quadrature (1), the electrical-power deviation (3), the
+    forcing over the disturbance slots (nd), the derivatives (3) and the RK
+    accumulate and next-stage input (4); per stage the stage forcing (2 nd) and
+    the reference speed (3); per step the state update (2n + 1).  nd is the
+    kernel's slot count (1, 2, 4 or 8).  Only for the issue-level fraction
+    reported beside the algorithmic one."""
+    nd = next(b for b in (1, 2, 4, 8) if d <= b)
+    per_stage = n * (4 * (n - 1) + 18 + nd) + 2 * nd + 3
+    return float(integrator_stages * per_stage + 2 * n + 1)
 
 
 def algorithmic_bytes_per_launch(N: int, n: int, d: int, K: int, Nt: int, split: bool = True) -> float:
@@ -519,6 +528,8 @@ def main():
     # weak scaling: every rank simulates `samples` samples, its own block of one
     # design of samples * world samples; the moment sums meet in one all-reduce
     sc = workload(args.samples * world, args.horizon, args.machines, args.disturbances)
+    sc = sc.replace(forcing=fs.FORCING_SMOOTH if args.forcing == "smooth" else fs.FORCING_INCREMENTS,
+                    correlation=fs.CORR_RANK if args.correlation == "rank" else fs.CORR_NONE)
     n, Nt = sc.n, sc.Nt
     from paper_2007_03847_gb300.distributed import shard_range
     k0, count = shard_range(sc.N, world, rank)
