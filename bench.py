@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--correlation", default="none", choices=["none", "rank"],
                     help="rank: the correlation-reducing permutation of the design (Section IV-B step 2)")
     ap.add_argument("--kernel", default="auto",
-                    choices=["auto", "per_sample", "split"],
+                    choices=["auto", "per_sample", "split", "split_tc"],
                     help="fused-path kernel policy of the timed calls (see fmc_set_kernel_policy)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

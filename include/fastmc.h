@@ -560,16 +560,19 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
 int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);
 
 /* ---- kernel choice of the fused path (no counterpart in the paper) -------- */
-#define FMC_KERNEL_AUTO 0        /* per sample for n <= 16, split above */
+#define FMC_KERNEL_AUTO 0        /* per sample for n <= 16, split with the tensor-core network sum above */
 #define FMC_KERNEL_PER_SAMPLE 1  /* one thread integrates a whole sample (n <= FMC_MAX_MACHINES_PLAIN) */
 #define FMC_KERNEL_SPLIT 2       /* four warps share each sample's machines (any n up to FMC_MAX_MACHINES) */
+#define FMC_KERNEL_SPLIT_TC 3    /* the split kernel with each RK stage's network sums over the CTA's 128
+                                    samples as one tcgen05 TF32x3 product (13 <= n <= FMC_MAX_MACHINES) */
 
 /*
  * Chooses the fused kernel for this context's later single-scenario calls
  * (fmc_simulate, fmc_simulate_sums).  AUTO takes the per-sample kernel up to 16
  * machines (the faster one there, at any sample count) and the split kernel
- * above.  Batches and the server always use AUTO's choice.  FMC_EINVAL for an
- * unknown policy; a per-sample request above 16 machines fails at the call with
+ * with the tensor-core network sum above.  Batches and the server always use
+ * AUTO's choice.  FMC_EINVAL for an unknown policy; a per-sample request above
+ * 16 machines, or a SPLIT_TC request below 13, fails at the call with
  * FMC_EUNSUPPORTED.
  */
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy);

@@ -650,8 +650,9 @@ def test_sincos(x, ctx: Context | None = None, stream=None):
     return outs
 
 
-KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT = 0, 1, 2
-_KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT}
+KERNEL_AUTO, KERNEL_PER_SAMPLE, KERNEL_SPLIT, KERNEL_SPLIT_TC = 0, 1, 2, 3
+_KERNEL = {"auto": KERNEL_AUTO, "per_sample": KERNEL_PER_SAMPLE, "split": KERNEL_SPLIT,
+           "split_tc": KERNEL_SPLIT_TC}
 
 
 def set_launch_rules(rules, ctx: "Context | None" = None) -> None:
@@ -667,7 +668,8 @@ def set_launch_rules(rules, ctx: "Context | None" = None) -> None:
 
 
 def set_kernel_policy(policy, ctx: Context | None = None) -> None:
-    """Fused-path kernel for later single-scenario calls: "auto", "per_sample" or "split"."""
+    """Fused-path kernel for later single-scenario calls: "auto", "per_sample", "split" or
+    "split_tc"."""
     ctx = ctx or default_context()
     ctx.check(ctx.lib.fmc_set_kernel_policy(ctx.h, _KERNEL.get(policy, policy)))
 

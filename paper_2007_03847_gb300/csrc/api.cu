@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "swing.cuh"
 #include "tc_common.cuh"
+#include "wide_tc.cuh"
 #include "api_internal.h"
 
 using namespace fmc;
@@ -416,7 +417,24 @@ static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const dou
 // Constant block of the large-system kernel (layout at wide_const_floats): the
 // same deviation-form constants as build_params, with the network matrices
 // arranged [j][h][k] for machine i = h + 4k.
-static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, std::vector<float>& out)
+// Nearest TF32 value (ties to even) of x, as an FP32 number.
+static float tf32_round(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x0fffu + ((u >> 13) & 1u);
+        u &= 0xffffe000u;
+    }
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Offset (floats) of the tensor-core network matrix in the constant block.
+static size_t wide_net_offset(int n, int nmt, int nd) { return ((size_t)wide_const_floats(n, nmt, nd) + 31) & ~(size_t)31; }
+
+static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, bool tcn, std::vector<float>& out)
 {
     const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
     const int dx = d + (s->event_machine >= 0 ? 1 : 0);
@@ -458,6 +476,35 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
     double hsum = 0.0;
     for (int i = 0; i < n; ++i) hsum += s->H[i];
     for (int i = 0; i < n; ++i) pm[7 * g4 + i] = (float)(s->H[i] / hsum);
+    if (tcn) {
+        // the network matrix of the tensor-core sum (wide_tc.cuh), 128-byte
+        // aligned after the constant block: Net[(i, u|v)][(j, gamma|eta)] =
+        //   u: ( GE_ij, -BE_ij ),  v: ( BE_ij, GE_ij ),  diagonal and padding zero,
+        // as Net_hi = TF32(Net) and Net_lo = TF32(Net - Net_hi)
+        const int KH = wide_kh(nmt), NN = wide_nn(nmt);
+        const size_t base = (out.size() + 31) & ~(size_t)31;
+        out.resize(base + 2 * (size_t)NN * NN, 0.f);
+        float* hi = out.data() + base;
+        float* lo = hi + (size_t)NN * NN;
+        auto put = [&](int row, int col, double x) {
+            const float h = tf32_round(x);
+            hi[(size_t)row * NN + col] = h;
+            lo[(size_t)row * NN + col] = tf32_round(x - (double)h);
+        };
+        for (int i = 0; i < n; ++i) {
+            const int ru = (i % 4) * KH + 2 * (i / 4);
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const int cg = (j % 4) * KH + 2 * (j / 4);
+                const double ge = s->E[i] * s->E[j] * s->G[i * n + j];
+                const double be = s->E[i] * s->E[j] * s->B[i * n + j];
+                put(ru, cg, ge);
+                put(ru, cg + 1, -be);
+                put(ru + 1, cg, be);
+                put(ru + 1, cg + 1, ge);
+            }
+        }
+    }
     if (s->event_machine >= 0) pm[(8 + d) * g4 + s->event_machine] = (float)s->event_dpm;
 }
 
@@ -504,6 +551,23 @@ static int run_equilibrium_ws(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s
 static int run_equilibrium(fmc_ctx* ctx, const fmc_scenario* s, cudaStream_t st)
 {
     return run_equilibrium_ws(ctx, ctx->ws, s, st);
+}
+
+// Tensor map of the tensor-core network matrix: FP32 [2 NN][NN] (Net_hi rows,
+// then Net_lo rows), boxes of 16 values x NN rows, 64-byte swizzle.
+static int make_map_net(fmc_ctx* ctx, CUtensorMap* m, const void* base, int NN)
+{
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return fail(ctx, FMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)NN, (cuuint64_t)(2 * NN)};
+    cuuint64_t strides[1] = {(cuuint64_t)NN * 4};
+    cuuint32_t box[2] = {16, (cuuint32_t)NN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, FMC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FMC_OK;
 }
 
 static int make_map_bf16(fmc_ctx* ctx, CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
@@ -1025,6 +1089,7 @@ struct Prepared {
 
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
+    bool tcn = false;  // the large-system kernel sums the network on the tensor cores
     bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
@@ -1073,12 +1138,16 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (path == FMC_PATH_FUSED && per_sample && P.nm < 0)
         return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
                     FMC_MAX_MACHINES_PLAIN, n);
-    if (path == FMC_PATH_FUSED && policy == FMC_KERNEL_SPLIT)
+    if (path == FMC_PATH_FUSED && (policy == FMC_KERNEL_SPLIT || policy == FMC_KERNEL_SPLIT_TC))
         P.nmt = wide_nmt_for(n);
     else if (path == FMC_PATH_FUSED && per_sample)
         P.nmt = 0;
     else
         P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
+    P.tcn = P.nmt > 0 && (policy == FMC_KERNEL_SPLIT_TC || (policy == FMC_KERNEL_AUTO && wide_tc_built(P.nmt)));
+    if (policy == FMC_KERNEL_SPLIT_TC && !wide_tc_built(P.nmt))
+        return fail(ctx, FMC_EUNSUPPORTED, "the tensor-core network sum handles 13 to %d machines (n = %d)",
+                    FMC_MAX_MACHINES, n);
     if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && P.nmt > 0)
         return fail(ctx, FMC_EUNSUPPORTED,
                     "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
@@ -1104,7 +1173,7 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         // constants of the large-system kernel go to the device once, here
         // (outside any stream capture)
         std::vector<float> wc;
-        build_wide_consts(s, delta0.data(), P.nmt, wc);
+        build_wide_consts(s, delta0.data(), P.nmt, P.tcn, wc);
         if ((rc = ensure(ctx, ws.wconst, wc.size() * sizeof(float)))) return rc;
         FMC_CUDA(ctx, cudaMemcpyAsync(ws.wconst.ptr, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice, st),
                  "copy constants");
@@ -1172,6 +1241,12 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
     int TC = (wide || per == 2) ? 128 : 256;
     if (rule && rule->TC > 0 && rule->TC < TC) TC = rule->TC;
     while (TC > 16 && per * d * TC > cols) TC >>= 1;
+    if (P.tcn) {
+        // the network sum's A_hi, A_lo and D columns come first: the chunk takes
+        // the largest multiple of 16 steps that the rest holds
+        const int t = ((512 - wide_tc_cols(P.nmt)) / d) & ~15;
+        if (t < TC) TC = t < 16 ? 16 : t;
+    }
     f.TC = TC;
     f.ctas = (P.count + f.rows - 1) / f.rows;
     return f;
@@ -1361,7 +1436,16 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         }
         wa.rrf = rrf;
         build_ito<8>(s, wa.ito);
-        e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
+        if (P.tcn) {
+            CUtensorMap maps5[5] = {maps[0], maps[1], maps[2], maps[3], {}};
+            if ((rc = make_map_net(ctx, &maps5[4], (const float*)ws.wconst.ptr + wide_net_offset(n, P.nmt, P.nd),
+                                   wide_nn(P.nmt))))
+                return rc;
+            wa.tmem_cols = tmem_cols = 512;
+            e = launch_simulate_wide_tc(P.nmt, P.nd, maps5, wa, st, &occ);
+        } else {
+            e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
+        }
     } else {
         // a launch that has the GPU to itself keeps as many design tiles in L2 as
         // 60 % of it holds: every chunk re-reads each tile, and the whole design
@@ -1858,7 +1942,7 @@ int fmc_set_launch_rules(fmc_ctx* ctx, const fmc_launch_rule* rules, int32_t cou
         const fmc_launch_rule& r = rules[k];
         const bool tc_ok = r.TC == 0 || (r.TC >= 16 && r.TC <= 256 && (r.TC & (r.TC - 1)) == 0);
         if (r.n_min > r.n_max || r.d_min > r.d_max || r.N_min > r.N_max || r.kernel < FMC_KERNEL_AUTO ||
-            r.kernel > FMC_KERNEL_SPLIT || r.max_ctas < 0 || r.max_ctas > 4 || !tc_ok)
+            r.kernel > FMC_KERNEL_SPLIT_TC || r.max_ctas < 0 || r.max_ctas > 4 || !tc_ok)
             return fail(ctx, FMC_EINVAL, "launch rule %d is malformed", k);
     }
     ctx->rules.assign(rules, rules + count);
@@ -1868,7 +1952,7 @@ int fmc_set_launch_rules(fmc_ctx* ctx, const fmc_launch_rule* rules, int32_t cou
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy)
 {
     if (!ctx) return FMC_EINVAL;
-    if (policy < FMC_KERNEL_AUTO || policy > FMC_KERNEL_SPLIT)
+    if (policy < FMC_KERNEL_AUTO || policy > FMC_KERNEL_SPLIT_TC)
         return fail(ctx, FMC_EINVAL, "kernel policy %d", policy);
     ctx->kernel_policy = policy;
     return FMC_OK;

@@ -26,6 +26,7 @@
 #include "swing.cuh"
 #include "tc_common.cuh"
 #include "disturb_chunk.cuh"
+#include "wide_tc.cuh"
 
 namespace fmc {
 
@@ -49,11 +50,13 @@ __device__ __forceinline__ float2 wide_gamma_eta(float x, float cs, float ss, bo
     return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
 }
 
-template <int NMT, int ND>
+// TCN: the network sums on the tensor cores (wide_tc.cuh) instead of the FP32
+// pipes; the per-machine arithmetic around them is the same.
+template <int NMT, int ND, bool TCN>
 __global__ void __launch_bounds__(WI_THREADS, 1)
     simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                          const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                         const __grid_constant__ WideArgs a)
+                         const __grid_constant__ CUtensorMap mN, const __grid_constant__ WideArgs a)
 {
     constexpr int NMTP = wide_nmtp(NMT);
     constexpr int KP = NMT > 10 ? 8 : NMT;  // machine slots per pass over the network sum
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     // integer round trip), so that every access through these pointers stays a
     // shared-memory access rather than a generic one
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    __shared__ uint64_t bars[2 * TC_MAX_STAGES + 1];  // full[ns], freed[ns], done
+    __shared__ uint64_t bars[2 * TC_MAX_STAGES + 3];  // full[ns], freed[ns], done, net, net load
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -81,6 +84,13 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const int64_t srow = row0 + r;
     const bool active = srow < a.count;
     const int TC = a.TC;
+    constexpr int NN = wide_nn(NMT);
+    // TCN: TMEM columns of A_hi, A_lo and D past the disturbance columns
+    const uint32_t net0 = (uint32_t)((d * TC + 15) & ~15);
+    if (TCN && net0 + (uint32_t)wide_tc_cols(NMT) > a.tmem_cols) {
+        if (tid == 0) atomicExch(a.err, DEV_BAD_CONFIG);
+        return;
+    }
 
     // shared memory: [ring | moment buffers] [gamma/eta x2] [w0 x2] [constants]
     TcRing ring;
@@ -98,16 +108,23 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const uint32_t u_bytes = ((ring_bytes > mom_bytes ? ring_bytes : mom_bytes) + 1023u) & ~1023u;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;   // [32][WROW] per warp
     float* msum = reinterpret_cast<float*>(smem) + 16 * 32 * WROW;     // [WI_MS][q][h][4 NMT]
-    float2* gh = reinterpret_cast<float2*>(smem + u_bytes);            // [2][n][128]
-    float* w0buf = reinterpret_cast<float*>(gh + 2 * n * 128);         // [2][128]
+    // TCN: Net_hi | Net_lo (1 KB aligned); else the (gamma, eta) exchange [2][n][128]
+    uint8_t* net_s = smem + u_bytes;
+    float2* gh = reinterpret_cast<float2*>(smem + u_bytes);
+    float* w0buf = TCN ? reinterpret_cast<float*>(net_s + wide_tc_net_bytes(NMT))
+                       : reinterpret_cast<float*>(gh + 2 * n * 128);  // [2][128]
     float* racc_s = w0buf + 256;                                        // [128] (warps h = 0)
-    float* cst_s = w0buf + 384;
+    // TCN: [2][4 (h)][128] partial sums of a stage input's deviations over the warp's machines
+    float* cpart = w0buf + 384;
+    float* cst_s = w0buf + 384 + (TCN ? 1024 : 0);
     const int dx = a.dx;
-    const int nconst = wide_const_floats(n, NMT, ND);
-    for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[e];
+    // TCN keeps only the per-machine rows (the network is in net_s)
+    const int nskip = TCN ? 2 * n * 4 * NMTP : 0;
+    const int nconst = wide_const_floats(n, NMT, ND) - nskip;
+    for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[nskip + e];
     // [j][h][GE row of NMTP | BE row of NMTP]: one address serves both rows
     const float* GB = cst_s;
-    const float* pm = cst_s + 2 * n * 4 * NMTP;
+    const float* pm = cst_s + 2 * n * 4 * NMTP - nskip;
     const float* c_cst = pm;
     const float* c_sst = pm + G4;
     const float* c_ust = pm + 2 * G4;
@@ -121,14 +138,24 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     float* coi_part = msum + WI_MS * 16 * GS;  // [WI_MS][4 (h)][128]
 
     const bool em = a.em.on != 0;
+    uint64_t* netbar = &bars[2 * TC_MAX_STAGES + 1];
+    uint64_t* netld = &bars[2 * TC_MAX_STAGES + 2];
     if (tid == 0) {
         if (!em) {
             prefetch_tmap(&mAh);
             prefetch_tmap(&mBh);
         }
-        for (int b = 0; b < 2 * TC_MAX_STAGES + 1; ++b) mbar_init(&bars[b], 1);
+        for (int b = 0; b < 2 * TC_MAX_STAGES + 3; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
         abort_flag = 0;
+        if (TCN) {
+            // Net_hi and Net_lo, one box of NN rows per K block of 16 values
+            mbar_arrive_expect_tx(netld, (uint32_t)wide_tc_net_bytes(NMT));
+            for (int kb = 0; kb < NN / 16; ++kb) {
+                tma_load_2d(net_s + kb * NN * 64, &mN, kb * 16, 0, netld);
+                tma_load_2d(net_s + (NN / 16 + kb) * NN * 64, &mN, kb * 16, NN, netld);
+            }
+        }
     }
     if (warp == 0) tmem_alloc(&tmem_base, a.tmem_cols);
     tc_fence_before();
@@ -136,6 +163,16 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    // TCN: this warp's columns of A_hi, A_lo and D
+    const uint32_t a_hi = lane_addr + net0 + (uint32_t)(h * wide_kh(NMT));
+    const uint32_t a_lo = a_hi + NN, a_d = a_hi + 2 * NN;
+    int bad = 0;          // TCN: a bounded wait of this thread gave up
+    bool failed = false;  // TCN: the CTA stops (uniform)
+    uint32_t nph = 0;     // TCN: parity of the network product's barrier
+    if (TCN && tid == 0 && !mbar_wait(netld, 0)) {
+        bad = 1;
+        atomicExch(a.err, DEV_TIMEOUT_TMA);
+    }
 
     float del[NMT], w[NMT], theta = 0.f;  // deviations from the equilibrium
     float x0[ND];
@@ -165,10 +202,24 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 
     // stage-0 input of the first step: every deviation is zero
     int gb = 0;
+    // TCN: the deviations enter the trigonometric terms less their per-sample mean
+    // (of the previous stage input; the electrical power depends on angle
+    // differences alone, so any common shift is exact without an infinite bus),
+    // which keeps the product's inputs, and so its rounding, at the size of the
+    // machines' relative motion
+    float csh = 0.f;
+    const float inv_n = a.rel ? 1.0f / (float)n : 0.f;
+    if constexpr (TCN) {
 #pragma unroll
-    for (int k = 0; k < NMT; ++k) {
-        const int i = h + 4 * k;
-        if (i < n) gh[i * 128 + r] = make_float2(0.f, 0.f);
+        for (int k = 0; k < NMT; k += 2) net_store4(a_hi, a_lo, 2 * k, 0.f, 0.f, 0.f, 0.f);
+        tmem_st_wait();
+        cpart[h * 128 + r] = 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < NMT; ++k) {
+            const int i = h + 4 * k;
+            if (i < n) gh[i * 128 + r] = make_float2(0.f, 0.f);
+        }
     }
     if (h == 0) w0buf[r] = 0.f;
 
@@ -260,6 +311,107 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 ad[k] = 0.f;
                 aw[k] = 0.f;
             }
+if constexpr (TCN) {
+#pragma unroll 1
+            for (int st = 0; st < nst; ++st) {
+                float b, cn, xw;
+                if (rk4) {
+                    b = (st == 1 || st == 2) ? 2.f : 1.f;
+                    cn = (st == 2) ? dt : 0.5f * dt;
+                    xw = (st == 0) ? 0.f : ((st == 3) ? 1.f : 0.5f);
+                } else {
+                    b = 1.f;
+                    cn = dt;
+                    xw = (st == 0) ? 0.f : 1.f;
+                }
+                // every warp's A columns of this stage's input are written and
+                // every read of the previous product is done
+                tc_fence_before();
+                if (__syncthreads_or(bad)) {
+                    failed = true;
+                    break;
+                }
+                if (tid == 0) {
+                    tc_fence_after();
+                    net_mma<NMT>(tmem + net0 + 2 * NN, tmem + net0, tmem + net0 + NN, smem_u32(net_s));
+                    umma_commit(netbar);
+                }
+                {
+                    const float* cp = cpart + gb * 512 + r;
+                    csh = (((cp[0] + cp[128]) + cp[256]) + cp[384]) * inv_n;
+                }
+                if (!mbar_wait(netbar, nph)) {
+                    bad = 1;
+                    atomicExch(a.err, DEV_TIMEOUT_MMA);
+                }
+                nph ^= 1u;
+                tc_fence_after();
+                const float w0 = w0buf[gb * 128 + r] * ref;
+                float xs[ND];
+#pragma unroll
+                for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
+                const bool pub = (st + 1 < nst);
+                // D with the (gamma, eta) it was formed from, in pieces of 4 machines
+                // (8 columns), so that few values are live at once; the next stage's
+                // input goes out in pairs of machines as soon as they are computed
+                constexpr int RP = 4;
+                float dd[2 * RP], ah[2 * RP], al[2 * RP];
+                float pg = 0.f, pe = 0.f;  // (gamma, eta) of the pair's first machine
+                float ps = 0.f;            // sum of the next stage input's deviations
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    if (k % RP == 0) {
+                        // columns of a last, partial piece
+                        constexpr int WT = NMT % RP == 0 ? 2 * RP : (2 * (NMT % RP) + 3) & ~3;
+                        if (NMT - k >= RP)
+                            net_read<2 * RP>(a_d, a_hi, a_lo, 2 * k, dd, ah, al);
+                        else
+                            net_read<WT>(a_d, a_hi, a_lo, 2 * k, reinterpret_cast<float(&)[WT]>(dd),
+                                         reinterpret_cast<float(&)[WT]>(ah), reinterpret_cast<float(&)[WT]>(al));
+                    }
+                    const int i = h + 4 * k;
+                    const int c = 2 * (k % RP);
+                    const float du = dd[c], dv = dd[c + 1];
+                    const float gi = ah[c] + al[c], ei = ah[c + 1] + al[c + 1];
+                    const float cs = c_cst[i], ss = c_sst[i];
+                    float dpe = fmaf(cs, du, ss * dv);
+                    dpe = fmaf(gi, c_ust[i] + du, dpe);
+                    dpe = fmaf(ei, c_vst[i] + dv, dpe);
+                    float f = 0.f;
+#pragma unroll
+                    for (int e = 0; e < ND; ++e)
+                        f = fmaf(c_inj[e * G4 + i], xs[e], f);  // rows past the slots in use are zero
+                    const float kd = a.omega_s * (yw[k] - w0);
+                    const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
+                    ad[k] = fmaf(b, kd, ad[k]);
+                    aw[k] = fmaf(b, kw, aw[k]);
+                    const float yd = fmaf(cn, kd, del[k]);
+                    yw[k] = fmaf(cn, kw, w[k]);
+                    if (pub) {
+                        // the next stage's input of machine i (its columns were read above)
+                        const float yr = yd - csh;
+                        const bool big = __any_sync(0xffffffffu, i < n && fabsf(yr) > 0.8f);
+                        const float2 g = wide_gamma_eta(yr, cs, ss, big);
+                        const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
+                        ps += i < n ? yd : 0.f;
+                        if (k & 1)
+                            net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
+                        else if (k == NMT - 1)
+                            net_store4(a_hi, a_lo, 2 * k, gx, ex, 0.f, 0.f);
+                        pg = gx;
+                        pe = ex;
+                    }
+                }
+                if (pub) {
+                    tmem_st_wait();
+                    cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                }
+                if (pub && h == 0) w0buf[(gb ^ 1) * 128 + r] = yw[0];
+                ath = fmaf(b, a.omega_s * w0, ath);
+                if (pub) gb ^= 1;
+            }
+            if (failed) break;
+} else {
 #pragma unroll 1
             for (int st = 0; st < nst; ++st) {
                 float b, cn, xw;
@@ -391,6 +543,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 ath = fmaf(b, a.omega_s * w0, ath);
                 if (pub) gb ^= 1;
             }
+}
 #pragma unroll
             for (int k = 0; k < NMT; ++k) {
                 del[k] = fmaf(hh, ad[k], del[k]);
@@ -400,7 +553,28 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 #pragma unroll
             for (int e = 0; e < ND; ++e) x0[e] = x1[e];
             // stage-0 input of the next step
-            {
+            if constexpr (TCN) {
+                float pg = 0.f, pe = 0.f, ps = 0.f;
+#pragma unroll
+                for (int k = 0; k < NMT; ++k) {
+                    const int i = h + 4 * k;
+                    const float yr = del[k] - csh;
+                    const bool big = __any_sync(0xffffffffu, i < n && fabsf(yr) > 0.8f);
+                    const float2 g = wide_gamma_eta(yr, c_cst[i], c_sst[i], big);
+                    const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
+                    ps += i < n ? del[k] : 0.f;
+                    if (k & 1)
+                        net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
+                    else if (k == NMT - 1)
+                        net_store4(a_hi, a_lo, 2 * k, gx, ex, 0.f, 0.f);
+                    pg = gx;
+                    pe = ex;
+                }
+                tmem_st_wait();
+                cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
+                gb ^= 1;
+            } else {
                 float2* ghn = gh + (gb ^ 1) * n * 128 + r;
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) {
@@ -490,6 +664,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
                 __syncthreads();
             }
         }
+        if (failed) break;
     }
     if (a.rrf && h == 0) rrf_accumulate(active ? sqrtf(racc_s[r] / (float)a.Nt) : 0.f, a.rrf);
     tc_fence_before();
@@ -498,25 +673,29 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
 }
 
 // Dynamic shared memory of the kernel (bytes), alignment slack included.
-template <int NMT, int ND>
+template <int NMT, int ND, bool TCN>
 inline int wide_smem_bytes(int TC, int split, int n, int ns)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
     const int mom = wide_mom_floats<NMT>() * 4;
     const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
+    if (TCN)
+        return 1024 + u + wide_tc_net_bytes(NMT) + (384 + 1024) * 4 + (8 + ND) * 4 * NMT * 4;
     return 1024 + u + 2 * n * 128 * 8 + 384 * 4 + wide_const_floats(n, NMT, ND) * 4;
 }
 
-template <int NMT, int ND>
+// maps: the four contraction maps, then (TCN) the map of the network matrix.
+template <int NMT, int ND, bool TCN = false>
 cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStream_t st, int* occ_out)
 {
-    auto kern = simulate_wide_kernel<NMT, ND>;
+    auto kern = simulate_wide_kernel<NMT, ND, TCN>;
     // as many ring stages as the shared memory left by the other buffers holds
     WideArgs a = args;
     a.ns = 2;
-    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT, ND>(a.TC, a.split, a.n, a.ns + 1) <= TC_SMEM_DYN_MAX)
+    while (a.ns < TC_MAX_STAGES &&
+           wide_smem_bytes<NMT, ND, TCN>(a.TC, a.split, a.n, a.ns + 1) <= TC_SMEM_DYN_MAX)
         ++a.ns;
-    const int smem = wide_smem_bytes<NMT, ND>(a.TC, a.split, a.n, a.ns);
+    const int smem = wide_smem_bytes<NMT, ND, TCN>(a.TC, a.split, a.n, a.ns);
     if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size
@@ -529,7 +708,7 @@ cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStr
     if (occ < 1 || (uint32_t)occ * a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
     const int64_t ntiles = (a.count + TC_M - 1) / TC_M;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
-    kern<<<(unsigned)ntiles, WI_THREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    kern<<<(unsigned)ntiles, WI_THREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[TCN ? 4 : 0], a);
     return cudaGetLastError();
 }
 

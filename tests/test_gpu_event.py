@@ -53,12 +53,14 @@ def _rrf_check(rrf, ref_rrf):
     assert abs(v - ref_rrf.var(ddof=1)) <= 2.0 * eps * rms * sd * len(ref_rrf) / (len(ref_rrf) - 1) + 1e-30
 
 
-@pytest.mark.parametrize("kernel", ["per_sample", "split"])
+@pytest.mark.parametrize("kernel", ["per_sample", "split", "split_tc"])
 @pytest.mark.parametrize("case", ["mm10_trip", "mm7_d4_gain", "mm22_trip", "smib_step"])
 def test_event_fused(fmc, orc, kernel, case):
     sc = _cases()[case]
     if kernel.startswith("per_sample") and sc.n > 16:
         pytest.skip("the per-sample kernel takes up to 16 machines")
+    if kernel == "split_tc" and sc.n < 13:
+        pytest.skip("the tensor-core network sum takes 13 machines and more")
     fmc.set_kernel_policy(kernel)
     try:
         mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)

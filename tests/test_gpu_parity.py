@@ -52,7 +52,7 @@ def _same_to_fp32(m, v, m1, v1):
 
 def _batch_kernel(fmc, sc):
     # the kernel a batch (shared GPU) takes for this scenario
-    fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
+    fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split_tc")
 
 
 def _zeta_tol(zref):

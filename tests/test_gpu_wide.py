@@ -1,5 +1,6 @@
 """GPU parity of the large-system fused kernel (17..52 machines, four warps per
-sample group) against the FP64 oracle.
+sample group) against the FP64 oracle, with the network sums on the FP32 pipes
+("split") and as the tensor-core TF32x3 product ("split_tc", the automatic choice).
 
 Same tolerances as the other simulation parity tests: trajectories within 1e-4
 normwise relative error on delta and on omega separately, moments within 1e-5.
@@ -36,10 +37,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("kernel", ["split", "split_tc"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_wide_trajectories_and_moments(fmc, orc, case):
+def test_wide_trajectories_and_moments(fmc, orc, case, kernel):
     sc = fs.multimachine_case(**CASES[case])
-    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    fmc.set_kernel_policy(kernel)
+    try:
+        mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    finally:
+        fmc.set_kernel_policy("auto")
     fmc.device_status()
     zr = orc.lhs_sample(sc.seed, sc.N, sc.M)
     ref = orc.simulate(sc, zr, want_traj=True, nthreads=8)
@@ -121,7 +127,7 @@ def test_wide_in_a_batch(fmc):
     fmc.device_status()
     for sc, m, v in zip(scs, means, vars_):
         # the kernel the batch takes for this scenario on a shared GPU
-        fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split")
+        fmc.set_kernel_policy("per_sample" if sc.n <= 16 else "split_tc")
         m1, v1 = fmc.simulate(sc, path="fused", precision="bf16x3")
         fmc.set_kernel_policy("auto")
         # FP32 merge of tile groups in a single call, FP64 tile sums in the batch:
@@ -132,3 +138,31 @@ def test_wide_in_a_batch(fmc):
             assert np.max(np.abs(mm[:, sl] - mm1[:, sl])) <= 1e-6 * sd + 1e-15
             assert np.allclose(vv[:, sl], vv1[:, sl], rtol=2e-6, atol=1e-18)
     b.close()
+
+
+@pytest.mark.parametrize("n,d", [(13, 2), (20, 3), (50, 3), (52, 8)])
+def test_tensor_core_network_sum_matches_fp32_sum(fmc, n, d):
+    # the TF32x3 product drops terms below 2^-21 of each product: the two forms of
+    # the same design agree far inside the oracle tolerance
+    sc = fs.multimachine_case(n=n, d=d, K=40, T=1.0, dt=0.005, N=300, seed=40 + n)
+    out = {}
+    for kernel in ("split", "split_tc"):
+        fmc.set_kernel_policy(kernel)
+        try:
+            out[kernel] = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+        finally:
+            fmc.set_kernel_policy("auto")
+        fmc.device_status()
+    ed, ew = traj_errors(out["split_tc"][2].cpu().numpy(), out["split"][2].cpu().numpy().astype(np.float64), n)
+    assert ed <= 1e-5 and ew <= 1e-5, (ed, ew)
+
+
+def test_tensor_core_network_sum_refuses_small_systems(fmc):
+    sc = fs.multimachine_case(n=12, d=2, K=10, T=0.1, dt=0.005, N=64)
+    fmc.set_kernel_policy("split_tc")
+    try:
+        with pytest.raises(fmc.FastMCError) as e:
+            fmc.simulate(sc)
+        assert e.value.code == 8
+    finally:
+        fmc.set_kernel_policy("auto")
