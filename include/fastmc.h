@@ -586,8 +586,9 @@ int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy);
  * scenario calls under FMC_KERNEL_AUTO and to its batches.  A chunk is cut to
  * what the TMEM share of max_ctas CTAs holds (and to 16 at least); the
  * large-system kernel keeps one CTA per SM.  The rules are copied; count 0
- * clears them.  FMC_EINVAL on a malformed rule (empty range, kernel, max_ctas
- * outside 0..4, TC not 0 or a power of two in 16..256).
+ * clears them.  FMC_EINVAL on a malformed rule (empty range, kernel not an
+ * FMC_KERNEL_* value, max_ctas outside 0..4, TC not 0 or a power of two in
+ * 16..256).
  */
 typedef struct fmc_launch_rule {
     int32_t n_min, n_max;   /* machines */

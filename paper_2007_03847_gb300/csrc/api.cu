@@ -476,6 +476,8 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
     double hsum = 0.0;
     for (int i = 0; i < n; ++i) hsum += s->H[i];
     for (int i = 0; i < n; ++i) pm[7 * g4 + i] = (float)(s->H[i] / hsum);
+    if (s->event_machine >= 0) pm[(8 + d) * g4 + s->event_machine] = (float)s->event_dpm;
+    // (GB and pm point into out: nothing below writes through them, out may move)
     if (tcn) {
         // the network matrix of the tensor-core sum (wide_tc.cuh), 128-byte
         // aligned after the constant block: Net[(i, u|v)][(j, gamma|eta)] =
@@ -505,7 +507,6 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
             }
         }
     }
-    if (s->event_machine >= 0) pm[(8 + d) * g4 + s->event_machine] = (float)s->event_dpm;
 }
 
 // Copies the system arrays to the device and launches the FP64 Newton kernel.

@@ -52,6 +52,25 @@ __device__ __forceinline__ float2 wide_gamma_eta(float x, float cs, float ss, bo
 
 // TCN: the network sums on the tensor cores (wide_tc.cuh) instead of the FP32
 // pipes; the per-machine arithmetic around them is the same.
+// Warp-collective: the same with the series degree chosen from the warp's
+// largest |x| over the lanes where `use` holds (the tiers and their truncation
+// bounds of swing.cuh: 3/4 up to 0.05, 5/6 up to 0.25, 9/10 up to 0.8, then the
+// reduced-argument form).  Magnitudes compare as their FP32 bit patterns.
+__device__ __forceinline__ float2 wide_gamma_eta_tier(float x, float cs, float ss, bool use)
+{
+    const uint32_t m = __reduce_max_sync(0xffffffffu, use ? __float_as_uint(fabsf(x)) : 0u);
+    float sn, cm1;
+    if (m <= __float_as_uint(0.05f))
+        sin_cosm1_tiny(x, &sn, &cm1);
+    else if (m <= __float_as_uint(0.25f))
+        sin_cosm1_mid(x, &sn, &cm1);
+    else if (m <= __float_as_uint(0.8f))
+        sin_cosm1_small(x, &sn, &cm1);
+    else
+        sin_cosm1_any(x, &sn, &cm1);
+    return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
+}
+
 template <int NMT, int ND, bool TCN>
 __global__ void __launch_bounds__(WI_THREADS, 1)
     simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
@@ -118,10 +137,20 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     float* cpart = w0buf + 384;
     float* cst_s = w0buf + 384 + (TCN ? 1024 : 0);
     const int dx = a.dx;
-    // TCN keeps only the per-machine rows (the network is in net_s)
+    // TCN keeps only the per-machine rows (the network is in net_s), transposed to
+    // [4 NMT][CST] so that a machine's constants are a few 16-byte loads:
+    // (cos D*, sin D*, u*, v*), (delta*, 1/(2H), D, H / sum H), injection row
+    constexpr int CST = (8 + ND + 3) & ~3;
     const int nskip = TCN ? 2 * n * 4 * NMTP : 0;
     const int nconst = wide_const_floats(n, NMT, ND) - nskip;
-    for (int e = tid; e < nconst; e += WI_THREADS) cst_s[e] = a.consts[nskip + e];
+    for (int e = tid; e < nconst; e += WI_THREADS) {
+        if (TCN) {
+            const int row = e / G4, i = e - row * G4;
+            cst_s[i * CST + row] = a.consts[nskip + e];
+        } else {
+            cst_s[e] = a.consts[nskip + e];
+        }
+    }
     // [j][h][GE row of NMTP | BE row of NMTP]: one address serves both rows
     const float* GB = cst_s;
     const float* pm = cst_s + 2 * n * 4 * NMTP - nskip;
@@ -134,6 +163,9 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const float* c_D = pm + 6 * G4;
     const float* c_hw = pm + 7 * G4;
     const float* c_inj = pm + 8 * G4;  // [dx][4 NMT]
+    // constant `row` (0 cos D*, 1 sin D*, 2 u*, 3 v*, 4 delta*, 5 1/(2H), 6 D, 7 H / sum H,
+    // 8.. injection) of machine slot i, in either layout
+    auto cst = [&](int row, int i) -> float { return TCN ? cst_s[i * CST + row] : pm[row * G4 + i]; };
     // per step and warp, the partial centre-of-inertia speed of the warp's machines
     float* coi_part = msum + WI_MS * 16 * GS;  // [WI_MS][4 (h)][128]
 
@@ -191,7 +223,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
         for (int k = 0; k < NMT; ++k) {
             const int i = h + 4 * k;
             if (i < n) {
-                traj[i] = c_dst[i];
+                traj[i] = cst(4, i);
                 traj[n + i] = 0.f;
             }
         }
@@ -340,7 +372,7 @@ if constexpr (TCN) {
                     const float* cp = cpart + gb * 512 + r;
                     csh = (((cp[0] + cp[128]) + cp[256]) + cp[384]) * inv_n;
                 }
-                if (!mbar_wait(netbar, nph)) {
+                if (!net_wait(netbar, nph)) {
                     bad = 1;
                     atomicExch(a.err, DEV_TIMEOUT_MMA);
                 }
@@ -351,10 +383,11 @@ if constexpr (TCN) {
 #pragma unroll
                 for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
                 const bool pub = (st + 1 < nst);
-                // D with the (gamma, eta) it was formed from, in pieces of 4 machines
-                // (8 columns), so that few values are live at once; the next stage's
-                // input goes out in pairs of machines as soon as they are computed
-                constexpr int RP = 4;
+                // D with the (gamma, eta) it was formed from, in pieces of RP machines
+                // (2 RP columns; 2 above 40 machines, where registers are scarcest),
+                // so that few values are live at once; the next stage's input goes
+                // out in pairs of machines as soon as they are computed
+                constexpr int RP = NMT >= 10 ? 2 : 4;
                 float dd[2 * RP], ah[2 * RP], al[2 * RP];
                 float pg = 0.f, pe = 0.f;  // (gamma, eta) of the pair's first machine
                 float ps = 0.f;            // sum of the next stage input's deviations
@@ -373,16 +406,18 @@ if constexpr (TCN) {
                     const int c = 2 * (k % RP);
                     const float du = dd[c], dv = dd[c + 1];
                     const float gi = ah[c] + al[c], ei = ah[c + 1] + al[c + 1];
-                    const float cs = c_cst[i], ss = c_sst[i];
+                    const float4 ca = *reinterpret_cast<const float4*>(cst_s + i * CST);
+                    const float cs = ca.x, ss = ca.y;
                     float dpe = fmaf(cs, du, ss * dv);
-                    dpe = fmaf(gi, c_ust[i] + du, dpe);
-                    dpe = fmaf(ei, c_vst[i] + dv, dpe);
+                    dpe = fmaf(gi, ca.z + du, dpe);
+                    dpe = fmaf(ei, ca.w + dv, dpe);
                     float f = 0.f;
 #pragma unroll
                     for (int e = 0; e < ND; ++e)
-                        f = fmaf(c_inj[e * G4 + i], xs[e], f);  // rows past the slots in use are zero
+                        f = fmaf(cst_s[i * CST + 8 + e], xs[e], f);  // rows past the slots in use are zero
                     const float kd = a.omega_s * (yw[k] - w0);
-                    const float kw = (f - dpe - c_D[i] * yw[k]) * c_i2h[i];
+                    const float2 cb = *reinterpret_cast<const float2*>(cst_s + i * CST + 5);
+                    const float kw = (f - dpe - cb.y * yw[k]) * cb.x;
                     ad[k] = fmaf(b, kd, ad[k]);
                     aw[k] = fmaf(b, kw, aw[k]);
                     const float yd = fmaf(cn, kd, del[k]);
@@ -390,8 +425,7 @@ if constexpr (TCN) {
                     if (pub) {
                         // the next stage's input of machine i (its columns were read above)
                         const float yr = yd - csh;
-                        const bool big = __any_sync(0xffffffffu, i < n && fabsf(yr) > 0.8f);
-                        const float2 g = wide_gamma_eta(yr, cs, ss, big);
+                        const float2 g = wide_gamma_eta_tier(yr, cs, ss, i < n);
                         const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
                         ps += i < n ? yd : 0.f;
                         if (k & 1)
@@ -559,8 +593,8 @@ if constexpr (TCN) {
                 for (int k = 0; k < NMT; ++k) {
                     const int i = h + 4 * k;
                     const float yr = del[k] - csh;
-                    const bool big = __any_sync(0xffffffffu, i < n && fabsf(yr) > 0.8f);
-                    const float2 g = wide_gamma_eta(yr, c_cst[i], c_sst[i], big);
+                    const float2 csn = *reinterpret_cast<const float2*>(cst_s + i * CST);
+                    const float2 g = wide_gamma_eta_tier(yr, csn.x, csn.y, i < n);
                     const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
                     ps += i < n ? del[k] : 0.f;
                     if (k & 1)
@@ -593,7 +627,7 @@ if constexpr (TCN) {
                 for (int k = 0; k < NMT; ++k) {
                     const int i = h + 4 * k;
                     if (i < n) {
-                        o[i] = (theta + del[k]) + c_dst[i];
+                        o[i] = (theta + del[k]) + cst(4, i);
                         o[n + i] = w[k];
                     }
                 }
@@ -621,7 +655,7 @@ if constexpr (TCN) {
             if (a.rrf) {
                 float cp = 0.f;
 #pragma unroll
-                for (int k = 0; k < NMT; ++k) cp = fmaf(c_hw[h + 4 * k], w[k], cp);
+                for (int k = 0; k < NMT; ++k) cp = fmaf(cst(7, h + 4 * k), w[k], cp);
                 coi_part[(ms * 4 + h) * 128 + r] = cp;
             }
             __syncwarp();
@@ -680,7 +714,7 @@ inline int wide_smem_bytes(int TC, int split, int n, int ns)
     const int mom = wide_mom_floats<NMT>() * 4;
     const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
     if (TCN)
-        return 1024 + u + wide_tc_net_bytes(NMT) + (384 + 1024) * 4 + (8 + ND) * 4 * NMT * 4;
+        return 1024 + u + wide_tc_net_bytes(NMT) + (384 + 1024) * 4 + 4 * NMT * ((8 + ND + 3) & ~3) * 4;
     return 1024 + u + 2 * n * 128 * 8 + 384 * 4 + wide_const_floats(n, NMT, ND) * 4;
 }
 

@@ -112,6 +112,16 @@ __device__ __forceinline__ void net_mma(uint32_t d_tmem, uint32_t ahi_tmem, uint
     }
 }
 
+// Bounded wait for a stage's product: polls without sleeping first (the product
+// takes well under a microsecond, and a sleep would delay the wake-up), then with
+// the production limit and its sleeps.
+__device__ __forceinline__ bool net_wait(uint64_t* bar, uint32_t parity)
+{
+    for (int it = 0; it < 4096; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait(bar, parity);
+}
+
 // Warp-collective: four (gamma, eta) values of a pair of machines, split into
 // TF32 hi and lo, to columns col .. col + 3 of A_hi and A_lo (the caller waits
 // for the stores with tmem_st_wait before the next product).

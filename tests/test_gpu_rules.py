@@ -38,7 +38,7 @@ def test_malformed_rules_are_refused():
     fmc = need_gpu()
     ctx = fmc.Context(0)
     try:
-        for bad in (dict(n_min=5, n_max=4), dict(kernel=3), dict(max_ctas=5), dict(TC=48), dict(TC=512)):
+        for bad in (dict(n_min=5, n_max=4), dict(kernel=4), dict(max_ctas=5), dict(TC=48), dict(TC=512)):
             with pytest.raises(fmc.FastMCError) as e:
                 fmc.set_launch_rules([bad], ctx=ctx)
             assert e.value.code == fmc.EINVAL
