@@ -71,6 +71,53 @@ __device__ __forceinline__ float2 wide_gamma_eta_tier(float x, float cs, float s
     return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
 }
 
+// Warp-collective (tensor-core network sum): (gamma, eta) of the deviations
+// x[k] - csh of the warp's machines by the series of tier TIER, split and stored
+// pairwise to the warp's A_hi, A_lo columns; waits for the stores.
+template <int NMT, int TIER, int CST>
+__device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
+                                             const float* cst_s, int h, int n)
+{
+    float pg = 0.f, pe = 0.f;
+#pragma unroll
+    for (int k = 0; k < NMT; ++k) {
+        const int i = h + 4 * k;
+        const float2 csn = *reinterpret_cast<const float2*>(cst_s + i * CST);
+        float sn, cm1;
+        deviation_trig1<TIER>(x[k] - csh, &sn, &cm1);
+        const float gx = i < n ? fmaf(csn.x, cm1, -csn.y * sn) : 0.f;
+        const float ex = i < n ? fmaf(csn.y, cm1, csn.x * sn) : 0.f;
+        if (k & 1)
+            net_store4(hi, lo, 2 * (k - 1), pg, pe, gx, ex);
+        else if (k == NMT - 1)
+            net_store4(hi, lo, 2 * k, gx, ex, 0.f, 0.f);
+        pg = gx;
+        pe = ex;
+    }
+    tmem_st_wait();
+}
+
+// The same with one tier for all of the warp's machines, from their largest
+// shifted deviation (the tiers of wide_gamma_eta_tier).
+template <int NMT, int CST>
+__device__ __forceinline__ void publish_angles(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
+                                               const float* cst_s, int h, int n)
+{
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < NMT; ++k)
+        if (h + 4 * k < n) m = fmaxf(m, fabsf(x[k] - csh));
+    const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if (mm <= __float_as_uint(0.05f))
+        publish_tier<NMT, 0, CST>(hi, lo, x, csh, cst_s, h, n);
+    else if (mm <= __float_as_uint(0.25f))
+        publish_tier<NMT, 1, CST>(hi, lo, x, csh, cst_s, h, n);
+    else if (mm <= __float_as_uint(0.8f))
+        publish_tier<NMT, 2, CST>(hi, lo, x, csh, cst_s, h, n);
+    else
+        publish_tier<NMT, 3, CST>(hi, lo, x, csh, cst_s, h, n);
+}
+
 template <int NMT, int ND, bool TCN>
 __global__ void __launch_bounds__(WI_THREADS, 1)
     simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
@@ -158,10 +205,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const float* c_sst = pm + G4;
     const float* c_ust = pm + 2 * G4;
     const float* c_vst = pm + 3 * G4;
-    const float* c_dst = pm + 4 * G4;
     const float* c_i2h = pm + 5 * G4;
     const float* c_D = pm + 6 * G4;
-    const float* c_hw = pm + 7 * G4;
     const float* c_inj = pm + 8 * G4;  // [dx][4 NMT]
     // constant `row` (0 cos D*, 1 sin D*, 2 u*, 3 v*, 4 delta*, 5 1/(2H), 6 D, 7 H / sum H,
     // 8.. injection) of machine slot i, in either layout
@@ -195,7 +240,8 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    // TCN: this warp's columns of A_hi, A_lo and D
+    // TCN: this warp's columns of A_hi, A_lo (buffer 0; AB2: buffer 1 at +3 NN) and D
+    constexpr bool AB2 = TCN && wide_tc_abuf2(NMT);
     const uint32_t a_hi = lane_addr + net0 + (uint32_t)(h * wide_kh(NMT));
     const uint32_t a_lo = a_hi + NN, a_d = a_hi + 2 * NN;
     int bad = 0;          // TCN: a bounded wait of this thread gave up
@@ -356,6 +402,8 @@ if constexpr (TCN) {
                     cn = dt;
                     xw = (st == 0) ? 0.f : 1.f;
                 }
+                // A buffers of this stage's input and of the next
+                const uint32_t ab = AB2 && gb ? 3u * NN : 0u, an = AB2 && !gb ? 3u * NN : 0u;
                 // every warp's A columns of this stage's input are written and
                 // every read of the previous product is done
                 tc_fence_before();
@@ -365,41 +413,58 @@ if constexpr (TCN) {
                 }
                 if (tid == 0) {
                     tc_fence_after();
-                    net_mma<NMT>(tmem + net0 + 2 * NN, tmem + net0, tmem + net0 + NN, smem_u32(net_s));
+                    net_mma<NMT>(tmem + net0 + 2 * NN, tmem + net0 + ab, tmem + net0 + ab + NN, smem_u32(net_s));
                     umma_commit(netbar);
                 }
                 {
                     const float* cp = cpart + gb * 512 + r;
                     csh = (((cp[0] + cp[128]) + cp[256]) + cp[384]) * inv_n;
                 }
+                const float w0 = w0buf[gb * 128 + r] * ref;
+                const bool pub = (st + 1 < nst);
+                float pg = 0.f, pe = 0.f;  // (gamma, eta) of the pair's first machine
+                float ps = 0.f;            // sum of the next input's deviations
+                if constexpr (AB2) {
+                    // the angle half while the product runs: delta' depends on omega
+                    // alone, so the next stage's angle input (after the last stage:
+                    // the step's new angles, the next step's first input) and its
+                    // (gamma, eta) are known before the network sums
+                    float yn[NMT];
+#pragma unroll
+                    for (int k = 0; k < NMT; ++k) {
+                        const float kd = a.omega_s * (yw[k] - w0);
+                        ad[k] = fmaf(b, kd, ad[k]);
+                        yn[k] = pub ? fmaf(cn, kd, del[k]) : fmaf(hh, ad[k], del[k]);
+                        ps += h + 4 * k < n ? yn[k] : 0.f;
+                    }
+                    publish_angles<NMT, CST>(a_hi + an, a_lo + an, yn, csh, cst_s, h, n);
+                    cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                }
+                float xs[ND];
+#pragma unroll
+                for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
                 if (!net_wait(netbar, nph)) {
                     bad = 1;
                     atomicExch(a.err, DEV_TIMEOUT_MMA);
                 }
                 nph ^= 1u;
                 tc_fence_after();
-                const float w0 = w0buf[gb * 128 + r] * ref;
-                float xs[ND];
-#pragma unroll
-                for (int e = 0; e < ND; ++e) xs[e] = fmaf(xw, x1[e] - x0[e], x0[e]);
-                const bool pub = (st + 1 < nst);
                 // D with the (gamma, eta) it was formed from, in pieces of RP machines
-                // (2 RP columns; 2 above 40 machines, where registers are scarcest),
-                // so that few values are live at once; the next stage's input goes
-                // out in pairs of machines as soon as they are computed
-                constexpr int RP = NMT >= 10 ? 2 : 4;
+                // (2 RP columns; 2 from 7 slots on, where registers are scarcest),
+                // so that few values are live at once; with one A buffer the next
+                // stage's input goes out in pairs of machines as soon as they are
+                // computed
+                constexpr int RP = NMT >= 7 ? 2 : 4;
                 float dd[2 * RP], ah[2 * RP], al[2 * RP];
-                float pg = 0.f, pe = 0.f;  // (gamma, eta) of the pair's first machine
-                float ps = 0.f;            // sum of the next stage input's deviations
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) {
                     if (k % RP == 0) {
                         // columns of a last, partial piece
                         constexpr int WT = NMT % RP == 0 ? 2 * RP : (2 * (NMT % RP) + 3) & ~3;
                         if (NMT - k >= RP)
-                            net_read<2 * RP>(a_d, a_hi, a_lo, 2 * k, dd, ah, al);
+                            net_read<2 * RP>(a_d, a_hi + ab, a_lo + ab, 2 * k, dd, ah, al);
                         else
-                            net_read<WT>(a_d, a_hi, a_lo, 2 * k, reinterpret_cast<float(&)[WT]>(dd),
+                            net_read<WT>(a_d, a_hi + ab, a_lo + ab, 2 * k, reinterpret_cast<float(&)[WT]>(dd),
                                          reinterpret_cast<float(&)[WT]>(ah), reinterpret_cast<float(&)[WT]>(al));
                     }
                     const int i = h + 4 * k;
@@ -413,30 +478,36 @@ if constexpr (TCN) {
                     dpe = fmaf(ei, ca.w + dv, dpe);
                     float f = 0.f;
 #pragma unroll
-                    for (int e = 0; e < ND; ++e)
-                        f = fmaf(cst_s[i * CST + 8 + e], xs[e], f);  // rows past the slots in use are zero
-                    const float kd = a.omega_s * (yw[k] - w0);
+                    for (int e4 = 0; e4 < ND; e4 += 4) {
+                        // rows past the slots in use are zero
+                        const float4 cj = *reinterpret_cast<const float4*>(cst_s + i * CST + 8 + e4);
+                        const float cjv[4] = {cj.x, cj.y, cj.z, cj.w};
+#pragma unroll
+                        for (int e = e4; e < ND && e < e4 + 4; ++e) f = fmaf(cjv[e - e4], xs[e], f);
+                    }
                     const float2 cb = *reinterpret_cast<const float2*>(cst_s + i * CST + 5);
                     const float kw = (f - dpe - cb.y * yw[k]) * cb.x;
-                    ad[k] = fmaf(b, kd, ad[k]);
-                    aw[k] = fmaf(b, kw, aw[k]);
-                    const float yd = fmaf(cn, kd, del[k]);
-                    yw[k] = fmaf(cn, kw, w[k]);
-                    if (pub) {
-                        // the next stage's input of machine i (its columns were read above)
-                        const float yr = yd - csh;
-                        const float2 g = wide_gamma_eta_tier(yr, cs, ss, i < n);
-                        const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
-                        ps += i < n ? yd : 0.f;
-                        if (k & 1)
-                            net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
-                        else if (k == NMT - 1)
-                            net_store4(a_hi, a_lo, 2 * k, gx, ex, 0.f, 0.f);
-                        pg = gx;
-                        pe = ex;
+                    if constexpr (!AB2) {
+                        const float kd = a.omega_s * (yw[k] - w0);
+                        ad[k] = fmaf(b, kd, ad[k]);
+                        const float yd = fmaf(cn, kd, del[k]);
+                        if (pub) {
+                            // the next stage's input of machine i (its columns were read above)
+                            const float2 g = wide_gamma_eta_tier(yd - csh, cs, ss, i < n);
+                            const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
+                            ps += i < n ? yd : 0.f;
+                            if (k & 1)
+                                net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
+                            else if (k == NMT - 1)
+                                net_store4(a_hi, a_lo, 2 * k, gx, ex, 0.f, 0.f);
+                            pg = gx;
+                            pe = ex;
+                        }
                     }
+                    aw[k] = fmaf(b, kw, aw[k]);
+                    yw[k] = fmaf(cn, kw, w[k]);
                 }
-                if (pub) {
+                if (!AB2 && pub) {
                     tmem_st_wait();
                     cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
                 }
@@ -586,25 +657,15 @@ if constexpr (TCN) {
             theta = fmaf(hh, ath, theta);
 #pragma unroll
             for (int e = 0; e < ND; ++e) x0[e] = x1[e];
-            // stage-0 input of the next step
-            if constexpr (TCN) {
-                float pg = 0.f, pe = 0.f, ps = 0.f;
+            // stage-0 input of the next step (AB2: already published by the last stage)
+            if constexpr (AB2) {
+                if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
+                gb ^= 1;
+            } else if constexpr (TCN) {
+                float ps = 0.f;
 #pragma unroll
-                for (int k = 0; k < NMT; ++k) {
-                    const int i = h + 4 * k;
-                    const float yr = del[k] - csh;
-                    const float2 csn = *reinterpret_cast<const float2*>(cst_s + i * CST);
-                    const float2 g = wide_gamma_eta_tier(yr, csn.x, csn.y, i < n);
-                    const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
-                    ps += i < n ? del[k] : 0.f;
-                    if (k & 1)
-                        net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
-                    else if (k == NMT - 1)
-                        net_store4(a_hi, a_lo, 2 * k, gx, ex, 0.f, 0.f);
-                    pg = gx;
-                    pe = ex;
-                }
-                tmem_st_wait();
+                for (int k = 0; k < NMT; ++k) ps += h + 4 * k < n ? del[k] : 0.f;
+                publish_angles<NMT, CST>(a_hi, a_lo, del, csh, cst_s, h, n);
                 cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
                 if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
                 gb ^= 1;

@@ -35,8 +35,14 @@ __host__ __device__ constexpr bool wide_tc_built(int nmt)
     return nmt == 4 || nmt == 5 || nmt == 7 || nmt == 10 || nmt == 13;
 }
 
-// TMEM columns the network sum takes past the disturbance columns: A_hi, A_lo, D.
-__host__ __device__ constexpr int wide_tc_cols(int nmt) { return 3 * wide_nn(nmt); }
+// Up to 7 slots (28 machines) the stage inputs alternate between two A buffers,
+// so that the angle half of a stage (which needs no network sum) can publish the
+// next input while the tensor cores still read the current one.
+__host__ __device__ constexpr bool wide_tc_abuf2(int nmt) { return nmt <= 7; }
+
+// TMEM columns the network sum takes past the disturbance columns: A_hi, A_lo, D
+// (then A_hi, A_lo of the second buffer).
+__host__ __device__ constexpr int wide_tc_cols(int nmt) { return (wide_tc_abuf2(nmt) ? 5 : 3) * wide_nn(nmt); }
 
 // Shared-memory bytes of Net_hi and Net_lo: per matrix NN / 16 K blocks of NN
 // rows x 64 bytes (16 TF32 values), 64-byte swizzle, as one TMA box each.
