@@ -434,7 +434,8 @@ static float tf32_round(double x)
 // Offset (floats) of the tensor-core network matrix in the constant block.
 static size_t wide_net_offset(int n, int nmt, int nd) { return ((size_t)wide_const_floats(n, nmt, nd) + 31) & ~(size_t)31; }
 
-static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, bool tcn, std::vector<float>& out)
+static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, bool tcn, int H,
+                              std::vector<float>& out)
 {
     const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
     const int dx = d + (s->event_machine >= 0 ? 1 : 0);
@@ -483,7 +484,7 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
         // aligned after the constant block: Net[(i, u|v)][(j, gamma|eta)] =
         //   u: ( GE_ij, -BE_ij ),  v: ( BE_ij, GE_ij ),  diagonal and padding zero,
         // as Net_hi = TF32(Net) and Net_lo = TF32(Net - Net_hi)
-        const int KH = wide_kh(nmt), NN = wide_nn(nmt);
+        const int KH = wide_kh(nmt), NN = wide_nn(nmt, H);
         const size_t base = (out.size() + 31) & ~(size_t)31;
         out.resize(base + 2 * (size_t)NN * NN, 0.f);
         float* hi = out.data() + base;
@@ -494,10 +495,10 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
             lo[(size_t)row * NN + col] = tf32_round(x - (double)h);
         };
         for (int i = 0; i < n; ++i) {
-            const int ru = (i % 4) * KH + 2 * (i / 4);
+            const int ru = (i % H) * KH + 2 * (i / H);
             for (int j = 0; j < n; ++j) {
                 if (j == i) continue;
-                const int cg = (j % 4) * KH + 2 * (j / 4);
+                const int cg = (j % H) * KH + 2 * (j / H);
                 const double ge = s->E[i] * s->E[j] * s->G[i * n + j];
                 const double be = s->E[i] * s->E[j] * s->B[i * n + j];
                 put(ru, cg, ge);
@@ -1091,6 +1092,7 @@ struct Prepared {
     int Nt = 0, nm = 0, nd = 0, path = 0;
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
     bool tcn = false;  // the large-system kernel sums the network on the tensor cores
+    int H = 4;         // its warps per sample (2: two CTAs per SM, nmt slots of 2)
     bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
@@ -1149,6 +1151,17 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (policy == FMC_KERNEL_SPLIT_TC && !wide_tc_built(P.nmt))
         return fail(ctx, FMC_EUNSUPPORTED, "the tensor-core network sum handles 13 to %d machines (n = %d)",
                     FMC_MAX_MACHINES, n);
+    // 17..26 machines: two warps per sample and two CTAs per SM (10 or 13 slots
+    // per thread), whose barriers and product waits overlap, where the halved
+    // TMEM share holds the product's columns and a 16-step chunk of the
+    // disturbances (up to 7 with 10 slots, 4 with 13)
+    if (P.tcn && P.nmt == 5 && 16 * s->d + wide_tc_cols(10, 2) <= 256) {
+        P.H = 2;
+        P.nmt = 10;
+    } else if (P.tcn && P.nmt == 7 && n <= 26 && 16 * s->d + wide_tc_cols(13, 2) <= 256) {
+        P.H = 2;
+        P.nmt = 13;
+    }
     if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && P.nmt > 0)
         return fail(ctx, FMC_EUNSUPPORTED,
                     "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
@@ -1174,7 +1187,7 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         // constants of the large-system kernel go to the device once, here
         // (outside any stream capture)
         std::vector<float> wc;
-        build_wide_consts(s, delta0.data(), P.nmt, P.tcn, wc);
+        build_wide_consts(s, delta0.data(), P.nmt, P.tcn, P.H, wc);
         if ((rc = ensure(ctx, ws.wconst, wc.size() * sizeof(float)))) return rc;
         FMC_CUDA(ctx, cudaMemcpyAsync(ws.wconst.ptr, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice, st),
                  "copy constants");
@@ -1245,7 +1258,7 @@ static FusedShape fused_shape(const fmc_ctx* ctx, const Prepared& P)
     if (P.tcn) {
         // the network sum's A_hi, A_lo and D columns come first: the chunk takes
         // the largest multiple of 16 steps that the rest holds
-        const int t = ((512 - wide_tc_cols(P.nmt)) / d) & ~15;
+        const int t = ((512 / (4 / P.H) - wide_tc_cols(P.nmt, P.H)) / d) & ~15;
         if (t < TC) TC = t < 16 ? 16 : t;
     }
     f.TC = TC;
@@ -1440,10 +1453,10 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         if (P.tcn) {
             CUtensorMap maps5[5] = {maps[0], maps[1], maps[2], maps[3], {}};
             if ((rc = make_map_net(ctx, &maps5[4], (const float*)ws.wconst.ptr + wide_net_offset(n, P.nmt, P.nd),
-                                   wide_nn(P.nmt))))
+                                   wide_nn(P.nmt, P.H))))
                 return rc;
-            wa.tmem_cols = tmem_cols = 512;
-            e = launch_simulate_wide_tc(P.nmt, P.nd, maps5, wa, st, &occ);
+            wa.tmem_cols = tmem_cols = 512 / (4 / P.H);
+            e = launch_simulate_wide_tc(P.nmt, P.H, P.nd, maps5, wa, st, &occ);
         } else {
             e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
         }

@@ -30,11 +30,19 @@ static cudaError_t wide_tc_nmt7(int nd, const CUtensorMap* maps, const WideArgs&
 
 cudaError_t wide_tc_nmt10(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt10(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
-cudaError_t launch_simulate_wide_tc(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
-                                    int* max_ctas_per_sm)
+cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, const CUtensorMap* maps, const WideArgs& a,
+                                    cudaStream_t st, int* max_ctas_per_sm)
 {
-    if (a.n > 4 * nmt || a.d > nd || a.tmem_cols != 512u) return cudaErrorInvalidValue;
+    if (a.n > H * nmt || a.d > nd || a.tmem_cols != (H == 2 ? 256u : 512u)) return cudaErrorInvalidValue;
+    if (H == 2) {
+        if (nmt == 10) return wide_tc_h2_nmt10(nd, maps, a, st, max_ctas_per_sm);
+        if (nmt == 13) return wide_tc_h2_nmt13(nd, maps, a, st, max_ctas_per_sm);
+        return cudaErrorInvalidValue;
+    }
+    if (H != 4) return cudaErrorInvalidValue;
     switch (nmt) {
         case 4: return wide_tc_nmt4(nd, maps, a, st, max_ctas_per_sm);
         case 5: return wide_tc_nmt5(nd, maps, a, st, max_ctas_per_sm);

@@ -33,10 +33,12 @@ namespace fmc {
 constexpr int WI_THREADS = 512;
 constexpr int WI_MS = 4;  // steps between flushes of the moment buffer
 
-template <int NMT>
+// Moment buffers of a CTA of H warps per sample (4 H warps): per-warp transposes,
+// the (step, sample group, h) triples, the per-step centre-of-inertia partials.
+template <int NMT, int H = 4>
 __host__ __device__ inline int wide_mom_floats()
 {
-    return 16 * 32 * (2 * NMT + 1) + WI_MS * 16 * 6 * NMT + WI_MS * 4 * 128;
+    return 4 * H * 32 * (2 * NMT + 1) + WI_MS * 4 * H * 6 * NMT + WI_MS * H * 128;
 }
 
 // sin and cos - 1 of a deviation, rotated into (gamma, eta) about the equilibrium.
@@ -50,8 +52,6 @@ __device__ __forceinline__ float2 wide_gamma_eta(float x, float cs, float ss, bo
     return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
 }
 
-// TCN: the network sums on the tensor cores (wide_tc.cuh) instead of the FP32
-// pipes; the per-machine arithmetic around them is the same.
 // Warp-collective: the same with the series degree chosen from the warp's
 // largest |x| over the lanes where `use` holds (the tiers and their truncation
 // bounds of swing.cuh: 3/4 up to 0.05, 5/6 up to 0.25, 9/10 up to 0.8, then the
@@ -74,14 +74,14 @@ __device__ __forceinline__ float2 wide_gamma_eta_tier(float x, float cs, float s
 // Warp-collective (tensor-core network sum): (gamma, eta) of the deviations
 // x[k] - csh of the warp's machines by the series of tier TIER, split and stored
 // pairwise to the warp's A_hi, A_lo columns; waits for the stores.
-template <int NMT, int TIER, int CST>
+template <int NMT, int TIER, int CST, int H>
 __device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
                                              const float* cst_s, int h, int n)
 {
     float pg = 0.f, pe = 0.f;
 #pragma unroll
     for (int k = 0; k < NMT; ++k) {
-        const int i = h + 4 * k;
+        const int i = h + H * k;
         const float2 csn = *reinterpret_cast<const float2*>(cst_s + i * CST);
         float sn, cm1;
         deviation_trig1<TIER>(x[k] - csh, &sn, &cm1);
@@ -99,27 +99,30 @@ __device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const flo
 
 // The same with one tier for all of the warp's machines, from their largest
 // shifted deviation (the tiers of wide_gamma_eta_tier).
-template <int NMT, int CST>
+template <int NMT, int CST, int H>
 __device__ __forceinline__ void publish_angles(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
                                                const float* cst_s, int h, int n)
 {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < NMT; ++k)
-        if (h + 4 * k < n) m = fmaxf(m, fabsf(x[k] - csh));
+        if (h + H * k < n) m = fmaxf(m, fabsf(x[k] - csh));
     const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
     if (mm <= __float_as_uint(0.05f))
-        publish_tier<NMT, 0, CST>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 0, CST, H>(hi, lo, x, csh, cst_s, h, n);
     else if (mm <= __float_as_uint(0.25f))
-        publish_tier<NMT, 1, CST>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 1, CST, H>(hi, lo, x, csh, cst_s, h, n);
     else if (mm <= __float_as_uint(0.8f))
-        publish_tier<NMT, 2, CST>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 2, CST, H>(hi, lo, x, csh, cst_s, h, n);
     else
-        publish_tier<NMT, 3, CST>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 3, CST, H>(hi, lo, x, csh, cst_s, h, n);
 }
 
-template <int NMT, int ND, bool TCN>
-__global__ void __launch_bounds__(WI_THREADS, 1)
+// TCN: the network sums on the tensor cores (wide_tc.cuh) instead of the FP32
+// pipes; the per-machine arithmetic around them is the same.  H: warps per sample
+// (4; or 2 with TCN: two CTAs of 256 threads per SM), machine i = h + H k.
+template <int NMT, int ND, bool TCN, int H = 4>
+__global__ void __launch_bounds__(H * 128, 4 / H)
     simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                          const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                          const __grid_constant__ CUtensorMap mN, const __grid_constant__ WideArgs a)
@@ -150,10 +153,12 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const int64_t srow = row0 + r;
     const bool active = srow < a.count;
     const int TC = a.TC;
-    constexpr int NN = wide_nn(NMT);
+    static_assert(H == 4 || (H == 2 && TCN), "two warps per sample with the tensor-core network sum only");
+    constexpr int NTHR = H * 128;
+    constexpr int NN = wide_nn(NMT, H);
     // TCN: TMEM columns of A_hi, A_lo and D past the disturbance columns
     const uint32_t net0 = (uint32_t)((d * TC + 15) & ~15);
-    if (TCN && net0 + (uint32_t)wide_tc_cols(NMT) > a.tmem_cols) {
+    if (TCN && net0 + (uint32_t)wide_tc_cols(NMT, H) > a.tmem_cols) {
         if (tid == 0) atomicExch(a.err, DEV_BAD_CONFIG);
         return;
     }
@@ -169,15 +174,15 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     ring.full = &bars[0];
     ring.freed = &bars[TC_MAX_STAGES];
     uint64_t* done = &bars[2 * TC_MAX_STAGES];
-    const uint32_t mom_bytes = (uint32_t)wide_mom_floats<NMT>() * 4u;
+    const uint32_t mom_bytes = (uint32_t)wide_mom_floats<NMT, H>() * 4u;
     const uint32_t ring_bytes = (uint32_t)a.ns * stage_bytes;
     const uint32_t u_bytes = ((ring_bytes > mom_bytes ? ring_bytes : mom_bytes) + 1023u) & ~1023u;
     float* wbuf = reinterpret_cast<float*>(smem) + warp * 32 * WROW;   // [32][WROW] per warp
-    float* msum = reinterpret_cast<float*>(smem) + 16 * 32 * WROW;     // [WI_MS][q][h][4 NMT]
+    float* msum = reinterpret_cast<float*>(smem) + 4 * H * 32 * WROW;  // [WI_MS][q][h][GS]
     // TCN: Net_hi | Net_lo (1 KB aligned); else the (gamma, eta) exchange [2][n][128]
     uint8_t* net_s = smem + u_bytes;
     float2* gh = reinterpret_cast<float2*>(smem + u_bytes);
-    float* w0buf = TCN ? reinterpret_cast<float*>(net_s + wide_tc_net_bytes(NMT))
+    float* w0buf = TCN ? reinterpret_cast<float*>(net_s + wide_tc_net_bytes(NMT, H))
                        : reinterpret_cast<float*>(gh + 2 * n * 128);  // [2][128]
     float* racc_s = w0buf + 256;                                        // [128] (warps h = 0)
     // TCN: [2][4 (h)][128] partial sums of a stage input's deviations over the warp's machines
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     constexpr int CST = (8 + ND + 3) & ~3;
     const int nskip = TCN ? 2 * n * 4 * NMTP : 0;
     const int nconst = wide_const_floats(n, NMT, ND) - nskip;
-    for (int e = tid; e < nconst; e += WI_THREADS) {
+    for (int e = tid; e < nconst; e += NTHR) {
         if (TCN) {
             const int row = e / G4, i = e - row * G4;
             cst_s[i * CST + row] = a.consts[nskip + e];
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     // 8.. injection) of machine slot i, in either layout
     auto cst = [&](int row, int i) -> float { return TCN ? cst_s[i * CST + row] : pm[row * G4 + i]; };
     // per step and warp, the partial centre-of-inertia speed of the warp's machines
-    float* coi_part = msum + WI_MS * 16 * GS;  // [WI_MS][4 (h)][128]
+    float* coi_part = msum + WI_MS * 4 * H * GS;  // [WI_MS][H (h)][128]
 
     const bool em = a.em.on != 0;
     uint64_t* netbar = &bars[2 * TC_MAX_STAGES + 1];
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
         abort_flag = 0;
         if (TCN) {
             // Net_hi and Net_lo, one box of NN rows per K block of 16 values
-            mbar_arrive_expect_tx(netld, (uint32_t)wide_tc_net_bytes(NMT));
+            mbar_arrive_expect_tx(netld, (uint32_t)wide_tc_net_bytes(NMT, H));
             for (int kb = 0; kb < NN / 16; ++kb) {
                 tma_load_2d(net_s + kb * NN * 64, &mN, kb * 16, 0, netld);
                 tma_load_2d(net_s + (NN / 16 + kb) * NN * 64, &mN, kb * 16, NN, netld);
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     const uint32_t tmem = tmem_base;
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     // TCN: this warp's columns of A_hi, A_lo (buffer 0; AB2: buffer 1 at +3 NN) and D
-    constexpr bool AB2 = TCN && wide_tc_abuf2(NMT);
+    constexpr bool AB2 = TCN && wide_tc_abuf2(NMT, H);
     const uint32_t a_hi = lane_addr + net0 + (uint32_t)(h * wide_kh(NMT));
     const uint32_t a_lo = a_hi + NN, a_d = a_hi + 2 * NN;
     int bad = 0;          // TCN: a bounded wait of this thread gave up
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     if (traj) {
 #pragma unroll
         for (int k = 0; k < NMT; ++k) {
-            const int i = h + 4 * k;
+            const int i = h + H * k;
             if (i < n) {
                 traj[i] = cst(4, i);
                 traj[n + i] = 0.f;
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     }
     float* part_tile = a.part ? a.part + (int64_t)blockIdx.x * (a.Nt + 1) * S3 : nullptr;
     if (part_tile)
-        for (int v = tid; v < S3; v += WI_THREADS) part_tile[v] = 0.f;
+        for (int v = tid; v < S3; v += NTHR) part_tile[v] = 0.f;
 
     // stage-0 input of the first step: every deviation is zero
     int gb = 0;
@@ -290,12 +295,16 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
     if constexpr (TCN) {
 #pragma unroll
         for (int k = 0; k < NMT; k += 2) net_store4(a_hi, a_lo, 2 * k, 0.f, 0.f, 0.f, 0.f);
+        // A's columns past the H KH in use (NN is a multiple of 16) stay zero
+        if (h == H - 1)
+            for (int c = H * wide_kh(NMT); c < NN; c += 4)
+                net_store4(lane_addr + net0, lane_addr + net0 + NN, c, 0.f, 0.f, 0.f, 0.f);
         tmem_st_wait();
         cpart[h * 128 + r] = 0.f;
     } else {
 #pragma unroll
         for (int k = 0; k < NMT; ++k) {
-            const int i = h + 4 * k;
+            const int i = h + H * k;
             if (i < n) gh[i * 128 + r] = make_float2(0.f, 0.f);
         }
     }
@@ -359,8 +368,13 @@ __global__ void __launch_bounds__(WI_THREADS, 1)
             __syncthreads();
             tc_fence_after();
         }
+        // (warp h forms the disturbances w = h mod 4; with two warps per sample,
+        // also w = h + 2 mod 4)
         disturbance_chunk<ND, 8, false>(lane_addr, TC, steps, n0, d, h, x0, a.ou_a, a.ou_s, a.ito, dt, a.em,
                                  (uint32_t)(a.em.k0 + srow));
+        if (H == 2)
+            disturbance_chunk<ND, 8, false>(lane_addr, TC, steps, n0, d, h + 2, x0, a.ou_a, a.ou_s, a.ito, dt, a.em,
+                                            (uint32_t)(a.em.k0 + srow));
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
@@ -413,12 +427,16 @@ if constexpr (TCN) {
                 }
                 if (tid == 0) {
                     tc_fence_after();
-                    net_mma<NMT>(tmem + net0 + 2 * NN, tmem + net0 + ab, tmem + net0 + ab + NN, smem_u32(net_s));
+                    net_mma<NMT, H>(tmem + net0 + 2 * NN, tmem + net0 + ab, tmem + net0 + ab + NN,
+                                    smem_u32(net_s));
                     umma_commit(netbar);
                 }
                 {
-                    const float* cp = cpart + gb * 512 + r;
-                    csh = (((cp[0] + cp[128]) + cp[256]) + cp[384]) * inv_n;
+                    const float* cp = cpart + gb * (H * 128) + r;
+                    float sum = cp[0];
+#pragma unroll
+                    for (int hh2 = 1; hh2 < H; ++hh2) sum += cp[hh2 * 128];
+                    csh = sum * inv_n;
                 }
                 const float w0 = w0buf[gb * 128 + r] * ref;
                 const bool pub = (st + 1 < nst);
@@ -435,10 +453,10 @@ if constexpr (TCN) {
                         const float kd = a.omega_s * (yw[k] - w0);
                         ad[k] = fmaf(b, kd, ad[k]);
                         yn[k] = pub ? fmaf(cn, kd, del[k]) : fmaf(hh, ad[k], del[k]);
-                        ps += h + 4 * k < n ? yn[k] : 0.f;
+                        ps += h + H * k < n ? yn[k] : 0.f;
                     }
-                    publish_angles<NMT, CST>(a_hi + an, a_lo + an, yn, csh, cst_s, h, n);
-                    cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                    publish_angles<NMT, CST, H>(a_hi + an, a_lo + an, yn, csh, cst_s, h, n);
+                    cpart[(gb ^ 1) * (H * 128) + h * 128 + r] = ps;
                 }
                 float xs[ND];
 #pragma unroll
@@ -467,7 +485,7 @@ if constexpr (TCN) {
                             net_read<WT>(a_d, a_hi + ab, a_lo + ab, 2 * k, reinterpret_cast<float(&)[WT]>(dd),
                                          reinterpret_cast<float(&)[WT]>(ah), reinterpret_cast<float(&)[WT]>(al));
                     }
-                    const int i = h + 4 * k;
+                    const int i = h + H * k;
                     const int c = 2 * (k % RP);
                     const float du = dd[c], dv = dd[c + 1];
                     const float gi = ah[c] + al[c], ei = ah[c + 1] + al[c + 1];
@@ -509,7 +527,7 @@ if constexpr (TCN) {
                 }
                 if (!AB2 && pub) {
                     tmem_st_wait();
-                    cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                    cpart[(gb ^ 1) * (H * 128) + h * 128 + r] = ps;
                 }
                 if (pub && h == 0) w0buf[(gb ^ 1) * 128 + r] = yw[0];
                 ath = fmaf(b, a.omega_s * w0, ath);
@@ -620,7 +638,7 @@ if constexpr (TCN) {
                     for (int kq = 0; kq < KP; ++kq) {
                         const int k = k0 + kq;
                         if (k < NMT) {
-                            const int i = h + 4 * k;
+                            const int i = h + H * k;
                             const float2 ge = ghc[(i < n ? i : 0) * 128];
                             const float cs = c_cst[i], ss = c_sst[i];
                             float dpe = fmaf(cs, du[kq], ss * dv[kq]);
@@ -664,16 +682,16 @@ if constexpr (TCN) {
             } else if constexpr (TCN) {
                 float ps = 0.f;
 #pragma unroll
-                for (int k = 0; k < NMT; ++k) ps += h + 4 * k < n ? del[k] : 0.f;
-                publish_angles<NMT, CST>(a_hi, a_lo, del, csh, cst_s, h, n);
-                cpart[(gb ^ 1) * 512 + h * 128 + r] = ps;
+                for (int k = 0; k < NMT; ++k) ps += h + H * k < n ? del[k] : 0.f;
+                publish_angles<NMT, CST, H>(a_hi, a_lo, del, csh, cst_s, h, n);
+                cpart[(gb ^ 1) * (H * 128) + h * 128 + r] = ps;
                 if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
                 gb ^= 1;
             } else {
                 float2* ghn = gh + (gb ^ 1) * n * 128 + r;
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) {
-                    const int i = h + 4 * k;
+                    const int i = h + H * k;
                     const bool big = __any_sync(0xffffffffu, i < n && fabsf(del[k]) > 0.8f);
                     if (i < n) ghn[i * 128] = wide_gamma_eta(del[k], c_cst[i], c_sst[i], big);
                 }
@@ -686,7 +704,7 @@ if constexpr (TCN) {
                 float* o = traj + (int64_t)tn * trow;
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) {
-                    const int i = h + 4 * k;
+                    const int i = h + H * k;
                     if (i < n) {
                         o[i] = (theta + del[k]) + cst(4, i);
                         o[n + i] = w[k];
@@ -708,7 +726,7 @@ if constexpr (TCN) {
                 const int na = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
                 float rf, dv, m2;
                 column_sums(wbuf + lane, WROW, na, &rf, &dv, &m2);
-                float* slot = msum + ((ms * 4 + q) * 4 + h) * GS;
+                float* slot = msum + ((ms * 4 + q) * H + h) * GS;
                 slot[lane] = rf;
                 slot[2 * NMT + lane] = dv;
                 slot[4 * NMT + lane] = m2;
@@ -716,16 +734,18 @@ if constexpr (TCN) {
             if (a.rrf) {
                 float cp = 0.f;
 #pragma unroll
-                for (int k = 0; k < NMT; ++k) cp = fmaf(cst(7, h + 4 * k), w[k], cp);
-                coi_part[(ms * 4 + h) * 128 + r] = cp;
+                for (int k = 0; k < NMT; ++k) cp = fmaf(cst(7, h + H * k), w[k], cp);
+                coi_part[(ms * H + h) * 128 + r] = cp;
             }
             __syncwarp();
             if (ms == WI_MS - 1 || s == steps - 1) {
                 __syncthreads();
                 if (a.rrf && h == 0) {
                     for (int sl = 0; sl <= ms; ++sl) {
-                        const float* cq = coi_part + sl * 4 * 128 + r;
-                        const float c = ((cq[0] + cq[128]) + cq[256]) + cq[384];
+                        const float* cq = coi_part + sl * H * 128 + r;
+                        float c = cq[0];
+#pragma unroll
+                        for (int hh2 = 1; hh2 < H; ++hh2) c += cq[hh2 * 128];
                         racc_s[r] = fmaf(c, c, racc_s[r]);
                     }
                 }
@@ -734,15 +754,15 @@ if constexpr (TCN) {
                 // samples of this tile (the last tile may be partly empty)
                 const int64_t left = a.count - row0;
                 const int n_tile = left <= 0 ? 0 : (left >= 128 ? 128 : (int)left);
-                for (int e = tid; e < nsl * S; e += WI_THREADS) {
+                for (int e = tid; e < nsl * S; e += NTHR) {
                     const int sl = e / S, stt = e - sl * S;
                     // state stt < n is delta_i, else omega_(stt - n)
                     const int isw = stt >= n ? 1 : 0;
                     const int i = stt - isw * n;
-                    const float* m = msum + (sl * 16 + (i & 3)) * GS + isw * NMT + (i >> 2);
+                    const float* m = msum + (sl * 4 * H + (i % H)) * GS + isw * NMT + (i / H);
                     // the tile's triple over its four sample groups
                     float c, dv, m2;
-                    combine_groups(m, m + 2 * NMT, m + 4 * NMT, 4 * GS, left, 4, &c, &dv, &m2);
+                    combine_groups(m, m + 2 * NMT, m + 4 * NMT, H * GS, left, 4, &c, &dv, &m2);
                     if (part_tile) {
                         float* o = part_tile + (int64_t)(tn0 + sl) * S3;
                         o[stt] = c;
@@ -768,42 +788,43 @@ if constexpr (TCN) {
 }
 
 // Dynamic shared memory of the kernel (bytes), alignment slack included.
-template <int NMT, int ND, bool TCN>
+template <int NMT, int ND, bool TCN, int H = 4>
 inline int wide_smem_bytes(int TC, int split, int n, int ns)
 {
     const int stage = (TC_M * 64 + TC * 64) * (split ? 2 : 1);
-    const int mom = wide_mom_floats<NMT>() * 4;
+    const int mom = wide_mom_floats<NMT, H>() * 4;
     const int u = ((ns * stage > mom ? ns * stage : mom) + 1023) & ~1023;
     if (TCN)
-        return 1024 + u + wide_tc_net_bytes(NMT) + (384 + 1024) * 4 + 4 * NMT * ((8 + ND + 3) & ~3) * 4;
+        return 1024 + u + wide_tc_net_bytes(NMT, H) + (384 + 1024) * 4 + 4 * NMT * ((8 + ND + 3) & ~3) * 4;
     return 1024 + u + 2 * n * 128 * 8 + 384 * 4 + wide_const_floats(n, NMT, ND) * 4;
 }
 
 // maps: the four contraction maps, then (TCN) the map of the network matrix.
-template <int NMT, int ND, bool TCN = false>
+// H = 2: two CTAs per SM, each with at most half of the SM's shared memory.
+template <int NMT, int ND, bool TCN = false, int H = 4>
 cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStream_t st, int* occ_out)
 {
-    auto kern = simulate_wide_kernel<NMT, ND, TCN>;
+    auto kern = simulate_wide_kernel<NMT, ND, TCN, H>;
+    const int cap = H == 4 ? TC_SMEM_DYN_MAX : 233472 / 2 - 2048;
     // as many ring stages as the shared memory left by the other buffers holds
     WideArgs a = args;
     a.ns = 2;
-    while (a.ns < TC_MAX_STAGES &&
-           wide_smem_bytes<NMT, ND, TCN>(a.TC, a.split, a.n, a.ns + 1) <= TC_SMEM_DYN_MAX)
-        ++a.ns;
-    const int smem = wide_smem_bytes<NMT, ND, TCN>(a.TC, a.split, a.n, a.ns);
+    while (a.ns < TC_MAX_STAGES && wide_smem_bytes<NMT, ND, TCN, H>(a.TC, a.split, a.n, a.ns + 1) <= cap) ++a.ns;
+    const int smem = wide_smem_bytes<NMT, ND, TCN, H>(a.TC, a.split, a.n, a.ns);
+    if (smem > cap) return cudaErrorInvalidValue;
     if (smem > TC_SMEM_DYN_MAX) return cudaErrorInvalidValue;
     // the attribute is process-wide and launches from several host threads may
     // race on it: always the same (largest) bound, the launch passes its own size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_DYN_MAX);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WI_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, H * 128, smem);
     if (e != cudaSuccess) return e;
     *occ_out = occ;
     if (occ < 1 || (uint32_t)occ * a.tmem_cols > 512u) return cudaErrorInvalidConfiguration;
     const int64_t ntiles = (a.count + TC_M - 1) / TC_M;
     if (ntiles > 2147483647LL) return cudaErrorInvalidValue;
-    kern<<<(unsigned)ntiles, WI_THREADS, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[TCN ? 4 : 0], a);
+    kern<<<(unsigned)ntiles, H * 128, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[TCN ? 4 : 0], a);
     return cudaGetLastError();
 }
 

@@ -13,9 +13,11 @@
 // whose dropped terms are below 2^-21 of each product.
 //
 // Column layout (both the K index of A and the N index of D): slot
-// c = h KH + 2 k + {0: gamma / du, 1: eta / dv} for machine i = h + 4 k, with
-// KH = 2 NMT rounded up to a multiple of 4, so that every warp (q, h) reads and
-// writes whole 16-byte groups of its own columns.  NN = 4 KH columns in all.
+// c = h KH + 2 k + {0: gamma / du, 1: eta / dv} for machine i = h + H k (H warps
+// per sample: 4, or 2 for two CTAs per SM), with KH = 2 NMT rounded up to a
+// multiple of 4, so that every warp (q, h) reads and writes whole 16-byte groups
+// of its own columns.  NN = H KH columns rounded up to a multiple of 16 (the
+// MMA's N and K granularity); the padding columns of A are zero.
 #pragma once
 
 #include <cuda.h>
@@ -27,7 +29,7 @@
 namespace fmc {
 
 __host__ __device__ constexpr int wide_kh(int nmt) { return (2 * nmt + 3) & ~3; }
-__host__ __device__ constexpr int wide_nn(int nmt) { return 4 * wide_kh(nmt); }
+__host__ __device__ constexpr int wide_nn(int nmt, int H = 4) { return (H * wide_kh(nmt) + 15) & ~15; }
 
 // Machine-slot buckets the tensor-core network sum is built for (13 .. 52 machines).
 __host__ __device__ constexpr bool wide_tc_built(int nmt)
@@ -38,15 +40,21 @@ __host__ __device__ constexpr bool wide_tc_built(int nmt)
 // Up to 7 slots (28 machines) the stage inputs alternate between two A buffers,
 // so that the angle half of a stage (which needs no network sum) can publish the
 // next input while the tensor cores still read the current one.
-__host__ __device__ constexpr bool wide_tc_abuf2(int nmt) { return nmt <= 7; }
+__host__ __device__ constexpr bool wide_tc_abuf2(int nmt, int H = 4) { return H == 4 && nmt <= 7; }
 
 // TMEM columns the network sum takes past the disturbance columns: A_hi, A_lo, D
 // (then A_hi, A_lo of the second buffer).
-__host__ __device__ constexpr int wide_tc_cols(int nmt) { return (wide_tc_abuf2(nmt) ? 5 : 3) * wide_nn(nmt); }
+__host__ __device__ constexpr int wide_tc_cols(int nmt, int H = 4)
+{
+    return (wide_tc_abuf2(nmt, H) ? 5 : 3) * wide_nn(nmt, H);
+}
 
 // Shared-memory bytes of Net_hi and Net_lo: per matrix NN / 16 K blocks of NN
 // rows x 64 bytes (16 TF32 values), 64-byte swizzle, as one TMA box each.
-__host__ __device__ constexpr int wide_tc_net_bytes(int nmt) { return 2 * wide_nn(nmt) * wide_nn(nmt) * 4; }
+__host__ __device__ constexpr int wide_tc_net_bytes(int nmt, int H = 4)
+{
+    return 2 * wide_nn(nmt, H) * wide_nn(nmt, H) * 4;
+}
 
 // Instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32 (FP32
 // bit patterns), both K-major, shape M x N.
@@ -94,10 +102,10 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t v0, uint32_t v
 // The two small correction terms go first, while the accumulator is small, so
 // that only the last NN / 8 MMAs add to a full-size accumulator.
 // net: shared address of Net_hi's first K block; Net_lo follows after NN/16 blocks.
-template <int NMT>
+template <int NMT, int H>
 __device__ __forceinline__ void net_mma(uint32_t d_tmem, uint32_t ahi_tmem, uint32_t alo_tmem, uint32_t net)
 {
-    constexpr int NN = wide_nn(NMT);
+    constexpr int NN = wide_nn(NMT, H);
     constexpr uint32_t KB_BYTES = NN * 64;  // one K block: NN rows of 64 bytes
     constexpr uint32_t LO = (NN / 16) * KB_BYTES;
     constexpr uint32_t idesc = umma_idesc_tf32(TC_M, NN);
@@ -175,11 +183,14 @@ __device__ __forceinline__ void net_read(uint32_t d_addr, uint32_t hi_addr, uint
 }
 #endif
 
-// The large-system kernel with the tensor-core network sum.  maps: the four
+// The large-system kernel with the tensor-core network sum.  nmt: machine slots
+// per thread for H warps per sample (4: one 512-thread CTA per SM; 2: two
+// 256-thread CTAs per SM, each with half the SM's TMEM).  maps: the four
 // contraction maps, then the map of Net (FP32 [2 NN][NN]: Net_hi rows, then
-// Net_lo rows; box 16 x NN, 64-byte swizzle).  a.tmem_cols must be 512 and the
-// disturbance columns d TC (rounded up to 16) plus wide_tc_cols(nmt) within it.
-cudaError_t launch_simulate_wide_tc(int nmt, int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st,
-                                    int* max_ctas_per_sm);
+// Net_lo rows; box 16 x NN, 64-byte swizzle).  a.tmem_cols must be 512 / (4 / H)
+// and hold the disturbance columns d TC (rounded up to 16) plus
+// wide_tc_cols(nmt, H).
+cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, const CUtensorMap* maps, const WideArgs& a,
+                                    cudaStream_t st, int* max_ctas_per_sm);
 
 }  // namespace fmc
