@@ -1,8 +1,10 @@
 """Measured launch shapes of the fused path.
 
 For buckets of machine count, disturbance count and sample count, every
-candidate shape -- the kernel (per-sample or split, up to 16 machines), the
-resident CTAs per SM and the time chunk -- is timed with CUDA events on a seeded
+candidate shape -- the kernel (per-sample up to 16 machines; split with the
+network sums on the FP32 pipes or on the tensor cores, the latter from 13
+machines), the resident CTAs per SM and the time chunk -- is timed with CUDA
+events on a seeded
 system of the bucket's largest size, and the fastest per machine-step becomes a
 launch rule (``fmc_set_launch_rules``).  The table is cached per GPU model and
 SM count under ``tuning/`` and applied to every new context on that GPU.
@@ -18,7 +20,9 @@ import re
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING_DIR = os.path.join(HERE, "tuning")
 
-N_BUCKETS = [(1, 4), (5, 10), (11, 16), (17, 32), (33, 52)]
+# the large-system buckets follow the tensor-core kernel's layouts: two warps per
+# sample with 10 and 13 slots (17..20, 21..26), then four with 7, 10, 13 slots
+N_BUCKETS = [(1, 4), (5, 10), (11, 16), (17, 20), (21, 26), (27, 32), (33, 40), (41, 52)]
 D_BUCKETS = [(1, 2), (3, 4), (5, 8)]
 SAMPLE_BUCKETS = [(1, 32767), (32768, 1 << 30)]
 
@@ -29,7 +33,7 @@ def table_path(name: str, sms: int) -> str:
 
 def candidates(n: int):
     """(kernel, max_ctas, TC) triples; 0 = the library's own choice."""
-    from . import KERNEL_PER_SAMPLE, KERNEL_SPLIT
+    from . import KERNEL_PER_SAMPLE, KERNEL_SPLIT, KERNEL_SPLIT_TC
     out = []
     if n <= 16:
         for mc in (0, 4, 2, 1):
@@ -38,8 +42,11 @@ def candidates(n: int):
         out.append((KERNEL_SPLIT, 0, 0))
         out.append((KERNEL_SPLIT, 0, 32))
     else:
-        for tc in (0, 64, 32):
-            out.append((KERNEL_SPLIT, 0, tc))
+        out.append((KERNEL_SPLIT, 0, 0))
+        out.append((KERNEL_SPLIT, 0, 64))
+    if n >= 13:
+        for tc in (0, 32, 16):
+            out.append((KERNEL_SPLIT_TC, 0, tc))
     return out
 
 
@@ -67,7 +74,7 @@ def tune(ctx=None, quick: bool = False, horizon: float = 2.0, reps: int = 2):
     ctx = ctx or Context(0)
     set_launch_rules([], ctx=ctx)
     rules, measured = [], []
-    n_buckets = N_BUCKETS[1:2] + N_BUCKETS[3:4] if quick else N_BUCKETS
+    n_buckets = N_BUCKETS[1:2] + N_BUCKETS[3:4] + N_BUCKETS[-1:] if quick else N_BUCKETS
     for nb in n_buckets:
         for db in D_BUCKETS:
             for sb in SAMPLE_BUCKETS:

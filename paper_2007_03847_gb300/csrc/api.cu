@@ -1133,8 +1133,11 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     // four warps per sample for systems above 16 machines (or on request)
     int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
     if (policy == FMC_KERNEL_AUTO && path == FMC_PATH_FUSED) {
+        // (a rule's kernel that cannot take this system is ignored: a bucket's
+        // rule was measured at its largest machine count)
         const fmc_launch_rule* rule = find_rule(ctx, s, count);
-        if (rule && rule->kernel != FMC_KERNEL_AUTO && !(rule->kernel == FMC_KERNEL_PER_SAMPLE && P.nm < 0))
+        if (rule && rule->kernel != FMC_KERNEL_AUTO && !(rule->kernel == FMC_KERNEL_PER_SAMPLE && P.nm < 0) &&
+            !(rule->kernel == FMC_KERNEL_SPLIT_TC && !wide_tc_built(wide_nmt_for(n))))
             policy = rule->kernel;
     }
     const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE;

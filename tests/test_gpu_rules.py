@@ -45,3 +45,26 @@ def test_malformed_rules_are_refused():
         fmc.set_launch_rules([], ctx=ctx)
     finally:
         ctx.close()
+
+
+def test_rule_kernel_that_cannot_take_the_system_is_ignored():
+    # a bucket's rule is measured at its largest machine count: a tensor-core
+    # split rule over 11..16 machines leaves 11 machines to the library's choice
+    fmc = need_gpu()
+    ctx = fmc.Context(0)
+    try:
+        sc = fs.multimachine_case(n=11, d=2, K=30, T=0.2, dt=0.005, N=200, seed=83)
+        fmc.set_launch_rules([], ctx=ctx)
+        m0, v0 = fmc.simulate(sc, ctx=ctx)
+        fmc.set_launch_rules([dict(n_min=11, n_max=16, kernel=3)], ctx=ctx)
+        m1, v1 = fmc.simulate(sc, ctx=ctx)
+        fmc.device_status(ctx)
+        assert np.array_equal(m0.cpu().numpy(), m1.cpu().numpy())
+        assert np.array_equal(v0.cpu().numpy(), v1.cpu().numpy())
+        # from 13 machines the rule's kernel takes the system
+        sc = fs.multimachine_case(n=14, d=2, K=30, T=0.2, dt=0.005, N=200, seed=84)
+        fmc.simulate(sc, ctx=ctx)
+        fmc.device_status(ctx)
+    finally:
+        fmc.set_launch_rules([], ctx=ctx)
+        ctx.close()
