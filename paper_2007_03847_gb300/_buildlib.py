@@ -76,7 +76,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(os.path.basename(f) for f in failed))
     objs = [os.path.join(OBJDIR, os.path.basename(s)[:-3] + ".o") for s in sources]
-    if force or jobs or not os.path.exists(LIB):
+    # relink whenever an object is newer than the library (also after a failed link)
+    stale = not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if force or jobs or stale:
         libdir = os.path.join(_cuda_home(nvcc), "lib64")
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [

@@ -414,9 +414,6 @@ static void build_params_bucket(int nm, int nd, const fmc_scenario* s, const dou
     }
 }
 
-// Constant block of the large-system kernel (layout at wide_const_floats): the
-// same deviation-form constants as build_params, with the network matrices
-// arranged [j][h][k] for machine i = h + 4k.
 // Nearest TF32 value (ties to even) of x, as an FP32 number.
 static float tf32_round(double x)
 {
@@ -434,12 +431,15 @@ static float tf32_round(double x)
 // Offset (floats) of the tensor-core network matrix in the constant block.
 static size_t wide_net_offset(int n, int nmt, int nd) { return ((size_t)wide_const_floats(n, nmt, nd) + 31) & ~(size_t)31; }
 
-static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, bool tcn, int H,
+// Constant block of the large-system kernel (layout at wide_const_floats): the
+// same deviation-form constants as build_params, with the network matrices
+// arranged [j][h][k] for machine i = h + 4k; with tcn, the tensor-core network
+// matrix after it.
+static void build_wide_consts(const fmc_scenario* s, const double* delta0, int nmt, int nd, bool tcn, int H,
                               std::vector<float>& out)
 {
     const int n = s->n, d = s->d, nmtp = wide_nmtp(nmt), g4 = 4 * nmt;
-    const int dx = d + (s->event_machine >= 0 ? 1 : 0);
-    out.assign(wide_const_floats(n, nmt, nd_bucket_for(dx)), 0.f);
+    out.assign(wide_const_floats(n, nmt, nd), 0.f);  // nd: the kernel's disturbance-slot bucket
     float* GB = out.data();  // [j][h][GE row | BE row], nmtp each
     float* pm = GB + 2 * n * 4 * nmtp;
     const bool rel = !s->has_inf_bus;
@@ -483,7 +483,9 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
         // the network matrix of the tensor-core sum (wide_tc.cuh), 128-byte
         // aligned after the constant block: Net[(i, u|v)][(j, gamma|eta)] =
         //   u: ( GE_ij, -BE_ij ),  v: ( BE_ij, GE_ij ),  diagonal and padding zero,
-        // as Net_hi = TF32(Net) and Net_lo = TF32(Net - Net_hi)
+        // as Net_hi = TF32(Net) and Net_lo = TF32(Net - Net_hi); an infinite bus is
+        // a node in the last machine slot (E = V, G_ib = Ginf_i, B_ib = Binf_i),
+        // which the kernel fills with the bus's deviation in its shifted frame
         const int KH = wide_kh(nmt), NN = wide_nn(nmt, H);
         const size_t base = (out.size() + 31) & ~(size_t)31;
         out.resize(base + 2 * (size_t)NN * NN, 0.f);
@@ -505,6 +507,16 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
                 put(ru, cg + 1, -be);
                 put(ru + 1, cg, be);
                 put(ru + 1, cg + 1, ge);
+            }
+            if (s->has_inf_bus) {
+                const int nb = H * nmt - 1;  // the last machine slot (free: n < H nmt)
+                const int cb = (nb % H) * KH + 2 * (nb / H);
+                const double ge = s->E[i] * s->Vinf * s->Ginf[i];
+                const double be = s->E[i] * s->Vinf * s->Binf[i];
+                put(ru, cb, ge);
+                put(ru, cb + 1, -be);
+                put(ru + 1, cb, be);
+                put(ru + 1, cb + 1, ge);
             }
         }
     }
@@ -1093,6 +1105,7 @@ struct Prepared {
     int nmt = 0;  // > 0: the large-system kernel with nmt machine slots per thread
     bool tcn = false;  // the large-system kernel sums the network on the tensor cores
     int H = 4;         // its warps per sample (2: two CTAs per SM, nmt slots of 2)
+    bool bus = false;  // ... for a system with an infinite bus (its own instantiations)
     bool exclusive = true;  // the launch has the GPU to itself (see fused_shape)
     int64_t k0 = 0, count = 0;
     std::vector<unsigned char> params;
@@ -1165,11 +1178,26 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         P.H = 2;
         P.nmt = 13;
     }
+    // an infinite bus: the tensor-core layout holds it in its last machine slot
+    // (instantiated for four warps per sample and the 8-disturbance bucket)
+    if (P.tcn && s->has_inf_bus) {
+        P.H = 4;
+        P.nmt = wide_nmt_for(n);
+        P.bus = true;
+        if (n >= 4 * P.nmt) {
+            if (exclusive && ctx->kernel_policy == FMC_KERNEL_SPLIT_TC)
+                return fail(ctx, FMC_EUNSUPPORTED,
+                            "the tensor-core network sum needs a free machine slot for the infinite bus (n = %d)",
+                            n);
+            P.tcn = false;
+            P.bus = false;
+        }
+    }
     if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && P.nmt > 0)
         return fail(ctx, FMC_EUNSUPPORTED,
                     "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
                     FMC_MAX_MACHINES_PLAIN);
-    P.nd = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+    P.nd = P.bus ? 8 : nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
     P.path = path;
     P.k0 = k0;
     P.count = count;
@@ -1190,7 +1218,7 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
         // constants of the large-system kernel go to the device once, here
         // (outside any stream capture)
         std::vector<float> wc;
-        build_wide_consts(s, delta0.data(), P.nmt, P.tcn, P.H, wc);
+        build_wide_consts(s, delta0.data(), P.nmt, P.nd, P.tcn, P.H, wc);
         if ((rc = ensure(ctx, ws.wconst, wc.size() * sizeof(float)))) return rc;
         FMC_CUDA(ctx, cudaMemcpyAsync(ws.wconst.ptr, wc.data(), wc.size() * sizeof(float), cudaMemcpyHostToDevice, st),
                  "copy constants");
@@ -1459,7 +1487,7 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
                                    wide_nn(P.nmt, P.H))))
                 return rc;
             wa.tmem_cols = tmem_cols = 512 / (4 / P.H);
-            e = launch_simulate_wide_tc(P.nmt, P.H, P.nd, maps5, wa, st, &occ);
+            e = launch_simulate_wide_tc(P.nmt, P.H, P.nd, P.bus, maps5, wa, st, &occ);
         } else {
             e = launch_simulate_wide(P.nmt, P.nd, maps, wa, st, &occ);
         }

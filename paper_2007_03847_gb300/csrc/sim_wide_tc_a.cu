@@ -33,10 +33,16 @@ cudaError_t wide_tc_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cu
 cudaError_t wide_tc_h2_nmt10(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_h2_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
-cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, const CUtensorMap* maps, const WideArgs& a,
+cudaError_t wide_tc_bus(int nmt, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+
+cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, bool bus, const CUtensorMap* maps, const WideArgs& a,
                                     cudaStream_t st, int* max_ctas_per_sm)
 {
     if (a.n > H * nmt || a.d > nd || a.tmem_cols != (H == 2 ? 256u : 512u)) return cudaErrorInvalidValue;
+    if (bus) {
+        if (H != 4 || nd != 8 || a.n >= H * nmt) return cudaErrorInvalidValue;
+        return wide_tc_bus(nmt, maps, a, st, max_ctas_per_sm);
+    }
     if (H == 2) {
         if (nmt == 10) return wide_tc_h2_nmt10(nd, maps, a, st, max_ctas_per_sm);
         if (nmt == 13) return wide_tc_h2_nmt13(nd, maps, a, st, max_ctas_per_sm);

@@ -71,12 +71,18 @@ __device__ __forceinline__ float2 wide_gamma_eta_tier(float x, float cs, float s
     return make_float2(fmaf(cs, cm1, -ss * sn), fmaf(ss, cm1, cs * sn));
 }
 
+// cos c - 1 and sin c of an infinite bus's shift (a call, not inlined: only the
+// warp that holds the bus's slot of a system with an infinite bus takes it, and
+// the hot loops keep their registers).
+static __device__ __noinline__ void bus_deviation(float c, float* cm1, float* sn) { sin_cosm1_any(c, sn, cm1); }
+
 // Warp-collective (tensor-core network sum): (gamma, eta) of the deviations
 // x[k] - csh of the warp's machines by the series of tier TIER, split and stored
-// pairwise to the warp's A_hi, A_lo columns; waits for the stores.
+// pairwise to the warp's A_hi, A_lo columns; waits for the stores.  Slot nb (an
+// infinite bus, or -1) takes the bus's (bcm, -bsn) = (cos csh - 1, -sin csh).
 template <int NMT, int TIER, int CST, int H>
 __device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
-                                             const float* cst_s, int h, int n)
+                                             const float* cst_s, int h, int n, int nb, float bcm, float bsn)
 {
     float pg = 0.f, pe = 0.f;
 #pragma unroll
@@ -85,8 +91,9 @@ __device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const flo
         const float2 csn = *reinterpret_cast<const float2*>(cst_s + i * CST);
         float sn, cm1;
         deviation_trig1<TIER>(x[k] - csh, &sn, &cm1);
-        const float gx = i < n ? fmaf(csn.x, cm1, -csn.y * sn) : 0.f;
-        const float ex = i < n ? fmaf(csn.y, cm1, csn.x * sn) : 0.f;
+        const bool bus = k == NMT - 1 && i == nb;  // (the bus holds a warp's last slot)
+        const float gx = i < n ? fmaf(csn.x, cm1, -csn.y * sn) : (bus ? bcm : 0.f);
+        const float ex = i < n ? fmaf(csn.y, cm1, csn.x * sn) : (bus ? -bsn : 0.f);
         if (k & 1)
             net_store4(hi, lo, 2 * (k - 1), pg, pe, gx, ex);
         else if (k == NMT - 1)
@@ -101,27 +108,30 @@ __device__ __forceinline__ void publish_tier(uint32_t hi, uint32_t lo, const flo
 // shifted deviation (the tiers of wide_gamma_eta_tier).
 template <int NMT, int CST, int H>
 __device__ __forceinline__ void publish_angles(uint32_t hi, uint32_t lo, const float (&x)[NMT], float csh,
-                                               const float* cst_s, int h, int n)
+                                               const float* cst_s, int h, int n, int nb)
 {
+    float bcm = 0.f, bsn = 0.f;
+    if (nb >= 0 && nb % H == h) bus_deviation(csh, &bcm, &bsn);
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < NMT; ++k)
         if (h + H * k < n) m = fmaxf(m, fabsf(x[k] - csh));
     const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
     if (mm <= __float_as_uint(0.05f))
-        publish_tier<NMT, 0, CST, H>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 0, CST, H>(hi, lo, x, csh, cst_s, h, n, nb, bcm, bsn);
     else if (mm <= __float_as_uint(0.25f))
-        publish_tier<NMT, 1, CST, H>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 1, CST, H>(hi, lo, x, csh, cst_s, h, n, nb, bcm, bsn);
     else if (mm <= __float_as_uint(0.8f))
-        publish_tier<NMT, 2, CST, H>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 2, CST, H>(hi, lo, x, csh, cst_s, h, n, nb, bcm, bsn);
     else
-        publish_tier<NMT, 3, CST, H>(hi, lo, x, csh, cst_s, h, n);
+        publish_tier<NMT, 3, CST, H>(hi, lo, x, csh, cst_s, h, n, nb, bcm, bsn);
 }
 
 // TCN: the network sums on the tensor cores (wide_tc.cuh) instead of the FP32
 // pipes; the per-machine arithmetic around them is the same.  H: warps per sample
 // (4; or 2 with TCN: two CTAs of 256 threads per SM), machine i = h + H k.
-template <int NMT, int ND, bool TCN, int H = 4>
+// BUS (with TCN): the system has an infinite bus, held in the last machine slot.
+template <int NMT, int ND, bool TCN, int H = 4, bool BUS = false>
 __global__ void __launch_bounds__(H * 128, 4 / H)
     simulate_wide_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                          const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -287,11 +297,15 @@ __global__ void __launch_bounds__(H * 128, 4 / H)
     int gb = 0;
     // TCN: the deviations enter the trigonometric terms less their per-sample mean
     // (of the previous stage input; the electrical power depends on angle
-    // differences alone, so any common shift is exact without an infinite bus),
-    // which keeps the product's inputs, and so its rounding, at the size of the
-    // machines' relative motion
+    // differences alone, so any common shift is exact), which keeps the product's
+    // inputs, and so its rounding, at the size of the machines' relative motion.
+    // An infinite bus is one more node at angle 0, so at -csh in the shifted
+    // frame: the last machine slot nb = H NMT - 1 (unused: the host takes this
+    // layout only when n < H NMT) carries its (cos csh - 1, -sin csh), and the
+    // network matrix its column.
     float csh = 0.f;
-    const float inv_n = a.rel ? 1.0f / (float)n : 0.f;
+    const float inv_n = 1.0f / (float)n;
+    const int nb = BUS ? H * NMT - 1 : -1;  // (BUS: built for systems with an infinite bus)
     if constexpr (TCN) {
 #pragma unroll
         for (int k = 0; k < NMT; k += 2) net_store4(a_hi, a_lo, 2 * k, 0.f, 0.f, 0.f, 0.f);
@@ -455,7 +469,7 @@ if constexpr (TCN) {
                         yn[k] = pub ? fmaf(cn, kd, del[k]) : fmaf(hh, ad[k], del[k]);
                         ps += h + H * k < n ? yn[k] : 0.f;
                     }
-                    publish_angles<NMT, CST, H>(a_hi + an, a_lo + an, yn, csh, cst_s, h, n);
+                    publish_angles<NMT, CST, H>(a_hi + an, a_lo + an, yn, csh, cst_s, h, n, nb);
                     cpart[(gb ^ 1) * (H * 128) + h * 128 + r] = ps;
                 }
                 float xs[ND];
@@ -474,6 +488,9 @@ if constexpr (TCN) {
                 // computed
                 constexpr int RP = NMT >= 7 ? 2 : 4;
                 float dd[2 * RP], ah[2 * RP], al[2 * RP];
+                // (one A buffer: the infinite bus's slot of the next input, from csh)
+                float bcm = 0.f, bsn = 0.f;
+                if (!AB2 && pub && nb >= 0 && nb % H == h) bus_deviation(csh, &bcm, &bsn);
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) {
                     if (k % RP == 0) {
@@ -512,7 +529,9 @@ if constexpr (TCN) {
                         if (pub) {
                             // the next stage's input of machine i (its columns were read above)
                             const float2 g = wide_gamma_eta_tier(yd - csh, cs, ss, i < n);
-                            const float gx = i < n ? g.x : 0.f, ex = i < n ? g.y : 0.f;
+                            const bool bus = k == NMT - 1 && i == nb;
+                            const float gx = i < n ? g.x : (bus ? bcm : 0.f);
+                            const float ex = i < n ? g.y : (bus ? -bsn : 0.f);
                             ps += i < n ? yd : 0.f;
                             if (k & 1)
                                 net_store4(a_hi, a_lo, 2 * (k - 1), pg, pe, gx, ex);
@@ -683,7 +702,7 @@ if constexpr (TCN) {
                 float ps = 0.f;
 #pragma unroll
                 for (int k = 0; k < NMT; ++k) ps += h + H * k < n ? del[k] : 0.f;
-                publish_angles<NMT, CST, H>(a_hi, a_lo, del, csh, cst_s, h, n);
+                publish_angles<NMT, CST, H>(a_hi, a_lo, del, csh, cst_s, h, n, nb);
                 cpart[(gb ^ 1) * (H * 128) + h * 128 + r] = ps;
                 if (h == 0) w0buf[(gb ^ 1) * 128 + r] = w[0];
                 gb ^= 1;
@@ -801,10 +820,14 @@ inline int wide_smem_bytes(int TC, int split, int n, int ns)
 
 // maps: the four contraction maps, then (TCN) the map of the network matrix.
 // H = 2: two CTAs per SM, each with at most half of the SM's shared memory.
-template <int NMT, int ND, bool TCN = false, int H = 4>
+template <int NMT, int ND, bool TCN = false, int H = 4, bool BUS = false>
 cudaError_t launch_wide_t(const CUtensorMap* maps, const WideArgs& args, cudaStream_t st, int* occ_out)
 {
-    auto kern = simulate_wide_kernel<NMT, ND, TCN, H>;
+    static_assert(!BUS || (TCN && H == 4), "the infinite-bus form is built for four warps per sample");
+    // (the tensor-core form shifts the angles: exact with a network alone, or with
+    // the infinite bus held in its slot)
+    if (TCN && BUS == (args.rel != 0)) return cudaErrorInvalidValue;
+    auto kern = simulate_wide_kernel<NMT, ND, TCN, H, BUS>;
     const int cap = H == 4 ? TC_SMEM_DYN_MAX : 233472 / 2 - 2048;
     // as many ring stages as the shared memory left by the other buffers holds
     WideArgs a = args;

@@ -190,7 +190,9 @@ __device__ __forceinline__ void net_read(uint32_t d_addr, uint32_t hi_addr, uint
 // Net_lo rows; box 16 x NN, 64-byte swizzle).  a.tmem_cols must be 512 / (4 / H)
 // and hold the disturbance columns d TC (rounded up to 16) plus
 // wide_tc_cols(nmt, H).
-cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, const CUtensorMap* maps, const WideArgs& a,
+// bus: the system has an infinite bus (then H = 4 and nd = 8, and the last
+// machine slot must be free: n < 4 nmt).
+cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, bool bus, const CUtensorMap* maps, const WideArgs& a,
                                     cudaStream_t st, int* max_ctas_per_sm);
 
 }  // namespace fmc

@@ -167,3 +167,94 @@ def test_tensor_core_network_sum_refuses_small_systems(fmc):
         assert e.value.code == 8
     finally:
         fmc.set_kernel_policy("auto")
+
+
+def _with_infinite_bus(sc, seed):
+    """The system tied to an infinite bus (Binf = 2 at every machine), its mechanical
+    powers those of a chosen equilibrium, so that no machine is the angle reference
+    and the tensor-core kernel takes its deviations unshifted."""
+    rng = np.random.default_rng(seed)
+    n = sc.n
+    d_t = rng.uniform(-0.2, 0.3, n)
+    s2 = sc.replace(has_inf_bus=True, Ginf=np.zeros(n), Binf=np.full(n, 2.0), Vinf=1.0)
+    V = s2.E * np.exp(1j * d_t)
+    current = (s2.G + 1j * s2.B) @ V + (s2.Ginf + 1j * s2.Binf) * s2.Vinf
+    return s2.replace(Pm=np.real(V * np.conj(current)))
+
+
+def _tc_run(fmc, sc, **kw):
+    fmc.set_kernel_policy("split_tc")
+    try:
+        out = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True, **kw)
+    finally:
+        fmc.set_kernel_policy("auto")
+    fmc.device_status()
+    return out
+
+
+@pytest.mark.parametrize("n,d,N", [(19, 3, 130), (44, 2, 129)])
+def test_tensor_core_split_with_infinite_bus(fmc, orc, n, d, N):
+    sc = _with_infinite_bus(fs.multimachine_case(n=n, d=d, K=30, T=0.4, dt=0.005, N=N, seed=60 + n), 70 + n)
+    mean, var, traj = _tc_run(fmc, sc)
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+@pytest.mark.parametrize("n,d", [(20, 2), (36, 5)])
+def test_tensor_core_split_traditional_monte_carlo(fmc, orc, n, d):
+    # per-step normals drawn in the chunk pass (Section V-B's comparator)
+    sc = fs.multimachine_case(n=n, d=d, K=20, T=0.3, dt=0.005, N=140, seed=90 + n).replace(sampling=fs.SRS_EM)
+    mean, var, traj = _tc_run(fmc, sc)
+    ref = orc.simulate_em(sc, want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_tensor_core_split_heun_two_warps_per_sample(fmc, orc):
+    sc = fs.multimachine_case(n=19, d=4, K=30, T=0.4, dt=0.005, N=131, seed=95).replace(integrator=fs.HEUN)
+    mean, var, traj = _tc_run(fmc, sc)
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+
+
+def test_tensor_core_split_sample_blocks_add_up(fmc, orc):
+    # two warps per sample (20 machines): blocks of the design through the sums
+    # entry point give the whole design's moments
+    sc = fs.multimachine_case(n=20, d=3, K=30, T=0.3, dt=0.005, N=300, seed=97)
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), nthreads=8)
+    fmc.set_kernel_policy("split_tc")
+    try:
+        a1, a2, shift = fmc.simulate_sums(sc, 0, 131)
+        b1, b2, _ = fmc.simulate_sums(sc, 131, sc.N - 131)
+    finally:
+        fmc.set_kernel_policy("auto")
+    S1 = (a1 + b1).cpu().numpy()
+    S2 = (a2 + b2).cpu().numpy()
+    N = sc.N
+    mean = shift.cpu().numpy()[None, :] + S1 / N
+    var = (S2 - S1 * S1 / N) / (N - 1)
+    _check_moments(mean, var, ref["mean"], ref["var"], sc.n)
+
+
+def test_infinite_bus_without_a_free_slot(fmc, orc):
+    # 20 machines fill every slot of both tensor-core layouts: the automatic choice
+    # takes the FP32 split kernel, a forced tensor-core kernel is refused
+    sc = _with_infinite_bus(fs.multimachine_case(n=20, d=2, K=30, T=0.3, dt=0.005, N=130, seed=98), 99)
+    mean, var, traj = fmc.simulate(sc, path="fused", precision="bf16x3", want_traj=True)
+    fmc.device_status()
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
+    fmc.set_kernel_policy("split_tc")
+    try:
+        with pytest.raises(fmc.FastMCError) as e:
+            fmc.simulate(sc)
+        assert e.value.code == 8
+    finally:
+        fmc.set_kernel_policy("auto")
