@@ -1337,8 +1337,13 @@ static int reserve(fmc_ctx* ctx, Workspace& ws, const Prepared& P, bool want_tra
 // Enqueues the path for P on `st` (no allocation, no synchronisation: usable
 // under stream capture once reserve() has run).  S1, S2 [Nt+1][2n] receive the
 // shifted sums over the block; the shift is at ws.eq + 2n.
+// R > 1 (replicates): the block holds R designs of count / R samples each, the
+// design of replicate k from seeds[k] in rows k count/R ..; their moment sums go
+// to S1 + k (Nt+1) 2n and S2 + k (Nt+1) 2n (per-tile partials; count / R a
+// multiple of 128, so that no tile straddles two designs).
 static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, double* S2, float* traj_dev,
-                   bool per_tile_partials, cudaStream_t st, double* rrf = nullptr)
+                   bool per_tile_partials, cudaStream_t st, double* rrf = nullptr, int R = 1,
+                   const uint64_t* seeds = nullptr)
 {
     const fmc_scenario* s = &P.s;
     const int n = s->n, d = s->d, K = s->K, Nt = P.Nt;
@@ -1419,13 +1424,24 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
         memset(maps, 0, sizeof maps);
     } else {
         prof_begin(ctx, PH_LHS, st, &pr);
-        FMC_CUDA(ctx,
-                 s->correlation == FMC_CORR_RANK
-                     ? launch_ic_split(s->seed, N, k0, count, d, K, s->sampling, (const uint32_t*)ws.ic_strata.ptr,
-                                       ws.zeta_hi.ptr, split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st)
-                     : launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr,
-                                        split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st),
-                 "lhs kernel");
+        if (R > 1) {
+            const int64_t per = count / R;
+            const size_t rb = (size_t)per * d * Ks * 2;  // bytes of one design (BF16 rows of d Ks)
+            for (int k = 0; k < R; ++k)
+                FMC_CUDA(ctx,
+                         launch_lhs_split(seeds[k], per, 0, per, d, K, s->sampling, (char*)ws.zeta_hi.ptr + k * rb,
+                                          split ? (char*)ws.zeta_lo.ptr + k * rb : nullptr, ctx->sms, st),
+                         "lhs kernel");
+        } else {
+            FMC_CUDA(ctx,
+                     s->correlation == FMC_CORR_RANK
+                         ? launch_ic_split(s->seed, N, k0, count, d, K, s->sampling,
+                                           (const uint32_t*)ws.ic_strata.ptr, ws.zeta_hi.ptr,
+                                           split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st)
+                         : launch_lhs_split(s->seed, N, k0, count, d, K, s->sampling, ws.zeta_hi.ptr,
+                                            split ? ws.zeta_lo.ptr : nullptr, ctx->sms, st),
+                     "lhs kernel");
+        }
         prof_end(pr, st);
         prof_begin(ctx, PH_BASIS, st, &pr);
         FMC_CUDA(ctx,
@@ -1514,7 +1530,18 @@ static int enqueue(fmc_ctx* ctx, Workspace& ws, const Prepared& P, double* S1, d
     prof_end(pr, st);
     if (per_tile_partials) {
         prof_begin(ctx, PH_REDUCE, st, &pr);
-        FMC_CUDA(ctx, launch_fused_sums((const float*)ws.part.ptr, (int)ntiles, Nt1, S, count, shape.rows, S1, S2, st), "moment sums");
+        if (R > 1) {
+            const int64_t tiles = ntiles / R;
+            for (int k = 0; k < R; ++k)
+                FMC_CUDA(ctx,
+                         launch_fused_sums((const float*)ws.part.ptr + (size_t)k * tiles * Nt1 * 3 * S, (int)tiles,
+                                           Nt1, S, count / R, shape.rows, S1 + (size_t)k * Nt1 * S,
+                                           S2 + (size_t)k * Nt1 * S, st),
+                         "moment sums");
+        } else {
+            FMC_CUDA(ctx, launch_fused_sums((const float*)ws.part.ptr, (int)ntiles, Nt1, S, count, shape.rows, S1, S2, st),
+                     "moment sums");
+        }
         prof_end(pr, st);
     }
     return FMC_OK;
@@ -1552,6 +1579,31 @@ int fmc::simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, dou
              launch_finalize(mean_dev, var_dev, (const double*)ctx->eq.ptr + 2 * s->n, s->N, (int64_t)P.Nt + 1,
                              2 * s->n, mean_dev, var_dev, st),
              "moment finalize");
+    return FMC_OK;
+}
+
+int fmc::simulate_moments_replicates(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int R,
+                                     const uint64_t* seeds, double* mean_dev, double* var_dev, cudaStream_t st)
+{
+    if (!ctx) return FMC_EINVAL;
+    if (!s || !seeds || !mean_dev || !var_dev || R < 2) return fail(ctx, FMC_EINVAL, "replicates");
+    if (path != FMC_PATH_FUSED || s->sampling == FMC_SRS_EM || s->correlation == FMC_CORR_RANK || s->N % TC_M != 0)
+        return fail(ctx, FMC_EUNSUPPORTED, "replicates in one launch: fused path, a KL design, N a multiple of 128");
+    if (ctx->stream_ordered) ctx->ws_stream = st;
+    fmc_scenario sr = *s;
+    sr.N = (int64_t)R * s->N;
+    Prepared P;
+    int rc = prepare(ctx, ctx->ws, &sr, 0, sr.N, path, st, P, false);  // requests of the server share the GPU
+    if (rc) return rc;
+    if ((rc = reserve(ctx, ctx->ws, P, false, true))) return rc;
+    if ((rc = enqueue(ctx, ctx->ws, P, mean_dev, var_dev, nullptr, true, st, nullptr, R, seeds))) return rc;
+    const int64_t Nt1 = (int64_t)P.Nt + 1;
+    const size_t cols = (size_t)Nt1 * 2 * s->n;
+    for (int k = 0; k < R; ++k)
+        FMC_CUDA(ctx,
+                 launch_finalize(mean_dev + k * cols, var_dev + k * cols, (const double*)ctx->eq.ptr + 2 * s->n, s->N,
+                                 Nt1, 2 * s->n, mean_dev + k * cols, var_dev + k * cols, st),
+                 "moment finalize");
     return FMC_OK;
 }
 

@@ -75,6 +75,16 @@ int reserve_workspace(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int64_t
 int simulate_moments(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, double* mean_dev, double* var_dev,
                      bool per_tile_partials, cudaStream_t st);
 
+// simulate_moments for R independent designs of the same scenario in one launch:
+// replicate k draws its design of s->N samples from seeds[k]; its moments go to
+// mean_dev + k (Nt+1) 2n and var_dev + k (Nt+1) 2n, equal to simulate_moments of
+// the scenario with that seed (the same tiles reduced in the same order).
+// FMC_EUNSUPPORTED unless the path is fused, the design a KL design without the
+// correlation-reducing permutation and s->N a multiple of 128 (the caller then
+// runs the replicates one by one).
+int simulate_moments_replicates(fmc_ctx* ctx, const fmc_scenario* s, int32_t path, int R, const uint64_t* seeds,
+                                double* mean_dev, double* var_dev, cudaStream_t st);
+
 // fmc_device_status for the work enqueued on one stream: waits for that stream
 // only (not the device), so concurrent requests of the server keep running.
 int device_status_on(fmc_ctx* ctx, cudaStream_t st);

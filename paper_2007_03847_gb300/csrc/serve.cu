@@ -57,9 +57,11 @@ uint64_t mix64(uint64_t x)
 }
 
 // Runs a target-error request on the slot's contexts and streams (see
-// fmc_submit_target): rounds of kReplicates independent designs, each on its
-// own context and stream so that they run concurrently, n growing fourfold
-// until the replicate spread meets the targets or max_N is reached.
+// fmc_submit_target): rounds of kReplicates independent designs, n growing
+// fourfold until the replicate spread meets the targets or max_N is reached.
+// A round's designs share one launch (one equilibrium, one design block of
+// R n samples, per-replicate sums) where simulate_moments_replicates takes the
+// request; otherwise each runs on its own context and stream, concurrently.
 int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
 {
     cudaStream_t st = rst[0];
@@ -69,15 +71,20 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
     const size_t cols = (size_t)(Nt + 1) * 2 * (size_t)s.n;
     double* dbuf = nullptr;
     if (cudaMallocAsync((void**)&dbuf, sizeof(double) * cols * 2 * R, st) != cudaSuccess) return FMC_ENOMEM;
+    // one launch for a round's designs: the fused path, a KL design without the
+    // correlation-reducing permutation, tile-aligned designs (n stays a multiple
+    // of 128 as it grows fourfold)
+    const bool merged = r->path == FMC_PATH_FUSED && s.sampling != FMC_SRS_EM && s.correlation != FMC_CORR_RANK &&
+                        s.N >= 128 && s.N % 128 == 0;
     // every replicate's workspace sized once for the largest round this request
     // may reach, so that no round grows (and reallocates) it
     {
         fmc_scenario big = s;
         int64_t nb = s.N < 2 ? 2 : s.N;
         while (4 * (int64_t)R * nb <= r->max_N) nb *= 4;
-        big.N = nb;
-        for (int k = 0; k < R; ++k) {
-            const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, nb, rst[k]);
+        big.N = merged ? (int64_t)R * nb : nb;
+        for (int k = 0; k < (merged ? 1 : R); ++k) {
+            const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, big.N, rst[k]);
             if (rc0 != FMC_OK) {
                 r->error = fmc_last_error(rctx[k]);
                 cudaFreeAsync(dbuf, st);
@@ -94,9 +101,15 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
             rc = FMC_ECUDA;
             break;
         }
-        for (int k = 0; k < R && rc == FMC_OK; ++k) {
-            s.N = n;
-            s.seed = mix64(seed0 ^ ((uint64_t)(round * R + k + 1) << 32));
+        s.N = n;
+        uint64_t seeds[kReplicates];
+        for (int k = 0; k < R; ++k) seeds[k] = mix64(seed0 ^ ((uint64_t)(round * R + k + 1) << 32));
+        if (merged) {
+            rc = fmc::simulate_moments_replicates(rctx[0], &s, r->path, R, seeds, dbuf, dbuf + (size_t)R * cols, st);
+            if (rc != FMC_OK) r->error = fmc_last_error(rctx[0]);
+        }
+        for (int k = 0; k < R && rc == FMC_OK && !merged; ++k) {
+            s.seed = seeds[k];
             rc = fmc::simulate_moments(rctx[k], &s, r->path, dbuf + (size_t)k * cols, dbuf + (size_t)(R + k) * cols,
                                        false, rst[k]);
             if (rc != FMC_OK) r->error = fmc_last_error(rctx[k]);

@@ -145,3 +145,32 @@ def test_target_error_request_stops_at_max_n(fmc):
         srv.submit(sc, tol_E=1e-3, max_N=100)         # below four designs of N samples
     assert e.value.code == fmc.EINVAL
     srv.close()
+
+
+def _mix64(x):
+    """splitmix64's finaliser (the server's replicate seeds)."""
+    m = (1 << 64) - 1
+    x = (x + 0x9E3779B97F4A7C15) & m
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & m
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & m
+    return x ^ (x >> 31)
+
+
+@pytest.mark.parametrize("n", [10, 20])
+def test_round_of_replicates_in_one_launch(fmc, n):
+    # a round's four designs share one launch; its pooled moments are those of
+    # the four designs run one by one (seed k: splitmix64 of seed ^ (k + 1) << 32)
+    sc = fs.multimachine_case(n=n, d=3, K=50, T=0.5, dt=0.005, N=256, seed=41)
+    srv = fmc.Server(slots=1)
+    h = srv.submit(sc, tol_E=10.0, tol_Var=10.0, max_N=1 << 14)
+    res, m, v = srv.wait(h, timeout_s=60)
+    srv.close()
+    assert res["status"] == 0 and res["target_met"] and res["n_used"] == 4 * 256
+    ms, vs = [], []
+    for k in range(4):
+        mk, vk = fmc.simulate(sc.replace(seed=_mix64(sc.seed ^ ((k + 1) << 32))), path="fused", precision="bf16x3")
+        ms.append(mk.cpu().numpy())
+        vs.append(vk.cpu().numpy())
+    m0 = ((ms[0] + ms[1]) + ms[2]) + ms[3]
+    v0 = ((vs[0] + vs[1]) + vs[2]) + vs[3]
+    _same_within_rounding(m.cpu().numpy(), v.cpu().numpy(), m0 / 4, v0 / 4, n)
