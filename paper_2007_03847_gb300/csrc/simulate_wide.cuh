@@ -1,24 +1,29 @@
 // Algorithm 1 steps 2-4 fused for systems too large to keep one sample's whole
 // state in one thread (17..52 machines); smaller systems on request.
 //
-// One CTA = 128 samples = 128 TMEM lanes, 16 warps.  Warp (q, h) = (w mod 4,
-// w / 4) integrates the machines i = h + 4k (k < NMT) of the 32 samples whose
-// TMEM lanes it may read (subpartition q), so four warps share every sample and
-// each thread holds a quarter of its sample's state.  The KL contraction into
-// TMEM is the fused kernel's (one thread issues TMA loads and tcgen05.mma per
-// time chunk); the four warps of a sample group then turn the increments into
-// the chunk's disturbance paths in place in TMEM (warp h the disturbances
-// w = h mod 4), and all four read every path.
+// One CTA = 128 samples = 128 TMEM lanes, 4 H warps (H = 4, or 2 with two CTAs
+// per SM).  Warp (q, h) = (w mod 4, w / 4) integrates the machines i = h + H k
+// (k < NMT) of the 32 samples whose TMEM lanes it may read (subpartition q), so
+// H warps share every sample and each thread holds 1/H of its sample's state.
+// The KL contraction into TMEM is the fused kernel's (one thread issues TMA
+// loads and tcgen05.mma per time chunk); the warps of a sample group then turn
+// the increments into the chunk's disturbance paths in place in TMEM (warp h
+// the disturbances w = h mod 4, and h + 2 mod 4 when H = 2), and all of them
+// read every path.
 //
-// Per RK stage every thread publishes, for its machines, the deviations
-//   gamma_i = cos(D*_i + Delta_i) - cos D*_i,  eta_i = sin(D*_i + Delta_i) - sin D*_i
-// of the stage input to shared memory (double-buffered, so one named barrier of
-// the 128 threads of a sample group per stage suffices), then accumulates the
-// network sums of its machines over all machines j, reading (gamma_j, eta_j)
-// once per j.  The network matrices sit in shared memory laid out
-// [j][h][k] (k padded to a multiple of 4) so that a warp reads its column slice
-// with broadcast 16-byte loads.  The arithmetic per machine is that of
-// swing_step (deviation form around the FP64 equilibrium, diagonal excluded).
+// The network sums of an RK stage need, for every machine j, the deviations
+//   gamma_j = cos(D*_j + Delta_j) - cos D*_j,  eta_j = sin(D*_j + Delta_j) - sin D*_j
+// of the stage input.  FP32 form (TCN false): every thread publishes its
+// machines' (gamma, eta) to shared memory (double-buffered, so one named barrier
+// of the 128 threads of a sample group per stage suffices), then accumulates the
+// sums of its machines over all j, the network matrices laid out [j][h][k] in
+// shared memory (k padded to a multiple of 4) so that a warp reads its column
+// slice with broadcast 16-byte loads.  Tensor-core form (TCN, wide_tc.cuh): the
+// (gamma, eta) go to TMEM and one tcgen05 TF32x3 product per stage forms the sums
+// of all 128 samples; the deviations are taken less their per-sample mean, and
+// an infinite bus (BUS) is a network node in the last machine slot.  The
+// arithmetic per machine is that of swing_step (deviation form around the FP64
+// equilibrium, diagonal excluded).
 #pragma once
 
 #include "fmc_common.cuh"
