@@ -347,23 +347,6 @@ int fmc_kle_reconstruct(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int3
 int fmc_kle_reconstruct_noalloc(fmc_ctx* ctx, const float* zeta_dev, int64_t count, int32_t d, int32_t K, double T,
                                 double dt, int32_t precision, float* dW_dev, void* stream);
 
-/*
- * Self-check of the failure-detection path (no counterpart in the paper).  Every
- * spin of the library's kernels on an mbarrier is bounded; when it runs out the
- * kernel records a timeout code in a device status word and returns, and
- * fmc_device_status reports FMC_ETIMEOUT.  This call exercises that path without
- * a fault: it clears the status word and launches one CTA whose thread waits, at
- * most poll_limit polls (1 .. 2^24), on an mbarrier that nothing arrives at,
- * with no bulk copy or MMA in flight, so the wait runs out and the timeout is
- * recorded.
- *   target 0: the context's status word (as fmc_simulate's kernels use it);
- *   target 1: the allocation-free reconstruction's word in its scratch array
- *             (same device rule as fmc_kle_reconstruct_noalloc).
- * Asynchronous on `stream`; a following fmc_device_status returns FMC_ETIMEOUT.
- * Errors: FMC_EINVAL (target, poll_limit, device), FMC_ENOMEM, FMC_ECUDA.
- */
-int fmc_check_wait_path(fmc_ctx* ctx, int32_t target, int64_t poll_limit, void* stream);
-
 /* ---- equilibrium (Section V-A: "at equilibrium at t = 0") --------------------- */
 
 /*
@@ -536,28 +519,8 @@ int fmc_moments(fmc_ctx* ctx, const float* x_dev, int64_t N, int64_t C, double* 
  */
 int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error);
 
-/*
- * Kernel timing with CUDA events recorded on the launching stream around every
- * kernel phase of later calls (at most max_records phases; enable = 0 stops and
- * clears).  Phases: 0 LHS, 1 KL basis, 2 equilibrium, 3 fused simulation,
- * 4 fused moment reduce, 5 FP32 contraction, 6 plain integrator, 7 moments,
- * 8 a whole batch graph launch.
- */
-int fmc_profile(fmc_ctx* ctx, int32_t enable, int64_t max_records);
 
-/* Synchronises, then sums the recorded durations of one phase. */
-int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* launches);
 
-/*
- * Test hook (no counterpart in the paper): evaluates the integrator's own
- * sin/cos (Cody-Waite reduction + Taylor series, FP32) and CUDA's sincosf on
- * x_dev[n], writing s_dev, c_dev and s_ref_dev, c_ref_dev (device, float[n]).
- */
-int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, float* c_dev, float* s_ref_dev,
-                    float* c_ref_dev, void* stream);
-
-/* CTAs per SM the last fused launch could keep resident (occupancy API). */
-int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);
 
 /* ---- kernel choice of the fused path (no counterpart in the paper) -------- */
 #define FMC_KERNEL_AUTO 0        /* per sample for n <= 16, split with the tensor-core network sum above */

@@ -18,6 +18,7 @@
 #include "tc_common.cuh"
 #include "wide_tc.cuh"
 #include "api_internal.h"
+#include "../../include/fastmc_diag.h"
 
 using namespace fmc;
 

@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every
-entry point that include/fastmc.h declares.  No compute calls are made here."""
+entry point that the headers under include/ declare (fastmc.h, the method's API;
+fastmc_diag.h, diagnostics and test hooks).  No compute calls are made here."""
 import ctypes
 import os
 import re
@@ -8,10 +9,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "fastmc.h")
+HEADERS = [HEADER, os.path.join(ROOT, "include", "fastmc_diag.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(fmc_[a-z_0-9]+)\s*\(", text, flags=re.M)))
 
@@ -26,8 +28,13 @@ def lib():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for must in ["fmc_create", "fmc_destroy", "fmc_last_error", "fmc_lhs_sample", "fmc_lhs_sample_split",
-                 "fmc_kl_basis", "fmc_kle_reconstruct", "fmc_equilibrium", "fmc_simulate", "fmc_moments"]:
+                 "fmc_kl_basis", "fmc_kle_reconstruct", "fmc_equilibrium", "fmc_simulate", "fmc_moments",
+                 "fmc_profile", "fmc_check_wait_path"]:
         assert must in names
+    # the method's header declares no test hook
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for hook in ["fmc_test_sincos", "fmc_check_wait_path", "fmc_profile", "fmc_last_fused_occupancy"]:
+        assert hook + "(" not in text
 
 
 def test_every_declared_symbol_is_exported(lib):
