@@ -32,6 +32,9 @@ cudaError_t wide_tc_nmt10(int nd, const CUtensorMap* maps, const WideArgs& a, cu
 cudaError_t wide_tc_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_h2_nmt10(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_h2_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt9(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt11(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt12(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
 cudaError_t wide_tc_bus(int nmt, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
@@ -44,7 +47,10 @@ cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, bool bus, const CUte
         return wide_tc_bus(nmt, maps, a, st, max_ctas_per_sm);
     }
     if (H == 2) {
+        if (nmt == 9) return wide_tc_h2_nmt9(nd, maps, a, st, max_ctas_per_sm);
         if (nmt == 10) return wide_tc_h2_nmt10(nd, maps, a, st, max_ctas_per_sm);
+        if (nmt == 11) return wide_tc_h2_nmt11(nd, maps, a, st, max_ctas_per_sm);
+        if (nmt == 12) return wide_tc_h2_nmt12(nd, maps, a, st, max_ctas_per_sm);
         if (nmt == 13) return wide_tc_h2_nmt13(nd, maps, a, st, max_ctas_per_sm);
         return cudaErrorInvalidValue;
     }

@@ -30,6 +30,7 @@ def _check_moments(m, v, rm, rv, n, tol=1e-5):
 
 CASES = {
     "n17_d1": dict(n=17, d=1, K=30, T=0.5, dt=0.005, N=131, seed=21),
+    "n22_d5": dict(n=22, d=5, K=30, T=0.4, dt=0.005, N=150, seed=28),
     "n24_d4": dict(n=24, d=4, K=40, T=0.5, dt=0.005, N=200, seed=27),
     "n28_d3": dict(n=28, d=3, K=40, T=0.5, dt=0.005, N=200, seed=22),
     "n37_d5": dict(n=37, d=5, K=23, T=0.333, dt=0.003, N=129, seed=23),
@@ -141,7 +142,8 @@ def test_wide_in_a_batch(fmc):
     b.close()
 
 
-@pytest.mark.parametrize("n,d", [(13, 2), (20, 3), (20, 8), (23, 2), (26, 4), (50, 3), (52, 8)])
+@pytest.mark.parametrize("n,d", [(13, 2), (18, 3), (20, 3), (20, 8), (21, 7), (23, 2), (24, 6), (26, 4), (50, 3),
+                                 (52, 8)])
 def test_tensor_core_network_sum_matches_fp32_sum(fmc, n, d):
     # the TF32x3 product drops terms below 2^-21 of each product: the two forms of
     # the same design agree far inside the oracle tolerance
