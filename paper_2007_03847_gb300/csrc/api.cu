@@ -1168,13 +1168,16 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
     if (policy == FMC_KERNEL_SPLIT_TC && !wide_tc_built(P.nmt))
         return fail(ctx, FMC_EUNSUPPORTED, "the tensor-core network sum handles 13 to %d machines (n = %d)",
                     FMC_MAX_MACHINES, n);
-    // 17..26 machines: two warps per sample and two CTAs per SM (9 .. 13 slots
+    // 17..28 machines: two warps per sample and two CTAs per SM (9 .. 14 slots
     // per thread), whose barriers and product waits overlap, where the halved
     // TMEM share holds the product's columns and a 16-step chunk of the
-    // disturbances (up to 7 with 9..12 slots, 4 with 13)
-    if (P.tcn && (P.nmt == 5 || (P.nmt == 7 && n <= 26))) {
-        const int h2 = n <= 18 ? 9 : n <= 20 ? 10 : n <= 22 ? 11 : n <= 24 ? 12 : 13;
-        if (16 * s->d + wide_tc_cols(h2, 2) <= 256) {
+    // disturbances (up to 7 with 9..12 slots, 4 with 13 and 14)
+    if (P.tcn && (P.nmt == 5 || P.nmt == 7)) {
+        const int h2 = n <= 18 ? 9 : n <= 20 ? 10 : n <= 22 ? 11 : n <= 24 ? 12 : n <= 26 ? 13 : 14;
+        // (13 and 14 slots are built for the disturbance-slot buckets up to 4,
+        // the generator-trip slot included)
+        const int ndx = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+        if (16 * s->d + wide_tc_cols(h2, 2) <= 256 && (h2 < 13 || ndx <= 4)) {
             P.H = 2;
             P.nmt = h2;
         }

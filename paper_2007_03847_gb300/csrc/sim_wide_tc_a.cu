@@ -35,6 +35,7 @@ cudaError_t wide_tc_h2_nmt13(int nd, const CUtensorMap* maps, const WideArgs& a,
 cudaError_t wide_tc_h2_nmt9(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_h2_nmt11(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 cudaError_t wide_tc_h2_nmt12(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
+cudaError_t wide_tc_h2_nmt14(int nd, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
 cudaError_t wide_tc_bus(int nmt, const CUtensorMap* maps, const WideArgs& a, cudaStream_t st, int* occ);
 
@@ -52,6 +53,7 @@ cudaError_t launch_simulate_wide_tc(int nmt, int H, int nd, bool bus, const CUte
         if (nmt == 11) return wide_tc_h2_nmt11(nd, maps, a, st, max_ctas_per_sm);
         if (nmt == 12) return wide_tc_h2_nmt12(nd, maps, a, st, max_ctas_per_sm);
         if (nmt == 13) return wide_tc_h2_nmt13(nd, maps, a, st, max_ctas_per_sm);
+        if (nmt == 14) return wide_tc_h2_nmt14(nd, maps, a, st, max_ctas_per_sm);
         return cudaErrorInvalidValue;
     }
     if (H != 4) return cudaErrorInvalidValue;

@@ -142,8 +142,8 @@ def test_wide_in_a_batch(fmc):
     b.close()
 
 
-@pytest.mark.parametrize("n,d", [(13, 2), (18, 3), (20, 3), (20, 8), (21, 7), (23, 2), (24, 6), (26, 4), (50, 3),
-                                 (52, 8)])
+@pytest.mark.parametrize("n,d", [(13, 2), (18, 3), (20, 3), (20, 8), (21, 7), (23, 2), (24, 6), (26, 4), (28, 3),
+                                 (50, 3), (52, 8)])
 def test_tensor_core_network_sum_matches_fp32_sum(fmc, n, d):
     # the TF32x3 product drops terms below 2^-21 of each product: the two forms of
     # the same design agree far inside the oracle tolerance
@@ -260,3 +260,15 @@ def test_infinite_bus_without_a_free_slot(fmc, orc):
         assert e.value.code == 8
     finally:
         fmc.set_kernel_policy("auto")
+
+
+def test_two_warps_per_sample_with_a_trip_event(fmc, orc):
+    # 4 disturbances and a generator trip fill the 8-slot bucket, which the 13-slot
+    # two-warp layout is not built for: the four-warp layout takes the system
+    sc = fs.multimachine_case(n=25, d=4, K=20, T=0.3, dt=0.005, N=130, seed=99).replace(
+        event_machine=3, event_time=0.1, event_dpm=-0.5)
+    mean, var, traj = _tc_run(fmc, sc)
+    ref = orc.simulate(sc, orc.lhs_sample(sc.seed, sc.N, sc.M), want_traj=True, nthreads=8)
+    ed, ew = traj_errors(traj.cpu().numpy(), ref["traj"], sc.n)
+    assert ed <= 1e-4 and ew <= 1e-4, (ed, ew)
+    _check_moments(mean.cpu().numpy(), var.cpu().numpy(), ref["mean"], ref["var"], sc.n)
