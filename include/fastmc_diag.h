@@ -1,8 +1,9 @@
 /*
  * fastmc_diag.h -- diagnostics and test hooks of libfastmc (no counterpart in
  * the paper): the self-check of the bounded-wait failure path, kernel-phase
- * timing with CUDA events, the integrator's sin/cos against CUDA's sincosf, and
- * the occupancy of the last fused launch.  The method itself needs none of
+ * timing with CUDA events, the integrator's sin/cos against CUDA's sincosf, the
+ * split kernel's tensor-core network matrix, and the occupancy of the last fused
+ * launch.  The method itself needs none of
  * them (fastmc.h); the same library exports them.
  */
 #ifndef FASTMC_DIAG_H
@@ -50,6 +51,19 @@ int fmc_profile_read(fmc_ctx* ctx, int32_t phase, double* total_ms, int64_t* lau
  */
 int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, float* c_dev, float* s_ref_dev,
                     float* c_ref_dev, void* stream);
+
+/*
+ * The split kernel's tensor-core network matrix as the library builds it for a
+ * launch (host only, no device): FP32 [2][NN][NN], Net_hi then Net_lo, with
+ * NN = 2 KH H rounded up to a multiple of 16, KH = 2 nmt rounded up to a
+ * multiple of 4, row and column of machine i at (i mod H) KH + 2 (i / H) (then
+ * +1 for the v row and the eta column): Net = [[GE, -BE], [BE, GE]] with
+ * GE = E_i E_j G_ij, BE = E_i E_j B_ij, zero diagonal and padding; with an
+ * infinite bus its column E_i V (Ginf_i, Binf_i) sits in machine slot
+ * H nmt - 1.  H is 2 or 4, n <= H nmt (< with an infinite bus).
+ * Errors: FMC_EINVAL (arguments, out_floats < 2 NN^2).
+ */
+int fmc_diag_net_matrix(const fmc_scenario* scen, int32_t nmt, int32_t H, float* out, int64_t out_floats);
 
 /* CTAs per SM the last fused launch could keep resident (occupancy API). */
 int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);

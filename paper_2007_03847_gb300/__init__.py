@@ -118,6 +118,7 @@ def load_library():
             "fmc_profile": ([vp, i32, i64], ctypes.c_int),
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "fmc_diag_net_matrix": ([vp, i32, i32, vp, i64], ctypes.c_int),
             "fmc_set_kernel_policy": ([vp, ctypes.c_int32], ctypes.c_int),
             "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_batch_create": ([vp, ctypes.POINTER(_Scenario), i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -665,6 +666,21 @@ def set_launch_rules(rules, ctx: "Context | None" = None) -> None:
                             int(r.get("d_max", 1 << 30)), int(r.get("N_min", 1)), int(r.get("N_max", 1 << 62)),
                             int(r.get("kernel", 0)), int(r.get("max_ctas", 0)), int(r.get("TC", 0)), 0)
     ctx.check(ctx.lib.fmc_set_launch_rules(ctx.h, arr, len(rules)))
+
+
+def net_matrix(scenario, nmt: int, H: int = 4):
+    """fmc_diag_net_matrix: the split kernel's tensor-core network matrix as the
+    library builds it for a launch (host only, no GPU): (Net_hi, Net_lo), each
+    float32 [NN][NN]."""
+    lib = load_library()
+    kh = (2 * nmt + 3) & ~3
+    nn = (H * kh + 15) & ~15
+    out = np.zeros(2 * nn * nn, dtype=np.float32)
+    ss = ScenarioStruct(scenario)
+    rc = lib.fmc_diag_net_matrix(ctypes.byref(ss.s), int(nmt), int(H), out.ctypes.data, out.size)
+    if rc != OK:
+        raise FastMCError(rc, "fmc_diag_net_matrix failed")
+    return out[: nn * nn].reshape(nn, nn), out[nn * nn:].reshape(nn, nn)
 
 
 def set_kernel_policy(policy, ctx: Context | None = None) -> None:

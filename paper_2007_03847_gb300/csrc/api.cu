@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -432,6 +433,49 @@ static float tf32_round(double x)
 // Offset (floats) of the tensor-core network matrix in the constant block.
 static size_t wide_net_offset(int n, int nmt, int nd) { return ((size_t)wide_const_floats(n, nmt, nd) + 31) & ~(size_t)31; }
 
+// The network matrix of the tensor-core sum (wide_tc.cuh) into hi_lo (FP32
+// [2][NN][NN], zeroed here): Net[(i, u|v)][(j, gamma|eta)] =
+//   u: ( GE_ij, -BE_ij ),  v: ( BE_ij, GE_ij ),  diagonal and padding zero,
+// row and column of machine i at (i mod H) KH + 2 (i / H), as Net_hi = TF32(Net)
+// and Net_lo = TF32(Net - Net_hi); an infinite bus is a node in the last machine
+// slot (E = V, G_ib = Ginf_i, B_ib = Binf_i), which the kernel fills with the
+// bus's deviation in its shifted frame.
+static void build_wide_net(const fmc_scenario* s, int nmt, int H, float* hi_lo)
+{
+    const int n = s->n, KH = wide_kh(nmt), NN = wide_nn(nmt, H);
+    float* hi = hi_lo;
+    float* lo = hi + (size_t)NN * NN;
+    std::fill(hi, hi + 2 * (size_t)NN * NN, 0.f);
+    auto put = [&](int row, int col, double x) {
+        const float h = tf32_round(x);
+        hi[(size_t)row * NN + col] = h;
+        lo[(size_t)row * NN + col] = tf32_round(x - (double)h);
+    };
+    for (int i = 0; i < n; ++i) {
+        const int ru = (i % H) * KH + 2 * (i / H);
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const int cg = (j % H) * KH + 2 * (j / H);
+            const double ge = s->E[i] * s->E[j] * s->G[i * n + j];
+            const double be = s->E[i] * s->E[j] * s->B[i * n + j];
+            put(ru, cg, ge);
+            put(ru, cg + 1, -be);
+            put(ru + 1, cg, be);
+            put(ru + 1, cg + 1, ge);
+        }
+        if (s->has_inf_bus) {
+            const int nb = H * nmt - 1;  // the last machine slot (free: n < H nmt)
+            const int cb = (nb % H) * KH + 2 * (nb / H);
+            const double ge = s->E[i] * s->Vinf * s->Ginf[i];
+            const double be = s->E[i] * s->Vinf * s->Binf[i];
+            put(ru, cb, ge);
+            put(ru, cb + 1, -be);
+            put(ru + 1, cb, be);
+            put(ru + 1, cb + 1, ge);
+        }
+    }
+}
+
 // Constant block of the large-system kernel (layout at wide_const_floats): the
 // same deviation-form constants as build_params, with the network matrices
 // arranged [j][h][k] for machine i = h + 4k; with tcn, the tensor-core network
@@ -481,45 +525,12 @@ static void build_wide_consts(const fmc_scenario* s, const double* delta0, int n
     if (s->event_machine >= 0) pm[(8 + d) * g4 + s->event_machine] = (float)s->event_dpm;
     // (GB and pm point into out: nothing below writes through them, out may move)
     if (tcn) {
-        // the network matrix of the tensor-core sum (wide_tc.cuh), 128-byte
-        // aligned after the constant block: Net[(i, u|v)][(j, gamma|eta)] =
-        //   u: ( GE_ij, -BE_ij ),  v: ( BE_ij, GE_ij ),  diagonal and padding zero,
-        // as Net_hi = TF32(Net) and Net_lo = TF32(Net - Net_hi); an infinite bus is
-        // a node in the last machine slot (E = V, G_ib = Ginf_i, B_ib = Binf_i),
-        // which the kernel fills with the bus's deviation in its shifted frame
-        const int KH = wide_kh(nmt), NN = wide_nn(nmt, H);
+        // the network matrix of the tensor-core sum, 128-byte aligned after the
+        // constant block
+        const int NN = wide_nn(nmt, H);
         const size_t base = (out.size() + 31) & ~(size_t)31;
         out.resize(base + 2 * (size_t)NN * NN, 0.f);
-        float* hi = out.data() + base;
-        float* lo = hi + (size_t)NN * NN;
-        auto put = [&](int row, int col, double x) {
-            const float h = tf32_round(x);
-            hi[(size_t)row * NN + col] = h;
-            lo[(size_t)row * NN + col] = tf32_round(x - (double)h);
-        };
-        for (int i = 0; i < n; ++i) {
-            const int ru = (i % H) * KH + 2 * (i / H);
-            for (int j = 0; j < n; ++j) {
-                if (j == i) continue;
-                const int cg = (j % H) * KH + 2 * (j / H);
-                const double ge = s->E[i] * s->E[j] * s->G[i * n + j];
-                const double be = s->E[i] * s->E[j] * s->B[i * n + j];
-                put(ru, cg, ge);
-                put(ru, cg + 1, -be);
-                put(ru + 1, cg, be);
-                put(ru + 1, cg + 1, ge);
-            }
-            if (s->has_inf_bus) {
-                const int nb = H * nmt - 1;  // the last machine slot (free: n < H nmt)
-                const int cb = (nb % H) * KH + 2 * (nb / H);
-                const double ge = s->E[i] * s->Vinf * s->Ginf[i];
-                const double be = s->E[i] * s->Vinf * s->Binf[i];
-                put(ru, cb, ge);
-                put(ru, cb + 1, -be);
-                put(ru + 1, cb, be);
-                put(ru + 1, cb + 1, ge);
-            }
-        }
+        build_wide_net(s, nmt, H, out.data() + base);
     }
 }
 
@@ -2063,6 +2074,19 @@ int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm)
 {
     if (!ctx || !ctas_per_sm) return FMC_EINVAL;
     *ctas_per_sm = ctx->last_fused_ctas_per_sm;
+    return FMC_OK;
+}
+
+int fmc_diag_net_matrix(const fmc_scenario* scen, int32_t nmt, int32_t H, float* out, int64_t out_floats)
+{
+    if (!scen || !out || scen->n < 1 || scen->n > FMC_MAX_MACHINES || !scen->G || !scen->B || !scen->E)
+        return FMC_EINVAL;
+    if ((H != 2 && H != 4) || nmt < 1 || nmt > 16 || scen->n > H * nmt ||
+        (scen->has_inf_bus && (scen->n >= H * nmt || !scen->Ginf || !scen->Binf)))
+        return FMC_EINVAL;
+    const int NN = wide_nn(nmt, H);
+    if (out_floats < 2 * (int64_t)NN * NN) return FMC_EINVAL;
+    build_wide_net(scen, nmt, H, out);
     return FMC_OK;
 }
 
