@@ -2,8 +2,8 @@
  * fastmc_diag.h -- diagnostics and test hooks of libfastmc (no counterpart in
  * the paper): the self-check of the bounded-wait failure path, kernel-phase
  * timing with CUDA events, the integrator's sin/cos against CUDA's sincosf, the
- * split kernel's tensor-core network matrix, and the occupancy of the last fused
- * launch.  The method itself needs none of
+ * split kernel's tensor-core network matrix and layout choice, and the occupancy
+ * of the last fused launch.  The method itself needs none of
  * them (fastmc.h); the same library exports them.
  */
 #ifndef FASTMC_DIAG_H
@@ -64,6 +64,18 @@ int fmc_test_sincos(fmc_ctx* ctx, const float* x_dev, int64_t n, float* s_dev, f
  * Errors: FMC_EINVAL (arguments, out_floats < 2 NN^2).
  */
 int fmc_diag_net_matrix(const fmc_scenario* scen, int32_t nmt, int32_t H, float* out, int64_t out_floats);
+
+/*
+ * The kernel and layout a single-scenario fused launch of `count` samples takes
+ * under `policy` (FMC_KERNEL_*; no launch rules), as the library decides it
+ * (host only, no device): out[0] the kernel (FMC_KERNEL_PER_SAMPLE, FMC_KERNEL_SPLIT
+ * or FMC_KERNEL_SPLIT_TC), out[1] machine slots per thread of the split kernel
+ * (0 for the per-sample kernel), out[2] its warps per sample, out[3] the
+ * disturbance-slot bucket, out[4] 1 for the infinite-bus form.  Returns the
+ * call's refusal (FMC_EUNSUPPORTED) where the launch would refuse.
+ * Errors: FMC_EINVAL (arguments).
+ */
+int fmc_diag_kernel_choice(const fmc_scenario* scen, int32_t path, int32_t policy, int64_t count, int32_t* out);
 
 /* CTAs per SM the last fused launch could keep resident (occupancy API). */
 int fmc_last_fused_occupancy(const fmc_ctx* ctx, int* ctas_per_sm);

@@ -119,6 +119,7 @@ def load_library():
             "fmc_profile_read": ([vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64)], ctypes.c_int),
             "fmc_last_fused_occupancy": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "fmc_diag_net_matrix": ([vp, i32, i32, vp, i64], ctypes.c_int),
+            "fmc_diag_kernel_choice": ([vp, i32, i32, i64, vp], ctypes.c_int),
             "fmc_set_kernel_policy": ([vp, ctypes.c_int32], ctypes.c_int),
             "fmc_test_sincos": ([vp, vp, i64, vp, vp, vp, vp, vp], ctypes.c_int),
             "fmc_batch_create": ([vp, ctypes.POINTER(_Scenario), i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -681,6 +682,24 @@ def net_matrix(scenario, nmt: int, H: int = 4):
     if rc != OK:
         raise FastMCError(rc, "fmc_diag_net_matrix failed")
     return out[: nn * nn].reshape(nn, nn), out[nn * nn:].reshape(nn, nn)
+
+
+def kernel_choice(scenario, policy="auto", path="fused", count=None):
+    """fmc_diag_kernel_choice: the kernel and layout of a single-scenario fused
+    launch (host only, no GPU, no launch rules) as a dict, or FastMCError with the
+    launch's refusal."""
+    lib = load_library()
+    out = np.zeros(5, dtype=np.int32)
+    ss = ScenarioStruct(scenario)
+    p = _PATH.get(path, path) if isinstance(path, str) else path
+    pol = _KERNEL.get(policy, policy) if isinstance(policy, str) else policy
+    rc = lib.fmc_diag_kernel_choice(ctypes.byref(ss.s), int(p), int(pol), int(scenario.N if count is None else count),
+                                    out.ctypes.data)
+    if rc != OK:
+        raise FastMCError(rc, "fmc_diag_kernel_choice refused")
+    names = {KERNEL_PER_SAMPLE: "per_sample", KERNEL_SPLIT: "split", KERNEL_SPLIT_TC: "split_tc"}
+    return {"kernel": names[int(out[0])], "nmt": int(out[1]), "H": int(out[2]), "nd": int(out[3]),
+            "bus": bool(out[4])}
 
 
 def set_kernel_policy(policy, ctx: Context | None = None) -> None:

@@ -1123,14 +1123,99 @@ struct Prepared {
     std::vector<unsigned char> params;
 };
 
-// The first launch rule that holds the scenario and sample count, or nullptr.
-static const fmc_launch_rule* find_rule(const fmc_ctx* ctx, const fmc_scenario* s, int64_t count)
+// The fused kernel a launch takes and its layout (host logic only): the
+// per-sample kernel, or the split kernel with its slots per thread, warps per
+// sample, tensor-core network sum and infinite-bus form; and the disturbance-slot
+// bucket.  user_policy: the caller's FMC_KERNEL_* (AUTO lets a matching rule of
+// `rules`, if given, choose).  Messages go to ctx when it is given.
+struct KernelChoice {
+    int nm = 0, nmt = 0, nd = 0;
+    bool tcn = false;  // the split kernel's network sums on the tensor cores
+    int H = 4;         // its warps per sample (2: two CTAs per SM)
+    bool bus = false;  // ... for a system with an infinite bus (its own instantiations)
+};
+
+// The first rule of `rules` that holds the scenario and sample count, or nullptr.
+static const fmc_launch_rule* find_rule_in(const std::vector<fmc_launch_rule>& rules, const fmc_scenario* s,
+                                           int64_t count)
 {
-    for (const fmc_launch_rule& r : ctx->rules)
+    for (const fmc_launch_rule& r : rules)
         if (s->n >= r.n_min && s->n <= r.n_max && s->d >= r.d_min && s->d <= r.d_max && count >= r.N_min &&
             count <= r.N_max)
             return &r;
     return nullptr;
+}
+
+// The first launch rule that holds the scenario and sample count, or nullptr.
+static const fmc_launch_rule* find_rule(const fmc_ctx* ctx, const fmc_scenario* s, int64_t count)
+{
+    return find_rule_in(ctx->rules, s, count);
+}
+
+static int choose_kernel(fmc_ctx* ctx, const std::vector<fmc_launch_rule>* rules, const fmc_scenario* s,
+                         int64_t count, int32_t path, int32_t user_policy, KernelChoice& C)
+{
+    const int n = s->n;
+    C.nm = nm_bucket_for(n);
+    // four warps per sample for systems above 16 machines (or on request)
+    int policy = user_policy;
+    if (policy == FMC_KERNEL_AUTO && path == FMC_PATH_FUSED && rules) {
+        // (a rule's kernel that cannot take this system is ignored: a bucket's
+        // rule was measured at its largest machine count)
+        const fmc_launch_rule* rule = find_rule_in(*rules, s, count);
+        if (rule && rule->kernel != FMC_KERNEL_AUTO && !(rule->kernel == FMC_KERNEL_PER_SAMPLE && C.nm < 0) &&
+            !(rule->kernel == FMC_KERNEL_SPLIT_TC && !wide_tc_built(wide_nmt_for(n))))
+            policy = rule->kernel;
+    }
+    const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE;
+    if (path == FMC_PATH_FUSED && per_sample && C.nm < 0)
+        return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
+                    FMC_MAX_MACHINES_PLAIN, n);
+    if (path == FMC_PATH_FUSED && (policy == FMC_KERNEL_SPLIT || policy == FMC_KERNEL_SPLIT_TC))
+        C.nmt = wide_nmt_for(n);
+    else if (path == FMC_PATH_FUSED && per_sample)
+        C.nmt = 0;
+    else
+        C.nmt = (C.nm < 0) ? wide_nmt_for(n) : 0;
+    C.tcn = C.nmt > 0 && (policy == FMC_KERNEL_SPLIT_TC || (policy == FMC_KERNEL_AUTO && wide_tc_built(C.nmt)));
+    if (policy == FMC_KERNEL_SPLIT_TC && !wide_tc_built(C.nmt))
+        return fail(ctx, FMC_EUNSUPPORTED, "the tensor-core network sum handles 13 to %d machines (n = %d)",
+                    FMC_MAX_MACHINES, n);
+    // 17..28 machines: two warps per sample and two CTAs per SM (9 .. 14 slots
+    // per thread), whose barriers and product waits overlap, where the halved
+    // TMEM share holds the product's columns and a 16-step chunk of the
+    // disturbances (up to 7 with 9..12 slots, 4 with 13 and 14)
+    if (C.tcn && (C.nmt == 5 || C.nmt == 7)) {
+        const int h2 = n <= 18 ? 9 : n <= 20 ? 10 : n <= 22 ? 11 : n <= 24 ? 12 : n <= 26 ? 13 : 14;
+        // (13 and 14 slots are built for the disturbance-slot buckets up to 4,
+        // the generator-trip slot included)
+        const int ndx = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+        if (16 * s->d + wide_tc_cols(h2, 2) <= 256 && (h2 < 13 || ndx <= 4)) {
+            C.H = 2;
+            C.nmt = h2;
+        }
+    }
+    // an infinite bus: the tensor-core layout holds it in its last machine slot
+    // (instantiated for four warps per sample and the 8-disturbance bucket)
+    if (C.tcn && s->has_inf_bus) {
+        C.H = 4;
+        C.nmt = wide_nmt_for(n);
+        C.bus = true;
+        if (n >= 4 * C.nmt) {
+            if (user_policy == FMC_KERNEL_SPLIT_TC)
+                return fail(ctx, FMC_EUNSUPPORTED,
+                            "the tensor-core network sum needs a free machine slot for the infinite bus (n = %d)",
+                            n);
+            C.tcn = false;
+            C.bus = false;
+        }
+    }
+    if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && C.nmt > 0)
+        return fail(ctx, FMC_EUNSUPPORTED,
+                    "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
+                    FMC_MAX_MACHINES_PLAIN);
+    C.nd = C.bus ? 8 : nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+    return FMC_OK;
 }
 
 static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k0, int64_t count, int32_t path,
@@ -1153,66 +1238,16 @@ static int prepare(fmc_ctx* ctx, Workspace& ws, const fmc_scenario* s, int64_t k
                     FMC_MAX_MACHINES_PLAIN, n);
     P.s = *s;
     P.Nt = Nt;
-    P.nm = nm_bucket_for(n);
     P.exclusive = exclusive;
-    // four warps per sample for systems above 16 machines (or on request)
-    int policy = exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO;
-    if (policy == FMC_KERNEL_AUTO && path == FMC_PATH_FUSED) {
-        // (a rule's kernel that cannot take this system is ignored: a bucket's
-        // rule was measured at its largest machine count)
-        const fmc_launch_rule* rule = find_rule(ctx, s, count);
-        if (rule && rule->kernel != FMC_KERNEL_AUTO && !(rule->kernel == FMC_KERNEL_PER_SAMPLE && P.nm < 0) &&
-            !(rule->kernel == FMC_KERNEL_SPLIT_TC && !wide_tc_built(wide_nmt_for(n))))
-            policy = rule->kernel;
-    }
-    const bool per_sample = policy == FMC_KERNEL_PER_SAMPLE;
-    if (path == FMC_PATH_FUSED && per_sample && P.nm < 0)
-        return fail(ctx, FMC_EUNSUPPORTED, "the per-sample kernel handles up to %d machines (n = %d)",
-                    FMC_MAX_MACHINES_PLAIN, n);
-    if (path == FMC_PATH_FUSED && (policy == FMC_KERNEL_SPLIT || policy == FMC_KERNEL_SPLIT_TC))
-        P.nmt = wide_nmt_for(n);
-    else if (path == FMC_PATH_FUSED && per_sample)
-        P.nmt = 0;
-    else
-        P.nmt = (P.nm < 0) ? wide_nmt_for(n) : 0;
-    P.tcn = P.nmt > 0 && (policy == FMC_KERNEL_SPLIT_TC || (policy == FMC_KERNEL_AUTO && wide_tc_built(P.nmt)));
-    if (policy == FMC_KERNEL_SPLIT_TC && !wide_tc_built(P.nmt))
-        return fail(ctx, FMC_EUNSUPPORTED, "the tensor-core network sum handles 13 to %d machines (n = %d)",
-                    FMC_MAX_MACHINES, n);
-    // 17..28 machines: two warps per sample and two CTAs per SM (9 .. 14 slots
-    // per thread), whose barriers and product waits overlap, where the halved
-    // TMEM share holds the product's columns and a 16-step chunk of the
-    // disturbances (up to 7 with 9..12 slots, 4 with 13 and 14)
-    if (P.tcn && (P.nmt == 5 || P.nmt == 7)) {
-        const int h2 = n <= 18 ? 9 : n <= 20 ? 10 : n <= 22 ? 11 : n <= 24 ? 12 : n <= 26 ? 13 : 14;
-        // (13 and 14 slots are built for the disturbance-slot buckets up to 4,
-        // the generator-trip slot included)
-        const int ndx = nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
-        if (16 * s->d + wide_tc_cols(h2, 2) <= 256 && (h2 < 13 || ndx <= 4)) {
-            P.H = 2;
-            P.nmt = h2;
-        }
-    }
-    // an infinite bus: the tensor-core layout holds it in its last machine slot
-    // (instantiated for four warps per sample and the 8-disturbance bucket)
-    if (P.tcn && s->has_inf_bus) {
-        P.H = 4;
-        P.nmt = wide_nmt_for(n);
-        P.bus = true;
-        if (n >= 4 * P.nmt) {
-            if (exclusive && ctx->kernel_policy == FMC_KERNEL_SPLIT_TC)
-                return fail(ctx, FMC_EUNSUPPORTED,
-                            "the tensor-core network sum needs a free machine slot for the infinite bus (n = %d)",
-                            n);
-            P.tcn = false;
-            P.bus = false;
-        }
-    }
-    if (path == FMC_PATH_FUSED && s->forcing == FMC_FORCING_SMOOTH && P.nmt > 0)
-        return fail(ctx, FMC_EUNSUPPORTED,
-                    "the smooth forcing runs on the per-sample fused kernel (up to %d machines) and the plain path",
-                    FMC_MAX_MACHINES_PLAIN);
-    P.nd = P.bus ? 8 : nd_bucket_for(s->d + (s->event_machine >= 0 ? 1 : 0));
+    KernelChoice C;
+    if ((rc = choose_kernel(ctx, &ctx->rules, s, count, path, exclusive ? ctx->kernel_policy : FMC_KERNEL_AUTO, C)))
+        return rc;
+    P.nm = C.nm;
+    P.nmt = C.nmt;
+    P.nd = C.nd;
+    P.tcn = C.tcn;
+    P.H = C.H;
+    P.bus = C.bus;
     P.path = path;
     P.k0 = k0;
     P.count = count;
@@ -2087,6 +2122,23 @@ int fmc_diag_net_matrix(const fmc_scenario* scen, int32_t nmt, int32_t H, float*
     const int NN = wide_nn(nmt, H);
     if (out_floats < 2 * (int64_t)NN * NN) return FMC_EINVAL;
     build_wide_net(scen, nmt, H, out);
+    return FMC_OK;
+}
+
+int fmc_diag_kernel_choice(const fmc_scenario* scen, int32_t path, int32_t policy, int64_t count, int32_t* out)
+{
+    if (!scen || !out || scen->n < 1 || scen->n > FMC_MAX_MACHINES || scen->d < 1 || scen->d > 8 || count < 1 ||
+        (path != FMC_PATH_FUSED && path != FMC_PATH_PLAIN) || policy < FMC_KERNEL_AUTO ||
+        policy > FMC_KERNEL_SPLIT_TC)
+        return FMC_EINVAL;
+    KernelChoice C;
+    const int rc = choose_kernel(nullptr, nullptr, scen, count, path, policy, C);
+    if (rc) return rc;
+    out[0] = C.nmt == 0 ? FMC_KERNEL_PER_SAMPLE : (C.tcn ? FMC_KERNEL_SPLIT_TC : FMC_KERNEL_SPLIT);
+    out[1] = C.nmt;
+    out[2] = C.H;
+    out[3] = C.nd;
+    out[4] = C.bus ? 1 : 0;
     return FMC_OK;
 }
 
