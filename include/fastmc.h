@@ -532,11 +532,13 @@ int fmc_device_status(fmc_ctx* ctx, int* eq_iterations, int* kernel_error);
 /*
  * Chooses the fused kernel for this context's later single-scenario calls
  * (fmc_simulate, fmc_simulate_sums).  AUTO takes the per-sample kernel up to 16
- * machines (the faster one there, at any sample count) and the split kernel
- * with the tensor-core network sum above.  Batches and the server always use
- * AUTO's choice.  FMC_EINVAL for an unknown policy; a per-sample request above
- * 16 machines, or a SPLIT_TC request below 13, fails at the call with
- * FMC_EUNSUPPORTED.
+ * machines and the split kernel with the tensor-core network sum above (launch
+ * rules, fmc_set_launch_rules, may choose otherwise per bucket); a system on an
+ * infinite bus that fills every machine slot of the tensor-core layout
+ * (n = 4 nmt: 20, 28, 40, 52 machines) takes the FP32 split kernel.  Batches and
+ * the server always use AUTO's choice.  FMC_EINVAL for an unknown policy; a
+ * per-sample request above 16 machines, or a SPLIT_TC request below 13 machines
+ * or for such an infinite-bus system, fails at the call with FMC_EUNSUPPORTED.
  */
 int fmc_set_kernel_policy(fmc_ctx* ctx, int32_t policy);
 
