@@ -46,6 +46,8 @@ struct Request {
 };
 
 constexpr int kReplicates = 4;
+// the largest per-tile partial buffer a request's merged replicate launches may use
+constexpr int64_t kMergedPartBytes = (int64_t)2 << 30;
 
 // splitmix64: seeds of the replicate designs
 uint64_t mix64(uint64_t x)
@@ -71,17 +73,21 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
     const size_t cols = (size_t)(Nt + 1) * 2 * (size_t)s.n;
     double* dbuf = nullptr;
     if (cudaMallocAsync((void**)&dbuf, sizeof(double) * cols * 2 * R, st) != cudaSuccess) return FMC_ENOMEM;
+    // the largest design a round of this request may draw, per replicate
+    int64_t nb = s.N < 2 ? 2 : s.N;
+    while (4 * (int64_t)R * nb <= r->max_N) nb *= 4;
     // one launch for a round's designs: the fused path, a KL design without the
     // correlation-reducing permutation, tile-aligned designs (n stays a multiple
-    // of 128 as it grows fourfold)
+    // of 128 as it grows fourfold), and per-tile partials of the largest round
+    // within kMergedPartBytes (the separate launches add their sums with FP64
+    // atomics and need no partials)
+    const int64_t part_bytes = ((int64_t)R * nb + 127) / 128 * (Nt + 1) * 6 * (int64_t)s.n * 4;
     const bool merged = r->path == FMC_PATH_FUSED && s.sampling != FMC_SRS_EM && s.correlation != FMC_CORR_RANK &&
-                        s.N >= 128 && s.N % 128 == 0;
+                        s.N >= 128 && s.N % 128 == 0 && part_bytes <= kMergedPartBytes;
     // every replicate's workspace sized once for the largest round this request
     // may reach, so that no round grows (and reallocates) it
     {
         fmc_scenario big = s;
-        int64_t nb = s.N < 2 ? 2 : s.N;
-        while (4 * (int64_t)R * nb <= r->max_N) nb *= 4;
         big.N = merged ? (int64_t)R * nb : nb;
         for (int k = 0; k < (merged ? 1 : R); ++k) {
             const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, big.N, rst[k]);
