@@ -49,6 +49,29 @@ constexpr int kReplicates = 4;
 // the largest per-tile partial buffer a request's merged replicate launches may use
 constexpr int64_t kMergedPartBytes = (int64_t)2 << 30;
 
+// Per-tile partial bytes of a merged launch of `samples` samples of s.
+int64_t merged_part_bytes(const fmc_scenario& s, int64_t samples)
+{
+    const int64_t Nt = (int64_t)std::llround(s.T / s.dt);
+    return (samples + 127) / 128 * (Nt + 1) * 6 * (int64_t)s.n * 4;
+}
+
+// The largest per-replicate design (N growing fourfold up to nb) whose round runs
+// as one merged launch, or 0 when the request's rounds never merge: the fused
+// path, a KL design without the correlation-reducing permutation, tile-aligned
+// designs, and per-tile partials within kMergedPartBytes (separate launches add
+// their sums with FP64 atomics and need no partials).
+int64_t merge_limit(const fmc_scenario& s, int32_t path, int64_t nb)
+{
+    if (path != FMC_PATH_FUSED || s.sampling == FMC_SRS_EM || s.correlation == FMC_CORR_RANK || s.N < 128 ||
+        s.N % 128 != 0)
+        return 0;
+    int64_t lim = 0;
+    for (int64_t n = s.N; n <= nb; n *= 4)
+        if (merged_part_bytes(s, kReplicates * n) <= kMergedPartBytes) lim = n;
+    return lim;
+}
+
 // splitmix64: seeds of the replicate designs
 uint64_t mix64(uint64_t x)
 {
@@ -73,29 +96,34 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
     const size_t cols = (size_t)(Nt + 1) * 2 * (size_t)s.n;
     double* dbuf = nullptr;
     if (cudaMallocAsync((void**)&dbuf, sizeof(double) * cols * 2 * R, st) != cudaSuccess) return FMC_ENOMEM;
-    // the largest design a round of this request may draw, per replicate
+    // the largest design a round of this request may draw, per replicate, and
+    // the largest whose round runs as one merged launch (merge_limit)
     int64_t nb = s.N < 2 ? 2 : s.N;
     while (4 * (int64_t)R * nb <= r->max_N) nb *= 4;
-    // one launch for a round's designs: the fused path, a KL design without the
-    // correlation-reducing permutation, tile-aligned designs (n stays a multiple
-    // of 128 as it grows fourfold), and per-tile partials of the largest round
-    // within kMergedPartBytes (the separate launches add their sums with FP64
-    // atomics and need no partials)
-    const int64_t part_bytes = ((int64_t)R * nb + 127) / 128 * (Nt + 1) * 6 * (int64_t)s.n * 4;
-    const bool merged = r->path == FMC_PATH_FUSED && s.sampling != FMC_SRS_EM && s.correlation != FMC_CORR_RANK &&
-                        s.N >= 128 && s.N % 128 == 0 && part_bytes <= kMergedPartBytes;
-    // every replicate's workspace sized once for the largest round this request
-    // may reach, so that no round grows (and reallocates) it
-    {
+    const int64_t n_mm = merge_limit(s, r->path, nb);
+    // workspaces sized once for the largest round of each form, so that no round
+    // grows (and reallocates) them: the merged rounds' on the first context; the
+    // separate rounds' on every context, reserved (after the merged workspace is
+    // released) when the first of them comes
+    bool separate_ready = false;
+    auto reserve_for = [&](int count, int64_t samples) -> int {
         fmc_scenario big = s;
-        big.N = merged ? (int64_t)R * nb : nb;
-        for (int k = 0; k < (merged ? 1 : R); ++k) {
-            const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, big.N, rst[k]);
+        big.N = samples;
+        for (int k = 0; k < count; ++k) {
+            const int rc0 = fmc::reserve_workspace(rctx[k], &big, r->path, samples, rst[k]);
             if (rc0 != FMC_OK) {
                 r->error = fmc_last_error(rctx[k]);
-                cudaFreeAsync(dbuf, st);
                 return rc0;
             }
+        }
+        return FMC_OK;
+    };
+    {
+        const int rc0 = n_mm > 0 ? reserve_for(1, (int64_t)R * n_mm) : reserve_for(R, nb);
+        separate_ready = n_mm == 0;
+        if (rc0 != FMC_OK) {
+            cudaFreeAsync(dbuf, st);
+            return rc0;
         }
     }
     std::vector<double> hm(cols * R), hv(cols * R), mbar(cols), vbar(cols);
@@ -110,6 +138,12 @@ int run_target(fmc_ctx* const* rctx, const cudaStream_t* rst, Request* r)
         s.N = n;
         uint64_t seeds[kReplicates];
         for (int k = 0; k < R; ++k) seeds[k] = mix64(seed0 ^ ((uint64_t)(round * R + k + 1) << 32));
+        const bool merged = n <= n_mm;
+        if (!merged && !separate_ready) {
+            if ((rc = fmc::release_workspace(rctx[0], rst[0])) == FMC_OK) rc = reserve_for(R, nb);
+            separate_ready = true;
+            if (rc != FMC_OK) break;
+        }
         if (merged) {
             rc = fmc::simulate_moments_replicates(rctx[0], &s, r->path, R, seeds, dbuf, dbuf + (size_t)R * cols, st);
             if (rc != FMC_OK) r->error = fmc_last_error(rctx[0]);
@@ -340,14 +374,18 @@ static int submit_request(fmc_server* srv, const fmc_scenario* scen, int32_t pat
     r->tol_E = tol_E;
     r->tol_Var = tol_Var;
     r->max_N = max_N;
-    // charged for the largest design it may draw, in each of its replicates
+    // charged for the largest design it may draw, in each of its replicates, and
+    // the per-tile partials of its largest merged round
     fmc_scenario largest = *scen;
+    int64_t n_mm = 0;
     if (target) {
         int64_t n = scen->N;
         while (4 * (int64_t)kReplicates * n <= max_N) n *= 4;
         largest.N = n;
+        n_mm = merge_limit(*scen, path, n);
     }
-    r->bytes = request_bytes(largest, path) * (target ? (size_t)kReplicates : 1u);
+    r->bytes = request_bytes(largest, path) * (target ? (size_t)kReplicates : 1u) +
+               (n_mm > 0 ? (size_t)merged_part_bytes(*scen, kReplicates * n_mm) : 0u);
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stopping) return FMC_ECANCELLED;
