@@ -10,8 +10,13 @@ or no GPU is present, the calls raise.
 
 Entry points (same names as the C ABI without the ``fmc_`` prefix):
 ``lhs_sample``, ``lhs_sample_split``, ``kl_basis``, ``kle_reconstruct``,
-``equilibrium``, ``simulate``, ``moments``, plus ``Context``, ``device_status``
-and the kernel-timing helpers ``profile``/``profile_read``.
+``equilibrium``, ``simulate``, ``simulate_sums``, ``simulate_rrf``, ``moments``,
+``lhs_decorrelate``, ``ito_objective``, ``ito_identify``, the ``Batch`` and
+``Server`` forms, plus ``Context``, ``device_status``, the fused kernel's choice
+(``set_kernel_policy``: "auto", "per_sample", "split", "split_tc";
+``set_launch_rules``) and the diagnostics of ``include/fastmc_diag.h``
+(``profile``/``profile_read``, ``check_wait_path``, ``kernel_choice``,
+``net_matrix``).
 """
 from __future__ import annotations
 
